@@ -1,0 +1,119 @@
+"""Pins for the lower-level solvers: steepest descent with exact line search
+(Algorithms 1 / 3 widened to a few steps), the multigrid V-cycle used as M, and
+the truncated-solve reverse mode."""
+import numpy as np
+import scipy.sparse as sp
+
+import workloads as W
+from oracle import adjoint, fem, outer, solve
+
+
+def _setup(nx=8, ny=4, nz=4, rho=None):
+    pb = W.cantilever(nx, ny, nz)
+    if rho is not None:
+        pb.rho0 = rho(pb.n_elem)
+    S = outer.Setup(pb)
+    _, Ee, _ = S.moduli(pb.rho0)
+    return pb, S, Ee
+
+
+def test_steepest_descent_decreases_energy_every_step():
+    pb, S, Ee = _setup(rho=lambda n: W.random_rho(n))
+    K = S.K(Ee)
+    D = fem.jacobi_diagonal(pb.nx, pb.ny, pb.nz, Ee, S.ke, pb.fixed_dof)
+    energy = lambda u: 0.5 * u @ (K @ u) - S.f @ u
+    u = np.zeros(pb.n_dof)
+    last = energy(u)
+    r0 = S.f - K @ u
+    u1, r1, _, _ = solve.inner_sd(lambda x: K @ x, S.f, u, lambda r: r / D, 1)
+    assert abs(r1 @ (r0 / D)) < 1e-12 * abs(r0 @ (r0 / D))
+    for _ in range(20):
+        u, r, betas, _ = solve.inner_sd(lambda x: K @ x, S.f, u, lambda r: r / D, 1)
+        e = energy(u)
+        assert e < last
+        last = e
+    # the recursively updated residual equals the true one
+    assert np.abs(r - (S.f - K @ u)).max() < 1e-12 * np.abs(S.f).max()
+
+
+def test_multigrid_galerkin_identity_uniform_modulus():
+    """Rediscretised coarse operator = P^T A P for constant E (nested trilinear spaces)."""
+    nx, ny, nz = 8, 4, 4
+    ke = fem.ke_hex8(0.3)
+    A = fem.assemble(nx, ny, nz, np.full(nx * ny * nz, 0.4), ke, [])
+    P = solve.prolongation(nx // 2, ny // 2, nz // 2)
+    Ac = fem.assemble(nx // 2, ny // 2, nz // 2, np.full(nx * ny * nz // 8, 0.4), 2.0 * ke, [])
+    assert abs(P.T @ A @ P - Ac).max() < 1e-14
+    # interpolation reproduces linear fields exactly
+    k, j, i = np.meshgrid(np.arange(nz // 2 + 1), np.arange(ny // 2 + 1), np.arange(nx // 2 + 1), indexing="ij")
+    lin = np.stack([2 * i.ravel() + 1.0, -j.ravel() * 2.0, 2 * k.ravel() * 0.5], axis=1).ravel()
+    kf, jf, if_ = np.meshgrid(np.arange(nz + 1), np.arange(ny + 1), np.arange(nx + 1), indexing="ij")
+    linf = np.stack([if_.ravel() + 1.0, -jf.ravel() * 1.0, kf.ravel() * 0.5], axis=1).ravel()
+    assert np.abs(P @ lin - linf).max() < 1e-14
+
+
+def test_multigrid_coarse_fixtures_and_modulus():
+    pb = W.cantilever(8, 4, 4)
+    cf = solve.coarse_fixed(8, 4, 4, pb.fixed_dof)
+    assert cf.size == 3 * 3 * 3          # the clamped face of the 4x2x2 grid
+    pbm = W.mbb_half(8, 4, 4)
+    cfm = set(solve.coarse_fixed(8, 4, 4, pbm.fixed_dof).tolist())
+    node = lambda i, j, k: i + 5 * (j + 3 * k)
+    assert 3 * node(4, 0, 1) + 1 in cfm and 3 * node(4, 0, 0) + 2 in cfm and 3 * node(0, 2, 2) + 0 in cfm
+    E = np.arange(8 * 4 * 4, dtype=float)
+    Ec = solve.coarse_modulus(8, 4, 4, E)
+    a = E.reshape(4, 4, 8)
+    assert Ec[0] == a[:2, :2, :2].mean() and Ec[-1] == a[2:, 2:, 6:].mean()
+
+
+def test_vcycle_symmetric_positive_definite_and_contracts():
+    pb, S, Ee = _setup(16, 8, 8)
+    mg = solve.Multigrid(pb.nx, pb.ny, pb.nz, pb.h, Ee, pb.nu, pb.fixed_dof)
+    assert mg.L == 3
+    r = np.random.default_rng(4)
+    a, b = r.normal(size=pb.n_dof), r.normal(size=pb.n_dof)
+    Va, Vb = mg(a), mg(b)
+    assert abs(Va @ b - a @ Vb) < 1e-10 * abs(Va @ b)
+    assert a @ Va > 0 and b @ Vb > 0
+    # as a stationary iteration on the full-density problem the V-cycle contracts the residual
+    pb1, S1, E1 = _setup(16, 8, 8, rho=lambda n: np.ones(n))
+    K = S1.K(E1)
+    mg1 = solve.Multigrid(pb1.nx, pb1.ny, pb1.nz, pb1.h, E1, pb1.nu, pb1.fixed_dof)
+    u = np.zeros(pb1.n_dof)
+    res = [np.linalg.norm(S1.f)]
+    for _ in range(6):
+        u = u + mg1(S1.f - K @ u)
+        res.append(np.linalg.norm(S1.f - K @ u))
+    assert all(res[i + 1] < 0.6 * res[i] for i in range(len(res) - 1))
+
+
+def test_vcycle_single_level_is_exact_solve():
+    pb, S, Ee = _setup(4, 2, 2)
+    mg = solve.Multigrid(pb.nx, pb.ny, pb.nz, pb.h, Ee, pb.nu, pb.fixed_dof, levels=1)
+    K = S.K(Ee)
+    b = np.random.default_rng(5).normal(size=pb.n_dof)
+    assert np.abs(K @ mg(b) - b).max() < 1e-9 * np.abs(b).max()
+
+
+def test_truncated_solve_reverse_mode_matches_finite_differences():
+    pb, S, _ = _setup(6, 4, 4, rho=lambda n: W.random_rho(n))
+    T, beta = 6, 0.5
+    J, g = adjoint.gradient(S, pb.rho0, T, beta)
+    h = 1e-6
+    for e in W.random_elements(pb.n_elem, 10):
+        rp, rm = pb.rho0.copy(), pb.rho0.copy()
+        rp[e] += h
+        rm[e] -= h
+        fd = (adjoint.forward(S, rp, T, beta)[0] - adjoint.forward(S, rm, T, beta)[0]) / (2 * h)
+        assert abs(g[e] - fd) <= 1e-6 * max(abs(fd), 1e-3 * np.abs(g).max())
+
+
+def test_truncated_gradient_tends_to_exact_sensitivity():
+    pb, S, _ = _setup(4, 2, 2, rho=lambda n: W.random_rho(n))
+    J, u = S.exact_compliance(pb.rho0)
+    _, _, Ed = S.moduli(pb.rho0)
+    from oracle import filt
+    g_exact = filt.filter_transpose(S.H, S.Hs, S.sens_rho_tilde(Ed, u))
+    JT, gT = adjoint.gradient(S, pb.rho0, 10000, 0.5)
+    assert abs(JT - J) < 1e-8 * J
+    assert np.abs(gT - g_exact).max() < 1e-9 * np.abs(g_exact).max()
