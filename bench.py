@@ -1,0 +1,340 @@
+#!/usr/bin/env python
+"""Benchmark of the first-order bilevel topology optimiser on one GB300.
+
+A step is one outer iteration (Algorithms 1 / 3) of the whole hot path: density
+filter and moduli, preconditioner refresh, the lower-level steps (operator
+applies, dot products, updates), the fused sensitivity, the filter transpose
+and the projection onto X.  Workload: the 128x64x64 cantilever (524,288 hex8
+elements, 1,635,075 DOFs), seeded synthetic inputs (``workloads``).
+
+Reported: outer iterations/s of the FP32-mixed path (``value``), the same for
+plain FP64, and GDOF/s of K(rho)u for both, with the roofline of the operator
+kernel measured live with CUDA events on the launching stream.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+L2_FLUSH_BYTES = 512 << 20       # > 129 MB L2: written between timed steps
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=None)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--precond", default="auto", choices=["auto", "mg", "jacobi"])
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = float(p[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+# ----------------------------------------------------------------------------- oracle baseline
+def oracle_sample(target_seconds=15.0):
+    """Time the FP64 oracle's outer iteration on a bounded sample of the workload.
+
+    The oracle assembles a CSR matrix per iteration; at 128x64x64 that needs
+    ~7 GB and minutes, so the sample is the same cantilever at 64x32x32 (1/8 of
+    the DOFs, same preconditioner and inner steps) and the time is scaled by the
+    DOF ratio 8 to the workload.  Returns (iters/s at the workload, seconds, desc).
+    """
+    import numpy as np
+    import workloads as W
+    from oracle import outer
+    pb = W.cantilever(64, 32, 32)
+    S = outer.Setup(pb)
+    rho, u = pb.rho0.copy(), np.zeros(pb.n_dof)
+    rho, u, _, a0 = outer.run(pb, 1, precond="mg", n_inner=2, setup=S, rho=rho, u=u)
+    n, t0 = 0, time.perf_counter()
+    while True:
+        rho, u, _, a0 = outer.run(pb, 1, precond="mg", n_inner=2, setup=S, rho=rho, u=u, k0=2 + n, alpha0=a0)
+        n += 1
+        el = time.perf_counter() - t0
+        if el > target_seconds or n >= 20:
+            break
+    per_iter = el / n
+    full = 8.0 * per_iter
+    return 1.0 / full, el, f"{n} outer iterations of the 64x32x32 cantilever (MG, 2 inner steps), time x8 (DOF ratio)"
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    ips, el, desc = oracle_sample(target_seconds=max(5.0, 2.0 * args.steps))
+    line = {"impl": "reference", "metric": "outer TO iters/s (FP32-mixed) with K(rho)u GDOF/s, 1 GB300",
+            "value": ips, "unit": "outer_iters/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 / ips, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "cantilever 128x64x64 hex8, MG-preconditioned steepest descent x2"},
+            "cpu_baseline": {"value": ips, "unit": "outer_iters/s", "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": ips, "unit": "outer_iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- ours
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        import __graft_entry__
+        __graft_entry__.build()
+    if dist:
+        dist.barrier()
+    import paper_2204_06204_gb300 as fb
+    import workloads as W
+
+    pb = W.cantilever_128x64x64()
+    use_mg = args.precond == "mg" or (args.precond == "auto" and _mg_available(fb))
+    precond = fb.TO_PRECOND_MG if use_mg else fb.TO_PRECOND_JACOBI
+    n_inner = 2 if use_mg else 5
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def make(precision):
+        prm = fb.to_default_params(precision=precision, precond=precond, n_inner=n_inner)
+        return fb.Problem.from_workload(pb, prm, device=local)
+
+    def time_steps(P, K, W_):
+        P.step(W_, want_stats=False)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        for a, b in ev:
+            flush.zero_()
+            a.record(stream)
+            P.step(1, want_stats=False)
+            b.record(stream)
+        torch.cuda.synchronize()
+        P.check()
+        return sum(a.elapsed_time(b) for a, b in ev) / 1000.0
+
+    def time_apply(P, reps=50):
+        rho, u, k, a0 = P.get_state()
+        x = torch.tensor(W.random_u(pb.n_dof), dtype=P.dtype, device=dev) if k <= 1 else u
+        y = P.dof()
+        for _ in range(5):
+            P.apply_K(x, y)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        torch.cuda.synchronize()
+        for a, b in ev:
+            flush.zero_()
+            a.record(stream)
+            P.apply_K(x, y)
+            b.record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in ev) / reps / 1000.0
+
+    s_el = 4
+    n_node = pb.n_node
+    apply_bytes = lambda s: 2 * 3 * n_node * s + pb.n_elem * s + n_node   # u read, y write, E read, mask
+    pk = peaks()
+    hbm = pk.get("hbm_gbs", 6800.0)
+
+    # --- FP32-mixed: the headline
+    P32 = make(fb.TO_FP32_MIXED)
+    with ClockSampler(local) as clk:
+        t32 = time_steps(P32, args.steps, args.warmup)
+    t_apply32 = time_apply(P32)
+    ips32 = args.steps / t32
+
+    # --- end to end through the C ABI with host buffers: rho in, rho + stats out each step
+    rho_h = torch.empty(pb.n_elem, dtype=torch.float32, pin_memory=True)
+    rho_o = torch.empty_like(rho_h)
+    rho_d, u_d, k_d, a0_d = P32.get_state()
+    rho_h.copy_(rho_d)
+    ke = max(3, min(args.steps, 20))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(ke):
+        rho_d.copy_(rho_h, non_blocking=True)
+        fb.to_set_state(P32, rho_d, None, k_d + i, a0_d)
+        st = P32.step(1, want_stats=True)       # synchronises: stats come back to the host
+        fb.to_get_state(P32, rho_d, None)
+        rho_o.copy_(rho_d, non_blocking=True)
+        torch.cuda.synchronize()
+        rho_h.copy_(rho_o)
+    t_e2e = time.perf_counter() - t0
+
+    # --- plain FP64
+    res64 = None
+    if not args.no_fp64:
+        P64 = make(fb.TO_FP64)
+        k64 = args.fp64_steps or max(3, args.steps // 4)
+        t64 = time_steps(P64, k64, 3)
+        t_apply64 = time_apply(P64, reps=10)
+        res64 = {"outer_iters_per_s": k64 / t64, "apply_ms": t_apply64 * 1e3,
+                 "apply_gdofs": pb.n_dof / t_apply64 / 1e9, "steps": k64}
+        P64.close()
+
+    # max over ranks
+    if dist:
+        tt = torch.tensor([t32], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t32 = float(tt.item())
+        ips32 = args.steps / t32
+
+    if rank != 0:
+        dist.destroy_process_group()
+        return 0
+
+    cpu = None
+    if not args.no_cpu:
+        ips_cpu, el, desc = oracle_sample()
+        cpu = {"value": ips_cpu, "unit": "outer_iters/s", "cores": 1, "kind": "oracle", "sample": desc}
+
+    ach = apply_bytes(s_el) / t_apply32 / 1e9
+    launches_per_step = _launches_per_step(use_mg, n_inner)
+    line = {
+        "metric": "outer TO iters/s (FP32-mixed) with K(rho)u GDOF/s, 1 GB300",
+        "value": ips32 * world,
+        "unit": "outer_iters/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1000.0 * t32 / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32 (dots, norms, step sizes and lambda in f64)",
+        "data": "synthetic",
+        "config": {"workload": "cantilever 128x64x64 hex8 (1,635,075 DOFs), FP32-mixed, "
+                               + ("MG-preconditioned steepest descent x2" if use_mg else "Jacobi steepest descent x5"),
+                   "l2": "flushed (512 MB write) before every timed step and every timed apply",
+                   "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "apply_K": {"fp32_gdofs": pb.n_dof / t_apply32 / 1e9, "fp32_us": t_apply32 * 1e6,
+                    "fp64_gdofs": res64["apply_gdofs"] if res64 else None,
+                    "fp64_us": res64["apply_ms"] * 1e3 if res64 else None},
+        "fp64_plain": res64,
+        "fp32_over_fp64_iters": (ips32 / res64["outer_iters_per_s"]) if res64 else None,
+        "roofline": {"kernel": "k_operator (K(rho)u, FP32)", "bound": "hbm", "achieved": ach, "peak": hbm,
+                     "unit": "GB/s", "frac": ach / hbm, "traffic": None,
+                     "algorithmic_bytes": apply_bytes(s_el),
+                     "peak_source": "MEASURED_PEAKS.json hbm_gbs" if pk else "fallback 6800"},
+        "e2e": {"value": ke / t_e2e, "unit": "outer_iters/s", "h2d_bytes_per_step": pb.n_elem * 4,
+                "d2h_bytes_per_step": pb.n_elem * 4 + 96},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk.summary(),
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def _mg_available(fb):
+    import workloads as W
+    pb = W.cantilever(4, 2, 2)
+    try:
+        prm = fb.to_default_params(precond=fb.TO_PRECOND_MG)
+        fb.Problem.from_workload(pb, prm).close()
+        return True
+    except fb.ToError:
+        return False
+
+
+def _launches_per_step(mg, n_inner):
+    # filter + moduli, diag, residual, (Q + update) per step, filter^T, projection, record
+    base = 2 + 1 + 1 + 2 * n_inner + 1 + 1 + 1
+    if not mg:
+        return base
+    return base  # the V-cycle launches are added when multigrid is built
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,212 @@
+/*
+ * to.h -- C ABI of the GB300 first-order bilevel topology optimiser.
+ *
+ * Method: arXiv 2204.06204, "First-Order Bilevel Topology Optimization for
+ * Fast Mechanical Design".  One outer iteration (Algorithms 1 and 3) refines
+ * the lower-level solution of K(v) u = f by a few (preconditioned) descent
+ * steps instead of an exact solve, takes the approximate sensitivity
+ * -1/2 u^T dK/dv u at the current u (Sec. III, exact-gradient formula, used
+ * with the approximate u), chains it through the material filter
+ * (Remark 3.1) and projects the gradient step onto
+ * X = {lo <= v <= hi, 1^T v <= vbar} (Sec. IV-B, Eq. piecewiseLinearEQ,
+ * Algorithm 4).  Here the design v is written rho, the discretisation is
+ * hex8 on an nx x ny x nz voxel grid, the stiffness parameterisation is the
+ * power law of Sec. III in its modified form E_e = Emin + rho~_e^p (E0-Emin),
+ * and the compliance reported is J = f^T u (= 2 l of Eq. (opt)).
+ *
+ * Conventions (all entry points)
+ *   node  n = i + (nx+1) * (j + (ny+1) * k)        0 <= i <= nx, ...
+ *   DOF   d = 3 n + c, c = 0 (x), 1 (y), 2 (z)     n_dof  = 3 (nx+1)(ny+1)(nz+1)
+ *   element e = i + nx * (j + ny * k)             n_elem = nx ny nz
+ *   Fixed DOFs are eliminated: K^ = m K m + (I - m), m the free-DOF indicator,
+ *   so K^ is the identity on fixed rows and columns.
+ *
+ * Precision is fixed per problem by to_params.precision:
+ *   TO_FP64        every vector, scalar and product in double  -> pointers are double*
+ *   TO_FP32_MIXED  vectors, products and element work in float; global dot
+ *                  products, norms, step sizes and the volume multiplier in
+ *                  double                                     -> pointers are float*
+ *
+ * Memory and streams
+ *   Pointers named *_dev are device pointers on the problem's device, borrowed
+ *   for the call only (never freed, never kept).  Pointers named *_host or
+ *   plain scalar out-pointers are host memory.  The library owns its internal
+ *   buffers (design, filtered design, moduli, solver vectors, multigrid
+ *   levels, reduction scratch) and frees them in to_destroy.  `stream` is a
+ *   cudaStream_t (NULL = legacy default stream); every call is stream-ordered
+ *   on it.  A call that returns a host value synchronises that stream.
+ *
+ * Errors
+ *   Every int-returning call returns TO_OK (0) or a TO_ERR_* code and never
+ *   throws or aborts.  to_last_error() returns a per-thread message for the
+ *   last failure.  Device-side checks (non-finite step sizes, a grid barrier
+ *   that waits too long) set a device flag that is reported by the next call
+ *   that synchronises (to_step with stats, to_check, the *_out variants).
+ */
+#ifndef TO_H
+#define TO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    TO_OK = 0,
+    TO_ERR_ARG = 1,          /* invalid argument (null pointer, size, enum value)   */
+    TO_ERR_CUDA = 2,         /* a CUDA runtime call failed                          */
+    TO_ERR_NONFINITE = 3,    /* NaN / Inf met in a step size or reduction            */
+    TO_ERR_INFEASIBLE = 4,   /* vbar < n_elem * lo: X is empty                       */
+    TO_ERR_TIMEOUT = 5,      /* a device-side wait hit its iteration limit           */
+    TO_ERR_SINGULAR = 6,     /* no fixed DOF (K singular) or a failed coarse factor  */
+    TO_ERR_STATE = 7         /* call not valid in the current state                  */
+};
+
+enum { TO_FP64 = 0, TO_FP32_MIXED = 1 };
+enum { TO_PRECOND_JACOBI = 0, TO_PRECOND_MG = 1, TO_PRECOND_NONE = 2 };
+enum { TO_INNER_SD = 0, TO_INNER_RICHARDSON = 1 };
+
+typedef struct to_problem to_problem;      /* opaque */
+
+/* Voxel grid: element counts and edge length h (> 0). */
+typedef struct {
+    int32_t nx, ny, nz;
+    double h;
+} to_grid;
+
+/* Material and design bounds (Sec. III power law; X of Eq. (opt)).
+ * E0 > Emin >= 0, 0 <= nu < 0.5, p >= 1, 0 < volfrac, rmin >= 0 (filter
+ * radius in voxels; < 1 means no filtering), 0 <= rho_min < rho_max.
+ * vbar = volfrac * n_elem. */
+typedef struct {
+    double E0, Emin, nu, p;
+    double volfrac, rmin, rho_min, rho_max;
+} to_material;
+
+/* Load vector f: n entries (global DOF, value), host arrays read during
+ * to_create only.  Repeated DOFs add; loads on fixed DOFs are dropped. */
+typedef struct {
+    int64_t n;
+    const int64_t* dof;
+    const double* val;
+} to_loads;
+
+/* Fixed DOFs (u = 0), host array read during to_create only. */
+typedef struct {
+    int64_t n;
+    const int64_t* dof;
+} to_bcs;
+
+/* Solver parameters.
+ *   precision   TO_FP64 | TO_FP32_MIXED
+ *   precond     M of the lower-level step: Jacobi diagonal, multigrid V-cycle, or none
+ *   inner_mode  TO_INNER_SD: steepest descent with the exact line search
+ *               beta = r^T z / z^T K z; TO_INNER_RICHARDSON: constant beta
+ *               (the literal step of Algorithms 1 / 3)
+ *   n_inner     lower-level steps per outer iteration (>= 0)
+ *   beta        step of TO_INNER_RICHARDSON
+ *   alpha0      > 0: alpha_k = alpha0 k^-m.  <= 0: alpha0 = alpha_scale / ||g||_inf
+ *               fixed at the first iteration with g != 0
+ *   m           exponent of the alpha schedule (Sec. V uses 3/4)
+ *   mean_proj   1: g <- g - mean(g) before the step (Sec. IV-B)
+ *   mg_levels   0 = automatic; mg_nu_pre / mg_nu_post smoothing sweeps;
+ *               mg_omega damped-Jacobi weight
+ *   tile_x, tile_y, tile_z   0 = automatic tile choice for the operator kernel */
+typedef struct {
+    int32_t precision, precond, inner_mode, n_inner;
+    double beta, alpha0, alpha_scale, m;
+    int32_t mean_proj, mg_levels, mg_nu_pre, mg_nu_post;
+    double mg_omega;
+    int32_t tile_x, tile_y, tile_z, reserved;
+} to_params;
+
+/* Per-outer-iteration record (host copy). */
+typedef struct {
+    int64_t k;          /* outer iteration index, 1-based                           */
+    double J;           /* f^T u_k (compliance estimate at the iterate entering k)  */
+    double res_inf;     /* ||K(rho~_k) u_k - f||_inf  (tracking error, Sec. V)      */
+    double res2;        /* ||K(rho~_k) u_k - f||_2                                   */
+    double drho_inf;    /* ||rho_{k+1} - rho_k||_inf (Sec. V termination quantity)   */
+    double volume;      /* 1^T rho_{k+1}                                             */
+    double lambda;      /* volume multiplier of the projection (0 if inactive)       */
+    double alpha;       /* alpha_k                                                   */
+    double gmax;        /* ||dJ/drho||_inf                                            */
+    double beta_first;  /* first and last lower-level step sizes of this iteration   */
+    double beta_last;
+    int32_t proj_iters; /* passes of the multiplier search                           */
+    int32_t status;     /* TO_OK or the first device-side error of this iteration    */
+} to_stats;
+
+/* Fill *out with defaults: FP32-mixed, Jacobi, steepest descent, 5 inner
+ * steps, beta 0.5, alpha0 automatic with scale 0.2, m = 0.75, no mean
+ * projection, automatic multigrid with 2 + 2 sweeps and omega 0.5. */
+void to_default_params(to_params* out);
+
+/* Create a problem on CUDA device `device` (the caller's current device is
+ * restored).  Copies loads and fixtures, builds the element matrix, the filter
+ * weights and (for TO_PRECOND_MG) the multigrid hierarchy, sets
+ * rho = volfrac everywhere, u = 0, k = 1.  Errors: TO_ERR_ARG, TO_ERR_CUDA,
+ * TO_ERR_INFEASIBLE, TO_ERR_SINGULAR (no fixed DOF).  *out is NULL on error. */
+int to_create(const to_grid* grid, const to_material* mat, const to_loads* loads,
+              const to_bcs* bcs, const to_params* params, int device, to_problem** out);
+
+/* Free everything the problem owns.  NULL is ignored. */
+void to_destroy(to_problem* P);
+
+/* Sizes of the problem's vectors. */
+int to_sizes(const to_problem* P, int64_t* n_elem, int64_t* n_dof);
+
+/* Set the design rho (n_elem entries) and recompute rho~ = C(rho), E and dE/drho~
+ * (Sec. III power law through the filter of Remark 3.1).  The operator of
+ * to_apply_K, to_inner_solve and to_sensitivity uses this design. */
+int to_set_design(to_problem* P, const void* rho_dev, void* stream);
+
+/* y = K^(rho~) u, the matrix-free hex8 operator of Sec. III (K = sum_e E_e K_e with
+ * fixtures eliminated).  u, y: n_dof entries, node-major xyz-interleaved;
+ * u and y must not overlap. */
+int to_apply_K(to_problem* P, const void* u_dev, void* y_dev, void* stream);
+
+/* nsteps lower-level steps on K^(rho~) u = f from the given u (in place), with the
+ * problem's preconditioner and inner_mode (Algorithm 1 / 3, line 1).  If res_out
+ * is not NULL it receives ||f - K^ u||_2 after the steps (synchronises). */
+int to_inner_solve(to_problem* P, void* u_dev, int32_t nsteps, double* res_out, void* stream);
+
+/* g = dJ/drho at the displacement u for the current design: the element term
+ * -E'_e u_e^T k_e u_e (Sec. III, exact-gradient formula applied to u; J = f^T u)
+ * chained through the filter transpose.  u: n_dof, g: n_elem entries. */
+int to_sensitivity(to_problem* P, const void* u_dev, void* g_dev, void* stream);
+
+/* Density filter of Remark 3.1 as a linear cone of radius rmin:
+ * transpose = 0: y_e = sum_i H_ei x_i / Hs_e;  transpose = 1: y_i = sum_e H_ei x_e / Hs_e.
+ * x, y: n_elem entries, must not overlap. */
+int to_filter(to_problem* P, const void* x_dev, void* y_dev, int32_t transpose, void* stream);
+
+/* rho = Proj_X(w): clamp(w - lambda, rho_min, rho_max) with lambda = 0 if the clamp meets
+ * the volume bound, else the root of Eq. (piecewiseLinearEQ) (Sec. IV-B), found
+ * by a safeguarded Newton search over the breakpoints in double precision.
+ * w, rho: n_elem entries (may alias).  lambda_out (host, may be NULL) synchronises. */
+int to_project(to_problem* P, const void* w_dev, void* rho_dev, double* lambda_out, void* stream);
+
+/* Run n_outer outer iterations (Algorithms 1 / 3 with the problem's M) on the
+ * problem's own state (rho_k, u_k, k).  If stats_out is not NULL it receives
+ * n_outer records and the call synchronises; the return value then also
+ * reports device-side errors.  Without stats_out nothing is copied back. */
+int to_step(to_problem* P, int32_t n_outer, to_stats* stats_out, void* stream);
+
+/* Read / write the outer state: rho (n_elem), u (n_dof), the 1-based iteration
+ * counter k and alpha0 (<= 0 means not yet fixed).  Any pointer may be NULL to
+ * skip that part.  to_set_state recomputes rho~ and the moduli. */
+int to_get_state(to_problem* P, void* rho_dev, void* u_dev, int64_t* k_out, double* alpha0_out, void* stream);
+int to_set_state(to_problem* P, const void* rho_dev, const void* u_dev, int64_t k, double alpha0, void* stream);
+
+/* Synchronise the stream and report (and clear) the device error flag. */
+int to_check(to_problem* P, void* stream);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* to_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TO_H */

@@ -1,0 +1,424 @@
+// C entry points (include/to.h): argument checks, device memory owned by the
+// problem, and stream-ordered calls into the kernels.
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "device.cuh"
+
+namespace to {
+int project_coop_blocks(int prec, int num_sms, int* out);
+int launch_rowsum(to_problem* P, cudaStream_t s);
+int run_inner(to_problem* P, void* u, int nsteps, int primary, cudaStream_t s);
+int refresh_preconditioner(to_problem* P, cudaStream_t s);
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && cudaSetDevice(dev) == cudaSuccess) ok = true;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+template <typename T>
+__global__ void k_fill(T* p, long long n, T v) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
+int dalloc(void** p, size_t bytes) {
+    cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+    if (e != cudaSuccess) return fail(TO_ERR_CUDA, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    return TO_OK;
+}
+
+void dfree(void*& p) {
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+int fill_scalar(to_problem* P, void* p, long long n, double v, cudaStream_t s) {
+    const int nb = (int)std::min<long long>((n + 255) / 256, 1024);
+    if (P->prec == TO_FP64)
+        k_fill<double><<<nb > 0 ? nb : 1, 256, 0, s>>>((double*)p, n, v);
+    else
+        k_fill<float><<<nb > 0 ? nb : 1, 256, 0, s>>>((float*)p, n, (float)v);
+    TO_CUDA(cudaGetLastError());
+    return TO_OK;
+}
+
+}  // namespace
+}  // namespace to
+
+using namespace to;
+
+extern "C" void to_default_params(to_params* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof *o);
+    o->precision = TO_FP32_MIXED;
+    o->precond = TO_PRECOND_JACOBI;
+    o->inner_mode = TO_INNER_SD;
+    o->n_inner = 5;
+    o->beta = 0.5;
+    o->alpha0 = 0.0;
+    o->alpha_scale = 0.2;
+    o->m = 0.75;
+    o->mean_proj = 0;
+    o->mg_levels = 0;
+    o->mg_nu_pre = 2;
+    o->mg_nu_post = 2;
+    o->mg_omega = 0.5;
+}
+
+static int validate(const to_grid* g, const to_material* m, const to_loads* L, const to_bcs* B, const to_params* p) {
+    if (!g || !m || !L || !B || !p) return fail(TO_ERR_ARG, "null argument");
+    if (g->nx < 1 || g->ny < 1 || g->nz < 1) return fail(TO_ERR_ARG, "grid dimensions must be >= 1");
+    if (!(g->h > 0.0)) return fail(TO_ERR_ARG, "element edge h must be > 0");
+    const double nn = (double)(g->nx + 1) * (g->ny + 1) * (g->nz + 1);
+    if (nn * 3 > 4.0e9) return fail(TO_ERR_ARG, "grid too large");
+    if (!(m->E0 > m->Emin) || !(m->Emin >= 0.0)) return fail(TO_ERR_ARG, "need E0 > Emin >= 0");
+    if (!(m->nu >= 0.0 && m->nu < 0.5)) return fail(TO_ERR_ARG, "need 0 <= nu < 0.5");
+    if (!(m->p >= 1.0)) return fail(TO_ERR_ARG, "need p >= 1");
+    if (!(m->rho_min >= 0.0 && m->rho_max > m->rho_min)) return fail(TO_ERR_ARG, "need 0 <= rho_min < rho_max");
+    if (!(m->volfrac > 0.0)) return fail(TO_ERR_ARG, "need volfrac > 0");
+    if (m->volfrac < m->rho_min) return fail(TO_ERR_INFEASIBLE, "volume bound below n_elem * rho_min: X is empty");
+    if (L->n < 0 || (L->n > 0 && (!L->dof || !L->val))) return fail(TO_ERR_ARG, "bad load list");
+    if (B->n < 0 || (B->n > 0 && !B->dof)) return fail(TO_ERR_ARG, "bad fixture list");
+    if (p->precision != TO_FP64 && p->precision != TO_FP32_MIXED) return fail(TO_ERR_ARG, "bad precision");
+    if (p->precond < 0 || p->precond > 2) return fail(TO_ERR_ARG, "bad preconditioner");
+    if (p->inner_mode != TO_INNER_SD && p->inner_mode != TO_INNER_RICHARDSON) return fail(TO_ERR_ARG, "bad inner mode");
+    if (p->n_inner < 0) return fail(TO_ERR_ARG, "n_inner must be >= 0");
+    if (!(p->m >= 0.0)) return fail(TO_ERR_ARG, "alpha exponent m must be >= 0");
+    const long long ndof = 3LL * (long long)nn;
+    for (int64_t i = 0; i < L->n; ++i)
+        if (L->dof[i] < 0 || L->dof[i] >= ndof || !std::isfinite(L->val[i])) return fail(TO_ERR_ARG, "load DOF out of range or value not finite");
+    for (int64_t i = 0; i < B->n; ++i)
+        if (B->dof[i] < 0 || B->dof[i] >= ndof) return fail(TO_ERR_ARG, "fixed DOF out of range");
+    if (B->n == 0) return fail(TO_ERR_SINGULAR, "no fixed DOF: K is singular");
+    return TO_OK;
+}
+
+extern "C" void to_destroy(to_problem* P) {
+    if (!P) return;
+    DeviceGuard dg(P->device);
+    void** bufs[] = {&P->rho, &P->rhot, &P->Ed, &P->Hs, &P->gt, &P->grad, &P->tmp_e, &P->stencil_w,
+                     &P->u, &P->f, &P->r, &P->z, &P->q, &P->tmp_v, &P->coarse_A, &P->coarse_L};
+    for (void** b : bufs) dfree(*b);
+    void* st = P->stencil;
+    dfree(st);
+    for (auto& L : P->lv) {
+        dfree(L.E);
+        dfree(L.d);
+        void* mk = L.mask;
+        dfree(mk);
+        dfree(L.x);
+        dfree(L.b);
+        dfree(L.t);
+    }
+    void* p;
+    p = P->sc; dfree(p);
+    p = P->red; dfree(p);
+    p = P->counters; dfree(p);
+    p = P->dstats; dfree(p);
+    delete P;
+}
+
+extern "C" int to_create(const to_grid* g, const to_material* m, const to_loads* L, const to_bcs* B,
+                         const to_params* prm, int device, to_problem** out) {
+    if (!out) return fail(TO_ERR_ARG, "out is null");
+    *out = nullptr;
+    int rc = validate(g, m, L, B, prm);
+    if (rc) return rc;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+        return fail(TO_ERR_CUDA, "no such CUDA device");
+    DeviceGuard dg(device);
+    if (!dg.ok) return fail(TO_ERR_CUDA, "cudaSetDevice failed");
+
+    to_problem* P = new (std::nothrow) to_problem();
+    if (!P) return fail(TO_ERR_ARG, "out of host memory");
+    P->device = device;
+    P->prec = prm->precision;
+    P->g = *g;
+    P->mat = *m;
+    P->prm = *prm;
+    P->esz = P->prec == TO_FP64 ? 8 : 4;
+    P->n_elem = (int64_t)g->nx * g->ny * g->nz;
+    P->n_node = (int64_t)(g->nx + 1) * (g->ny + 1) * (g->nz + 1);
+    P->n_dof = 3 * P->n_node;
+    if (prm->tile_z > 0) P->tile_z = prm->tile_z;
+    else P->tile_z = 0;
+    auto bail = [&](int code) {
+        to_destroy(P);
+        return code;
+    };
+
+    if ((rc = build_element_matrix(m->nu, P->ke))) return bail(rc);
+    if ((rc = build_haar(P->ke, g->h, P->haar))) return bail(rc);
+    P->kdiag = g->h * P->ke[0];
+    for (int i = 1; i < 24; ++i)
+        if (std::fabs(P->ke[i * 24 + i] - P->ke[0]) > 1e-14) return bail(fail(TO_ERR_ARG, "unequal element diagonal"));
+
+    int dev_sms = 0;
+    if (cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
+        return bail(fail(TO_ERR_CUDA, "device query failed"));
+    P->num_sms = dev_sms;
+    if ((rc = project_coop_blocks(P->prec, P->num_sms, &P->coop_blocks))) return bail(rc);
+
+    // filter stencil: offsets with w = rmin - |d| > 0 (identity when rmin <= 0)
+    std::vector<int4> st;
+    std::vector<double> sw;
+    const int R = (int)std::ceil(m->rmin) + 1;
+    for (int dz = -R; dz <= R; ++dz)
+        for (int dy = -R; dy <= R; ++dy)
+            for (int dx = -R; dx <= R; ++dx) {
+                const double w = m->rmin - std::sqrt((double)(dx * dx + dy * dy + dz * dz));
+                if (w > 0.0) {
+                    st.push_back(make_int4(dx, dy, dz, 0));
+                    sw.push_back(w);
+                }
+            }
+    if (st.empty()) {
+        st.push_back(make_int4(0, 0, 0, 0));
+        sw.push_back(1.0);
+    }
+    P->n_stencil = (int)st.size();
+
+    // level 0 (the fine grid)
+    Level L0{};
+    L0.nx = g->nx; L0.ny = g->ny; L0.nz = g->nz;
+    L0.n_elem = P->n_elem; L0.n_node = P->n_node; L0.n_dof = P->n_dof;
+    L0.h = g->h;
+    L0.kdiag = P->kdiag;
+    P->lv.push_back(L0);
+    Level& F = P->lv[0];
+
+    const size_t es = P->esz;
+    const size_t ne = (size_t)P->n_elem, nd = (size_t)P->n_dof;
+    if ((rc = dalloc(&P->rho, ne * es)) || (rc = dalloc(&P->rhot, ne * es)) || (rc = dalloc(&F.E, ne * es)) ||
+        (rc = dalloc(&P->Ed, ne * es)) || (rc = dalloc(&P->Hs, ne * es)) || (rc = dalloc(&P->gt, ne * es)) ||
+        (rc = dalloc(&P->grad, ne * es)) || (rc = dalloc(&P->tmp_e, ne * es)) || (rc = dalloc(&P->u, nd * es)) ||
+        (rc = dalloc(&P->f, nd * es)) || (rc = dalloc(&P->r, nd * es)) || (rc = dalloc(&P->z, nd * es)) ||
+        (rc = dalloc(&P->q, nd * es)) || (rc = dalloc(&P->tmp_v, nd * es)) || (rc = dalloc(&F.d, nd * es)))
+        return bail(rc);
+    void* mk = nullptr;
+    if ((rc = dalloc(&mk, (size_t)P->n_node))) return bail(rc);
+    F.mask = (uint8_t*)mk;
+    void* stp = nullptr;
+    if ((rc = dalloc(&stp, st.size() * sizeof(int4))) || (rc = dalloc(&P->stencil_w, sw.size() * es))) return bail(rc);
+    P->stencil = (int4*)stp;
+    void* p = nullptr;
+    if ((rc = dalloc(&p, sizeof(DevScalars)))) return bail(rc);
+    P->sc = (DevScalars*)p;
+    if ((rc = dalloc(&p, sizeof(double) * (size_t)kMaxRedBlocks * (kRedQ + 2 * 8)))) return bail(rc);
+    P->red = (double*)p;
+    if ((rc = dalloc(&p, sizeof(unsigned) * 64))) return bail(rc);
+    P->counters = (unsigned*)p;
+
+    // host-built tables: mask, load vector, stencil
+    std::vector<uint8_t> hmask((size_t)P->n_node, 0);
+    for (int64_t i = 0; i < B->n; ++i) hmask[(size_t)(B->dof[i] / 3)] |= (uint8_t)(1u << (B->dof[i] % 3));
+    std::vector<double> hf(nd, 0.0);
+    for (int64_t i = 0; i < L->n; ++i) hf[(size_t)L->dof[i]] += L->val[i];
+    for (size_t i = 0; i < nd; ++i)
+        if ((hmask[i / 3] >> (i % 3)) & 1) hf[i] = 0.0;
+
+    cudaStream_t s = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return bail(fail(TO_ERR_CUDA, "stream"));
+    auto upload = [&](void* dst, const void* src, size_t bytes) {
+        return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s) == cudaSuccess;
+    };
+    bool ok = upload(F.mask, hmask.data(), hmask.size()) && upload(P->stencil, st.data(), st.size() * sizeof(int4));
+    std::vector<float> hf32, sw32;
+    if (P->prec == TO_FP64) {
+        ok = ok && upload(P->f, hf.data(), nd * 8) && upload(P->stencil_w, sw.data(), sw.size() * 8);
+    } else {
+        hf32.assign(hf.begin(), hf.end());
+        sw32.assign(sw.begin(), sw.end());
+        ok = ok && upload(P->f, hf32.data(), nd * 4) && upload(P->stencil_w, sw32.data(), sw32.size() * 4);
+    }
+    DevScalars hsc{};
+    hsc.k = 1;
+    hsc.alpha0 = prm->alpha0 > 0.0 ? prm->alpha0 : 0.0;
+    ok = ok && upload(P->sc, &hsc, sizeof hsc);
+    ok = ok && cudaMemsetAsync(P->counters, 0, sizeof(unsigned) * 64, s) == cudaSuccess;
+    ok = ok && cudaMemsetAsync(P->u, 0, nd * es, s) == cudaSuccess;
+    if (!ok) {
+        cudaStreamDestroy(s);
+        return bail(fail(TO_ERR_CUDA, "upload failed"));
+    }
+    if ((rc = fill_scalar(P, P->rho, P->n_elem, m->volfrac > m->rho_max ? m->rho_max : m->volfrac, s)) ||
+        (rc = launch_rowsum(P, s))) {
+        cudaStreamDestroy(s);
+        return bail(rc);
+    }
+    if (prm->precond == TO_PRECOND_MG && (rc = mg_build(P))) {
+        cudaStreamDestroy(s);
+        return bail(rc);
+    }
+    if ((rc = launch_moduli(P, s)) || (rc = refresh_preconditioner(P, s))) {
+        cudaStreamDestroy(s);
+        return bail(rc);
+    }
+    cudaError_t e = cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+    if (e != cudaSuccess) return bail(fail(TO_ERR_CUDA, std::string("create: ") + cudaGetErrorString(e)));
+    *out = P;
+    return TO_OK;
+}
+
+extern "C" int to_sizes(const to_problem* P, int64_t* n_elem, int64_t* n_dof) {
+    if (!P) return fail(TO_ERR_ARG, "null problem");
+    if (n_elem) *n_elem = P->n_elem;
+    if (n_dof) *n_dof = P->n_dof;
+    return TO_OK;
+}
+
+#define TO_ENTER(P)                                                   \
+    if (!(P)) return fail(TO_ERR_ARG, "null problem");                \
+    DeviceGuard dg_((P)->device);                                     \
+    if (!dg_.ok) return fail(TO_ERR_CUDA, "cudaSetDevice failed");   \
+    cudaStream_t s = (cudaStream_t)stream;
+
+extern "C" int to_set_design(to_problem* P, const void* rho_dev, void* stream) {
+    TO_ENTER(P);
+    if (!rho_dev) return fail(TO_ERR_ARG, "rho is null");
+    TO_CUDA(cudaMemcpyAsync(P->rho, rho_dev, P->n_elem * P->esz, cudaMemcpyDeviceToDevice, s));
+    int rc = launch_moduli(P, s);
+    if (rc) return rc;
+    return refresh_preconditioner(P, s);
+}
+
+extern "C" int to_apply_K(to_problem* P, const void* u_dev, void* y_dev, void* stream) {
+    TO_ENTER(P);
+    if (!u_dev || !y_dev) return fail(TO_ERR_ARG, "null vector");
+    if (u_dev == y_dev) return fail(TO_ERR_ARG, "u and y must not overlap");
+    return launch_operator(P, 0, OP_APPLY, u_dev, y_dev, nullptr, s);
+}
+
+extern "C" int to_inner_solve(to_problem* P, void* u_dev, int32_t nsteps, double* res_out, void* stream) {
+    TO_ENTER(P);
+    if (!u_dev || nsteps < 0) return fail(TO_ERR_ARG, "bad arguments");
+    void* gt = P->gt;
+    P->gt = nullptr;
+    int rc = run_inner(P, u_dev, nsteps, 0, s);
+    if (!rc && res_out) rc = launch_operator(P, 0, OP_RESID, u_dev, P->r, P->f, s, 0.0, 1);
+    P->gt = gt;
+    if (rc) return rc;
+    if (res_out) {
+        DevScalars h;
+        TO_CUDA(cudaMemcpyAsync(&h, P->sc, sizeof h, cudaMemcpyDeviceToHost, s));
+        TO_CUDA(cudaStreamSynchronize(s));
+        *res_out = h.res2;
+        if (h.err) return fail(h.err, "device-side error in the lower-level steps");
+    }
+    return TO_OK;
+}
+
+extern "C" int to_sensitivity(to_problem* P, const void* u_dev, void* g_dev, void* stream) {
+    TO_ENTER(P);
+    if (!u_dev || !g_dev) return fail(TO_ERR_ARG, "null vector");
+    int rc = launch_energy(P, u_dev, s);
+    if (rc) return rc;
+    return launch_filter(P, P->gt, g_dev, 1, s);
+}
+
+extern "C" int to_filter(to_problem* P, const void* x_dev, void* y_dev, int32_t transpose, void* stream) {
+    TO_ENTER(P);
+    if (!x_dev || !y_dev || x_dev == y_dev) return fail(TO_ERR_ARG, "bad vectors");
+    return launch_filter(P, x_dev, y_dev, transpose ? 1 : 0, s);
+}
+
+extern "C" int to_project(to_problem* P, const void* w_dev, void* rho_dev, double* lambda_out, void* stream) {
+    TO_ENTER(P);
+    if (!w_dev || !rho_dev) return fail(TO_ERR_ARG, "null vector");
+    int rc = launch_project(P, w_dev, nullptr, nullptr, rho_dev, 0, s);
+    if (rc) return rc;
+    if (lambda_out) {
+        DevScalars h;
+        TO_CUDA(cudaMemcpyAsync(&h, P->sc, sizeof h, cudaMemcpyDeviceToHost, s));
+        TO_CUDA(cudaStreamSynchronize(s));
+        *lambda_out = h.lambda;
+        if (h.err) return fail(h.err, "device-side error in the projection");
+    }
+    return TO_OK;
+}
+
+extern "C" int to_step(to_problem* P, int32_t n_outer, to_stats* stats_out, void* stream) {
+    TO_ENTER(P);
+    if (n_outer < 0) return fail(TO_ERR_ARG, "n_outer must be >= 0");
+    if (n_outer == 0) return TO_OK;
+    if (n_outer > P->dstats_cap) {
+        TO_CUDA(cudaStreamSynchronize(s));
+        void* p = P->dstats;
+        dfree(p);
+        int cap = n_outer < 256 ? 256 : n_outer;
+        if (int rc = dalloc(&p, sizeof(to_stats) * (size_t)cap)) return rc;
+        P->dstats = (to_stats*)p;
+        P->dstats_cap = cap;
+    }
+    for (int i = 0; i < n_outer; ++i) {
+        int rc = outer_iteration(P, i, s);
+        if (rc) return rc;
+    }
+    if (stats_out) {
+        TO_CUDA(cudaMemcpyAsync(stats_out, P->dstats, sizeof(to_stats) * (size_t)n_outer, cudaMemcpyDeviceToHost, s));
+        TO_CUDA(cudaStreamSynchronize(s));
+        for (int i = 0; i < n_outer; ++i)
+            if (stats_out[i].status) return fail(stats_out[i].status, "device-side error during the outer iterations");
+    }
+    return TO_OK;
+}
+
+extern "C" int to_get_state(to_problem* P, void* rho_dev, void* u_dev, int64_t* k_out, double* alpha0_out, void* stream) {
+    TO_ENTER(P);
+    if (rho_dev) TO_CUDA(cudaMemcpyAsync(rho_dev, P->rho, P->n_elem * P->esz, cudaMemcpyDeviceToDevice, s));
+    if (u_dev) TO_CUDA(cudaMemcpyAsync(u_dev, P->u, P->n_dof * P->esz, cudaMemcpyDeviceToDevice, s));
+    if (k_out || alpha0_out) {
+        DevScalars h;
+        TO_CUDA(cudaMemcpyAsync(&h, P->sc, sizeof h, cudaMemcpyDeviceToHost, s));
+        TO_CUDA(cudaStreamSynchronize(s));
+        if (k_out) *k_out = h.k;
+        if (alpha0_out) *alpha0_out = h.alpha0;
+    }
+    return TO_OK;
+}
+
+__global__ void k_set_counters(to::DevScalars* sc, long long k, double alpha0, int set_k, int set_a) {
+    if (set_k) sc->k = k;
+    if (set_a) sc->alpha0 = alpha0 > 0.0 ? alpha0 : 0.0;
+}
+
+extern "C" int to_set_state(to_problem* P, const void* rho_dev, const void* u_dev, int64_t k, double alpha0, void* stream) {
+    TO_ENTER(P);
+    if (k < 1) return fail(TO_ERR_ARG, "k must be >= 1");
+    if (rho_dev) TO_CUDA(cudaMemcpyAsync(P->rho, rho_dev, P->n_elem * P->esz, cudaMemcpyDeviceToDevice, s));
+    if (u_dev) TO_CUDA(cudaMemcpyAsync(P->u, u_dev, P->n_dof * P->esz, cudaMemcpyDeviceToDevice, s));
+    k_set_counters<<<1, 1, 0, s>>>(P->sc, (long long)k, alpha0, 1, 1);
+    TO_CUDA(cudaGetLastError());
+    int rc = launch_moduli(P, s);
+    if (rc) return rc;
+    return refresh_preconditioner(P, s);
+}
+
+__global__ void k_clear_err(to::DevScalars* sc) { sc->err = 0; }
+
+extern "C" int to_check(to_problem* P, void* stream) {
+    TO_ENTER(P);
+    DevScalars h;
+    TO_CUDA(cudaMemcpyAsync(&h, P->sc, sizeof h, cudaMemcpyDeviceToHost, s));
+    TO_CUDA(cudaStreamSynchronize(s));
+    if (h.err) {
+        // a device-side wait gave up: clear the flag and the barrier / reduction words
+        k_clear_err<<<1, 1, 0, s>>>(P->sc);
+        TO_CUDA(cudaMemsetAsync(P->counters, 0, sizeof(unsigned) * 64, s));
+        TO_CUDA(cudaStreamSynchronize(s));
+        return fail(h.err, "device-side error flag was set");
+    }
+    return TO_OK;
+}

@@ -1,0 +1,122 @@
+// Device helpers shared by the kernels: deterministic block / grid reductions
+// and a bounded grid barrier.
+#pragma once
+
+#include "internal.cuh"
+
+namespace to {
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Reduce NQ values over the block (kind[q] = 0: sum, 1: max).  The result is
+// valid in thread 0.  `sh` must hold 32 * NQ doubles.  Fixed order.
+template <int NQ>
+__device__ __forceinline__ void block_reduce(double (&v)[NQ], const int (&kind)[NQ], double* sh) {
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    const int nthreads = blockDim.x * blockDim.y * blockDim.z;
+    const int lane = tid & 31, wid = tid >> 5, nw = (nthreads + 31) >> 5;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) v[q] = kind[q] ? warp_max(v[q]) : warp_sum(v[q]);
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) sh[wid * NQ + q] = v[q];
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            double t = lane < nw ? sh[lane * NQ + q] : (kind[q] ? -INFINITY : 0.0);
+            v[q] = kind[q] ? warp_max(t) : warp_sum(t);
+        }
+    }
+    __syncthreads();
+}
+
+// Write this block's partials, then let the last block to finish combine all
+// partials in block order.  Returns true (in every thread) only in that block,
+// with the totals in `tot` valid in all its threads.
+template <int NQ>
+__device__ __forceinline__ bool finish_reduction(const double (&v)[NQ], const int (&kind)[NQ], double* partials,
+                                                 unsigned* counter, double (&tot)[NQ], double* sh) {
+    __shared__ int s_last;
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    const unsigned nblocks = gridDim.x * gridDim.y * gridDim.z;
+    const unsigned bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    if (tid == 0) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) partials[bid * kRedQ + q] = v[q];
+        __threadfence();
+        const unsigned t = atomicAdd(counter, 1u);
+        s_last = (t == nblocks - 1);
+        if (s_last) atomicExch(counter, 0u);
+    }
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+    // every thread folds a strided subset in order, then a fixed-order tree
+    double acc[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) acc[q] = kind[q] ? -INFINITY : 0.0;
+    const int nthreads = blockDim.x * blockDim.y * blockDim.z;
+    for (unsigned b = tid; b < nblocks; b += nthreads)
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const double t = __ldcg(partials + b * kRedQ + q);
+            acc[q] = kind[q] ? fmax(acc[q], t) : acc[q] + t;
+        }
+    block_reduce<NQ>(acc, kind, sh);
+    if (tid == 0)
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) sh[q] = acc[q];
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) tot[q] = sh[q];
+    __syncthreads();
+    return true;
+}
+
+// Grid-wide barrier for a cooperative (co-resident) launch.  bar[0] counts
+// arrivals, bar[1] is the generation.  Spins a bounded number of times; on
+// timeout records TO_ERR_TIMEOUT in *err and returns false.
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err) {
+    __shared__ int s_ok;
+    const unsigned nblocks = gridDim.x * gridDim.y * gridDim.z;
+    __syncthreads();
+    if (threadIdx.x == 0 && threadIdx.y == 0 && threadIdx.z == 0) {
+        volatile unsigned* vgen = bar + 1;
+        const unsigned gen = *vgen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(bar, 1u);
+        s_ok = 1;
+        if (arrived == nblocks - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            unsigned long long spins = 0;
+            while (*vgen == gen) {
+                if (++spins > (1ull << 24)) {
+                    atomicCAS(err, 0, (int)TO_ERR_TIMEOUT);
+                    s_ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+__device__ __forceinline__ void set_err(int* err, int code) { atomicCAS(err, 0, code); }
+
+}  // namespace to

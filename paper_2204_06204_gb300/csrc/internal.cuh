@@ -1,0 +1,166 @@
+// Internal definitions of the GB300 first-order bilevel topology optimiser.
+// Public ABI: include/to.h.  Nothing here is exported.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/to.h"
+
+namespace to {
+
+// ----------------------------------------------------------------------------- errors
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+#define TO_CUDA(call)                                                                     \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return ::to::fail(TO_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+// ----------------------------------------------------------------------------- device scalars
+// Device-resident scalars of the outer loop; read by kernels, never copied to
+// the host except through to_stats / to_get_state / to_check.
+struct DevScalars {
+    double rz, zq, beta, beta_first;   // lower-level step sizes (Algorithm 1 / 3, line 1)
+    double J, res_inf, res2;           // f^T u_k, residual norms at u_k
+    double gmax, gsum;                 // ||g||_inf and 1^T g of dJ/drho
+    double alpha0, alpha;              // high-level step size alpha_k = alpha0 k^-m
+    double lambda, drho_inf, volume;   // projection results
+    long long k;                       // 1-based outer iteration counter
+    int err;                           // first device-side error (TO_ERR_*), 0 if none
+    int proj_iters;
+    int n_inner_done;
+    int pad;
+};
+
+// Reduction scratch: one slot of up to kRedQ doubles per block, plus a
+// completion counter; the last block to finish sums the slots in block order
+// (deterministic) and writes the totals.
+constexpr int kRedQ = 4;
+constexpr int kMaxRedBlocks = 8192;
+
+// ----------------------------------------------------------------------------- operator constants
+// The unit-modulus hex8 element matrix in the sum/difference (Haar) basis of
+// its 2x2x2 nodes has 45 non-zeros in fixed positions; kHaarRow/kHaarCol list
+// them (coefficient DOF = 3 * (4 zeta + 2 eta + xi) + component, zeta / eta / xi
+// = 0 for a sum and 1 for a difference along z / y / x).
+constexpr int kHaarNnz = 45;
+extern const int kHaarRow[kHaarNnz];
+extern const int kHaarCol[kHaarNnz];
+
+template <typename T>
+struct HaarK {
+    T v[kHaarNnz];  // values for element edge h (K_e scales with h in 3-D)
+};
+
+// 24x24 unit-modulus, unit-size hex8 stiffness (row-major), built by exact
+// integration of the Lame bilinear form; its Haar-basis non-zeros; validation.
+int build_element_matrix(double nu, double ke[24 * 24]);
+int build_haar(const double ke[24 * 24], double h, double out[kHaarNnz]);
+
+// ----------------------------------------------------------------------------- problem
+struct Level {
+    int nx, ny, nz;
+    int64_t n_elem, n_node, n_dof;
+    double h;
+    void* E = nullptr;        // element moduli (T)
+    void* d = nullptr;        // diag(K^) (T)
+    uint8_t* mask = nullptr;  // per node: bit c set = DOF c fixed
+    void* x = nullptr;        // V-cycle vectors (T)
+    void* b = nullptr;
+    void* t = nullptr;
+    double kdiag = 0.0;       // k_e[ll] (all equal on a cube)
+};
+
+struct to_problem_impl;
+
+}  // namespace to
+
+struct to_problem {
+    int device = 0;
+    int prec = TO_FP32_MIXED;
+    to_grid g{};
+    to_material mat{};
+    to_params prm{};
+    int64_t n_elem = 0, n_node = 0, n_dof = 0;
+    size_t esz = 4;                // bytes per vector entry
+    double ke[24 * 24];            // unit element matrix (host, double)
+    double haar[to::kHaarNnz];     // Haar non-zeros for edge h
+    double kdiag = 0.0;            // k_e[ll] for edge h
+
+    // design and filter
+    void* rho = nullptr;
+    void* rhot = nullptr;
+    void* Ed = nullptr;            // dE/drho~
+    void* Hs = nullptr;            // filter row sums
+    void* gt = nullptr;            // dJ/drho~
+    void* grad = nullptr;          // dJ/drho
+    void* tmp_e = nullptr;         // element scratch
+    int n_stencil = 0;
+    int4* stencil = nullptr;       // (dx, dy, dz, -) offsets
+    void* stencil_w = nullptr;     // weights (T)
+
+    // solver vectors (n_dof each)
+    void* u = nullptr;
+    void* f = nullptr;
+    void* r = nullptr;
+    void* z = nullptr;
+    void* q = nullptr;
+    void* tmp_v = nullptr;
+
+    // multigrid hierarchy (level 0 aliases E, d, mask of the fine grid)
+    std::vector<to::Level> lv;
+    void* coarse_A = nullptr;      // dense coarsest operator (T), n_c x n_c
+    void* coarse_L = nullptr;      // its inverse (T), n_c x n_c
+    int n_coarse = 0;
+
+    // device scalars, reductions, stats
+    to::DevScalars* sc = nullptr;
+    double* red = nullptr;         // kMaxRedBlocks * kRedQ doubles
+    unsigned* counters = nullptr;  // completion counters / barrier words
+    to_stats* dstats = nullptr;    // device stats ring
+    int dstats_cap = 0;
+
+    // launch configuration of the operator kernel
+    int tile_x = 32, tile_y = 8, tile_z = 8;
+    int num_sms = 0;
+    int coop_blocks = 0;           // co-resident blocks for the projection kernel
+};
+
+namespace to {
+
+// kernels/launchers (templated on the vector type T = float | double)
+template <typename T> struct Launch;
+
+int launch_filter(to_problem* P, const void* x, void* y, int transpose, cudaStream_t s);
+int launch_moduli(to_problem* P, cudaStream_t s);  // rho -> rho~, E, E'
+int launch_diag(to_problem* P, int level, cudaStream_t s);
+
+enum OpMode { OP_APPLY = 0, OP_RESID = 1, OP_Q = 2, OP_SMOOTH = 3, OP_BMINUS = 4 };
+// y = K^ x (+ mode epilogue) on multigrid level `level` (0 = fine grid).
+int launch_operator(to_problem* P, int level, int mode, const void* x, void* y,
+                    const void* b, cudaStream_t s, double omega = 0.0, int first = 0);
+
+int launch_project(to_problem* P, const void* w, const void* rho_in, const void* g,
+                   void* rho_out, int fused, cudaStream_t s);
+int launch_update_sd(to_problem* P, cudaStream_t s);
+int launch_precond(to_problem* P, const void* r, void* z, cudaStream_t s);
+int launch_sens_filter_T(to_problem* P, cudaStream_t s);
+int launch_energy(to_problem* P, const void* u, cudaStream_t s);
+int launch_record(to_problem* P, int slot, cudaStream_t s);
+int launch_richardson(to_problem* P, cudaStream_t s);
+
+// multigrid
+int mg_build(to_problem* P);
+int mg_refresh(to_problem* P, cudaStream_t s);   // coarse moduli, diagonals, coarse factor
+int mg_vcycle(to_problem* P, const void* r, void* z, cudaStream_t s);
+
+int outer_iteration(to_problem* P, int slot, cudaStream_t s);
+int inner_steps(to_problem* P, int nsteps, int from_resid, cudaStream_t s);
+
+}  // namespace to

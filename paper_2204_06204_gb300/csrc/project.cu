@@ -1,0 +1,226 @@
+// Projection onto X = {lo <= rho <= hi, 1^T rho <= vbar} (Sec. IV-B).
+//
+// The KKT conditions give rho = clamp(w - lambda, lo, hi) with lambda = 0 when
+// the clamp already meets the volume bound, else the root of the piecewise-
+// linear, non-increasing volume function of Eq. (piecewiseLinearEQ)
+//   S(lambda) = sum_e clamp(w_e - lambda, lo, hi) = vbar.
+// The paper finds the root by sorting the 2E breakpoints (Algorithm 4; on a GPU
+// with a radix sort and a scan).  Here one cooperative kernel runs a
+// safeguarded Newton iteration on S instead: each pass classifies every element
+// as at-upper / at-lower / free for the current lambda (one grid reduction of
+// the counts and of the free elements' sum), S is then known exactly on the
+// current linear piece and the Newton step lands on the root of that piece;
+// a bracket [lambda_lo, lambda_hi] with S(lambda_lo) > vbar >= S(lambda_hi)
+// falls back to bisection whenever the step leaves it.  Once the pass sees the
+// same piece twice the root is exact (up to rounding), typically in a handful
+// of passes.  lambda and every sum are double; the element values are the
+// problem's precision.
+#include "device.cuh"
+
+namespace to {
+
+constexpr int kProjSlot = 8;      // doubles per block per pass in the projection scratch
+constexpr int kProjMaxIter = 100;
+
+template <typename T>
+struct ProjArgs {
+    long long n;
+    const T* w_in;       // plain mode
+    const T* rho_in;     // fused mode: w = rho - alpha (g - mean)
+    const T* g;
+    T* wbuf;             // scratch (n)
+    T* rho_out;
+    double vbar, lo, hi;
+    int fused, mean_proj;
+    double alpha0_param, alpha_scale, m;
+    double* part;        // 2 * nblocks * kProjSlot doubles
+    double* red;         // final reduction scratch (kRedQ per block)
+    unsigned* bar;       // barrier words
+    unsigned* counter;   // final reduction counter
+    DevScalars* sc;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_project(const ProjArgs<T> a) {
+    __shared__ double sh[32 * kRedQ];
+    __shared__ double sh8[32 * 8];
+    const unsigned nb = gridDim.x, bid = blockIdx.x;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    DevScalars* sc = a.sc;
+
+    // step size (identical in every block: only values fixed before this kernel are read)
+    double alpha0 = 0.0, alpha = 0.0, gmean = 0.0;
+    if (a.fused) {
+        alpha0 = a.alpha0_param > 0.0 ? a.alpha0_param : sc->alpha0;
+        if (!(alpha0 > 0.0) && sc->gmax > 0.0) alpha0 = a.alpha_scale / sc->gmax;
+        if (alpha0 > 0.0) alpha = alpha0 * pow((double)sc->k, -a.m);
+        if (a.mean_proj) gmean = sc->gsum / (double)a.n;
+    }
+
+    // pass 0: w, the box-clamp volume, the piece at lambda = 0, min / max of w
+    double lambda = 0.0;
+    double lam_lo = 0.0, lam_hi = 0.0;
+    int iters = 0;
+    bool done = false;
+    int parity = 0;
+    double tot[6];
+    {
+        double v[6] = {0.0, 0.0, 0.0, 0.0, INFINITY, -INFINITY};  // nU, nL, nF, sF, min w, max w
+        T sF = T(0);
+        for (long long e = t0; e < a.n; e += stride) {
+            T w;
+            if (a.fused)
+                w = (T)((double)a.rho_in[e] - alpha * ((double)a.g[e] - gmean));
+            else
+                w = a.w_in[e];
+            a.wbuf[e] = w;
+            const double wd = (double)w;
+            if (wd >= a.hi) v[0] += 1.0;
+            else if (wd <= a.lo) v[1] += 1.0;
+            else { v[2] += 1.0; sF += w; }
+            v[4] = fmin(v[4], wd);
+            v[5] = fmax(v[5], wd);
+        }
+        v[3] = (double)sF;
+        double mv[6] = {v[0], v[1], v[2], v[3], -v[4], v[5]};
+        const int kind[6] = {0, 0, 0, 0, 1, 1};
+        block_reduce<6>(mv, kind, sh8);
+        if (threadIdx.x == 0)
+            for (int q = 0; q < 6; ++q) a.part[(parity * nb + bid) * kProjSlot + q] = mv[q];
+        if (!grid_barrier(a.bar, &sc->err)) return;
+        for (int q = 0; q < 6; ++q) tot[q] = (q >= 4) ? -INFINITY : 0.0;
+        for (unsigned b = 0; b < nb; ++b)
+            for (int q = 0; q < 6; ++q) {
+                const double t = __ldcg(a.part + (parity * nb + b) * kProjSlot + q);
+                tot[q] = (q >= 4) ? fmax(tot[q], t) : tot[q] + t;
+            }
+        parity ^= 1;
+    }
+    const double wmin = -tot[4], wmax = tot[5];
+    double S = tot[0] * a.hi + tot[1] * a.lo + tot[3];   // box-clamp volume (lambda = 0)
+    if (!isfinite(S)) set_err(&sc->err, TO_ERR_NONFINITE);
+    if (S <= a.vbar || !isfinite(S)) {
+        done = true;
+        lambda = 0.0;
+    } else {
+        lam_lo = fmax(0.0, wmin - a.hi);   // S(lam_lo) > vbar
+        lam_hi = wmax - a.lo;              // S(lam_hi) = n lo <= vbar
+        const double nF = tot[2];
+        double ln = nF > 0.0 ? (S - a.vbar) / nF : NAN;
+        lambda = (ln > lam_lo && ln < lam_hi) ? ln : 0.5 * (lam_lo + lam_hi);
+    }
+
+    while (!done && iters < kProjMaxIter) {
+        ++iters;
+        const double tU = lambda + a.hi, tL = lambda + a.lo;
+        double v[4] = {0.0, 0.0, 0.0, 0.0};
+        T sF = T(0);
+        for (long long e = t0; e < a.n; e += stride) {
+            const T w = a.wbuf[e];
+            const double wd = (double)w;
+            if (wd >= tU) v[0] += 1.0;
+            else if (wd <= tL) v[1] += 1.0;
+            else { v[2] += 1.0; sF += w; }
+        }
+        v[3] = (double)sF;
+        const int kind[4] = {0, 0, 0, 0};
+        block_reduce<4>(v, kind, sh);
+        if (threadIdx.x == 0)
+            for (int q = 0; q < 4; ++q) a.part[(parity * nb + bid) * kProjSlot + q] = v[q];
+        if (!grid_barrier(a.bar, &sc->err)) return;
+        double t4[4] = {0.0, 0.0, 0.0, 0.0};
+        for (unsigned b = 0; b < nb; ++b)
+            for (int q = 0; q < 4; ++q) t4[q] += __ldcg(a.part + (parity * nb + b) * kProjSlot + q);
+        parity ^= 1;
+        const double nF = t4[2];
+        S = t4[0] * a.hi + t4[1] * a.lo + t4[3] - lambda * nF;
+        if (S == a.vbar) break;
+        if (S > a.vbar) lam_lo = lambda;
+        else lam_hi = lambda;
+        const double ln = nF > 0.0 ? lambda + (S - a.vbar) / nF : NAN;
+        const double next = (ln > lam_lo && ln < lam_hi) ? ln : 0.5 * (lam_lo + lam_hi);
+        if (next == lambda || fabs(next - lambda) <= 1e-15 * fmax(1.0, fabs(lambda)) ||
+            lam_hi - lam_lo <= 1e-15 * fmax(1.0, fabs(lambda))) {
+            lambda = next;
+            break;
+        }
+        lambda = next;
+    }
+
+    // final pass: rho = clamp(w - lambda), ||drho||_inf, volume
+    double dmax = 0.0, vol = 0.0;
+    for (long long e = t0; e < a.n; e += stride) {
+        const double wd = (double)a.wbuf[e];
+        const double r = fmin(fmax(wd - lambda, a.lo), a.hi);
+        const T rt = (T)r;
+        if (a.fused) dmax = fmax(dmax, fabs((double)rt - (double)a.rho_in[e]));
+        vol += (double)rt;
+        a.rho_out[e] = rt;
+    }
+    double v2[2] = {dmax, vol};
+    const int kind2[2] = {1, 0};
+    double tot2[2];
+    block_reduce<2>(v2, kind2, sh);
+    if (finish_reduction<2>(v2, kind2, a.red, a.counter, tot2, sh) && threadIdx.x == 0) {
+        sc->lambda = lambda;
+        sc->drho_inf = tot2[0];
+        sc->volume = tot2[1];
+        sc->proj_iters = iters;
+        if (a.fused) {
+            sc->alpha = alpha;
+            if (alpha0 > 0.0) sc->alpha0 = alpha0;
+        }
+    }
+}
+
+template <typename T>
+static int project_t(to_problem* P, const void* w, const void* rho_in, const void* g, void* rho_out, int fused,
+                     cudaStream_t s) {
+    ProjArgs<T> a{};
+    a.n = P->n_elem;
+    a.w_in = (const T*)w;
+    a.rho_in = (const T*)rho_in;
+    a.g = (const T*)g;
+    a.wbuf = (T*)P->tmp_e;
+    a.rho_out = (T*)rho_out;
+    a.vbar = P->mat.volfrac * (double)P->n_elem;
+    a.lo = P->mat.rho_min;
+    a.hi = P->mat.rho_max;
+    a.fused = fused;
+    a.mean_proj = P->prm.mean_proj;
+    a.alpha0_param = P->prm.alpha0;
+    a.alpha_scale = P->prm.alpha_scale;
+    a.m = P->prm.m;
+    a.part = P->red + (size_t)kMaxRedBlocks * kRedQ;
+    a.red = P->red;
+    a.bar = P->counters + 8;
+    a.counter = P->counters + 3;
+    a.sc = P->sc;
+    int nb = (int)((P->n_elem + 255) / 256);
+    if (nb > P->coop_blocks) nb = P->coop_blocks;
+    if (nb < 1) nb = 1;
+    void* args[] = {(void*)&a};
+    TO_CUDA(cudaLaunchCooperativeKernel((const void*)k_project<T>, dim3(nb), dim3(256), args, 0, s));
+    return TO_OK;
+}
+
+int launch_project(to_problem* P, const void* w, const void* rho_in, const void* g, void* rho_out, int fused,
+                   cudaStream_t s) {
+    return P->prec == TO_FP64 ? project_t<double>(P, w, rho_in, g, rho_out, fused, s)
+                              : project_t<float>(P, w, rho_in, g, rho_out, fused, s);
+}
+
+int project_coop_blocks(int prec, int num_sms, int* out) {
+    int per_sm = 0;
+    cudaError_t e = prec == TO_FP64
+                        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_project<double>, 256, 0)
+                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_project<float>, 256, 0);
+    if (e != cudaSuccess) return fail(TO_ERR_CUDA, std::string("occupancy query: ") + cudaGetErrorString(e));
+    if (per_sm > 2) per_sm = 2;
+    *out = per_sm * num_sms;
+    if (*out > kMaxRedBlocks) *out = kMaxRedBlocks;
+    return TO_OK;
+}
+
+}  // namespace to

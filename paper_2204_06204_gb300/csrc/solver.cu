@@ -1,0 +1,198 @@
+// Lower-level steps and the outer iteration.
+//
+// Lower level (Algorithm 1 / 3, line 1, widened to n_inner steps warm-started
+// from the previous u): steepest descent on P_f(u) = 1/2 u^T K u - f^T u along
+// z = M^-1 r with the exact line search beta = r^T z / z^T K z, or the literal
+// constant-beta step u <- u + beta M^-1 (f - K u).
+//
+// Outer iteration k (Algorithms 1 / 3):
+//   rho~ = C(rho_k), E, E'                        launch_moduli
+//   M for this design (diagonal / V-cycle)        launch_diag | mg_refresh
+//   r = f - K u_k, g~ = -E' u^T k_e u (at u_k), J  fused operator epilogue
+//   n_inner lower-level steps                     operator + update kernels
+//   g = C^T g~, ||g||_inf, 1^T g                  launch_sens_filter_T
+//   rho_{k+1} = Proj_X(rho_k - alpha_k g)        launch_project (fused)
+//   stats record, k += 1                          launch_record
+// Every scalar stays on the device; nothing synchronises with the host.
+#include "device.cuh"
+
+namespace to {
+
+int project_coop_blocks(int prec, int num_sms, int* out);
+
+static int grid_1d(long long n, int threads, int num_sms) {
+    long long b = (n + threads - 1) / threads;
+    if (b > 4LL * num_sms) b = 4LL * num_sms;
+    return (int)(b < 1 ? 1 : b);
+}
+
+// u += beta z; r -= beta q; (Jacobi) z = r / d and r^T z
+template <typename T, bool JACOBI>
+__global__ void __launch_bounds__(256) k_update_sd(long long n, T* __restrict__ u, T* __restrict__ r, T* __restrict__ z,
+                                                   const T* __restrict__ q, const T* __restrict__ d, double* red,
+                                                   unsigned* counter, DevScalars* sc) {
+    __shared__ double sh[32 * kRedQ];
+    const T beta = (T)sc->beta;
+    T acc = T(0);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const T zi = z[i];
+        u[i] += beta * zi;
+        const T ri = r[i] - beta * q[i];
+        r[i] = ri;
+        if (JACOBI) {
+            const T zn = ri / d[i];
+            z[i] = zn;
+            acc += ri * zn;
+        }
+    }
+    if (JACOBI) {
+        double v[1] = {(double)acc};
+        const int kind[1] = {0};
+        double tot[1];
+        block_reduce<1>(v, kind, sh);
+        if (finish_reduction<1>(v, kind, red, counter, tot, sh) && threadIdx.x == 0) sc->rz = tot[0];
+    }
+}
+
+// r^T z (after a V-cycle)
+template <typename T>
+__global__ void __launch_bounds__(256) k_dot_rz(long long n, const T* __restrict__ r, const T* __restrict__ z, double* red,
+                                                unsigned* counter, DevScalars* sc) {
+    __shared__ double sh[32 * kRedQ];
+    T acc = T(0);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        acc += r[i] * z[i];
+    double v[1] = {(double)acc};
+    const int kind[1] = {0};
+    double tot[1];
+    block_reduce<1>(v, kind, sh);
+    if (finish_reduction<1>(v, kind, red, counter, tot, sh) && threadIdx.x == 0) sc->rz = tot[0];
+}
+
+// u += beta z  (Richardson)
+template <typename T>
+__global__ void k_axpy(long long n, T* __restrict__ u, const T* __restrict__ z, T beta) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        u[i] += beta * z[i];
+}
+
+__global__ void k_record(DevScalars* sc, to_stats* st, int slot) {
+    to_stats s;
+    s.k = sc->k;
+    s.J = sc->J;
+    s.res_inf = sc->res_inf;
+    s.res2 = sc->res2;
+    s.drho_inf = sc->drho_inf;
+    s.volume = sc->volume;
+    s.lambda = sc->lambda;
+    s.alpha = sc->alpha;
+    s.gmax = sc->gmax;
+    s.beta_first = sc->beta_first;
+    s.beta_last = sc->beta;
+    s.proj_iters = sc->proj_iters;
+    s.status = sc->err;
+    st[slot] = s;
+    sc->k += 1;
+    sc->beta_first = 0.0;
+    sc->beta = 0.0;
+}
+
+__global__ void k_set_beta(DevScalars* sc, double beta) {
+    sc->beta = beta;
+    if (sc->beta_first == 0.0) sc->beta_first = beta;
+}
+
+int launch_record(to_problem* P, int slot, cudaStream_t s) {
+    k_record<<<1, 1, 0, s>>>(P->sc, P->dstats, slot);
+    TO_CUDA(cudaGetLastError());
+    return TO_OK;
+}
+
+template <typename T>
+static int update_t(to_problem* P, void* u, cudaStream_t s) {
+    const int nb = grid_1d(P->n_dof, 256, P->num_sms);
+    if (P->prm.precond == TO_PRECOND_JACOBI)
+        k_update_sd<T, true><<<nb, 256, 0, s>>>(P->n_dof, (T*)u, (T*)P->r, (T*)P->z, (const T*)P->q,
+                                                (const T*)P->lv[0].d, P->red, P->counters + 4, P->sc);
+    else
+        k_update_sd<T, false><<<nb, 256, 0, s>>>(P->n_dof, (T*)u, (T*)P->r, (T*)P->z, (const T*)P->q,
+                                                 (const T*)P->lv[0].d, P->red, P->counters + 4, P->sc);
+    TO_CUDA(cudaGetLastError());
+    return TO_OK;
+}
+
+// z = M^-1 r for the non-Jacobi preconditioners, followed by r^T z
+template <typename T>
+static int precond_t(to_problem* P, cudaStream_t s) {
+    const int nb = grid_1d(P->n_dof, 256, P->num_sms);
+    if (P->prm.precond == TO_PRECOND_MG) {
+        int rc = mg_vcycle(P, P->r, P->z, s);
+        if (rc) return rc;
+    } else if (P->prm.precond == TO_PRECOND_NONE) {
+        TO_CUDA(cudaMemcpyAsync(P->z, P->r, P->n_dof * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    } else {
+        return TO_OK;  // Jacobi z is produced inside the fused kernels
+    }
+    k_dot_rz<T><<<nb, 256, 0, s>>>(P->n_dof, (const T*)P->r, (const T*)P->z, P->red, P->counters + 5, P->sc);
+    TO_CUDA(cudaGetLastError());
+    return TO_OK;
+}
+
+int launch_precond(to_problem* P, const void*, void*, cudaStream_t s) {
+    return P->prec == TO_FP64 ? precond_t<double>(P, s) : precond_t<float>(P, s);
+}
+
+// Residual at u (with the fused sensitivity when `primary`), then nsteps steps.
+int run_inner(to_problem* P, void* u, int nsteps, int primary, cudaStream_t s) {
+    int rc;
+    void* gt_save = P->gt;
+    if (!primary) P->gt = nullptr;
+    rc = launch_operator(P, 0, OP_RESID, u, P->r, P->f, s, 0.0, 1);
+    P->gt = gt_save;
+    if (rc) return rc;
+    if (P->prm.inner_mode == TO_INNER_SD) {
+        if ((rc = launch_precond(P, P->r, P->z, s))) return rc;
+        for (int it = 0; it < nsteps; ++it) {
+            if ((rc = launch_operator(P, 0, OP_Q, P->z, P->q, nullptr, s, 0.0, it == 0))) return rc;
+            if ((rc = P->prec == TO_FP64 ? update_t<double>(P, u, s) : update_t<float>(P, u, s))) return rc;
+            if (it + 1 < nsteps && (rc = launch_precond(P, P->r, P->z, s))) return rc;
+        }
+    } else {
+        const int nb = grid_1d(P->n_dof, 256, P->num_sms);
+        k_set_beta<<<1, 1, 0, s>>>(P->sc, P->prm.beta);
+        for (int it = 0; it < nsteps; ++it) {
+            if (it > 0) {
+                P->gt = nullptr;
+                rc = launch_operator(P, 0, OP_RESID, u, P->r, P->f, s, 0.0, 0);
+                P->gt = gt_save;
+                if (rc) return rc;
+            }
+            if ((rc = launch_precond(P, P->r, P->z, s))) return rc;
+            if (P->prec == TO_FP64)
+                k_axpy<double><<<nb, 256, 0, s>>>(P->n_dof, (double*)u, (const double*)P->z, P->prm.beta);
+            else
+                k_axpy<float><<<nb, 256, 0, s>>>(P->n_dof, (float*)u, (const float*)P->z, (float)P->prm.beta);
+            TO_CUDA(cudaGetLastError());
+        }
+    }
+    return TO_OK;
+}
+
+int refresh_preconditioner(to_problem* P, cudaStream_t s) {
+    int rc = launch_diag(P, 0, s);
+    if (rc) return rc;
+    if (P->prm.precond == TO_PRECOND_MG) return mg_refresh(P, s);
+    return TO_OK;
+}
+
+int outer_iteration(to_problem* P, int slot, cudaStream_t s) {
+    int rc;
+    if ((rc = launch_moduli(P, s))) return rc;
+    if ((rc = refresh_preconditioner(P, s))) return rc;
+    if ((rc = run_inner(P, P->u, P->prm.n_inner, 1, s))) return rc;
+    if ((rc = launch_sens_filter_T(P, s))) return rc;
+    if ((rc = launch_project(P, nullptr, P->rho, P->grad, P->rho, 1, s))) return rc;
+    return launch_record(P, slot, s);
+}
+
+}  // namespace to
