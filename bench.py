@@ -328,12 +328,24 @@ def _mg_available(fb):
         return False
 
 
-def _launches_per_step(mg, n_inner):
+def _mg_levels(nx, ny, nz):
+    t = 0
+    while all(d % (2 << t) == 0 for d in (nx, ny, nz)) and min(nx, ny, nz) // (2 << t) >= 2:
+        t += 1
+    return t + 1
+
+
+def _launches_per_step(mg, n_inner, dims=(128, 64, 64), nu1=2, nu2=2):
+    """Kernel launches of one outer iteration, as issued by the library."""
     # filter + moduli, diag, residual, (Q + update) per step, filter^T, projection, record
     base = 2 + 1 + 1 + 2 * n_inner + 1 + 1 + 1
     if not mg:
         return base
-    return base  # the V-cycle launches are added when multigrid is built
+    L = _mg_levels(*dims)
+    refresh = 2 * (L - 1) + 2                       # coarsen + diag per level, dense assemble + invert
+    vcycle = (L - 1) * (1 + (nu1 - 1) + 1 + 1 + 1 + nu2) + 1
+    precond = vcycle + 1                            # V-cycle + r^T z
+    return base + refresh + precond * n_inner       # one V-cycle per step (before each Q apply)
 
 
 if __name__ == "__main__":

@@ -121,6 +121,7 @@ extern "C" void to_destroy(to_problem* P) {
         dfree(L.t);
     }
     void* p;
+    p = P->ke_dev; dfree(p);
     p = P->sc; dfree(p);
     p = P->red; dfree(p);
     p = P->counters; dfree(p);

@@ -116,8 +116,9 @@ struct to_problem {
     // multigrid hierarchy (level 0 aliases E, d, mask of the fine grid)
     std::vector<to::Level> lv;
     void* coarse_A = nullptr;      // dense coarsest operator (T), n_c x n_c
-    void* coarse_L = nullptr;      // its inverse (T), n_c x n_c
+    void* coarse_L = nullptr;      // scaled inverse (T), n_c x n_c, then the n_c scale factors
     int n_coarse = 0;
+    double* ke_dev = nullptr;      // 24x24 unit element matrix (device, double)
 
     // device scalars, reductions, stats
     to::DevScalars* sc = nullptr;

@@ -1,12 +1,365 @@
-// Geometric multigrid V-cycle used as the lower-level preconditioner M.
+// Geometric-multigrid V-cycle used as the lower-level preconditioner M
+// (Algorithm 3 with a non-Krylov M; the paper cites multigrid as prior art in
+// Sec. II and IV-A/D and leaves its design open).  Definition:
+//   level l+1 halves every grid dimension and doubles the element edge; its
+//   element moduli are the mean of the 8 children, its operator is the hex8
+//   operator of that grid (K_e scales with the edge length in 3-D); a coarse
+//   DOF is fixed when any fine DOF of the same component at the fine nodes
+//   {2I-1, 2I, 2I+1}^3 is; transfer is trilinear prolongation P (restriction
+//   P^T) with fixed DOFs masked on both sides; smoothing is damped Jacobi with
+//   weight omega, nu_pre sweeps before and nu_post after the coarse
+//   correction; the coarsest grid is solved exactly.
+// Coarsest solve: the dense operator is assembled on the device, scaled to a
+// unit diagonal (S A S, S = diag(A)^-1/2, so that the 1e9 stiffness contrast of
+// void regions does not reach the factorisation) and inverted by Gauss-Jordan
+// elimination in one CTA's shared memory; each V-cycle then applies S A^-1 S.
+#include <algorithm>
+#include <cmath>
+
 #include "device.cuh"
 
 namespace to {
 
-int mg_build(to_problem* P) { return fail(TO_ERR_ARG, "multigrid preconditioner not available in this build"); }
-int mg_refresh(to_problem* P, cudaStream_t s) { return fail(TO_ERR_ARG, "multigrid preconditioner not available"); }
+constexpr int kMaxCoarseDof = 160;   // n^2 doubles fit in one CTA's shared memory
+
+static int grid1(long long n, int num_sms) {
+    long long b = (n + 255) / 256;
+    if (b > 8LL * num_sms) b = 8LL * num_sms;
+    return (int)(b < 1 ? 1 : b);
+}
+
+template <typename T>
+__global__ void k_coarsen_E(int cx, int cy, int cz, const T* __restrict__ Ef, T* __restrict__ Ec) {
+    const long long n = (long long)cx * cy * cz;
+    const int fx = 2 * cx, fy = 2 * cy;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const int I = (int)(e % cx), J = (int)((e / cx) % cy), K = (int)(e / ((long long)cx * cy));
+        T s = T(0);
+        for (int c = 0; c < 2; ++c)
+            for (int b = 0; b < 2; ++b)
+                for (int a = 0; a < 2; ++a)
+                    s += Ef[(2 * I + a) + (long long)fx * ((2 * J + b) + (long long)fy * (2 * K + c))];
+        Ec[e] = T(0.125) * s;
+    }
+}
+
+// b_c = m_c P^T (m_f t)
+template <typename T>
+__global__ void k_restrict(int cx, int cy, int cz, const T* __restrict__ tf, const uint8_t* __restrict__ mf,
+                           const uint8_t* __restrict__ mc, T* __restrict__ bc) {
+    const long long nn = (long long)(cx + 1) * (cy + 1) * (cz + 1);
+    const int fx = 2 * cx, fy = 2 * cy, fz = 2 * cz;
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < nn; n += (long long)gridDim.x * blockDim.x) {
+        const int I = (int)(n % (cx + 1)), J = (int)((n / (cx + 1)) % (cy + 1)), K = (int)(n / ((long long)(cx + 1) * (cy + 1)));
+        T acc[3] = {T(0), T(0), T(0)};
+        for (int dk = -1; dk <= 1; ++dk) {
+            const int k = 2 * K + dk;
+            if (k < 0 || k > fz) continue;
+            const T wk = dk ? T(0.5) : T(1);
+            for (int dj = -1; dj <= 1; ++dj) {
+                const int j = 2 * J + dj;
+                if (j < 0 || j > fy) continue;
+                const T wj = dj ? T(0.5) : T(1);
+                for (int di = -1; di <= 1; ++di) {
+                    const int i = 2 * I + di;
+                    if (i < 0 || i > fx) continue;
+                    const T w = (di ? T(0.5) : T(1)) * wj * wk;
+                    const long long fnode = i + (long long)(fx + 1) * (j + (long long)(fy + 1) * k);
+                    const uint8_t m = mf[fnode];
+                    for (int c = 0; c < 3; ++c)
+                        if (!((m >> c) & 1)) acc[c] += w * tf[3 * fnode + c];
+                }
+            }
+        }
+        const uint8_t m = mc[n];
+        for (int c = 0; c < 3; ++c) bc[3 * n + c] = ((m >> c) & 1) ? T(0) : acc[c];
+    }
+}
+
+// x_f += m_f P (m_c x_c)
+template <typename T>
+__global__ void k_prolong_add(int cx, int cy, int cz, const T* __restrict__ xc, const uint8_t* __restrict__ mc,
+                              const uint8_t* __restrict__ mf, T* __restrict__ xf) {
+    const int fx = 2 * cx, fy = 2 * cy, fz = 2 * cz;
+    const long long nn = (long long)(fx + 1) * (fy + 1) * (fz + 1);
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < nn; n += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(n % (fx + 1)), j = (int)((n / (fx + 1)) % (fy + 1)), k = (int)(n / ((long long)(fx + 1) * (fy + 1)));
+        const uint8_t m = mf[n];
+        if (m == 7) continue;
+        const int i0 = i >> 1, i1 = (i + 1) >> 1, j0 = j >> 1, j1 = (j + 1) >> 1, k0 = k >> 1, k1 = (k + 1) >> 1;
+        T acc[3] = {T(0), T(0), T(0)};
+        for (int kc = k0; kc <= k1; ++kc)
+            for (int jc = j0; jc <= j1; ++jc)
+                for (int ic = i0; ic <= i1; ++ic) {
+                    const T w = ((i & 1) ? T(0.5) : T(1)) * ((j & 1) ? T(0.5) : T(1)) * ((k & 1) ? T(0.5) : T(1));
+                    const long long cn = ic + (long long)(cx + 1) * (jc + (long long)(cy + 1) * kc);
+                    const uint8_t mcn = mc[cn];
+                    for (int c = 0; c < 3; ++c)
+                        if (!((mcn >> c) & 1)) acc[c] += w * xc[3 * cn + c];
+                }
+        for (int c = 0; c < 3; ++c)
+            if (!((m >> c) & 1)) xf[3 * n + c] += acc[c];
+    }
+}
+
+// x = omega D^-1 b  (first Jacobi sweep from x = 0)
+template <typename T>
+__global__ void k_jacobi_first(long long n, const T* __restrict__ b, const T* __restrict__ d, T* __restrict__ x, T omega) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        x[i] = omega * b[i] / d[i];
+}
+
+// dense coarsest operator (fixed rows / columns = identity)
+template <typename T>
+__global__ void k_dense_assemble(int nx, int ny, int nz, const T* __restrict__ E, const uint8_t* __restrict__ mask,
+                                 const double* __restrict__ ke, double hscale, T* __restrict__ A, int n) {
+    const int nxn = nx + 1, nyn = ny + 1;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < (long long)n * n;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int a = (int)(idx / n), b = (int)(idx % n);
+        const int na = a / 3, ca = a % 3, nb = b / 3, cb = b % 3;
+        const int ia = na % nxn, ja = (na / nxn) % nyn, kka = na / (nxn * nyn);
+        const int ib = nb % nxn, jb = (nb / nxn) % nyn, kkb = nb / (nxn * nyn);
+        const bool fa = (mask[na] >> ca) & 1, fbb = (mask[nb] >> cb) & 1;
+        double v = 0.0;
+        if (fa || fbb) {
+            v = (a == b) ? 1.0 : 0.0;
+        } else if (abs(ia - ib) <= 1 && abs(ja - jb) <= 1 && abs(kka - kkb) <= 1) {
+            for (int dk = -1; dk <= 0; ++dk)
+                for (int dj = -1; dj <= 0; ++dj)
+                    for (int di = -1; di <= 0; ++di) {
+                        const int ei = ia + di, ej = ja + dj, ek = kka + dk;
+                        if (ei < 0 || ei >= nx || ej < 0 || ej >= ny || ek < 0 || ek >= nz) continue;
+                        const int ob_i = ib - ei, ob_j = jb - ej, ob_k = kkb - ek;
+                        if (ob_i < 0 || ob_i > 1 || ob_j < 0 || ob_j > 1 || ob_k < 0 || ob_k > 1) continue;
+                        // local node numbering (0,0,0),(1,0,0),(1,1,0),(0,1,0),(0,0,1),(1,0,1),(1,1,1),(0,1,1)
+                        const int oa_i = -di, oa_j = -dj, oa_k = -dk;
+                        const int la = 4 * oa_k + (oa_j ? (oa_i ? 2 : 3) : oa_i);
+                        const int lb = 4 * ob_k + (ob_j ? (ob_i ? 2 : 3) : ob_i);
+                        v += (double)E[ei + nx * (ej + ny * ek)] * hscale * ke[(3 * la + ca) * 24 + 3 * lb + cb];
+                    }
+        }
+        A[idx] = (T)v;
+    }
+}
+
+// In-place inverse of the unit-diagonal-scaled SPD matrix by Gauss-Jordan
+// elimination (no pivoting needed for SPD) in shared memory; writes
+// Ainv_scaled and the scaling s = diag(A)^-1/2.
+template <typename T>
+__global__ void __launch_bounds__(1024) k_dense_invert(const T* __restrict__ A, T* __restrict__ Ainv, T* __restrict__ sc,
+                                                       int n, int* err) {
+    extern __shared__ unsigned char smem_raw[];
+    T* M = reinterpret_cast<T*>(smem_raw);
+    T* s = M + n * n;
+    __shared__ T row[kMaxCoarseDof];
+    __shared__ T col[kMaxCoarseDof];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int i = tid; i < n; i += nt) {
+        const T d = A[(long long)i * n + i];
+        s[i] = d > T(0) ? T(1) / sqrt(d) : T(0);
+        if (!(d > T(0))) set_err(err, TO_ERR_SINGULAR);
+    }
+    __syncthreads();
+    for (int idx = tid; idx < n * n; idx += nt) {
+        const int i = idx / n, j = idx % n;
+        M[idx] = s[i] * A[idx] * s[j];
+    }
+    __syncthreads();
+    for (int k = 0; k < n; ++k) {
+        const T piv = M[k * n + k];
+        if (!(piv > T(0))) {
+            if (tid == 0) set_err(err, TO_ERR_SINGULAR);
+            return;
+        }
+        const T ip = T(1) / piv;
+        for (int j = tid; j < n; j += nt) {
+            row[j] = (j == k ? T(1) : M[k * n + j]) * ip;
+            col[j] = M[j * n + k];
+        }
+        __syncthreads();
+        for (int idx = tid; idx < n * n; idx += nt) {
+            const int i = idx / n, j = idx % n;
+            if (i == k)
+                M[idx] = row[j];
+            else
+                M[idx] = (j == k ? T(0) : M[idx]) - col[i] * row[j];
+        }
+        __syncthreads();
+    }
+    for (int idx = tid; idx < n * n; idx += nt) Ainv[idx] = M[idx];
+    for (int i = tid; i < n; i += nt) sc[i] = s[i];
+}
+
+// x = S Ainv S b   (one CTA per row block)
+template <typename T>
+__global__ void k_dense_solve(const T* __restrict__ Ainv, const T* __restrict__ sc, const T* __restrict__ b,
+                              T* __restrict__ x, int n) {
+    const int i = blockIdx.x * blockDim.y + threadIdx.y;
+    if (i >= n) return;
+    T acc = T(0);
+    for (int j = threadIdx.x; j < n; j += 32) acc += Ainv[(long long)i * n + j] * sc[j] * b[j];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (threadIdx.x == 0) x[i] = sc[i] * acc;
+}
+
+// ----------------------------------------------------------------------------- host side
+
+static int auto_levels(int nx, int ny, int nz) {
+    int t = 0;
+    while (nx % (2 << t) == 0 && ny % (2 << t) == 0 && nz % (2 << t) == 0 && std::min(nx, std::min(ny, nz)) / (2 << t) >= 2)
+        ++t;
+    return t + 1;
+}
+
+int mg_build(to_problem* P) {
+    const int Lmax = auto_levels(P->g.nx, P->g.ny, P->g.nz);
+    int L = P->prm.mg_levels > 0 ? P->prm.mg_levels : Lmax;
+    if (L > Lmax) return fail(TO_ERR_ARG, "mg_levels exceeds the number of times the grid can be halved");
+    if (P->prm.mg_nu_pre < 1 || P->prm.mg_nu_post < 0 || !(P->prm.mg_omega > 0.0))
+        return fail(TO_ERR_ARG, "multigrid needs nu_pre >= 1, nu_post >= 0, omega > 0");
+    const size_t es = P->esz;
+    // coarse masks on the host (conservative rule, see the file comment)
+    std::vector<uint8_t> mf((size_t)P->n_node);
+    if (cudaMemcpy(mf.data(), P->lv[0].mask, mf.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail(TO_ERR_CUDA, "mask download");
+    for (int l = 1; l < L; ++l) {
+        const Level& F = P->lv[l - 1];
+        Level C{};
+        C.nx = F.nx / 2; C.ny = F.ny / 2; C.nz = F.nz / 2;
+        C.n_elem = (int64_t)C.nx * C.ny * C.nz;
+        C.n_node = (int64_t)(C.nx + 1) * (C.ny + 1) * (C.nz + 1);
+        C.n_dof = 3 * C.n_node;
+        C.h = F.h * 2.0;
+        C.kdiag = F.kdiag * 2.0;
+        std::vector<uint8_t> mc((size_t)C.n_node, 0);
+        for (int K = 0; K <= C.nz; ++K)
+            for (int J = 0; J <= C.ny; ++J)
+                for (int I = 0; I <= C.nx; ++I) {
+                    uint8_t m = 0;
+                    for (int k = std::max(2 * K - 1, 0); k <= std::min(2 * K + 1, F.nz); ++k)
+                        for (int j = std::max(2 * J - 1, 0); j <= std::min(2 * J + 1, F.ny); ++j)
+                            for (int i = std::max(2 * I - 1, 0); i <= std::min(2 * I + 1, F.nx); ++i)
+                                m |= mf[(size_t)i + (size_t)(F.nx + 1) * ((size_t)j + (size_t)(F.ny + 1) * k)];
+                    mc[(size_t)I + (size_t)(C.nx + 1) * ((size_t)J + (size_t)(C.ny + 1) * K)] = m;
+                }
+        void *E = nullptr, *d = nullptr, *mk = nullptr, *x = nullptr, *b = nullptr, *t = nullptr;
+        cudaError_t e = cudaMalloc(&E, C.n_elem * es);
+        if (e == cudaSuccess) e = cudaMalloc(&d, C.n_dof * es);
+        if (e == cudaSuccess) e = cudaMalloc(&mk, C.n_node);
+        if (e == cudaSuccess) e = cudaMalloc(&x, C.n_dof * es);
+        if (e == cudaSuccess) e = cudaMalloc(&b, C.n_dof * es);
+        if (e == cudaSuccess) e = cudaMalloc(&t, C.n_dof * es);
+        C.E = E; C.d = d; C.mask = (uint8_t*)mk; C.x = x; C.b = b; C.t = t;
+        P->lv.push_back(C);
+        if (e != cudaSuccess) return fail(TO_ERR_CUDA, std::string("multigrid allocation: ") + cudaGetErrorString(e));
+        if (cudaMemcpy(mk, mc.data(), mc.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+            return fail(TO_ERR_CUDA, "mask upload");
+        mf.swap(mc);
+    }
+    const Level& Cst = P->lv.back();
+    const int n = (int)Cst.n_dof;
+    if (n > kMaxCoarseDof)
+        return fail(TO_ERR_ARG, "coarsest multigrid grid too large for the dense solve (" + std::to_string(n) +
+                                    " DOFs > " + std::to_string(kMaxCoarseDof) + "): use a grid that halves more often");
+    P->n_coarse = n;
+    if (cudaMalloc(&P->coarse_A, (size_t)n * n * es) != cudaSuccess ||
+        cudaMalloc(&P->coarse_L, (size_t)n * n * es + (size_t)n * es) != cudaSuccess)
+        return fail(TO_ERR_CUDA, "coarse allocation");
+    void* ked = nullptr;
+    if (cudaMalloc(&ked, 576 * sizeof(double)) != cudaSuccess ||
+        cudaMemcpy(ked, P->ke, 576 * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(TO_ERR_CUDA, "element matrix upload");
+    P->ke_dev = (double*)ked;
+    // level-0 V-cycle scratch
+    if (cudaMalloc(&P->lv[0].t, P->n_dof * es) != cudaSuccess) return fail(TO_ERR_CUDA, "scratch allocation");
+    const size_t smem = (size_t)n * n * es + (size_t)n * es;
+    cudaError_t e = P->prec == TO_FP64
+                        ? cudaFuncSetAttribute(k_dense_invert<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                        : cudaFuncSetAttribute(k_dense_invert<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return fail(TO_ERR_CUDA, std::string("shared memory opt-in: ") + cudaGetErrorString(e));
+    return TO_OK;
+}
+
+template <typename T>
+static int refresh_t(to_problem* P, cudaStream_t s) {
+    const int L = (int)P->lv.size();
+    for (int l = 1; l < L; ++l) {
+        const Level& C = P->lv[l];
+        k_coarsen_E<T><<<grid1(C.n_elem, P->num_sms), 256, 0, s>>>(C.nx, C.ny, C.nz, (const T*)P->lv[l - 1].E, (T*)C.E);
+        TO_CUDA(cudaGetLastError());
+        int rc = launch_diag(P, l, s);
+        if (rc) return rc;
+    }
+    const Level& Cst = P->lv.back();
+    const int n = P->n_coarse;
+    k_dense_assemble<T><<<grid1((long long)n * n, P->num_sms), 256, 0, s>>>(
+        Cst.nx, Cst.ny, Cst.nz, (const T*)Cst.E, Cst.mask, P->ke_dev, Cst.h, (T*)P->coarse_A, n);
+    TO_CUDA(cudaGetLastError());
+    const size_t smem = (size_t)n * n * sizeof(T) + (size_t)n * sizeof(T);
+    T* inv = (T*)P->coarse_L;
+    k_dense_invert<T><<<1, 1024, smem, s>>>((const T*)P->coarse_A, inv, inv + (size_t)n * n, n, &P->sc->err);
+    TO_CUDA(cudaGetLastError());
+    return TO_OK;
+}
+
+int mg_refresh(to_problem* P, cudaStream_t s) {
+    return P->prec == TO_FP64 ? refresh_t<double>(P, s) : refresh_t<float>(P, s);
+}
+
+template <typename T>
+static int coarse_solve_t(to_problem* P, const void* b, void* x, cudaStream_t s) {
+    const int n = P->n_coarse;
+    const T* inv = (const T*)P->coarse_L;
+    k_dense_solve<T><<<(n + 7) / 8, dim3(32, 8), 0, s>>>(inv, inv + (size_t)n * n, (const T*)b, (T*)x, n);
+    TO_CUDA(cudaGetLastError());
+    return TO_OK;
+}
+
+// x_l = V(l, b_l); the result lands in `x`, `t` is scratch of the same size
+template <typename T>
+static int vcycle_t(to_problem* P, int l, const void* b, void* x, void* t, cudaStream_t s) {
+    const int L = (int)P->lv.size();
+    const Level& F = P->lv[l];
+    if (l == L - 1) return coarse_solve_t<T>(P, b, x, s);
+    const int nu1 = P->prm.mg_nu_pre, nu2 = P->prm.mg_nu_post;
+    const double om = P->prm.mg_omega;
+    int rc;
+    // choose the first target so that the last sweep writes into x
+    void* cur = ((nu1 - 1 + nu2) % 2 == 0) ? x : t;
+    void* oth = cur == x ? t : x;
+    k_jacobi_first<T><<<grid1(F.n_dof, P->num_sms), 256, 0, s>>>(F.n_dof, (const T*)b, (const T*)F.d, (T*)cur, (T)om);
+    TO_CUDA(cudaGetLastError());
+    for (int it = 1; it < nu1; ++it) {
+        if ((rc = launch_operator(P, l, OP_SMOOTH, cur, oth, b, s, om))) return rc;
+        std::swap(cur, oth);
+    }
+    // residual into oth, restrict to the coarse right-hand side
+    if ((rc = launch_operator(P, l, OP_BMINUS, cur, oth, b, s))) return rc;
+    const Level& C = P->lv[l + 1];
+    k_restrict<T><<<grid1(C.n_node, P->num_sms), 256, 0, s>>>(C.nx, C.ny, C.nz, (const T*)oth, F.mask, C.mask, (T*)C.b);
+    TO_CUDA(cudaGetLastError());
+    if ((rc = vcycle_t<T>(P, l + 1, C.b, C.x, C.t, s))) return rc;
+    k_prolong_add<T><<<grid1(F.n_node, P->num_sms), 256, 0, s>>>(C.nx, C.ny, C.nz, (const T*)C.x, C.mask, F.mask, (T*)cur);
+    TO_CUDA(cudaGetLastError());
+    for (int it = 0; it < nu2; ++it) {
+        if ((rc = launch_operator(P, l, OP_SMOOTH, cur, oth, b, s, om))) return rc;
+        std::swap(cur, oth);
+    }
+    if (cur != x) return fail(TO_ERR_STATE, "V-cycle buffer parity");
+    return TO_OK;
+}
+
 int mg_vcycle(to_problem* P, const void* r, void* z, cudaStream_t s) {
-    return fail(TO_ERR_ARG, "multigrid preconditioner not available");
+    return P->prec == TO_FP64 ? vcycle_t<double>(P, 0, r, z, P->lv[0].t, s)
+                              : vcycle_t<float>(P, 0, r, z, P->lv[0].t, s);
+}
+
+// kernel launches of one V-cycle (for launch accounting)
+int mg_launches(const to_problem* P) {
+    const int L = (int)P->lv.size();
+    const int nu1 = P->prm.mg_nu_pre, nu2 = P->prm.mg_nu_post;
+    return (L - 1) * (1 + (nu1 - 1) + 1 + 1 + 1 + nu2) + 1;
 }
 
 }  // namespace to

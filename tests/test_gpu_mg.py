@@ -1,0 +1,91 @@
+"""GPU parity of the multigrid-preconditioned path against the oracle's V-cycle
+(same definition, independent code): lower-level steps, and the outer loop on the
+cantilever and on the MBB half model (different fixtures reach the coarse masks)."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import fem, outer, solve
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _fb():
+    import __graft_entry__ as g
+    g.build()
+    import paper_2204_06204_gb300 as fb
+    return fb
+
+
+def _t(x, P):
+    return torch.tensor(np.asarray(x), dtype=P.dtype, device=P.device)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("dims", [(16, 8, 8), (24, 8, 16)])
+def test_mg_inner_steps(precision, dims):
+    fb = _fb()
+    pb = W.cantilever(*dims)
+    pb.rho0 = W.random_rho(pb.n_elem, 0.01, 1.0)
+    prec = fb.TO_FP64 if precision == "fp64" else fb.TO_FP32_MIXED
+    prm = fb.to_default_params(precision=prec, precond=fb.TO_PRECOND_MG, n_inner=2)
+    with fb.Problem.from_workload(pb, prm) as P:
+        P.set_design(_t(pb.rho0, P))
+        S = outer.Setup(pb)
+        _, Ee, _ = S.moduli(pb.rho0)
+        K = S.K(Ee)
+        mg = solve.Multigrid(pb.nx, pb.ny, pb.nz, pb.h, Ee, pb.nu, pb.fixed_dof)
+        u0 = np.zeros(pb.n_dof)
+        ut = _t(u0, P)
+        res = P.inner_solve(ut, 4, want_res=True)
+        uref, _, _, _ = solve.inner_sd(lambda x: K @ x, S.f, u0, mg, 4)
+        u = ut.cpu().numpy()
+        tol = 1e-10 if prec == fb.TO_FP64 else 2e-4
+        assert np.abs(u - uref).max() <= tol * np.abs(uref).max()
+        # the V-cycle contracts: four preconditioned steps reduce the residual
+        assert res < 0.5 * np.linalg.norm(S.f)
+
+
+@pytest.mark.parametrize("which", ["cantilever", "mbb"])
+def test_mg_outer_loop_fp64_matches_oracle(which):
+    fb = _fb()
+    pb = W.cantilever(16, 8, 8) if which == "cantilever" else W.mbb_half(16, 8, 8)
+    n = 15
+    prm = fb.to_default_params(precision=fb.TO_FP64, precond=fb.TO_PRECOND_MG, n_inner=2)
+    with fb.Problem.from_workload(pb, prm) as P:
+        st = P.step(n)
+        rho, u, k, a0 = P.get_state()
+    rho_o, u_o, hist, a0_o = outer.run(pb, n, precond="mg", n_inner=2)
+    assert np.abs(rho.cpu().numpy() - rho_o).max() <= 1e-8
+    J = np.array([s["J"] for s in st])
+    Jo = np.array([h["J"] for h in hist])
+    assert np.abs(J - Jo).max() <= 1e-8 * np.abs(Jo).max()
+    b = np.array([s["beta_first"] for s in st[1:]])
+    bo = np.array([h["betas"][0] for h in hist[1:]])
+    assert np.abs(b - bo).max() <= 1e-8 * np.abs(bo).max()
+
+
+def test_mg_outer_loop_fp32_compliance():
+    fb = _fb()
+    pb = W.cantilever(32, 16, 16)
+    n = 30
+    prm = fb.to_default_params(precision=fb.TO_FP32_MIXED, precond=fb.TO_PRECOND_MG, n_inner=2)
+    with fb.Problem.from_workload(pb, prm) as P:
+        P.step(n)
+        rho, u, k, a0 = P.get_state()
+    rho_o, u_o, hist, a0_o = outer.run(pb, n, precond="mg", n_inner=2)
+    S = outer.Setup(pb)
+    Jg = S.exact_compliance(rho.cpu().numpy().astype(np.float64))[0]
+    Jo = S.exact_compliance(rho_o)[0]
+    assert abs(Jg - Jo) <= 1e-3 * Jo
+    assert np.abs(rho.cpu().numpy() - rho_o).mean() <= 1e-2
+
+
+def test_mg_rejects_grid_without_coarse_levels():
+    fb = _fb()
+    pb = W.cantilever(17, 9, 5)
+    prm = fb.to_default_params(precond=fb.TO_PRECOND_MG)
+    with pytest.raises(fb.ToError) as e:
+        fb.Problem.from_workload(pb, prm)
+    assert e.value.code == 1

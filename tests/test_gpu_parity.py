@@ -109,7 +109,7 @@ def test_projection(precision, case):
         w = np.round(r.normal(0.4, 0.5, pb.n_elem), 1)
     else:
         pb.rho_min = 0.1
-        w = r.normal(0.2, 0.3, pb.n_elem)
+        w = r.normal(0.35, 0.3, pb.n_elem)
     prec = fb.TO_FP64 if precision == "fp64" else fb.TO_FP32_MIXED
     with _problem(pb, prec) as P:
         wt = _t(w, P)
@@ -119,8 +119,12 @@ def test_projection(precision, case):
         rho = rho.cpu().numpy()
         tol = 1e-12 if prec == fb.TO_FP64 else 1e-6
         assert np.abs(rho - vref).max() <= tol
-        if case != "inactive":
-            assert abs(rho.astype(np.float64).sum() - pb.volfrac * pb.n_elem) <= (1e-9 if prec == fb.TO_FP64 else 2e-3)
+        vol = rho.astype(np.float64).sum()
+        if lref > 0:       # active bound: the volume is met with equality
+            assert abs(vol - pb.volfrac * pb.n_elem) <= (1e-9 if prec == fb.TO_FP64 else 2e-3)
+        else:
+            assert vol <= pb.volfrac * pb.n_elem * (1 + 1e-12) and lam == 0.0
+        assert (case == "inactive") == (lref == 0.0)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
