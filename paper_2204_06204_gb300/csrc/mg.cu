@@ -12,7 +12,8 @@
 // Coarsest solve: the dense operator is assembled on the device, scaled to a
 // unit diagonal (S A S, S = diag(A)^-1/2, so that the 1e9 stiffness contrast of
 // void regions does not reach the factorisation) and inverted by Gauss-Jordan
-// elimination in one CTA's shared memory; each V-cycle then applies S A^-1 S.
+// elimination by one CTA (in shared memory while the matrix fits); each V-cycle
+// then applies S A^-1 S.
 #include <algorithm>
 #include <cmath>
 
@@ -20,7 +21,10 @@
 
 namespace to {
 
-constexpr int kMaxCoarseDof = 160;   // n^2 doubles fit in one CTA's shared memory
+constexpr int kMaxCoarseDof = 1024;  // dense coarsest solve; in shared memory while n^2 entries fit
+// dynamic shared memory left for the matrix next to the static row / column / scale arrays
+template <typename T>
+constexpr size_t smem_cap() { return 232448 - 3 * kMaxCoarseDof * sizeof(T) - 1024; }
 
 static int grid1(long long n, int num_sms) {
     long long b = (n + 255) / 256;
@@ -144,23 +148,31 @@ __global__ void k_dense_assemble(int nx, int ny, int nz, const T* __restrict__ E
 }
 
 // In-place inverse of the unit-diagonal-scaled SPD matrix by Gauss-Jordan
-// elimination (no pivoting needed for SPD) in shared memory; writes
-// Ainv_scaled and the scaling s = diag(A)^-1/2.
-template <typename T>
+// elimination (no pivoting needed for SPD), in shared memory when it fits
+// (SMEM) or in the output buffer otherwise; writes S A S inverted and the
+// scaling s = diag(A)^-1/2.
+template <typename T, bool SMEM>
 __global__ void __launch_bounds__(1024) k_dense_invert(const T* __restrict__ A, T* __restrict__ Ainv, T* __restrict__ sc,
                                                        int n, int* err) {
     extern __shared__ unsigned char smem_raw[];
-    T* M = reinterpret_cast<T*>(smem_raw);
-    T* s = M + n * n;
     __shared__ T row[kMaxCoarseDof];
     __shared__ T col[kMaxCoarseDof];
+    __shared__ T s[kMaxCoarseDof];
+    __shared__ int bad;
+    T* M = SMEM ? reinterpret_cast<T*>(smem_raw) : Ainv;
     const int tid = threadIdx.x, nt = blockDim.x;
+    if (tid == 0) bad = 0;
+    __syncthreads();
     for (int i = tid; i < n; i += nt) {
         const T d = A[(long long)i * n + i];
         s[i] = d > T(0) ? T(1) / sqrt(d) : T(0);
-        if (!(d > T(0))) set_err(err, TO_ERR_SINGULAR);
+        if (!(d > T(0))) bad = 1;
     }
     __syncthreads();
+    if (bad) {
+        if (tid == 0) set_err(err, TO_ERR_SINGULAR);
+        return;
+    }
     for (int idx = tid; idx < n * n; idx += nt) {
         const int i = idx / n, j = idx % n;
         M[idx] = s[i] * A[idx] * s[j];
@@ -187,7 +199,8 @@ __global__ void __launch_bounds__(1024) k_dense_invert(const T* __restrict__ A, 
         }
         __syncthreads();
     }
-    for (int idx = tid; idx < n * n; idx += nt) Ainv[idx] = M[idx];
+    if (SMEM)
+        for (int idx = tid; idx < n * n; idx += nt) Ainv[idx] = M[idx];
     for (int i = tid; i < n; i += nt) sc[i] = s[i];
 }
 
@@ -273,11 +286,13 @@ int mg_build(to_problem* P) {
     P->ke_dev = (double*)ked;
     // level-0 V-cycle scratch
     if (cudaMalloc(&P->lv[0].t, P->n_dof * es) != cudaSuccess) return fail(TO_ERR_CUDA, "scratch allocation");
-    const size_t smem = (size_t)n * n * es + (size_t)n * es;
-    cudaError_t e = P->prec == TO_FP64
-                        ? cudaFuncSetAttribute(k_dense_invert<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-                        : cudaFuncSetAttribute(k_dense_invert<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return fail(TO_ERR_CUDA, std::string("shared memory opt-in: ") + cudaGetErrorString(e));
+    const size_t smem = (size_t)n * n * es;
+    if (smem <= (P->prec == TO_FP64 ? smem_cap<double>() : smem_cap<float>())) {
+        cudaError_t e = P->prec == TO_FP64
+                            ? cudaFuncSetAttribute(k_dense_invert<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                            : cudaFuncSetAttribute(k_dense_invert<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return fail(TO_ERR_CUDA, std::string("shared memory opt-in: ") + cudaGetErrorString(e));
+    }
     return TO_OK;
 }
 
@@ -296,9 +311,12 @@ static int refresh_t(to_problem* P, cudaStream_t s) {
     k_dense_assemble<T><<<grid1((long long)n * n, P->num_sms), 256, 0, s>>>(
         Cst.nx, Cst.ny, Cst.nz, (const T*)Cst.E, Cst.mask, P->ke_dev, Cst.h, (T*)P->coarse_A, n);
     TO_CUDA(cudaGetLastError());
-    const size_t smem = (size_t)n * n * sizeof(T) + (size_t)n * sizeof(T);
+    const size_t smem = (size_t)n * n * sizeof(T);
     T* inv = (T*)P->coarse_L;
-    k_dense_invert<T><<<1, 1024, smem, s>>>((const T*)P->coarse_A, inv, inv + (size_t)n * n, n, &P->sc->err);
+    if (smem <= smem_cap<T>())
+        k_dense_invert<T, true><<<1, 1024, smem, s>>>((const T*)P->coarse_A, inv, inv + (size_t)n * n, n, &P->sc->err);
+    else
+        k_dense_invert<T, false><<<1, 1024, 0, s>>>((const T*)P->coarse_A, inv, inv + (size_t)n * n, n, &P->sc->err);
     TO_CUDA(cudaGetLastError());
     return TO_OK;
 }
