@@ -39,7 +39,40 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--precond", default="auto", choices=["auto", "mg", "jacobi"])
+    ap.add_argument("--apply-only", nargs=3, type=int, metavar=("NX", "NY", "NZ"),
+                    help="time only K(rho)u on a cantilever of this size (random design), FP32-mixed")
+    ap.add_argument("--fp64", action="store_true", help="with --apply-only: the plain FP64 operator")
     return ap.parse_args()
+
+
+def apply_only(args):
+    """K(rho)u alone on an nx x ny x nz cantilever with rho ~ U[0, 1]: GDOF/s and GB/s."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2204_06204_gb300 as fb
+    import workloads as W
+    pb = W.cantilever(*args.apply_only)
+    prec = fb.TO_FP64 if args.fp64 else fb.TO_FP32_MIXED
+    P = fb.Problem.from_workload(pb, fb.to_default_params(precision=prec))
+    P.set_design(torch.tensor(W.random_rho(pb.n_elem, 0.0, 1.0), dtype=P.dtype, device=P.device))
+    u = torch.tensor(W.random_u(pb.n_dof), dtype=P.dtype, device=P.device)
+    y = P.dof()
+    for _ in range(max(args.warmup, 3)):
+        P.apply_K(u, y)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.steps):
+        P.apply_K(u, y)
+    b.record()
+    torch.cuda.synchronize()
+    t = a.elapsed_time(b) / 1000.0 / args.steps
+    s = 8 if args.fp64 else 4
+    byts = 2 * 3 * pb.n_node * s + pb.n_elem * s + pb.n_node
+    print(json.dumps({"apply_only": list(args.apply_only), "precision": "fp64" if args.fp64 else "fp32",
+                      "us": t * 1e6, "gdofs": pb.n_dof / t / 1e9, "gbs": byts / t / 1e9, "bytes": byts}))
+    return 0
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -155,6 +188,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.apply_only:
+        return apply_only(args)
 
     import numpy as np
     import torch
