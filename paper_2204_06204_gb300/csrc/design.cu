@@ -13,7 +13,7 @@ template <typename T, bool TRANSPOSE, bool STATS>
 __global__ void __launch_bounds__(256) k_filter(int nx, int ny, int nz, const T* __restrict__ x, T* __restrict__ y,
                                                 const T* __restrict__ Hs, const int4* __restrict__ st,
                                                 const T* __restrict__ w, int ns, double* red, unsigned* counter,
-                                                DevScalars* sc) {
+                                                DevScalars* sc, double alpha0_param, double alpha_scale, double m_exp) {
     __shared__ double sh[32 * kRedQ];
     const long long n = (long long)nx * ny * nz;
     double amax = 0.0, sum = 0.0;
@@ -48,6 +48,11 @@ __global__ void __launch_bounds__(256) k_filter(int nx, int ny, int nz, const T*
             sc->gmax = tot[0];
             sc->gsum = tot[1];
             if (!isfinite(tot[0]) || !isfinite(tot[1])) set_err(&sc->err, TO_ERR_NONFINITE);
+            // high-level step alpha_k = alpha0 k^-m; alpha0 fixed at the first k with g != 0
+            double a0 = alpha0_param > 0.0 ? alpha0_param : sc->alpha0;
+            if (!(a0 > 0.0) && tot[0] > 0.0) a0 = alpha_scale / tot[0];
+            sc->alpha0 = a0 > 0.0 ? a0 : 0.0;
+            sc->alpha = a0 > 0.0 ? a0 * pow((double)sc->k, -m_exp) : 0.0;
         }
     }
 }
@@ -138,13 +143,14 @@ static int filter_t(to_problem* P, const void* x, void* y, int transpose, int st
     if (transpose) {
         if (stats)
             k_filter<T, true, true><<<nb, 256, 0, s>>>(P->g.nx, P->g.ny, P->g.nz, (const T*)x, (T*)y, Hs, P->stencil, w,
-                                                       P->n_stencil, P->red, P->counters + 2, P->sc);
+                                                       P->n_stencil, P->red, P->counters + 2, P->sc, P->prm.alpha0,
+                                                       P->prm.alpha_scale, P->prm.m);
         else
             k_filter<T, true, false><<<nb, 256, 0, s>>>(P->g.nx, P->g.ny, P->g.nz, (const T*)x, (T*)y, Hs, P->stencil, w,
-                                                        P->n_stencil, nullptr, nullptr, nullptr);
+                                                        P->n_stencil, nullptr, nullptr, nullptr, 0.0, 0.0, 0.0);
     } else {
         k_filter<T, false, false><<<nb, 256, 0, s>>>(P->g.nx, P->g.ny, P->g.nz, (const T*)x, (T*)y, Hs, P->stencil, w,
-                                                     P->n_stencil, nullptr, nullptr, nullptr);
+                                                     P->n_stencil, nullptr, nullptr, nullptr, 0.0, 0.0, 0.0);
     }
     TO_CUDA(cudaGetLastError());
     return TO_OK;

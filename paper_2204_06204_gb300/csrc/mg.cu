@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(1024) k_dense_invert(const T* __restrict__ A, 
     __shared__ T s[kMaxCoarseDof];
     __shared__ int bad;
     T* M = SMEM ? reinterpret_cast<T*>(smem_raw) : Ainv;
-    const int tid = threadIdx.x, nt = blockDim.x;
+    const int tid = threadIdx.x + 32 * threadIdx.y, nt = blockDim.x * blockDim.y;
     if (tid == 0) bad = 0;
     __syncthreads();
     for (int i = tid; i < n; i += nt) {
@@ -173,10 +173,9 @@ __global__ void __launch_bounds__(1024) k_dense_invert(const T* __restrict__ A, 
         if (tid == 0) set_err(err, TO_ERR_SINGULAR);
         return;
     }
-    for (int idx = tid; idx < n * n; idx += nt) {
-        const int i = idx / n, j = idx % n;
-        M[idx] = s[i] * A[idx] * s[j];
-    }
+    const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 32 threads: column / row strides
+    for (int i = ty; i < n; i += 32)
+        for (int j = tx; j < n; j += 32) M[i * n + j] = s[i] * A[(long long)i * n + j] * s[j];
     __syncthreads();
     for (int k = 0; k < n; ++k) {
         const T piv = M[k * n + k];
@@ -190,17 +189,20 @@ __global__ void __launch_bounds__(1024) k_dense_invert(const T* __restrict__ A, 
             col[j] = M[j * n + k];
         }
         __syncthreads();
-        for (int idx = tid; idx < n * n; idx += nt) {
-            const int i = idx / n, j = idx % n;
-            if (i == k)
-                M[idx] = row[j];
-            else
-                M[idx] = (j == k ? T(0) : M[idx]) - col[i] * row[j];
+        for (int i = ty; i < n; i += 32) {
+            const T ci = col[i];
+            for (int j = tx; j < n; j += 32) {
+                if (i == k)
+                    M[i * n + j] = row[j];
+                else
+                    M[i * n + j] = (j == k ? T(0) : M[i * n + j]) - ci * row[j];
+            }
         }
         __syncthreads();
     }
     if (SMEM)
-        for (int idx = tid; idx < n * n; idx += nt) Ainv[idx] = M[idx];
+        for (int i = ty; i < n; i += 32)
+            for (int j = tx; j < n; j += 32) Ainv[i * n + j] = M[i * n + j];
     for (int i = tid; i < n; i += nt) sc[i] = s[i];
 }
 
@@ -314,9 +316,9 @@ static int refresh_t(to_problem* P, cudaStream_t s) {
     const size_t smem = (size_t)n * n * sizeof(T);
     T* inv = (T*)P->coarse_L;
     if (smem <= smem_cap<T>())
-        k_dense_invert<T, true><<<1, 1024, smem, s>>>((const T*)P->coarse_A, inv, inv + (size_t)n * n, n, &P->sc->err);
+        k_dense_invert<T, true><<<1, dim3(32, 32), smem, s>>>((const T*)P->coarse_A, inv, inv + (size_t)n * n, n, &P->sc->err);
     else
-        k_dense_invert<T, false><<<1, 1024, 0, s>>>((const T*)P->coarse_A, inv, inv + (size_t)n * n, n, &P->sc->err);
+        k_dense_invert<T, false><<<1, dim3(32, 32), 0, s>>>((const T*)P->coarse_A, inv, inv + (size_t)n * n, n, &P->sc->err);
     TO_CUDA(cudaGetLastError());
     return TO_OK;
 }

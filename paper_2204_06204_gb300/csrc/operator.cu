@@ -85,10 +85,62 @@ __device__ __forceinline__ void haar_apply(const T* __restrict__ k, const T u[24
     v[23] = k[44] * u[23];
 }
 
+// ----------------------------------------------------------------------------- pairs
+// (x, y) components travel as a pair: packed FP32x2 arithmetic for float,
+// two scalar operations for double.
+template <typename T> struct PairT;
+template <> struct PairT<float> { using t = float2; };
+template <> struct PairT<double> { using t = double2; };
+
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 psub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ double2 padd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 psub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 pmul(double2 a, double2 b) { return make_double2(a.x * b.x, a.y * b.y); }
+__device__ __forceinline__ double2 pfma(double2 a, double2 b, double2 c) { return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y)); }
+
+template <typename T> struct Node4;
+template <> struct Node4<float> { using t = float4; };
+struct alignas(16) Dbl4 {
+    double x, y, z, w;
+};
+template <> struct Node4<double> { using t = Dbl4; };
+
+// 12 face coefficients (ss, sd, ds, dd) x (x, y, z): xy pairs and z scalars
+template <typename T>
+struct Face {
+    typename PairT<T>::t p[4];
+    T z[4];
+};
+
+template <typename T, typename N4>
+__device__ __forceinline__ void face_forward4(const N4& a00, const N4& a10, const N4& a01, const N4& a11, Face<T>& F) {
+    using P = typename PairT<T>::t;
+    const P p00{a00.x, a00.y}, p10{a10.x, a10.y}, p01{a01.x, a01.y}, p11{a11.x, a11.y};
+    const P sx0 = padd(p10, p00), dx0 = psub(p10, p00), sx1 = padd(p11, p01), dx1 = psub(p11, p01);
+    F.p[0] = padd(sx1, sx0);
+    F.p[1] = padd(dx1, dx0);
+    F.p[2] = psub(sx1, sx0);
+    F.p[3] = psub(dx1, dx0);
+    const T zs0 = a10.z + a00.z, zd0 = a10.z - a00.z, zs1 = a11.z + a01.z, zd1 = a11.z - a01.z;
+    F.z[0] = zs1 + zs0;
+    F.z[1] = zd1 + zd0;
+    F.z[2] = zs1 - zs0;
+    F.z[3] = zd1 - zd0;
+}
+
 template <typename T, int TX, int TY, int MODE>
 __global__ void __launch_bounds__(TX * TY) k_operator(const OpArgs<T> a) {
-    __shared__ T plane[TY + 1][TX + 1][3];
-    __shared__ T corner[4][TY][TX][3];
+    static_assert(TX == 32, "one warp per row of element columns");
+    using P = typename PairT<T>::t;
+    using N4 = typename Node4<T>::t;
+    constexpr int NT = TX * TY;
+    constexpr int PN = (TX + 1) * (TY + 1);          // nodes per staged plane
+    constexpr int SR = (PN + NT - 1) / NT;           // staging rounds per thread
+    __shared__ N4 plane[3][PN];
+    __shared__ N4 ybuf[TY][TX];
     __shared__ double sh_red[32 * kRedQ];
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = tx + TX * ty;
@@ -96,127 +148,227 @@ __global__ void __launch_bounds__(TX * TY) k_operator(const OpArgs<T> a) {
     const int kb = blockIdx.z * a.kchunk;
     const int ke = min(kb + a.kchunk, a.nz + 1);
     const int nxn = a.nx + 1, nyn = a.ny + 1;
+    const long long nplane = (long long)nxn * nyn;
+    const long long eplane = (long long)a.nx * a.ny;
     const int ie = X0 - 1 + tx, je = Y0 - 1 + ty;
     const bool col_in = ie >= 0 && ie < a.nx && je >= 0 && je < a.ny;
     const int ni = X0 + tx, nj = Y0 + ty;
     const bool owner = tx < TX - 1 && ty < TY - 1 && ni < nxn && nj < nyn;
+    const long long own_base = (long long)ni + (long long)nxn * nj;          // + k * nplane
+    const long long elem_base = col_in ? (long long)ie + (long long)a.nx * je : 0;
 
-    // per-thread partial reductions (accumulated in T across the walk)
-    T acc0 = T(0), acc1 = T(0), acc3 = T(0);
-    T accmax = T(0);
-
-    auto load_plane = [&](int kp) {
-        const int row = 3 * (TX + 1);
-        for (int e = tid; e < row * (TY + 1); e += TX * TY) {
-            const int py = e / row, off = e - py * row, px = off / 3, c = off - 3 * px;
-            const int gi = X0 - 1 + px, gj = Y0 - 1 + py;
-            T v = T(0);
-            if (kp >= 0 && kp <= a.nz && gi >= 0 && gi < nxn && gj >= 0 && gj < nyn) {
-                const long long node = gi + (long long)nxn * (gj + (long long)nyn * kp);
-                if (!((a.mask[node] >> c) & 1)) v = a.x[3 * node + c];
+    // staging assignment: node s = tid + r * NT of the (TX+1) x (TY+1) plane tile
+    long long st_base[SR];
+    bool st_ok[SR];
+#pragma unroll
+    for (int r = 0; r < SR; ++r) {
+        const int sidx = tid + r * NT;
+        const int px = sidx % (TX + 1), py = sidx / (TX + 1);
+        const int gi = X0 - 1 + px, gj = Y0 - 1 + py;
+        st_ok[r] = sidx < PN && gi >= 0 && gi < nxn && gj >= 0 && gj < nyn;
+        st_base[r] = st_ok[r] ? (long long)gi + (long long)nxn * gj : 0;
+    }
+    T rv[SR][3];
+    uint8_t rm[SR];
+    auto stage_load = [&](int kp) {
+#pragma unroll
+        for (int r = 0; r < SR; ++r) {
+            rv[r][0] = rv[r][1] = rv[r][2] = T(0);
+            rm[r] = 7;
+            if (st_ok[r] && kp >= 0 && kp <= a.nz) {
+                const long long node = st_base[r] + kp * nplane;
+                rm[r] = a.mask[node];
+                rv[r][0] = a.x[3 * node + 0];
+                rv[r][1] = a.x[3 * node + 1];
+                rv[r][2] = a.x[3 * node + 2];
             }
-            plane[py][px][c] = v;
+        }
+    };
+    auto stage_store = [&](N4* buf) {
+#pragma unroll
+        for (int r = 0; r < SR; ++r) {
+            const int sidx = tid + r * NT;
+            if (sidx < PN) {
+                N4 v;
+                v.x = (rm[r] & 1) ? T(0) : rv[r][0];
+                v.y = (rm[r] & 2) ? T(0) : rv[r][1];
+                v.z = (rm[r] & 4) ? T(0) : rv[r][2];
+                v.w = T(0);
+                buf[sidx] = v;
+            }
+        }
+    };
+    // epilogue operands of the owned node at a plane, fetched one layer ahead
+    struct Epi {
+        uint8_t m;
+        T b[3], d[3];
+    };
+    auto epi_load = [&](int kp, Epi& e) {
+        e.m = 0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) e.b[c] = e.d[c] = T(0);
+        if (owner && kp >= kb && kp < ke) {
+            const long long node = own_base + kp * nplane;
+            e.m = a.mask[node];
+            if (MODE == OP_RESID || MODE == OP_SMOOTH || MODE == OP_BMINUS)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) e.b[c] = a.b[3 * node + c];
+            if (MODE == OP_SMOOTH || (MODE == OP_RESID && a.z != nullptr))
+#pragma unroll
+                for (int c = 0; c < 3; ++c) e.d[c] = a.d[3 * node + c];
         }
     };
 
-    T Fb[12], Gc[12];
-    load_plane(kb - 1);
+    T acc0 = T(0), acc1 = T(0), acc3 = T(0), accmax = T(0);
+
+    // prologue: planes kb-1 and kb staged, kb+1 in flight; bottom face of layer kb-1
+    int ib = 0, it = 1, in = 2;            // ring: bottom, top, next
+    stage_load(kb - 1);
+    stage_store(plane[ib]);
+    stage_load(kb);
+    stage_store(plane[it]);
     __syncthreads();
-    face_forward(plane[ty][tx], plane[ty][tx + 1], plane[ty + 1][tx], plane[ty + 1][tx + 1], Fb);
+    Face<T> Fb;
+    face_forward4<T>(plane[ib][ty * (TX + 1) + tx], plane[ib][ty * (TX + 1) + tx + 1],
+                     plane[ib][(ty + 1) * (TX + 1) + tx], plane[ib][(ty + 1) * (TX + 1) + tx + 1], Fb);
+    Face<T> Gc;
 #pragma unroll
-    for (int i = 0; i < 12; ++i) Gc[i] = T(0);
-    __syncthreads();
+    for (int f = 0; f < 4; ++f) {
+        Gc.p[f] = P{T(0), T(0)};
+        Gc.z[f] = T(0);
+    }
+    stage_load(kb + 1);
+    T Enext = (col_in && kb - 1 >= 0 && kb - 1 < a.nz) ? a.E[elem_base + (kb - 1) * eplane] : T(0);
+    Epi ep_next;
+    epi_load(kb - 1, ep_next);
 
     for (int k = kb - 1; k < ke; ++k) {
-        load_plane(k + 1);
-        __syncthreads();
-        T Ft[12];
-        face_forward(plane[ty][tx], plane[ty][tx + 1], plane[ty + 1][tx], plane[ty + 1][tx + 1], Ft);
-        T S[12];
+        const T Ee = Enext;
+        Enext = (col_in && k + 1 >= 0 && k + 1 < a.nz) ? a.E[elem_base + (k + 1) * eplane] : T(0);
+        const Epi ep = ep_next;
+        epi_load(k + 1, ep_next);
+
+        // top face of element layer k (node plane k+1)
+        const N4* tp = plane[it];
+        Face<T> Ft;
+        face_forward4<T>(tp[ty * (TX + 1) + tx], tp[ty * (TX + 1) + tx + 1], tp[(ty + 1) * (TX + 1) + tx],
+                         tp[(ty + 1) * (TX + 1) + tx + 1], Ft);
+        Face<T> S;
         const bool elem_in = col_in && k >= 0 && k < a.nz;
         if (elem_in) {
-            const long long e = ie + (long long)a.nx * (je + (long long)a.ny * k);
-            const T Ee = a.E[e];
-            T uh[24], v[24];
+            // 24 coefficients: z sums (ss*, first 12) and z differences (last 12)
+            T uh[24];
 #pragma unroll
-            for (int i = 0; i < 12; ++i) {
-                uh[i] = Ft[i] + Fb[i];
-                uh[12 + i] = Ft[i] - Fb[i];
+            for (int f = 0; f < 4; ++f) {
+                const P s = padd(Ft.p[f], Fb.p[f]), d = psub(Ft.p[f], Fb.p[f]);
+                uh[3 * f + 0] = s.x;
+                uh[3 * f + 1] = s.y;
+                uh[3 * f + 2] = Ft.z[f] + Fb.z[f];
+                uh[12 + 3 * f + 0] = d.x;
+                uh[12 + 3 * f + 1] = d.y;
+                uh[12 + 3 * f + 2] = Ft.z[f] - Fb.z[f];
             }
+            T v[24];
             haar_apply(a.kh.v, uh, v);
             if (MODE == OP_RESID) {
-                // fused sensitivity: element owned when its (1,1,1) corner node is owned
                 if (a.gt && owner && k + 1 >= kb && k + 1 < ke) {
                     T en = T(0);
 #pragma unroll
-                    for (int i = 3; i < 24; ++i) en += uh[i] * v[i];
+                    for (int i = 3; i < 24; ++i) en = fma(uh[i], v[i], en);
+                    const long long e = elem_base + k * eplane;
                     a.gt[e] = -a.Ed[e] * en;
                 }
             }
+            const P E2{Ee, Ee};
 #pragma unroll
-            for (int i = 0; i < 12; ++i) {
-                const T s = Ee * v[i], dd = Ee * v[12 + i];
-                S[i] = Gc[i] + (s - dd);
-                Gc[i] = s + dd;
+            for (int f = 0; f < 4; ++f) {
+                const P vs{v[3 * f], v[3 * f + 1]}, vd{v[12 + 3 * f], v[12 + 3 * f + 1]};
+                S.p[f] = pfma(E2, psub(vs, vd), Gc.p[f]);
+                Gc.p[f] = pmul(E2, padd(vs, vd));
+                const T zs = v[3 * f + 2], zd = v[12 + 3 * f + 2];
+                S.z[f] = fma(Ee, zs - zd, Gc.z[f]);
+                Gc.z[f] = Ee * (zs + zd);
             }
         } else {
 #pragma unroll
-            for (int i = 0; i < 12; ++i) {
-                S[i] = Gc[i];
-                Gc[i] = T(0);
+            for (int f = 0; f < 4; ++f) {
+                S.p[f] = Gc.p[f];
+                S.z[f] = Gc.z[f];
+                Gc.p[f] = P{T(0), T(0)};
+                Gc.z[f] = T(0);
             }
         }
-#pragma unroll
-        for (int i = 0; i < 12; ++i) Fb[i] = Ft[i];
+        Fb = Ft;
 
-        const bool out_plane = k >= kb;   // plane k complete and owned by this CTA
-        if (out_plane) {
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const T ss = S[0 + c], sd = S[3 + c], ds = S[6 + c], dd = S[9 + c];
-                const T sx0 = ss - ds, sx1 = ss + ds, dx0 = sd - dd, dx1 = sd + dd;
-                corner[0][ty][tx][c] = sx0 - dx0;   // node (0,0) of the column face
-                corner[1][ty][tx][c] = sx0 + dx0;   // (1,0)
-                corner[2][ty][tx][c] = sx1 - dx1;   // (0,1)
-                corner[3][ty][tx][c] = sx1 + dx1;   // (1,1)
-            }
+        // plane k: inverse face butterflies, x neighbours by shuffle, y neighbours via shared memory
+        const bool out_plane = k >= kb;
+        P Xp, Yp;
+        T Xz, Yz;
+        {
+            const P sx0 = psub(S.p[0], S.p[2]), sx1 = padd(S.p[0], S.p[2]);
+            const P dx0 = psub(S.p[1], S.p[3]), dx1 = padd(S.p[1], S.p[3]);
+            const P c00 = psub(sx0, dx0), c10 = padd(sx0, dx0), c01 = psub(sx1, dx1), c11 = padd(sx1, dx1);
+            const T zsx0 = S.z[0] - S.z[2], zsx1 = S.z[0] + S.z[2], zdx0 = S.z[1] - S.z[3], zdx1 = S.z[1] + S.z[3];
+            const T z00 = zsx0 - zdx0, z10 = zsx0 + zdx0, z01 = zsx1 - zdx1, z11 = zsx1 + zdx1;
+            P n01, n00;
+            n01.x = __shfl_down_sync(0xffffffffu, c01.x, 1);
+            n01.y = __shfl_down_sync(0xffffffffu, c01.y, 1);
+            n00.x = __shfl_down_sync(0xffffffffu, c00.x, 1);
+            n00.y = __shfl_down_sync(0xffffffffu, c00.y, 1);
+            const T m01 = __shfl_down_sync(0xffffffffu, z01, 1);
+            const T m00 = __shfl_down_sync(0xffffffffu, z00, 1);
+            Xp = padd(c11, n01);
+            Xz = z11 + m01;
+            Yp = padd(c10, n00);
+            Yz = z10 + m00;
         }
-        __syncthreads();
+        if (out_plane) ybuf[ty][tx] = N4{Yp.x, Yp.y, Yz, T(0)};
+        __syncthreads();   // (A) ybuf written; every read of plane[ib] done
         if (out_plane && owner) {
-            const long long node = ni + (long long)nxn * (nj + (long long)nyn * k);
-            const uint8_t mk = a.mask[node];
+            const N4 yb = ybuf[ty + 1][tx];
+            const T Kx3[3] = {Xp.x + yb.x, Xp.y + yb.y, Xz + yb.z};
+            const long long node = own_base + (long long)k * nplane;
+            const N4 xs = plane[ib][(ty + 1) * (TX + 1) + tx + 1];   // masked input at the owned node
+            const T xv3[3] = {xs.x, xs.y, xs.z};
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 const long long dof = 3 * node + c;
-                T Kx = corner[3][ty][tx][c] + corner[2][ty][tx + 1][c] + corner[1][ty + 1][tx][c] +
-                       corner[0][ty + 1][tx + 1][c];
-                const bool fixed = (mk >> c) & 1;
-                if (fixed) Kx = a.x[dof];          // K^ is the identity on fixed DOFs
+                T Kx = Kx3[c], xv = xv3[c];
+                if ((ep.m >> c) & 1) {           // K^ is the identity on fixed DOFs
+                    xv = a.x[dof];
+                    Kx = xv;
+                }
                 if (MODE == OP_APPLY) {
                     a.y[dof] = Kx;
                 } else if (MODE == OP_Q) {
                     a.y[dof] = Kx;
-                    acc0 += a.x[dof] * Kx;
+                    acc0 = fma(xv, Kx, acc0);
                 } else if (MODE == OP_BMINUS) {
-                    a.y[dof] = a.b[dof] - Kx;
+                    a.y[dof] = ep.b[c] - Kx;
                 } else if (MODE == OP_SMOOTH) {
-                    const T xv = a.x[dof];
-                    a.y[dof] = xv + a.omega * (a.b[dof] - Kx) / a.d[dof];
+                    a.y[dof] = xv + a.omega * (ep.b[c] - Kx) / ep.d[c];
                 } else if (MODE == OP_RESID) {
-                    const T fv = a.b[dof];
-                    const T rv = fv - Kx;
-                    a.y[dof] = rv;
+                    const T rv2 = ep.b[c] - Kx;
+                    a.y[dof] = rv2;
                     if (a.z) {
-                        const T zv = rv / a.d[dof];
+                        const T zv = rv2 / ep.d[c];
                         a.z[dof] = zv;
-                        acc0 += rv * zv;
+                        acc0 = fma(rv2, zv, acc0);
                     }
-                    acc1 += rv * rv;
-                    accmax = fmax(accmax, fabs(rv));
-                    acc3 += fv * a.x[dof];
+                    acc1 = fma(rv2, rv2, acc1);
+                    accmax = fmax(accmax, fabs(rv2));
+                    acc3 = fma(ep.b[c], xv, acc3);
                 }
             }
         }
+        // stage plane k+2 into the free buffer (plane k-1 is no longer read), fetch plane k+3
+        stage_store(plane[in]);
+        stage_load(k + 3);
+        __syncthreads();   // (B) plane k+2 visible; ybuf free
+        const int t0 = ib;
+        ib = it;
+        it = in;
+        in = t0;
     }
 
     if (MODE == OP_Q) {

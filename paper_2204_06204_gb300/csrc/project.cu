@@ -28,11 +28,11 @@ struct ProjArgs {
     const T* w_in;       // plain mode
     const T* rho_in;     // fused mode: w = rho - alpha (g - mean)
     const T* g;
-    T* wbuf;             // scratch (n)
+    T* wbuf;             // scratch (n), used when a block's chunk does not fit in shared memory
     T* rho_out;
     double vbar, lo, hi;
     int fused, mean_proj;
-    double alpha0_param, alpha_scale, m;
+    long long chunk;     // elements per block (contiguous)
     double* part;        // 2 * nblocks * kProjSlot doubles
     double* red;         // final reduction scratch (kRedQ per block)
     unsigned* bar;       // barrier words
@@ -40,53 +40,70 @@ struct ProjArgs {
     DevScalars* sc;
 };
 
-template <typename T>
+// element classification for the current lambda: at upper bound, at lower bound or free.
+// For float w the thresholds are rounded outward once (w >= t exactly iff w >= RU(t)
+// for a float w), so the per-element test needs no double arithmetic.
+__device__ __forceinline__ float round_up_f(double t) {
+    float f = (float)t;
+    if ((double)f < t) f = nextafterf(f, INFINITY);
+    return f;
+}
+__device__ __forceinline__ float round_down_f(double t) {
+    float f = (float)t;
+    if ((double)f > t) f = nextafterf(f, -INFINITY);
+    return f;
+}
+template <typename T> struct Thresh;
+template <> struct Thresh<float> {
+    float tu, tl;
+    __device__ Thresh(double lam, double lo, double hi) : tu(round_up_f(lam + hi)), tl(round_down_f(lam + lo)) {}
+    __device__ int cls(float w) const { return w >= tu ? 0 : (w <= tl ? 1 : 2); }
+};
+template <> struct Thresh<double> {
+    double tu, tl;
+    __device__ Thresh(double lam, double lo, double hi) : tu(lam + hi), tl(lam + lo) {}
+    __device__ int cls(double w) const { return w >= tu ? 0 : (w <= tl ? 1 : 2); }
+};
+
+template <typename T, bool CACHE>
 __global__ void __launch_bounds__(256) k_project(const ProjArgs<T> a) {
+    extern __shared__ unsigned char smem_raw[];
+    T* wloc = reinterpret_cast<T*>(smem_raw);
     __shared__ double sh[32 * kRedQ];
     __shared__ double sh8[32 * 8];
     const unsigned nb = gridDim.x, bid = blockIdx.x;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long b0 = (long long)bid * a.chunk;
+    const long long b1 = min(b0 + a.chunk, a.n);
+    const int tid = threadIdx.x;
     DevScalars* sc = a.sc;
 
-    // step size (identical in every block: only values fixed before this kernel are read)
-    double alpha0 = 0.0, alpha = 0.0, gmean = 0.0;
-    if (a.fused) {
-        alpha0 = a.alpha0_param > 0.0 ? a.alpha0_param : sc->alpha0;
-        if (!(alpha0 > 0.0) && sc->gmax > 0.0) alpha0 = a.alpha_scale / sc->gmax;
-        if (alpha0 > 0.0) alpha = alpha0 * pow((double)sc->k, -a.m);
-        if (a.mean_proj) gmean = sc->gsum / (double)a.n;
-    }
+    const double alpha = a.fused ? sc->alpha : 0.0;
+    const double gmean = (a.fused && a.mean_proj) ? sc->gsum / (double)a.n : 0.0;
+    const T alpha_t = (T)alpha, gmean_t = (T)gmean;
+    auto wat = [&](long long e) -> T { return CACHE ? wloc[e - b0] : a.wbuf[e]; };
 
-    // pass 0: w, the box-clamp volume, the piece at lambda = 0, min / max of w
-    double lambda = 0.0;
-    double lam_lo = 0.0, lam_hi = 0.0;
-    int iters = 0;
-    bool done = false;
-    int parity = 0;
+    // pass 0: w, the box-clamp volume (the piece at lambda = 0), min / max of w
     double tot[6];
+    int parity = 0;
     {
-        double v[6] = {0.0, 0.0, 0.0, 0.0, INFINITY, -INFINITY};  // nU, nL, nF, sF, min w, max w
-        T sF = T(0);
-        for (long long e = t0; e < a.n; e += stride) {
-            T w;
-            if (a.fused)
-                w = (T)((double)a.rho_in[e] - alpha * ((double)a.g[e] - gmean));
-            else
-                w = a.w_in[e];
-            a.wbuf[e] = w;
-            const double wd = (double)w;
-            if (wd >= a.hi) v[0] += 1.0;
-            else if (wd <= a.lo) v[1] += 1.0;
+        double v[6] = {0.0, 0.0, 0.0, 0.0, INFINITY, -INFINITY};
+        T sF = T(0), wmn = T(INFINITY), wmx = T(-INFINITY);
+        const Thresh<T> th(0.0, a.lo, a.hi);
+        for (long long e = b0 + tid; e < b1; e += blockDim.x) {
+            const T w = a.fused ? a.rho_in[e] - alpha_t * (a.g[e] - gmean_t) : a.w_in[e];
+            if (CACHE) wloc[e - b0] = w;
+            else a.wbuf[e] = w;
+            const int c = th.cls(w);
+            if (c == 0) v[0] += 1.0;
+            else if (c == 1) v[1] += 1.0;
             else { v[2] += 1.0; sF += w; }
-            v[4] = fmin(v[4], wd);
-            v[5] = fmax(v[5], wd);
+            wmn = fmin(wmn, w);
+            wmx = fmax(wmx, w);
         }
-        v[3] = (double)sF;
-        double mv[6] = {v[0], v[1], v[2], v[3], -v[4], v[5]};
+        double mv[6] = {v[0], v[1], v[2], (double)sF, -(double)wmn, (double)wmx};
         const int kind[6] = {0, 0, 0, 0, 1, 1};
         block_reduce<6>(mv, kind, sh8);
-        if (threadIdx.x == 0)
+        if (tid == 0)
             for (int q = 0; q < 6; ++q) a.part[(parity * nb + bid) * kProjSlot + q] = mv[q];
         if (!grid_barrier(a.bar, &sc->err)) return;
         for (int q = 0; q < 6; ++q) tot[q] = (q >= 4) ? -INFINITY : 0.0;
@@ -98,35 +115,37 @@ __global__ void __launch_bounds__(256) k_project(const ProjArgs<T> a) {
         parity ^= 1;
     }
     const double wmin = -tot[4], wmax = tot[5];
-    double S = tot[0] * a.hi + tot[1] * a.lo + tot[3];   // box-clamp volume (lambda = 0)
+    double S = tot[0] * a.hi + tot[1] * a.lo + tot[3];
+    double lambda = 0.0, lam_lo = 0.0, lam_hi = 0.0;
+    int iters = 0;
+    bool done = false;
     if (!isfinite(S)) set_err(&sc->err, TO_ERR_NONFINITE);
     if (S <= a.vbar || !isfinite(S)) {
         done = true;
-        lambda = 0.0;
     } else {
-        lam_lo = fmax(0.0, wmin - a.hi);   // S(lam_lo) > vbar
-        lam_hi = wmax - a.lo;              // S(lam_hi) = n lo <= vbar
+        lam_lo = fmax(0.0, wmin - a.hi);
+        lam_hi = wmax - a.lo;
         const double nF = tot[2];
-        double ln = nF > 0.0 ? (S - a.vbar) / nF : NAN;
+        const double ln = nF > 0.0 ? (S - a.vbar) / nF : NAN;
         lambda = (ln > lam_lo && ln < lam_hi) ? ln : 0.5 * (lam_lo + lam_hi);
     }
 
     while (!done && iters < kProjMaxIter) {
         ++iters;
-        const double tU = lambda + a.hi, tL = lambda + a.lo;
+        const Thresh<T> th(lambda, a.lo, a.hi);
         double v[4] = {0.0, 0.0, 0.0, 0.0};
         T sF = T(0);
-        for (long long e = t0; e < a.n; e += stride) {
-            const T w = a.wbuf[e];
-            const double wd = (double)w;
-            if (wd >= tU) v[0] += 1.0;
-            else if (wd <= tL) v[1] += 1.0;
+        for (long long e = b0 + tid; e < b1; e += blockDim.x) {
+            const T w = wat(e);
+            const int c = th.cls(w);
+            if (c == 0) v[0] += 1.0;
+            else if (c == 1) v[1] += 1.0;
             else { v[2] += 1.0; sF += w; }
         }
         v[3] = (double)sF;
         const int kind[4] = {0, 0, 0, 0};
         block_reduce<4>(v, kind, sh);
-        if (threadIdx.x == 0)
+        if (tid == 0)
             for (int q = 0; q < 4; ++q) a.part[(parity * nb + bid) * kProjSlot + q] = v[q];
         if (!grid_barrier(a.bar, &sc->err)) return;
         double t4[4] = {0.0, 0.0, 0.0, 0.0};
@@ -150,10 +169,9 @@ __global__ void __launch_bounds__(256) k_project(const ProjArgs<T> a) {
 
     // final pass: rho = clamp(w - lambda), ||drho||_inf, volume
     double dmax = 0.0, vol = 0.0;
-    for (long long e = t0; e < a.n; e += stride) {
-        const double wd = (double)a.wbuf[e];
-        const double r = fmin(fmax(wd - lambda, a.lo), a.hi);
-        const T rt = (T)r;
+    for (long long e = b0 + tid; e < b1; e += blockDim.x) {
+        const double wd = (double)wat(e);
+        const T rt = (T)fmin(fmax(wd - lambda, a.lo), a.hi);
         if (a.fused) dmax = fmax(dmax, fabs((double)rt - (double)a.rho_in[e]));
         vol += (double)rt;
         a.rho_out[e] = rt;
@@ -162,17 +180,15 @@ __global__ void __launch_bounds__(256) k_project(const ProjArgs<T> a) {
     const int kind2[2] = {1, 0};
     double tot2[2];
     block_reduce<2>(v2, kind2, sh);
-    if (finish_reduction<2>(v2, kind2, a.red, a.counter, tot2, sh) && threadIdx.x == 0) {
+    if (finish_reduction<2>(v2, kind2, a.red, a.counter, tot2, sh) && tid == 0) {
         sc->lambda = lambda;
         sc->drho_inf = tot2[0];
         sc->volume = tot2[1];
         sc->proj_iters = iters;
-        if (a.fused) {
-            sc->alpha = alpha;
-            if (alpha0 > 0.0) sc->alpha0 = alpha0;
-        }
     }
 }
+
+constexpr size_t kProjSmem = 96 * 1024;
 
 template <typename T>
 static int project_t(to_problem* P, const void* w, const void* rho_in, const void* g, void* rho_out, int fused,
@@ -189,19 +205,24 @@ static int project_t(to_problem* P, const void* w, const void* rho_in, const voi
     a.hi = P->mat.rho_max;
     a.fused = fused;
     a.mean_proj = P->prm.mean_proj;
-    a.alpha0_param = P->prm.alpha0;
-    a.alpha_scale = P->prm.alpha_scale;
-    a.m = P->prm.m;
     a.part = P->red + (size_t)kMaxRedBlocks * kRedQ;
     a.red = P->red;
     a.bar = P->counters + 8;
     a.counter = P->counters + 3;
     a.sc = P->sc;
-    int nb = (int)((P->n_elem + 255) / 256);
+    long long nb = (P->n_elem + 255) / 256;
     if (nb > P->coop_blocks) nb = P->coop_blocks;
     if (nb < 1) nb = 1;
+    a.chunk = (P->n_elem + nb - 1) / nb;
+    nb = (P->n_elem + a.chunk - 1) / a.chunk;
+    if (nb < 1) nb = 1;
     void* args[] = {(void*)&a};
-    TO_CUDA(cudaLaunchCooperativeKernel((const void*)k_project<T>, dim3(nb), dim3(256), args, 0, s));
+    const size_t smem = (size_t)a.chunk * sizeof(T);
+    if (smem <= kProjSmem) {
+        TO_CUDA(cudaLaunchCooperativeKernel((const void*)k_project<T, true>, dim3((unsigned)nb), dim3(256), args, smem, s));
+    } else {
+        TO_CUDA(cudaLaunchCooperativeKernel((const void*)k_project<T, false>, dim3((unsigned)nb), dim3(256), args, 0, s));
+    }
     return TO_OK;
 }
 
@@ -212,10 +233,19 @@ int launch_project(to_problem* P, const void* w, const void* rho_in, const void*
 }
 
 int project_coop_blocks(int prec, int num_sms, int* out) {
+    // co-residency with the largest shared-memory request: one block per SM is
+    // always possible; take two when the occupancy query allows it
     int per_sm = 0;
-    cudaError_t e = prec == TO_FP64
-                        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_project<double>, 256, 0)
-                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_project<float>, 256, 0);
+    cudaError_t e;
+    if (prec == TO_FP64) {
+        e = cudaFuncSetAttribute(k_project<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kProjSmem);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_project<double, true>, 256, kProjSmem);
+    } else {
+        e = cudaFuncSetAttribute(k_project<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kProjSmem);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_project<float, true>, 256, kProjSmem);
+    }
     if (e != cudaSuccess) return fail(TO_ERR_CUDA, std::string("occupancy query: ") + cudaGetErrorString(e));
     if (per_sm > 2) per_sm = 2;
     *out = per_sm * num_sms;
