@@ -208,7 +208,8 @@ extern "C" int to_create(const to_grid* g, const to_material* m, const to_loads*
         (rc = dalloc(&P->q, nd * es)) || (rc = dalloc(&P->tmp_v, nd * es)) || (rc = dalloc(&F.d, nd * es)))
         return bail(rc);
     void* mk = nullptr;
-    if ((rc = dalloc(&mk, (size_t)P->n_node))) return bail(rc);
+    // masks are read as aligned 4-byte words: round the allocation up
+    if ((rc = dalloc(&mk, ((size_t)P->n_node + 7) & ~(size_t)3))) return bail(rc);
     F.mask = (uint8_t*)mk;
     void* stp = nullptr;
     if ((rc = dalloc(&stp, st.size() * sizeof(int4))) || (rc = dalloc(&P->stencil_w, sw.size() * es))) return bail(rc);
@@ -234,7 +235,8 @@ extern "C" int to_create(const to_grid* g, const to_material* m, const to_loads*
     auto upload = [&](void* dst, const void* src, size_t bytes) {
         return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s) == cudaSuccess;
     };
-    bool ok = upload(F.mask, hmask.data(), hmask.size()) && upload(P->stencil, st.data(), st.size() * sizeof(int4));
+    bool ok = cudaMemsetAsync(F.mask, 0, ((size_t)P->n_node + 7) & ~(size_t)3, s) == cudaSuccess &&
+              upload(F.mask, hmask.data(), hmask.size()) && upload(P->stencil, st.data(), st.size() * sizeof(int4));
     std::vector<float> hf32, sw32;
     if (P->prec == TO_FP64) {
         ok = ok && upload(P->f, hf.data(), nd * 8) && upload(P->stencil_w, sw.data(), sw.size() * 8);

@@ -261,7 +261,8 @@ int mg_build(to_problem* P) {
         void *E = nullptr, *d = nullptr, *mk = nullptr, *x = nullptr, *b = nullptr, *t = nullptr;
         cudaError_t e = cudaMalloc(&E, C.n_elem * es);
         if (e == cudaSuccess) e = cudaMalloc(&d, C.n_dof * es);
-        if (e == cudaSuccess) e = cudaMalloc(&mk, C.n_node);
+        if (e == cudaSuccess) e = cudaMalloc(&mk, ((size_t)C.n_node + 7) & ~(size_t)3);   // read as 4-byte words
+        if (e == cudaSuccess) e = cudaMemset(mk, 0, ((size_t)C.n_node + 7) & ~(size_t)3);
         if (e == cudaSuccess) e = cudaMalloc(&x, C.n_dof * es);
         if (e == cudaSuccess) e = cudaMalloc(&b, C.n_dof * es);
         if (e == cudaSuccess) e = cudaMalloc(&t, C.n_dof * es);

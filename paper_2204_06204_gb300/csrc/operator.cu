@@ -131,17 +131,55 @@ __device__ __forceinline__ void face_forward4(const N4& a00, const N4& a10, cons
     F.z[3] = zd1 - zd0;
 }
 
+// ----------------------------------------------------------------------------- async copies
+__device__ __forceinline__ void cp_async_4(void* smem, const void* gmem, bool valid) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gmem), "r"(valid ? 4 : 0));
+}
+__device__ __forceinline__ void cp_async_8(void* smem, const void* gmem, bool valid) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(gmem), "r"(valid ? 8 : 0));
+}
+template <typename T>
+__device__ __forceinline__ void cp_async_t(T* smem, const T* gmem, bool valid) {
+    if (sizeof(T) == 8) cp_async_8(smem, gmem, valid);
+    else cp_async_4(smem, gmem, valid);
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+// Shared-memory layout of the operator kernel (NB-deep ring of staged planes).
+template <typename T, int TX, int TY, int NB>
+struct OpSmem {
+    using N4 = typename Node4<T>::t;
+    static constexpr int PN = (TX + 1) * (TY + 1);
+    N4 plane[NB][PN];          // node values (xyz, pad), fixed components zeroed after landing
+    uint32_t mword[NB][PN];    // 4-byte word holding each node's mask byte
+    T ebuf[NB][TY][TX];        // element moduli of the CTA's columns, per layer
+    T eb[NB][TY][TX][3];       // epilogue right-hand side at the owned node
+    T ed[NB][TY][TX][3];       // epilogue diagonal at the owned node
+    N4 ybuf[TY][TX];
+    double red[32 * kRedQ];
+};
+
+constexpr int kDepth = 2;                  // planes in flight ahead of the one being consumed
+constexpr int kRing = kDepth + 2;
+
 template <typename T, int TX, int TY, int MODE>
 __global__ void __launch_bounds__(TX * TY) k_operator(const OpArgs<T> a) {
     static_assert(TX == 32, "one warp per row of element columns");
     using P = typename PairT<T>::t;
     using N4 = typename Node4<T>::t;
+    using SM = OpSmem<T, TX, TY, kRing>;
     constexpr int NT = TX * TY;
-    constexpr int PN = (TX + 1) * (TY + 1);          // nodes per staged plane
-    constexpr int SR = (PN + NT - 1) / NT;           // staging rounds per thread
-    __shared__ N4 plane[3][PN];
-    __shared__ N4 ybuf[TY][TX];
-    __shared__ double sh_red[32 * kRedQ];
+    constexpr int PN = SM::PN;
+    constexpr int SR = (PN + NT - 1) / NT;
+    constexpr bool NEED_B = MODE == OP_RESID || MODE == OP_SMOOTH || MODE == OP_BMINUS;
+    constexpr bool NEED_D = MODE == OP_SMOOTH || MODE == OP_RESID;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SM& sm = *reinterpret_cast<SM*>(smem_raw);
+
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = tx + TX * ty;
     const int X0 = blockIdx.x * (TX - 1), Y0 = blockIdx.y * (TY - 1);
@@ -154,10 +192,10 @@ __global__ void __launch_bounds__(TX * TY) k_operator(const OpArgs<T> a) {
     const bool col_in = ie >= 0 && ie < a.nx && je >= 0 && je < a.ny;
     const int ni = X0 + tx, nj = Y0 + ty;
     const bool owner = tx < TX - 1 && ty < TY - 1 && ni < nxn && nj < nyn;
-    const long long own_base = (long long)ni + (long long)nxn * nj;          // + k * nplane
+    const long long own_base = (long long)ni + (long long)nxn * nj;
     const long long elem_base = col_in ? (long long)ie + (long long)a.nx * je : 0;
+    const bool dz = NEED_D && a.d != nullptr && (MODE != OP_RESID || a.z != nullptr);
 
-    // staging assignment: node s = tid + r * NT of the (TX+1) x (TY+1) plane tile
     long long st_base[SR];
     bool st_ok[SR];
 #pragma unroll
@@ -168,104 +206,102 @@ __global__ void __launch_bounds__(TX * TY) k_operator(const OpArgs<T> a) {
         st_ok[r] = sidx < PN && gi >= 0 && gi < nxn && gj >= 0 && gj < nyn;
         st_base[r] = st_ok[r] ? (long long)gi + (long long)nxn * gj : 0;
     }
-    T rv[SR][3];
-    uint8_t rm[SR];
-    auto stage_load = [&](int kp) {
-#pragma unroll
-        for (int r = 0; r < SR; ++r) {
-            rv[r][0] = rv[r][1] = rv[r][2] = T(0);
-            rm[r] = 7;
-            if (st_ok[r] && kp >= 0 && kp <= a.nz) {
-                const long long node = st_base[r] + kp * nplane;
-                rm[r] = a.mask[node];
-                rv[r][0] = a.x[3 * node + 0];
-                rv[r][1] = a.x[3 * node + 1];
-                rv[r][2] = a.x[3 * node + 2];
-            }
-        }
-    };
-    auto stage_store = [&](N4* buf) {
+    auto slot = [](int p) { return (p + kRing) % kRing; };
+
+    // issue every asynchronous copy that plane p (and element layer p-1) needs
+    auto issue = [&](int p) {
+        const int sp = slot(p);
+        const bool pin = p >= 0 && p <= a.nz;
 #pragma unroll
         for (int r = 0; r < SR; ++r) {
             const int sidx = tid + r * NT;
             if (sidx < PN) {
-                N4 v;
-                v.x = (rm[r] & 1) ? T(0) : rv[r][0];
-                v.y = (rm[r] & 2) ? T(0) : rv[r][1];
-                v.z = (rm[r] & 4) ? T(0) : rv[r][2];
-                v.w = T(0);
-                buf[sidx] = v;
+                const bool v = st_ok[r] && pin;
+                const long long node = v ? st_base[r] + p * nplane : 0;
+                T* dst = reinterpret_cast<T*>(&sm.plane[sp][sidx]);
+                cp_async_t<T>(dst + 0, a.x + 3 * node + 0, v);
+                cp_async_t<T>(dst + 1, a.x + 3 * node + 1, v);
+                cp_async_t<T>(dst + 2, a.x + 3 * node + 2, v);
+                cp_async_4(&sm.mword[sp][sidx], reinterpret_cast<const uint32_t*>(a.mask) + (node >> 2), v);
             }
         }
+        const int L = p - 1;   // element layer whose top face is plane p
+        const bool ev = col_in && L >= 0 && L < a.nz;
+        cp_async_t<T>(&sm.ebuf[sp][ty][tx], ev ? a.E + (elem_base + (long long)L * eplane) : a.E, ev);
+        if (NEED_B || dz) {
+            const bool ov = owner && p >= kb && p < ke;
+            const long long node = ov ? own_base + p * nplane : 0;
+            if (NEED_B)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) cp_async_t<T>(&sm.eb[sp][ty][tx][c], a.b + 3 * node + c, ov);
+            if (dz)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) cp_async_t<T>(&sm.ed[sp][ty][tx][c], a.d + 3 * node + c, ov);
+        }
+        cp_commit();
     };
-    // epilogue operands of the owned node at a plane, fetched one layer ahead
-    struct Epi {
-        uint8_t m;
-        T b[3], d[3];
-    };
-    auto epi_load = [&](int kp, Epi& e) {
-        e.m = 0;
+    // zero the fixed components of the nodes this thread staged for plane p (after they landed)
+    auto patch = [&](int p) {
+        const int sp = slot(p);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) e.b[c] = e.d[c] = T(0);
-        if (owner && kp >= kb && kp < ke) {
-            const long long node = own_base + kp * nplane;
-            e.m = a.mask[node];
-            if (MODE == OP_RESID || MODE == OP_SMOOTH || MODE == OP_BMINUS)
-#pragma unroll
-                for (int c = 0; c < 3; ++c) e.b[c] = a.b[3 * node + c];
-            if (MODE == OP_SMOOTH || (MODE == OP_RESID && a.z != nullptr))
-#pragma unroll
-                for (int c = 0; c < 3; ++c) e.d[c] = a.d[3 * node + c];
+        for (int r = 0; r < SR; ++r) {
+            const int sidx = tid + r * NT;
+            if (sidx < PN && st_ok[r] && p >= 0 && p <= a.nz) {
+                const long long node = st_base[r] + p * nplane;
+                const uint32_t m = (sm.mword[sp][sidx] >> (8 * (int)(node & 3))) & 0xffu;
+                if (m) {
+                    T* dst = reinterpret_cast<T*>(&sm.plane[sp][sidx]);
+                    if (m & 1) dst[0] = T(0);
+                    if (m & 2) dst[1] = T(0);
+                    if (m & 4) dst[2] = T(0);
+                }
+            }
         }
     };
 
     T acc0 = T(0), acc1 = T(0), acc3 = T(0), accmax = T(0);
 
-    // prologue: planes kb-1 and kb staged, kb+1 in flight; bottom face of layer kb-1
-    int ib = 0, it = 1, in = 2;            // ring: bottom, top, next
-    stage_load(kb - 1);
-    stage_store(plane[ib]);
-    stage_load(kb);
-    stage_store(plane[it]);
+    // prologue: planes kb-1 .. kb+kDepth-1 in flight; wait for kb-1 and kb
+#pragma unroll
+    for (int q = 0; q <= kDepth; ++q) issue(kb - 1 + q);
+    cp_wait<kDepth - 1>();
+    patch(kb - 1);
+    patch(kb);
     __syncthreads();
     Face<T> Fb;
-    face_forward4<T>(plane[ib][ty * (TX + 1) + tx], plane[ib][ty * (TX + 1) + tx + 1],
-                     plane[ib][(ty + 1) * (TX + 1) + tx], plane[ib][(ty + 1) * (TX + 1) + tx + 1], Fb);
+    {
+        const N4* bp = sm.plane[slot(kb - 1)];
+        face_forward4<T>(bp[ty * (TX + 1) + tx], bp[ty * (TX + 1) + tx + 1], bp[(ty + 1) * (TX + 1) + tx],
+                         bp[(ty + 1) * (TX + 1) + tx + 1], Fb);
+    }
     Face<T> Gc;
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
         Gc.p[f] = P{T(0), T(0)};
         Gc.z[f] = T(0);
     }
-    stage_load(kb + 1);
-    T Enext = (col_in && kb - 1 >= 0 && kb - 1 < a.nz) ? a.E[elem_base + (kb - 1) * eplane] : T(0);
-    Epi ep_next;
-    epi_load(kb - 1, ep_next);
 
     for (int k = kb - 1; k < ke; ++k) {
-        const T Ee = Enext;
-        Enext = (col_in && k + 1 >= 0 && k + 1 < a.nz) ? a.E[elem_base + (k + 1) * eplane] : T(0);
-        const Epi ep = ep_next;
-        epi_load(k + 1, ep_next);
+        issue(k + 1 + kDepth);
+        const int s_top = slot(k + 1), s_bot = slot(k);
 
-        // top face of element layer k (node plane k+1)
-        const N4* tp = plane[it];
+        const N4* tp = sm.plane[s_top];
         Face<T> Ft;
         face_forward4<T>(tp[ty * (TX + 1) + tx], tp[ty * (TX + 1) + tx + 1], tp[(ty + 1) * (TX + 1) + tx],
                          tp[(ty + 1) * (TX + 1) + tx + 1], Ft);
         Face<T> S;
         const bool elem_in = col_in && k >= 0 && k < a.nz;
         if (elem_in) {
-            // 24 coefficients: z sums (ss*, first 12) and z differences (last 12)
+            const T Ee = sm.ebuf[s_top][ty][tx];
             T uh[24];
 #pragma unroll
             for (int f = 0; f < 4; ++f) {
-                const P s = padd(Ft.p[f], Fb.p[f]), d = psub(Ft.p[f], Fb.p[f]);
-                uh[3 * f + 0] = s.x;
-                uh[3 * f + 1] = s.y;
+                const P sum = padd(Ft.p[f], Fb.p[f]), dif = psub(Ft.p[f], Fb.p[f]);
+                uh[3 * f + 0] = sum.x;
+                uh[3 * f + 1] = sum.y;
                 uh[3 * f + 2] = Ft.z[f] + Fb.z[f];
-                uh[12 + 3 * f + 0] = d.x;
-                uh[12 + 3 * f + 1] = d.y;
+                uh[12 + 3 * f + 0] = dif.x;
+                uh[12 + 3 * f + 1] = dif.y;
                 uh[12 + 3 * f + 2] = Ft.z[f] - Fb.z[f];
             }
             T v[24];
@@ -300,7 +336,6 @@ __global__ void __launch_bounds__(TX * TY) k_operator(const OpArgs<T> a) {
         }
         Fb = Ft;
 
-        // plane k: inverse face butterflies, x neighbours by shuffle, y neighbours via shared memory
         const bool out_plane = k >= kb;
         P Xp, Yp;
         T Xz, Yz;
@@ -322,19 +357,21 @@ __global__ void __launch_bounds__(TX * TY) k_operator(const OpArgs<T> a) {
             Yp = padd(c10, n00);
             Yz = z10 + m00;
         }
-        if (out_plane) ybuf[ty][tx] = N4{Yp.x, Yp.y, Yz, T(0)};
-        __syncthreads();   // (A) ybuf written; every read of plane[ib] done
+        if (out_plane) sm.ybuf[ty][tx] = N4{Yp.x, Yp.y, Yz, T(0)};
+        __syncthreads();   // (A)
         if (out_plane && owner) {
-            const N4 yb = ybuf[ty + 1][tx];
+            const N4 yb = sm.ybuf[ty + 1][tx];
             const T Kx3[3] = {Xp.x + yb.x, Xp.y + yb.y, Xz + yb.z};
             const long long node = own_base + (long long)k * nplane;
-            const N4 xs = plane[ib][(ty + 1) * (TX + 1) + tx + 1];   // masked input at the owned node
+            const int oidx = (ty + 1) * (TX + 1) + tx + 1;
+            const N4 xs = sm.plane[s_bot][oidx];
             const T xv3[3] = {xs.x, xs.y, xs.z};
+            const uint32_t mk = (sm.mword[s_bot][oidx] >> (8 * (int)(node & 3))) & 0xffu;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 const long long dof = 3 * node + c;
                 T Kx = Kx3[c], xv = xv3[c];
-                if ((ep.m >> c) & 1) {           // K^ is the identity on fixed DOFs
+                if ((mk >> c) & 1) {               // K^ is the identity on fixed DOFs
                     xv = a.x[dof];
                     Kx = xv;
                 }
@@ -344,32 +381,30 @@ __global__ void __launch_bounds__(TX * TY) k_operator(const OpArgs<T> a) {
                     a.y[dof] = Kx;
                     acc0 = fma(xv, Kx, acc0);
                 } else if (MODE == OP_BMINUS) {
-                    a.y[dof] = ep.b[c] - Kx;
+                    a.y[dof] = sm.eb[s_bot][ty][tx][c] - Kx;
                 } else if (MODE == OP_SMOOTH) {
-                    a.y[dof] = xv + a.omega * (ep.b[c] - Kx) / ep.d[c];
+                    a.y[dof] = xv + a.omega * (sm.eb[s_bot][ty][tx][c] - Kx) / sm.ed[s_bot][ty][tx][c];
                 } else if (MODE == OP_RESID) {
-                    const T rv2 = ep.b[c] - Kx;
+                    const T bv = sm.eb[s_bot][ty][tx][c];
+                    const T rv2 = bv - Kx;
                     a.y[dof] = rv2;
                     if (a.z) {
-                        const T zv = rv2 / ep.d[c];
+                        const T zv = rv2 / sm.ed[s_bot][ty][tx][c];
                         a.z[dof] = zv;
                         acc0 = fma(rv2, zv, acc0);
                     }
                     acc1 = fma(rv2, rv2, acc1);
                     accmax = fmax(accmax, fabs(rv2));
-                    acc3 = fma(ep.b[c], xv, acc3);
+                    acc3 = fma(bv, xv, acc3);
                 }
             }
         }
-        // stage plane k+2 into the free buffer (plane k-1 is no longer read), fetch plane k+3
-        stage_store(plane[in]);
-        stage_load(k + 3);
-        __syncthreads();   // (B) plane k+2 visible; ybuf free
-        const int t0 = ib;
-        ib = it;
-        it = in;
-        in = t0;
+        cp_wait<kDepth - 1>();     // plane k+2 (and its layer, operands) landed
+        patch(k + 2);
+        __syncthreads();   // (B)
     }
+    cp_wait<0>();
+    double* sh_red = sm.red;
 
     if (MODE == OP_Q) {
         double v[1] = {(double)acc0};
@@ -445,7 +480,7 @@ static int launch_t(to_problem* P, int level, int mode, const void* x, void* y, 
     if (kchunk <= 0) {
         // enough CTAs for two per SM, at least 4 planes per walk
         const long long per_plane = (long long)gx * gy;
-        const long long want = 2LL * P->num_sms;
+        const long long want = 3LL * P->num_sms;
         long long gz = (want + per_plane - 1) / per_plane;
         kchunk = (int)((L.nz + 1 + gz - 1) / gz);
         if (kchunk < 4) kchunk = 4;
@@ -456,12 +491,21 @@ static int launch_t(to_problem* P, int level, int mode, const void* x, void* y, 
     if ((long long)gx * gy * gz > kMaxRedBlocks && (mode == OP_RESID || mode == OP_Q))
         return fail(TO_ERR_ARG, "operator grid exceeds the reduction scratch; raise tile_z");
     dim3 grid(gx, gy, gz), block(TX, TY);
+    const size_t smem = sizeof(OpSmem<T, TX, TY, kRing>);
+    static bool attr_set = false;   // per (T, TX, TY) instantiation
+    if (!attr_set) {
+        const void* fns[5] = {(const void*)k_operator<T, TX, TY, OP_APPLY>, (const void*)k_operator<T, TX, TY, OP_RESID>,
+                              (const void*)k_operator<T, TX, TY, OP_Q>, (const void*)k_operator<T, TX, TY, OP_SMOOTH>,
+                              (const void*)k_operator<T, TX, TY, OP_BMINUS>};
+        for (const void* f : fns) TO_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr_set = true;
+    }
     switch (mode) {
-        case OP_APPLY: k_operator<T, TX, TY, OP_APPLY><<<grid, block, 0, s>>>(a); break;
-        case OP_RESID: k_operator<T, TX, TY, OP_RESID><<<grid, block, 0, s>>>(a); break;
-        case OP_Q: k_operator<T, TX, TY, OP_Q><<<grid, block, 0, s>>>(a); break;
-        case OP_SMOOTH: k_operator<T, TX, TY, OP_SMOOTH><<<grid, block, 0, s>>>(a); break;
-        case OP_BMINUS: k_operator<T, TX, TY, OP_BMINUS><<<grid, block, 0, s>>>(a); break;
+        case OP_APPLY: k_operator<T, TX, TY, OP_APPLY><<<grid, block, smem, s>>>(a); break;
+        case OP_RESID: k_operator<T, TX, TY, OP_RESID><<<grid, block, smem, s>>>(a); break;
+        case OP_Q: k_operator<T, TX, TY, OP_Q><<<grid, block, smem, s>>>(a); break;
+        case OP_SMOOTH: k_operator<T, TX, TY, OP_SMOOTH><<<grid, block, smem, s>>>(a); break;
+        case OP_BMINUS: k_operator<T, TX, TY, OP_BMINUS><<<grid, block, smem, s>>>(a); break;
         default: return fail(TO_ERR_ARG, "bad operator mode");
     }
     TO_CUDA(cudaGetLastError());
