@@ -200,6 +200,28 @@ int to_step(to_problem* P, int32_t n_outer, to_stats* stats_out, void* stream);
 int to_get_state(to_problem* P, void* rho_dev, void* u_dev, int64_t* k_out, double* alpha0_out, void* stream);
 int to_set_state(to_problem* P, const void* rho_dev, const void* u_dev, int64_t k, double alpha0, void* stream);
 
+/* Allocation-free projection.  The paper has no counterpart: this entry point
+ * exists for callers that may not allocate device memory, for instance code
+ * running inside a host framework that owns every device byte through its own
+ * pool, or a long-running service that must not call cudaMalloc / cudaFree
+ * (cudaFree synchronises the whole device) once it is serving.  It computes
+ * what to_project computes for a problem with n_elem = n, vbar, rho_min = lo and
+ * rho_max = hi, without a to_problem and without allocating: its scratch (block
+ * partials, barrier words, result scalars) is one static device array of about
+ * 170 KB that every GPU loading this library holds until the process exits.
+ *   w_dev, rho_dev  n entries on the current device (double for TO_FP64, float for
+ *                   TO_FP32_MIXED); they may alias.
+ *   n               1 <= n <= 2,097,152; larger n returns TO_ERR_ARG (also when the
+ *                   device cannot keep every per-block chunk in shared memory).
+ *   lambda_out      host, may be NULL; when set the call synchronises `stream`.
+ * The first call on a device looks up the array's device address and the
+ * kernel's co-residency limit for that device (with it current); make that first
+ * call before any stream capture.  Every call shares the one array and resets the
+ * parts that must start at zero, so calls that overlap on the GPU (different
+ * streams or threads) race: serialise them. */
+int to_project_noalloc(const void* w_dev, void* rho_dev, int64_t n, int32_t precision, double vbar,
+                       double lo, double hi, double* lambda_out, void* stream);
+
 /* Synchronise the stream and report (and clear) the device error flag. */
 int to_check(to_problem* P, void* stream);
 

@@ -18,7 +18,7 @@ from ._abi import (TO_FP32_MIXED, TO_FP64, TO_INNER_RICHARDSON, TO_INNER_SD, TO_
 
 __all__ = ["to_default_params", "to_create", "to_destroy", "to_sizes", "to_set_design", "to_apply_K",
            "to_inner_solve", "to_sensitivity", "to_filter", "to_project", "to_step", "to_get_state",
-           "to_set_state", "to_check", "to_last_error", "Problem", "ToError",
+           "to_set_state", "to_check", "to_last_error", "to_project_noalloc", "Problem", "ToError",
            "TO_FP64", "TO_FP32_MIXED", "TO_PRECOND_JACOBI", "TO_PRECOND_MG", "TO_PRECOND_NONE",
            "TO_INNER_SD", "TO_INNER_RICHARDSON"]
 
@@ -232,6 +232,21 @@ def to_set_state(P, rho=None, u=None, k=1, alpha0=0.0):
 
 def to_check(P):
     _abi.check(_lib().to_check(_h(P), _stream(P.device)))
+
+
+def to_project_noalloc(w, rho, vbar, lo=0.0, hi=1.0, want_lambda=True):
+    """Projection onto X without a problem and without any device allocation
+    (for callers that may not allocate device memory); see include/to.h."""
+    import torch
+    if w.dtype not in (torch.float32, torch.float64) or rho.dtype != w.dtype:
+        raise TypeError("w and rho must both be float32 or both float64")
+    n = w.numel()
+    prec = TO_FP64 if w.dtype == torch.float64 else TO_FP32_MIXED
+    lam = C.c_double()
+    _abi.check(_lib().to_project_noalloc(_ptr(w, w.dtype, n, "w"), _ptr(rho, w.dtype, n, "rho"), n, prec,
+                                         float(vbar), float(lo), float(hi), C.byref(lam) if want_lambda else None,
+                                         _stream(w.device)))
+    return lam.value if want_lambda else None
 
 
 def to_last_error() -> str:

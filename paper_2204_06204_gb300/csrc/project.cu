@@ -15,6 +15,10 @@
 // same piece twice the root is exact (up to rounding), typically in a handful
 // of passes.  lambda and every sum are double; the element values are the
 // problem's precision.
+#include <cmath>
+#include <cstddef>
+#include <mutex>
+
 #include "device.cuh"
 
 namespace to {
@@ -254,3 +258,129 @@ int project_coop_blocks(int prec, int num_sms, int* out) {
 }
 
 }  // namespace to
+
+// ----------------------------------------------------------------------------- allocation-free variant
+// The same projection kernel, for callers that must not allocate device
+// memory: its reduction slots, barrier words and result scalars live in one
+// file-scope device array instead of a problem's buffers.  Every GPU that
+// loads this library holds the array (about 170 KB) until the process exits.
+namespace to {
+namespace {
+
+constexpr int kNoAllocMaxBlocks = 1024;           // co-resident blocks the scratch has slots for
+constexpr long long kNoAllocMaxN = 1LL << 21;     // 2,097,152 design variables per call
+
+struct NoAllocScratch {
+    DevScalars sc;                                  // lambda, volume, error flag of the last call
+    unsigned words[64];                             // [3] reduction counter, [8], [9] grid barrier
+    double red[kNoAllocMaxBlocks * kRedQ];
+    double part[2 * kNoAllocMaxBlocks * kProjSlot];
+};
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocScratch)];
+
+struct NoAllocDevice {
+    bool ready = false;
+    NoAllocScratch* ptr = nullptr;   // device address of g_noalloc_scratch on this device
+    int coop[2] = {0, 0};            // co-resident blocks: [0] double, [1] float
+};
+std::mutex g_noalloc_mtx;
+NoAllocDevice g_noalloc_dev[64];
+
+// Once per device, with that device current: the symbol's device address, the
+// shared-memory opt-in and the co-residency limit of the kernel.  None of these
+// calls allocates device memory.
+int noalloc_setup(int dev, NoAllocDevice** out) {
+    std::lock_guard<std::mutex> lock(g_noalloc_mtx);
+    if (dev < 0 || dev >= 64) return fail(TO_ERR_ARG, "device index out of range for the allocation-free path");
+    NoAllocDevice& D = g_noalloc_dev[dev];
+    if (!D.ready) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return fail(TO_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+        int sms = 0;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return fail(TO_ERR_CUDA, std::string("device query: ") + cudaGetErrorString(e));
+        int per_sm[2] = {0, 0};
+        e = cudaFuncSetAttribute(k_project<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kProjSmem);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[0], k_project<double, true>, 256, kProjSmem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_project<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kProjSmem);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[1], k_project<float, true>, 256, kProjSmem);
+        if (e != cudaSuccess) return fail(TO_ERR_CUDA, std::string("occupancy query: ") + cudaGetErrorString(e));
+        for (int i = 0; i < 2; ++i) {
+            const int ps = per_sm[i] > 2 ? 2 : per_sm[i];
+            D.coop[i] = ps * sms > kNoAllocMaxBlocks ? kNoAllocMaxBlocks : ps * sms;
+        }
+        D.ptr = reinterpret_cast<NoAllocScratch*>(p);
+        D.ready = true;
+    }
+    *out = &D;
+    return TO_OK;
+}
+
+template <typename T>
+int project_noalloc_t(NoAllocDevice& D, const void* w, void* rho, long long n, double vbar, double lo, double hi,
+                      double* lambda_out, cudaStream_t s) {
+    NoAllocScratch* S = D.ptr;
+    // the last call's contents stay in the array: reset what must start at zero
+    TO_CUDA(cudaMemsetAsync(S, 0, offsetof(NoAllocScratch, red), s));
+    ProjArgs<T> a{};
+    a.n = n;
+    a.w_in = (const T*)w;
+    a.wbuf = nullptr;          // only the shared-memory variant runs here
+    a.rho_out = (T*)rho;
+    a.vbar = vbar;
+    a.lo = lo;
+    a.hi = hi;
+    a.fused = 0;
+    a.mean_proj = 0;
+    a.part = S->part;
+    a.red = S->red;
+    a.bar = S->words + 8;
+    a.counter = S->words + 3;
+    a.sc = &S->sc;
+    long long nb = (n + 255) / 256;
+    const int coop = D.coop[sizeof(T) == 4 ? 1 : 0];
+    if (nb > coop) nb = coop;
+    if (nb < 1) nb = 1;
+    a.chunk = (n + nb - 1) / nb;
+    nb = (n + a.chunk - 1) / a.chunk;
+    const size_t smem = (size_t)a.chunk * sizeof(T);
+    if (smem > kProjSmem)
+        return fail(TO_ERR_ARG, "n too large for the allocation-free projection on this device");
+    void* args[] = {(void*)&a};
+    TO_CUDA(cudaLaunchCooperativeKernel((const void*)k_project<T, true>, dim3((unsigned)nb), dim3(256), args, smem, s));
+    if (lambda_out) {
+        DevScalars h;
+        TO_CUDA(cudaMemcpyAsync(&h, &S->sc, sizeof h, cudaMemcpyDeviceToHost, s));
+        TO_CUDA(cudaStreamSynchronize(s));
+        *lambda_out = h.lambda;
+        if (h.err) return fail(h.err, "device-side error in the allocation-free projection");
+    }
+    return TO_OK;
+}
+
+}  // namespace
+}  // namespace to
+
+extern "C" int to_project_noalloc(const void* w_dev, void* rho_dev, int64_t n, int32_t precision, double vbar,
+                                  double lo, double hi, double* lambda_out, void* stream) {
+    using namespace to;
+    if (!w_dev || !rho_dev) return fail(TO_ERR_ARG, "null vector");
+    if (n < 1 || n > kNoAllocMaxN)
+        return fail(TO_ERR_ARG, "n must lie in [1, 2097152] for the allocation-free projection");
+    if (precision != TO_FP64 && precision != TO_FP32_MIXED) return fail(TO_ERR_ARG, "bad precision");
+    if (!(lo >= 0.0 && hi > lo) || !std::isfinite(vbar)) return fail(TO_ERR_ARG, "need 0 <= lo < hi and a finite vbar");
+    if (vbar < (double)n * lo) return fail(TO_ERR_INFEASIBLE, "vbar < n * lo: X is empty");
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return fail(TO_ERR_CUDA, "no current CUDA device");
+    NoAllocDevice* D = nullptr;
+    int rc = noalloc_setup(dev, &D);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    return precision == TO_FP64 ? project_noalloc_t<double>(*D, w_dev, rho_dev, n, vbar, lo, hi, lambda_out, s)
+                                : project_noalloc_t<float>(*D, w_dev, rho_dev, n, vbar, lo, hi, lambda_out, s);
+}
