@@ -112,13 +112,15 @@ typedef struct {
  *   mean_proj   1: g <- g - mean(g) before the step (Sec. IV-B)
  *   mg_levels   0 = automatic; mg_nu_pre / mg_nu_post smoothing sweeps;
  *               mg_omega damped-Jacobi weight
- *   tile_x, tile_y, tile_z   0 = automatic tile choice for the operator kernel */
+ *   tile_x, tile_y, tile_z   0 = automatic tile choice for the operator kernel
+ *   no_graph    0: to_step replays one captured CUDA graph per outer iteration;
+ *               1: to_step launches the kernels one by one */
 typedef struct {
     int32_t precision, precond, inner_mode, n_inner;
     double beta, alpha0, alpha_scale, m;
     int32_t mean_proj, mg_levels, mg_nu_pre, mg_nu_post;
     double mg_omega;
-    int32_t tile_x, tile_y, tile_z, reserved;
+    int32_t tile_x, tile_y, tile_z, no_graph;
 } to_params;
 
 /* Per-outer-iteration record (host copy). */

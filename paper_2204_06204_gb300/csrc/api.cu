@@ -11,6 +11,7 @@ int project_coop_blocks(int prec, int num_sms, int* out);
 int launch_rowsum(to_problem* P, cudaStream_t s);
 int run_inner(to_problem* P, void* u, int nsteps, int primary, cudaStream_t s);
 int refresh_preconditioner(to_problem* P, cudaStream_t s);
+int launch_filter_prescaled_T(to_problem* P, const void* x, void* y, cudaStream_t s);
 
 namespace {
 
@@ -120,6 +121,11 @@ extern "C" void to_destroy(to_problem* P) {
         dfree(L.b);
         dfree(L.t);
     }
+    if (P->gexec) cudaGraphExecDestroy(P->gexec);
+    if (P->gstream) cudaStreamSynchronize(P->gstream);
+    if (P->ev_in) cudaEventDestroy(P->ev_in);
+    if (P->ev_out) cudaEventDestroy(P->ev_out);
+    if (P->gstream) cudaStreamDestroy(P->gstream);
     void* p;
     p = P->ke_dev; dfree(p);
     p = P->sc; dfree(p);
@@ -170,6 +176,11 @@ extern "C" int to_create(const to_grid* g, const to_material* m, const to_loads*
         return bail(fail(TO_ERR_CUDA, "device query failed"));
     P->num_sms = dev_sms;
     if ((rc = project_coop_blocks(P->prec, P->num_sms, &P->coop_blocks))) return bail(rc);
+    if ((rc = operator_init(P))) return bail(rc);
+    if (cudaStreamCreateWithFlags(&P->gstream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&P->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&P->ev_out, cudaEventDisableTiming) != cudaSuccess)
+        return bail(fail(TO_ERR_CUDA, "stream / event creation failed"));
 
     // filter stencil: offsets with w = rmin - |d| > 0 (identity when rmin <= 0)
     std::vector<int4> st;
@@ -221,6 +232,9 @@ extern "C" int to_create(const to_grid* g, const to_material* m, const to_loads*
     P->red = (double*)p;
     if ((rc = dalloc(&p, sizeof(unsigned) * 64))) return bail(rc);
     P->counters = (unsigned*)p;
+    if ((rc = dalloc(&p, sizeof(to_stats) * 256))) return bail(rc);
+    P->dstats = (to_stats*)p;
+    P->dstats_cap = 256;
 
     // host-built tables: mask, load vector, stencil
     std::vector<uint8_t> hmask((size_t)P->n_node, 0);
@@ -328,7 +342,7 @@ extern "C" int to_sensitivity(to_problem* P, const void* u_dev, void* g_dev, voi
     if (!u_dev || !g_dev) return fail(TO_ERR_ARG, "null vector");
     int rc = launch_energy(P, u_dev, s);
     if (rc) return rc;
-    return launch_filter(P, P->gt, g_dev, 1, s);
+    return launch_filter_prescaled_T(P, P->gt, g_dev, s);
 }
 
 extern "C" int to_filter(to_problem* P, const void* x_dev, void* y_dev, int32_t transpose, void* stream) {
@@ -352,23 +366,74 @@ extern "C" int to_project(to_problem* P, const void* w_dev, void* rho_dev, doubl
     return TO_OK;
 }
 
+__global__ void k_reset_rec(to::DevScalars* sc) { sc->rec = 0; }
+
+// Capture one outer iteration on the library stream; on any failure the
+// iteration is launched kernel by kernel from then on.
+static int capture_outer(to_problem* P) {
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(P->gstream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        P->graph_state = -1;
+        return TO_OK;
+    }
+    const int rc = outer_iteration(P, P->gstream);
+    const cudaError_t e = cudaStreamEndCapture(P->gstream, &g);
+    if (rc != TO_OK || e != cudaSuccess || !g) {
+        cudaGetLastError();
+        if (g) cudaGraphDestroy(g);
+        P->graph_state = -1;
+        return TO_OK;
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&P->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+        cudaGetLastError();
+        P->gexec = nullptr;
+        P->graph_state = -1;
+        return TO_OK;
+    }
+    P->graph_state = 1;
+    return TO_OK;
+}
+
 extern "C" int to_step(to_problem* P, int32_t n_outer, to_stats* stats_out, void* stream) {
     TO_ENTER(P);
     if (n_outer < 0) return fail(TO_ERR_ARG, "n_outer must be >= 0");
     if (n_outer == 0) return TO_OK;
     if (n_outer > P->dstats_cap) {
         TO_CUDA(cudaStreamSynchronize(s));
+        TO_CUDA(cudaStreamSynchronize(P->gstream));
         void* p = P->dstats;
         dfree(p);
-        int cap = n_outer < 256 ? 256 : n_outer;
+        int cap = P->dstats_cap;
+        while (cap < n_outer) cap *= 2;
         if (int rc = dalloc(&p, sizeof(to_stats) * (size_t)cap)) return rc;
         P->dstats = (to_stats*)p;
         P->dstats_cap = cap;
+        if (P->gexec) cudaGraphExecDestroy(P->gexec);   // the captured record kernel holds the old ring
+        P->gexec = nullptr;
+        if (P->graph_state == 1) P->graph_state = 0;
     }
-    for (int i = 0; i < n_outer; ++i) {
-        int rc = outer_iteration(P, i, s);
+    // run on the library stream, ordered after the caller's stream and before its next work
+    TO_CUDA(cudaEventRecord(P->ev_in, s));
+    TO_CUDA(cudaStreamWaitEvent(P->gstream, P->ev_in, 0));
+    k_reset_rec<<<1, 1, 0, P->gstream>>>(P->sc);
+    TO_CUDA(cudaGetLastError());
+    if (P->prm.no_graph == 0 && P->graph_state == 0) {
+        int rc = capture_outer(P);
         if (rc) return rc;
     }
+    for (int i = 0; i < n_outer; ++i) {
+        if (P->graph_state == 1) {
+            TO_CUDA(cudaGraphLaunch(P->gexec, P->gstream));
+        } else {
+            int rc = outer_iteration(P, P->gstream);
+            if (rc) return rc;
+        }
+    }
+    TO_CUDA(cudaEventRecord(P->ev_out, P->gstream));
+    TO_CUDA(cudaStreamWaitEvent(s, P->ev_out, 0));
     if (stats_out) {
         TO_CUDA(cudaMemcpyAsync(stats_out, P->dstats, sizeof(to_stats) * (size_t)n_outer, cudaMemcpyDeviceToHost, s));
         TO_CUDA(cudaStreamSynchronize(s));

@@ -1,6 +1,8 @@
 // Design-side kernels: the density filter of Remark 3.1 (a linear cone of
 // radius rmin), the power-law moduli of Sec. III, the Jacobi diagonal, and the
 // chain rule of the sensitivity through the filter.
+#include <cmath>
+
 #include "device.cuh"
 
 namespace to {
@@ -8,26 +10,27 @@ namespace to {
 // ----------------------------------------------------------------------------- filter
 // forward:   y_e = sum_s w_s x_{e+s} / Hs_e
 // transpose: y_i = sum_s w_s x_{i+s} / Hs_{i+s}   (the stencil is symmetric)
-// Also reports max |y| and sum y (used when the output is the gradient).
-template <typename T, bool TRANSPOSE, bool STATS>
+// PRESCALED: the input already carries the 1 / Hs factor (the fused sensitivity
+// writes g~ / Hs), so the transpose is a plain weighted sum.
+// STATS also reports max |y| and sum y and fixes the step size alpha_k.
+template <typename T, bool TRANSPOSE, bool STATS, bool PRESCALED>
 __global__ void __launch_bounds__(256) k_filter(int nx, int ny, int nz, const T* __restrict__ x, T* __restrict__ y,
                                                 const T* __restrict__ Hs, const int4* __restrict__ st,
-                                                const T* __restrict__ w, int ns, double* red, unsigned* counter,
+                                                const T* __restrict__ w, int ns, int R, double* red, unsigned* counter,
                                                 DevScalars* sc, double alpha0_param, double alpha_scale, double m_exp) {
     __shared__ double sh[32 * kRedQ];
-    const long long n = (long long)nx * ny * nz;
     double amax = 0.0, sum = 0.0;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(e % nx);
-        const int j = (int)((e / nx) % ny);
-        const int k = (int)(e / ((long long)nx * ny));
+    const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y;
+    for (int k = blockIdx.z; k < nz && i < nx && j < ny; k += gridDim.z) {
+        const long long e = i + (long long)nx * (j + (long long)ny * k);
+        const bool interior = i >= R && i < nx - R && j >= R && j < ny - R && k >= R && k < nz - R;
         T acc = T(0);
         for (int s = 0; s < ns; ++s) {
             const int4 o = st[s];
             const int ii = i + o.x, jj = j + o.y, kk = k + o.z;
-            if (ii < 0 || ii >= nx || jj < 0 || jj >= ny || kk < 0 || kk >= nz) continue;
-            const long long m = ii + (long long)nx * (jj + (long long)ny * kk);
-            if (TRANSPOSE)
+            if (!interior && (ii < 0 || ii >= nx || jj < 0 || jj >= ny || kk < 0 || kk >= nz)) continue;
+            const long long m = e + o.x + (long long)nx * (o.y + (long long)ny * o.z);
+            if (TRANSPOSE && !PRESCALED)
                 acc += w[s] * x[m] / Hs[m];
             else
                 acc += w[s] * x[m];
@@ -44,7 +47,7 @@ __global__ void __launch_bounds__(256) k_filter(int nx, int ny, int nz, const T*
         const int kind[2] = {1, 0};
         double tot[2];
         block_reduce<2>(v, kind, sh);
-        if (finish_reduction<2>(v, kind, red, counter, tot, sh) && threadIdx.x == 0) {
+        if (finish_reduction<2>(v, kind, red, counter, tot, sh) && threadIdx.x == 0 && threadIdx.y == 0) {
             sc->gmax = tot[0];
             sc->gsum = tot[1];
             if (!isfinite(tot[0]) || !isfinite(tot[1])) set_err(&sc->err, TO_ERR_NONFINITE);
@@ -59,9 +62,10 @@ __global__ void __launch_bounds__(256) k_filter(int nx, int ny, int nz, const T*
 
 template <typename T>
 __global__ void k_filter_rowsum(int nx, int ny, int nz, T* Hs, const int4* st, const T* w, int ns) {
-    const long long n = (long long)nx * ny * nz;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(e % nx), j = (int)((e / nx) % ny), k = (int)(e / ((long long)nx * ny));
+    const Idx3 t = idx3(nx, ny, nz);
+    if (t.ok) {
+        const int i = t.i, j = t.j, k = t.k;
+        const long long e = i + (long long)nx * (j + (long long)ny * k);
         T acc = T(0);
         for (int s = 0; s < ns; ++s) {
             const int4 o = st[s];
@@ -95,24 +99,27 @@ __device__ __forceinline__ void simp(T rt, double E0, double Emin, double p, T& 
     Ed = (T)p * pw1 * dE;
 }
 
+// E and E' / Hs (the filter row sum is folded into E' so that the fused
+// sensitivity writes g~ / Hs, the input the filter transpose needs)
 template <typename T>
-__global__ void k_moduli(long long n, const T* rt, T* E, T* Ed, double E0, double Emin, double p, int* err) {
+__global__ void k_moduli(long long n, const T* rt, const T* Hs, T* E, T* Ed, double E0, double Emin, double p, int* err) {
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
         const T r = rt[e];
         if (!isfinite((double)r)) set_err(err, TO_ERR_NONFINITE);
         T a, b;
         simp<T>(r, E0, Emin, p, a, b);
         E[e] = a;
-        Ed[e] = b;
+        Ed[e] = b / Hs[e];
     }
 }
 
 // diag(K^): kdiag * sum of the moduli of the (up to 8) elements around a node; 1 on fixed DOFs
 template <typename T>
 __global__ void k_diag(int nx, int ny, int nz, const T* E, const uint8_t* mask, T* d, double kdiag) {
-    const long long nn = (long long)(nx + 1) * (ny + 1) * (nz + 1);
-    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < nn; n += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(n % (nx + 1)), j = (int)((n / (nx + 1)) % (ny + 1)), k = (int)(n / ((long long)(nx + 1) * (ny + 1)));
+    const Idx3 t = idx3(nx + 1, ny + 1, nz + 1);
+    if (t.ok) {
+        const int i = t.i, j = t.j, k = t.k;
+        const long long n = i + (long long)(nx + 1) * (j + (long long)(ny + 1) * k);
         T s = T(0);
         for (int dk = -1; dk <= 0; ++dk)
             for (int dj = -1; dj <= 0; ++dj)
@@ -136,41 +143,55 @@ static int grid_for(long long n, int threads, int num_sms) {
 }
 
 template <typename T>
-static int filter_t(to_problem* P, const void* x, void* y, int transpose, int stats, cudaStream_t s) {
-    const int nb = grid_for(P->n_elem, 256, P->num_sms);
+static int filter_t(to_problem* P, const void* x, void* y, int transpose, int stats, int prescaled, cudaStream_t s) {
     const T* Hs = (const T*)P->Hs;
     const T* w = (const T*)P->stencil_w;
-    if (transpose) {
-        if (stats)
-            k_filter<T, true, true><<<nb, 256, 0, s>>>(P->g.nx, P->g.ny, P->g.nz, (const T*)x, (T*)y, Hs, P->stencil, w,
-                                                       P->n_stencil, P->red, P->counters + 2, P->sc, P->prm.alpha0,
-                                                       P->prm.alpha_scale, P->prm.m);
-        else
-            k_filter<T, true, false><<<nb, 256, 0, s>>>(P->g.nx, P->g.ny, P->g.nz, (const T*)x, (T*)y, Hs, P->stencil, w,
-                                                        P->n_stencil, nullptr, nullptr, nullptr, 0.0, 0.0, 0.0);
-    } else {
-        k_filter<T, false, false><<<nb, 256, 0, s>>>(P->g.nx, P->g.ny, P->g.nz, (const T*)x, (T*)y, Hs, P->stencil, w,
-                                                     P->n_stencil, nullptr, nullptr, nullptr, 0.0, 0.0, 0.0);
+    const int nx = P->g.nx, ny = P->g.ny, nz = P->g.nz;
+    const int R = (int)std::ceil(P->mat.rmin);
+    dim3 grid = grid3(nx, ny, nz);
+    if (stats) {
+        // one reduction slot per block: fold z into the kernel's loop when the grid would exceed the slots
+        const long long per_z = (long long)grid.x * grid.y;
+        long long gz = kMaxRedBlocks / per_z;
+        if (gz < 1) return fail(TO_ERR_ARG, "filter grid exceeds the reduction scratch");
+        if (gz < nz) grid.z = (unsigned)gz;
     }
+#define TO_FILTER_ARGS nx, ny, nz, (const T*)x, (T*)y, Hs, P->stencil, w, P->n_stencil, R
+    if (transpose && stats && prescaled)
+        k_filter<T, true, true, true><<<grid, block3(), 0, s>>>(TO_FILTER_ARGS, P->red, P->counters + 2, P->sc,
+                                                                 P->prm.alpha0, P->prm.alpha_scale, P->prm.m);
+    else if (transpose && prescaled)
+        k_filter<T, true, false, true><<<grid, block3(), 0, s>>>(TO_FILTER_ARGS, nullptr, nullptr, nullptr, 0.0, 0.0, 0.0);
+    else if (transpose)
+        k_filter<T, true, false, false><<<grid, block3(), 0, s>>>(TO_FILTER_ARGS, nullptr, nullptr, nullptr, 0.0, 0.0, 0.0);
+    else
+        k_filter<T, false, false, false><<<grid, block3(), 0, s>>>(TO_FILTER_ARGS, nullptr, nullptr, nullptr, 0.0, 0.0, 0.0);
+#undef TO_FILTER_ARGS
     TO_CUDA(cudaGetLastError());
     return TO_OK;
 }
 
 int launch_filter(to_problem* P, const void* x, void* y, int transpose, cudaStream_t s) {
-    return P->prec == TO_FP64 ? filter_t<double>(P, x, y, transpose, 0, s) : filter_t<float>(P, x, y, transpose, 0, s);
+    return P->prec == TO_FP64 ? filter_t<double>(P, x, y, transpose, 0, 0, s) : filter_t<float>(P, x, y, transpose, 0, 0, s);
+}
+
+// g = C^T g~ from the prescaled g~ / Hs that the sensitivity kernels write
+int launch_filter_prescaled_T(to_problem* P, const void* x, void* y, cudaStream_t s) {
+    return P->prec == TO_FP64 ? filter_t<double>(P, x, y, 1, 0, 1, s) : filter_t<float>(P, x, y, 1, 0, 1, s);
 }
 
 int launch_sens_filter_T(to_problem* P, cudaStream_t s) {
-    return P->prec == TO_FP64 ? filter_t<double>(P, P->gt, P->grad, 1, 1, s) : filter_t<float>(P, P->gt, P->grad, 1, 1, s);
+    return P->prec == TO_FP64 ? filter_t<double>(P, P->gt, P->grad, 1, 1, 1, s)
+                              : filter_t<float>(P, P->gt, P->grad, 1, 1, 1, s);
 }
 
 template <typename T>
 static int moduli_t(to_problem* P, cudaStream_t s) {
-    int rc = filter_t<T>(P, P->rho, P->rhot, 0, 0, s);
+    int rc = filter_t<T>(P, P->rho, P->rhot, 0, 0, 0, s);
     if (rc) return rc;
     const int nb = grid_for(P->n_elem, 256, P->num_sms);
-    k_moduli<T><<<nb, 256, 0, s>>>(P->n_elem, (const T*)P->rhot, (T*)P->lv[0].E, (T*)P->Ed, P->mat.E0, P->mat.Emin,
-                                   P->mat.p, &P->sc->err);
+    k_moduli<T><<<nb, 256, 0, s>>>(P->n_elem, (const T*)P->rhot, (const T*)P->Hs, (T*)P->lv[0].E, (T*)P->Ed,
+                                   P->mat.E0, P->mat.Emin, P->mat.p, &P->sc->err);
     TO_CUDA(cudaGetLastError());
     return TO_OK;
 }
@@ -183,7 +204,9 @@ template <typename T>
 static int diag_t(to_problem* P, int level, cudaStream_t s) {
     const Level& L = P->lv[level];
     const int nb = grid_for(L.n_node, 256, P->num_sms);
-    k_diag<T><<<nb, 256, 0, s>>>(L.nx, L.ny, L.nz, (const T*)L.E, L.mask, (T*)L.d, L.kdiag);
+    (void)nb;
+    k_diag<T><<<grid3(L.nx + 1, L.ny + 1, L.nz + 1), block3(), 0, s>>>(L.nx, L.ny, L.nz, (const T*)L.E, L.mask,
+                                                                      (T*)L.d, L.kdiag);
     TO_CUDA(cudaGetLastError());
     return TO_OK;
 }
@@ -193,26 +216,29 @@ int launch_diag(to_problem* P, int level, cudaStream_t s) {
 }
 
 int launch_rowsum(to_problem* P, cudaStream_t s) {
-    const int nb = grid_for(P->n_elem, 256, P->num_sms);
+    const dim3 nb = grid3(P->g.nx, P->g.ny, P->g.nz);
+    const dim3 b3 = block3();
     if (P->prec == TO_FP64)
-        k_filter_rowsum<double><<<nb, 256, 0, s>>>(P->g.nx, P->g.ny, P->g.nz, (double*)P->Hs, P->stencil,
+        k_filter_rowsum<double><<<nb, b3, 0, s>>>(P->g.nx, P->g.ny, P->g.nz, (double*)P->Hs, P->stencil,
                                                    (const double*)P->stencil_w, P->n_stencil);
     else
-        k_filter_rowsum<float><<<nb, 256, 0, s>>>(P->g.nx, P->g.ny, P->g.nz, (float*)P->Hs, P->stencil,
+        k_filter_rowsum<float><<<nb, b3, 0, s>>>(P->g.nx, P->g.ny, P->g.nz, (float*)P->Hs, P->stencil,
                                                   (const float*)P->stencil_w, P->n_stencil);
     TO_CUDA(cudaGetLastError());
     return TO_OK;
 }
 
 // ----------------------------------------------------------------------------- element energy
-// gt_e = -E'_e u_e^T k_e u_e  (Sec. III exact-gradient formula applied to u, J = f^T u)
+// gt_e = -E'_e u_e^T k_e u_e / Hs_e (Sec. III exact-gradient formula applied to u, J = f^T u;
+// the 1 / Hs factor of the filter transpose is carried by the stored E' / Hs)
 template <typename T>
 __global__ void __launch_bounds__(256) k_energy(int nx, int ny, int nz, const T* __restrict__ u, const uint8_t* mask,
                                                 const T* __restrict__ Ed, T* __restrict__ gt, HaarK<T> kh) {
-    const long long n = (long long)nx * ny * nz;
     const int nxn = nx + 1, nyn = ny + 1;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(e % nx), j = (int)((e / nx) % ny), k = (int)(e / ((long long)nx * ny));
+    const Idx3 t = idx3(nx, ny, nz);
+    if (t.ok) {
+        const int i = t.i, j = t.j, k = t.k;
+        const long long e = i + (long long)nx * (j + (long long)ny * k);
         T nv[2][2][2][3];
         for (int c2 = 0; c2 < 2; ++c2)
             for (int b2 = 0; b2 < 2; ++b2)
@@ -258,16 +284,17 @@ __global__ void __launch_bounds__(256) k_energy(int nx, int ny, int nz, const T*
 }
 
 int launch_energy(to_problem* P, const void* u, cudaStream_t s) {
-    const int nb = grid_for(P->n_elem, 256, P->num_sms);
+    const dim3 nb = grid3(P->g.nx, P->g.ny, P->g.nz);
+    const dim3 b3 = block3();
     if (P->prec == TO_FP64) {
         HaarK<double> kh;
         for (int i = 0; i < kHaarNnz; ++i) kh.v[i] = P->haar[i];
-        k_energy<double><<<nb, 256, 0, s>>>(P->g.nx, P->g.ny, P->g.nz, (const double*)u, P->lv[0].mask,
+        k_energy<double><<<nb, b3, 0, s>>>(P->g.nx, P->g.ny, P->g.nz, (const double*)u, P->lv[0].mask,
                                             (const double*)P->Ed, (double*)P->gt, kh);
     } else {
         HaarK<float> kh;
         for (int i = 0; i < kHaarNnz; ++i) kh.v[i] = (float)P->haar[i];
-        k_energy<float><<<nb, 256, 0, s>>>(P->g.nx, P->g.ny, P->g.nz, (const float*)u, P->lv[0].mask,
+        k_energy<float><<<nb, b3, 0, s>>>(P->g.nx, P->g.ny, P->g.nz, (const float*)u, P->lv[0].mask,
                                            (const float*)P->Ed, (float*)P->gt, kh);
     }
     TO_CUDA(cudaGetLastError());

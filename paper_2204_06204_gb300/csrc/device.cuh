@@ -119,4 +119,20 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err) {
 
 __device__ __forceinline__ void set_err(int* err, int code) { atomicCAS(err, 0, code); }
 
+// 3-D lattice launches: block (32, 8), grid (ceil(X/32), ceil(Y/8), Z); no divisions per thread.
+inline dim3 grid3(int X, int Y, int Z) { return dim3((unsigned)((X + 31) / 32), (unsigned)((Y + 7) / 8), (unsigned)Z); }
+inline dim3 block3() { return dim3(32, 8, 1); }
+struct Idx3 {
+    int i, j, k;
+    bool ok;
+};
+__device__ __forceinline__ Idx3 idx3(int X, int Y, int Z) {
+    Idx3 r;
+    r.i = blockIdx.x * 32 + threadIdx.x;
+    r.j = blockIdx.y * 8 + threadIdx.y;
+    r.k = blockIdx.z;
+    r.ok = r.i < X && r.j < Y && r.k < Z;
+    return r;
+}
+
 }  // namespace to

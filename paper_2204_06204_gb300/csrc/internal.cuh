@@ -35,7 +35,7 @@ struct DevScalars {
     int err;                           // first device-side error (TO_ERR_*), 0 if none
     int proj_iters;
     int n_inner_done;
-    int pad;
+    int rec;                           // next stats slot written by the record kernel
 };
 
 // Reduction scratch: one slot of up to kRedQ doubles per block, plus a
@@ -127,6 +127,12 @@ struct to_problem {
     to_stats* dstats = nullptr;    // device stats ring
     int dstats_cap = 0;
 
+    // captured outer iteration (replayed by to_step) on a library-owned stream
+    cudaStream_t gstream = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    int graph_state = 0;           // 0: not captured yet, 1: ready, -1: capture unavailable
+
     // launch configuration of the operator kernel
     int tile_x = 32, tile_y = 8, tile_z = 8;
     int num_sms = 0;
@@ -153,7 +159,8 @@ int launch_update_sd(to_problem* P, cudaStream_t s);
 int launch_precond(to_problem* P, const void* r, void* z, cudaStream_t s);
 int launch_sens_filter_T(to_problem* P, cudaStream_t s);
 int launch_energy(to_problem* P, const void* u, cudaStream_t s);
-int launch_record(to_problem* P, int slot, cudaStream_t s);
+int launch_record(to_problem* P, cudaStream_t s);
+int operator_init(to_problem* P);
 int launch_richardson(to_problem* P, cudaStream_t s);
 
 // multigrid
@@ -161,7 +168,7 @@ int mg_build(to_problem* P);
 int mg_refresh(to_problem* P, cudaStream_t s);   // coarse moduli, diagonals, coarse factor
 int mg_vcycle(to_problem* P, const void* r, void* z, cudaStream_t s);
 
-int outer_iteration(to_problem* P, int slot, cudaStream_t s);
+int outer_iteration(to_problem* P, cudaStream_t s);
 int inner_steps(to_problem* P, int nsteps, int from_resid, cudaStream_t s);
 
 }  // namespace to

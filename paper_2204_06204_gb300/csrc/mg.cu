@@ -34,10 +34,11 @@ static int grid1(long long n, int num_sms) {
 
 template <typename T>
 __global__ void k_coarsen_E(int cx, int cy, int cz, const T* __restrict__ Ef, T* __restrict__ Ec) {
-    const long long n = (long long)cx * cy * cz;
     const int fx = 2 * cx, fy = 2 * cy;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-        const int I = (int)(e % cx), J = (int)((e / cx) % cy), K = (int)(e / ((long long)cx * cy));
+    const Idx3 t = idx3(cx, cy, cz);
+    if (t.ok) {
+        const int I = t.i, J = t.j, K = t.k;
+        const long long e = I + (long long)cx * (J + (long long)cy * K);
         T s = T(0);
         for (int c = 0; c < 2; ++c)
             for (int b = 0; b < 2; ++b)
@@ -51,10 +52,11 @@ __global__ void k_coarsen_E(int cx, int cy, int cz, const T* __restrict__ Ef, T*
 template <typename T>
 __global__ void k_restrict(int cx, int cy, int cz, const T* __restrict__ tf, const uint8_t* __restrict__ mf,
                            const uint8_t* __restrict__ mc, T* __restrict__ bc) {
-    const long long nn = (long long)(cx + 1) * (cy + 1) * (cz + 1);
     const int fx = 2 * cx, fy = 2 * cy, fz = 2 * cz;
-    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < nn; n += (long long)gridDim.x * blockDim.x) {
-        const int I = (int)(n % (cx + 1)), J = (int)((n / (cx + 1)) % (cy + 1)), K = (int)(n / ((long long)(cx + 1) * (cy + 1)));
+    const Idx3 t = idx3(cx + 1, cy + 1, cz + 1);
+    if (t.ok) {
+        const int I = t.i, J = t.j, K = t.k;
+        const long long n = I + (long long)(cx + 1) * (J + (long long)(cy + 1) * K);
         T acc[3] = {T(0), T(0), T(0)};
         for (int dk = -1; dk <= 1; ++dk) {
             const int k = 2 * K + dk;
@@ -85,11 +87,12 @@ template <typename T>
 __global__ void k_prolong_add(int cx, int cy, int cz, const T* __restrict__ xc, const uint8_t* __restrict__ mc,
                               const uint8_t* __restrict__ mf, T* __restrict__ xf) {
     const int fx = 2 * cx, fy = 2 * cy, fz = 2 * cz;
-    const long long nn = (long long)(fx + 1) * (fy + 1) * (fz + 1);
-    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < nn; n += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(n % (fx + 1)), j = (int)((n / (fx + 1)) % (fy + 1)), k = (int)(n / ((long long)(fx + 1) * (fy + 1)));
+    const Idx3 t = idx3(fx + 1, fy + 1, fz + 1);
+    if (t.ok) {
+        const int i = t.i, j = t.j, k = t.k;
+        const long long n = i + (long long)(fx + 1) * (j + (long long)(fy + 1) * k);
         const uint8_t m = mf[n];
-        if (m == 7) continue;
+        if (m == 7) return;
         const int i0 = i >> 1, i1 = (i + 1) >> 1, j0 = j >> 1, j1 = (j + 1) >> 1, k0 = k >> 1, k1 = (k + 1) >> 1;
         T acc[3] = {T(0), T(0), T(0)};
         for (int kc = k0; kc <= k1; ++kc)
@@ -206,6 +209,96 @@ __global__ void __launch_bounds__(1024) k_dense_invert(const T* __restrict__ A, 
     for (int i = tid; i < n; i += nt) sc[i] = s[i];
 }
 
+// Register-blocked variant for n <= 160: thread (tx, ty) of a 32 x 32 block keeps
+// entries (ty + 32a, tx + 32b), a, b < 5, in registers; each elimination step
+// publishes the pivot row and column through double-buffered shared memory
+// (one barrier per step) and updates the held entries in place.
+constexpr int kRegDof = 160;
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_dense_invert_reg(const T* __restrict__ A, T* __restrict__ Ainv,
+                                                           T* __restrict__ sc, int n, int* err) {
+    __shared__ T rowb[2][kRegDof];
+    __shared__ T colb[2][kRegDof];
+    __shared__ T s[kRegDof];
+    __shared__ int bad;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + 32 * ty;
+    if (tid == 0) bad = 0;
+    __syncthreads();
+    for (int i = tid; i < n; i += 1024) {
+        const T d = A[(long long)i * n + i];
+        s[i] = d > T(0) ? T(1) / sqrt(d) : T(0);
+        if (!(d > T(0))) bad = 1;
+    }
+    __syncthreads();
+    if (bad) {
+        if (tid == 0) set_err(err, TO_ERR_SINGULAR);
+        return;
+    }
+    T R[5][5];
+#pragma unroll
+    for (int a = 0; a < 5; ++a)
+#pragma unroll
+        for (int b = 0; b < 5; ++b) {
+            const int i = ty + 32 * a, j = tx + 32 * b;
+            R[a][b] = (i < n && j < n) ? s[i] * A[(long long)i * n + j] * s[j] : T(0);
+        }
+    for (int k = 0; k < n; ++k) {
+        const int buf = k & 1, ka = k >> 5, kr = k & 31;
+        // publish the pivot row (old values) and column
+        if (ty == kr) {
+#pragma unroll
+            for (int b = 0; b < 5; ++b)
+                if (ka == 0) rowb[buf][tx + 32 * b] = R[0][b];
+                else if (ka == 1) rowb[buf][tx + 32 * b] = R[1][b];
+                else if (ka == 2) rowb[buf][tx + 32 * b] = R[2][b];
+                else if (ka == 3) rowb[buf][tx + 32 * b] = R[3][b];
+                else rowb[buf][tx + 32 * b] = R[4][b];
+        }
+        if (tx == kr) {
+#pragma unroll
+            for (int a = 0; a < 5; ++a)
+                if (ka == 0) colb[buf][ty + 32 * a] = R[a][0];
+                else if (ka == 1) colb[buf][ty + 32 * a] = R[a][1];
+                else if (ka == 2) colb[buf][ty + 32 * a] = R[a][2];
+                else if (ka == 3) colb[buf][ty + 32 * a] = R[a][3];
+                else colb[buf][ty + 32 * a] = R[a][4];
+        }
+        __syncthreads();
+        const T piv = rowb[buf][k];
+        if (!(piv > T(0))) {
+            if (tid == 0) set_err(err, TO_ERR_SINGULAR);
+            return;
+        }
+        const T ip = T(1) / piv;
+        T rn[5], co[5];
+#pragma unroll
+        for (int b = 0; b < 5; ++b) {
+            const int j = tx + 32 * b;
+            rn[b] = (j == k ? T(1) : rowb[buf][j < kRegDof ? j : 0]) * ip;
+        }
+#pragma unroll
+        for (int a = 0; a < 5; ++a) co[a] = colb[buf][(ty + 32 * a) < kRegDof ? ty + 32 * a : 0];
+#pragma unroll
+        for (int a = 0; a < 5; ++a) {
+            const bool rowk = (ty + 32 * a) == k;
+#pragma unroll
+            for (int b = 0; b < 5; ++b) {
+                const bool colk = (tx + 32 * b) == k;
+                R[a][b] = rowk ? rn[b] : (colk ? T(0) : R[a][b]) - co[a] * rn[b];
+            }
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 5; ++a)
+#pragma unroll
+        for (int b = 0; b < 5; ++b) {
+            const int i = ty + 32 * a, j = tx + 32 * b;
+            if (i < n && j < n) Ainv[(long long)i * n + j] = R[a][b];
+        }
+    for (int i = tid; i < n; i += 1024) sc[i] = s[i];
+}
+
 // x = S Ainv S b   (one CTA per row block)
 template <typename T>
 __global__ void k_dense_solve(const T* __restrict__ Ainv, const T* __restrict__ sc, const T* __restrict__ b,
@@ -304,7 +397,7 @@ static int refresh_t(to_problem* P, cudaStream_t s) {
     const int L = (int)P->lv.size();
     for (int l = 1; l < L; ++l) {
         const Level& C = P->lv[l];
-        k_coarsen_E<T><<<grid1(C.n_elem, P->num_sms), 256, 0, s>>>(C.nx, C.ny, C.nz, (const T*)P->lv[l - 1].E, (T*)C.E);
+        k_coarsen_E<T><<<grid3(C.nx, C.ny, C.nz), block3(), 0, s>>>(C.nx, C.ny, C.nz, (const T*)P->lv[l - 1].E, (T*)C.E);
         TO_CUDA(cudaGetLastError());
         int rc = launch_diag(P, l, s);
         if (rc) return rc;
@@ -316,7 +409,9 @@ static int refresh_t(to_problem* P, cudaStream_t s) {
     TO_CUDA(cudaGetLastError());
     const size_t smem = (size_t)n * n * sizeof(T);
     T* inv = (T*)P->coarse_L;
-    if (smem <= smem_cap<T>())
+    if (n <= kRegDof)
+        k_dense_invert_reg<T><<<1, dim3(32, 32), 0, s>>>((const T*)P->coarse_A, inv, inv + (size_t)n * n, n, &P->sc->err);
+    else if (smem <= smem_cap<T>())
         k_dense_invert<T, true><<<1, dim3(32, 32), smem, s>>>((const T*)P->coarse_A, inv, inv + (size_t)n * n, n, &P->sc->err);
     else
         k_dense_invert<T, false><<<1, dim3(32, 32), 0, s>>>((const T*)P->coarse_A, inv, inv + (size_t)n * n, n, &P->sc->err);
@@ -358,10 +453,10 @@ static int vcycle_t(to_problem* P, int l, const void* b, void* x, void* t, cudaS
     // residual into oth, restrict to the coarse right-hand side
     if ((rc = launch_operator(P, l, OP_BMINUS, cur, oth, b, s))) return rc;
     const Level& C = P->lv[l + 1];
-    k_restrict<T><<<grid1(C.n_node, P->num_sms), 256, 0, s>>>(C.nx, C.ny, C.nz, (const T*)oth, F.mask, C.mask, (T*)C.b);
+    k_restrict<T><<<grid3(C.nx + 1, C.ny + 1, C.nz + 1), block3(), 0, s>>>(C.nx, C.ny, C.nz, (const T*)oth, F.mask, C.mask, (T*)C.b);
     TO_CUDA(cudaGetLastError());
     if ((rc = vcycle_t<T>(P, l + 1, C.b, C.x, C.t, s))) return rc;
-    k_prolong_add<T><<<grid1(F.n_node, P->num_sms), 256, 0, s>>>(C.nx, C.ny, C.nz, (const T*)C.x, C.mask, F.mask, (T*)cur);
+    k_prolong_add<T><<<grid3(F.nx + 1, F.ny + 1, F.nz + 1), block3(), 0, s>>>(C.nx, C.ny, C.nz, (const T*)C.x, C.mask, F.mask, (T*)cur);
     TO_CUDA(cudaGetLastError());
     for (int it = 0; it < nu2; ++it) {
         if ((rc = launch_operator(P, l, OP_SMOOTH, cur, oth, b, s, om))) return rc;

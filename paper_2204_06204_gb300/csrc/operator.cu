@@ -492,14 +492,6 @@ static int launch_t(to_problem* P, int level, int mode, const void* x, void* y, 
         return fail(TO_ERR_ARG, "operator grid exceeds the reduction scratch; raise tile_z");
     dim3 grid(gx, gy, gz), block(TX, TY);
     const size_t smem = sizeof(OpSmem<T, TX, TY, kRing>);
-    static bool attr_set = false;   // per (T, TX, TY) instantiation
-    if (!attr_set) {
-        const void* fns[5] = {(const void*)k_operator<T, TX, TY, OP_APPLY>, (const void*)k_operator<T, TX, TY, OP_RESID>,
-                              (const void*)k_operator<T, TX, TY, OP_Q>, (const void*)k_operator<T, TX, TY, OP_SMOOTH>,
-                              (const void*)k_operator<T, TX, TY, OP_BMINUS>};
-        for (const void* f : fns) TO_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr_set = true;
-    }
     switch (mode) {
         case OP_APPLY: k_operator<T, TX, TY, OP_APPLY><<<grid, block, smem, s>>>(a); break;
         case OP_RESID: k_operator<T, TX, TY, OP_RESID><<<grid, block, smem, s>>>(a); break;
@@ -510,6 +502,21 @@ static int launch_t(to_problem* P, int level, int mode, const void* x, void* y, 
     }
     TO_CUDA(cudaGetLastError());
     return TO_OK;
+}
+
+template <typename T, int TX, int TY>
+static int init_t() {
+    const size_t smem = sizeof(OpSmem<T, TX, TY, kRing>);
+    const void* fns[5] = {(const void*)k_operator<T, TX, TY, OP_APPLY>, (const void*)k_operator<T, TX, TY, OP_RESID>,
+                          (const void*)k_operator<T, TX, TY, OP_Q>, (const void*)k_operator<T, TX, TY, OP_SMOOTH>,
+                          (const void*)k_operator<T, TX, TY, OP_BMINUS>};
+    for (const void* f : fns) TO_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    return TO_OK;
+}
+
+// shared-memory opt-in of the operator kernels (on the problem's device, before any capture)
+int operator_init(to_problem* P) {
+    return P->prec == TO_FP64 ? init_t<double, 32, 8>() : init_t<float, 32, 8>();
 }
 
 int launch_operator(to_problem* P, int level, int mode, const void* x, void* y, const void* b,

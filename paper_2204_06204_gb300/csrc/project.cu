@@ -69,12 +69,41 @@ template <> struct Thresh<double> {
     __device__ int cls(double w) const { return w >= tu ? 0 : (w <= tl ? 1 : 2); }
 };
 
+// Totals of the per-block partials of one pass: warp 0 folds a lane-strided
+// subset in block order and reduces in a fixed tree, then broadcasts through
+// shared memory (identical, deterministic totals in every block).
+template <int NQ>
+__device__ __forceinline__ void combine_partials(const double* part, unsigned nb, const int (&kind)[NQ], double (&tot)[NQ],
+                                                 double* shb) {
+    if (threadIdx.x < 32) {
+        double acc[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) acc[q] = kind[q] ? -INFINITY : 0.0;
+        for (unsigned b = threadIdx.x; b < nb; b += 32)
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                const double t = __ldcg(part + b * kProjSlot + q);
+                acc[q] = kind[q] ? fmax(acc[q], t) : acc[q] + t;
+            }
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) acc[q] = kind[q] ? warp_max(acc[q]) : warp_sum(acc[q]);
+        if (threadIdx.x == 0)
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) shb[q] = acc[q];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) tot[q] = shb[q];
+    __syncthreads();
+}
+
 template <typename T, bool CACHE>
 __global__ void __launch_bounds__(256) k_project(const ProjArgs<T> a) {
     extern __shared__ unsigned char smem_raw[];
     T* wloc = reinterpret_cast<T*>(smem_raw);
     __shared__ double sh[32 * kRedQ];
     __shared__ double sh8[32 * 8];
+    __shared__ double shb[8];
     const unsigned nb = gridDim.x, bid = blockIdx.x;
     const long long b0 = (long long)bid * a.chunk;
     const long long b1 = min(b0 + a.chunk, a.n);
@@ -110,12 +139,7 @@ __global__ void __launch_bounds__(256) k_project(const ProjArgs<T> a) {
         if (tid == 0)
             for (int q = 0; q < 6; ++q) a.part[(parity * nb + bid) * kProjSlot + q] = mv[q];
         if (!grid_barrier(a.bar, &sc->err)) return;
-        for (int q = 0; q < 6; ++q) tot[q] = (q >= 4) ? -INFINITY : 0.0;
-        for (unsigned b = 0; b < nb; ++b)
-            for (int q = 0; q < 6; ++q) {
-                const double t = __ldcg(a.part + (parity * nb + b) * kProjSlot + q);
-                tot[q] = (q >= 4) ? fmax(tot[q], t) : tot[q] + t;
-            }
+        combine_partials<6>(a.part + parity * nb * kProjSlot, nb, kind, tot, shb);
         parity ^= 1;
     }
     const double wmin = -tot[4], wmax = tot[5];
@@ -152,9 +176,8 @@ __global__ void __launch_bounds__(256) k_project(const ProjArgs<T> a) {
         if (tid == 0)
             for (int q = 0; q < 4; ++q) a.part[(parity * nb + bid) * kProjSlot + q] = v[q];
         if (!grid_barrier(a.bar, &sc->err)) return;
-        double t4[4] = {0.0, 0.0, 0.0, 0.0};
-        for (unsigned b = 0; b < nb; ++b)
-            for (int q = 0; q < 4; ++q) t4[q] += __ldcg(a.part + (parity * nb + b) * kProjSlot + q);
+        double t4[4];
+        combine_partials<4>(a.part + parity * nb * kProjSlot, nb, kind, t4, shb);
         parity ^= 1;
         const double nF = t4[2];
         S = t4[0] * a.hi + t4[1] * a.lo + t4[3] - lambda * nF;

@@ -76,7 +76,7 @@ __global__ void k_axpy(long long n, T* __restrict__ u, const T* __restrict__ z, 
         u[i] += beta * z[i];
 }
 
-__global__ void k_record(DevScalars* sc, to_stats* st, int slot) {
+__global__ void k_record(DevScalars* sc, to_stats* st, int cap) {
     to_stats s;
     s.k = sc->k;
     s.J = sc->J;
@@ -91,7 +91,9 @@ __global__ void k_record(DevScalars* sc, to_stats* st, int slot) {
     s.beta_last = sc->beta;
     s.proj_iters = sc->proj_iters;
     s.status = sc->err;
-    st[slot] = s;
+    const int slot = sc->rec;
+    if (slot >= 0 && slot < cap) st[slot] = s;
+    sc->rec = slot + 1;
     sc->k += 1;
     sc->beta_first = 0.0;
     sc->beta = 0.0;
@@ -102,8 +104,8 @@ __global__ void k_set_beta(DevScalars* sc, double beta) {
     if (sc->beta_first == 0.0) sc->beta_first = beta;
 }
 
-int launch_record(to_problem* P, int slot, cudaStream_t s) {
-    k_record<<<1, 1, 0, s>>>(P->sc, P->dstats, slot);
+int launch_record(to_problem* P, cudaStream_t s) {
+    k_record<<<1, 1, 0, s>>>(P->sc, P->dstats, P->dstats_cap);
     TO_CUDA(cudaGetLastError());
     return TO_OK;
 }
@@ -185,14 +187,14 @@ int refresh_preconditioner(to_problem* P, cudaStream_t s) {
     return TO_OK;
 }
 
-int outer_iteration(to_problem* P, int slot, cudaStream_t s) {
+int outer_iteration(to_problem* P, cudaStream_t s) {
     int rc;
     if ((rc = launch_moduli(P, s))) return rc;
     if ((rc = refresh_preconditioner(P, s))) return rc;
     if ((rc = run_inner(P, P->u, P->prm.n_inner, 1, s))) return rc;
     if ((rc = launch_sens_filter_T(P, s))) return rc;
     if ((rc = launch_project(P, nullptr, P->rho, P->grad, P->rho, 1, s))) return rc;
-    return launch_record(P, slot, s);
+    return launch_record(P, s);
 }
 
 }  // namespace to
