@@ -125,6 +125,10 @@ extern "C" void to_destroy(to_problem* P) {
     if (P->gstream) cudaStreamSynchronize(P->gstream);
     if (P->ev_in) cudaEventDestroy(P->ev_in);
     if (P->ev_out) cudaEventDestroy(P->ev_out);
+    if (P->side) cudaStreamSynchronize(P->side);
+    if (P->ev_fork) cudaEventDestroy(P->ev_fork);
+    if (P->ev_join) cudaEventDestroy(P->ev_join);
+    if (P->side) cudaStreamDestroy(P->side);
     if (P->gstream) cudaStreamDestroy(P->gstream);
     void* p;
     p = P->ke_dev; dfree(p);
@@ -191,7 +195,7 @@ extern "C" int to_create(const to_grid* g, const to_material* m, const to_loads*
             for (int dx = -R; dx <= R; ++dx) {
                 const double w = m->rmin - std::sqrt((double)(dx * dx + dy * dy + dz * dz));
                 if (w > 0.0) {
-                    st.push_back(make_int4(dx, dy, dz, 0));
+                    st.push_back(make_int4(dx, dy, dz, dx + g->nx * (dy + g->ny * dz)));
                     sw.push_back(w);
                 }
             }
@@ -199,6 +203,7 @@ extern "C" int to_create(const to_grid* g, const to_material* m, const to_loads*
         st.push_back(make_int4(0, 0, 0, 0));
         sw.push_back(1.0);
     }
+    if (st.size() > 1024) return bail(fail(TO_ERR_ARG, "filter radius too large (more than 1024 stencil points)"));
     P->n_stencil = (int)st.size();
 
     // level 0 (the fine grid)

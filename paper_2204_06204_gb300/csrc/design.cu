@@ -7,6 +7,8 @@
 
 namespace to {
 
+constexpr int kMaxStencil = 1024;   // cone of radius < 6 voxels
+
 // ----------------------------------------------------------------------------- filter
 // forward:   y_e = sum_s w_s x_{e+s} / Hs_e
 // transpose: y_i = sum_s w_s x_{i+s} / Hs_{i+s}   (the stencil is symmetric)
@@ -19,6 +21,13 @@ __global__ void __launch_bounds__(256) k_filter(int nx, int ny, int nz, const T*
                                                 const T* __restrict__ w, int ns, int R, double* red, unsigned* counter,
                                                 DevScalars* sc, double alpha0_param, double alpha_scale, double m_exp) {
     __shared__ double sh[32 * kRedQ];
+    __shared__ int4 s_st[kMaxStencil];
+    __shared__ T s_w[kMaxStencil];
+    for (int q = threadIdx.x + 32 * threadIdx.y; q < ns; q += 256) {
+        s_st[q] = st[q];
+        s_w[q] = w[q];
+    }
+    __syncthreads();
     double amax = 0.0, sum = 0.0;
     const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y;
     for (int k = blockIdx.z; k < nz && i < nx && j < ny; k += gridDim.z) {
@@ -26,14 +35,14 @@ __global__ void __launch_bounds__(256) k_filter(int nx, int ny, int nz, const T*
         const bool interior = i >= R && i < nx - R && j >= R && j < ny - R && k >= R && k < nz - R;
         T acc = T(0);
         for (int s = 0; s < ns; ++s) {
-            const int4 o = st[s];
+            const int4 o = s_st[s];
             const int ii = i + o.x, jj = j + o.y, kk = k + o.z;
             if (!interior && (ii < 0 || ii >= nx || jj < 0 || jj >= ny || kk < 0 || kk >= nz)) continue;
-            const long long m = e + o.x + (long long)nx * (o.y + (long long)ny * o.z);
+            const long long m = e + o.w;   // precomputed linear offset
             if (TRANSPOSE && !PRESCALED)
-                acc += w[s] * x[m] / Hs[m];
+                acc += s_w[s] * x[m] / Hs[m];
             else
-                acc += w[s] * x[m];
+                acc += s_w[s] * x[m];
         }
         const T out = TRANSPOSE ? acc : acc / Hs[e];
         y[e] = out;

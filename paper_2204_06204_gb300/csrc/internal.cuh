@@ -132,6 +132,8 @@ struct to_problem {
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     cudaGraphExec_t gexec = nullptr;
     int graph_state = 0;           // 0: not captured yet, 1: ready, -1: capture unavailable
+    cudaStream_t side = nullptr;   // branch for the coarsest inverse (overlaps the fine-level work)
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 
     // launch configuration of the operator kernel
     int tile_x = 32, tile_y = 8, tile_z = 8;

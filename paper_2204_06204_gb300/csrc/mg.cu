@@ -275,18 +275,33 @@ __global__ void __launch_bounds__(1024) k_dense_invert_reg(const T* __restrict__
 #pragma unroll
         for (int b = 0; b < 5; ++b) {
             const int j = tx + 32 * b;
-            rn[b] = (j == k ? T(1) : rowb[buf][j < kRegDof ? j : 0]) * ip;
+            rn[b] = (j == k ? T(1) : rowb[buf][j]) * ip;        // the new pivot row
         }
 #pragma unroll
-        for (int a = 0; a < 5; ++a) co[a] = colb[buf][(ty + 32 * a) < kRegDof ? ty + 32 * a : 0];
+        for (int a = 0; a < 5; ++a) co[a] = colb[buf][ty + 32 * a];
+        // the pivot column is eliminated: its entries enter the update as 0
+        if (tx == kr) {
 #pragma unroll
-        for (int a = 0; a < 5; ++a) {
-            const bool rowk = (ty + 32 * a) == k;
+            for (int a = 0; a < 5; ++a)
+                if (ka == 0) R[a][0] = T(0);
+                else if (ka == 1) R[a][1] = T(0);
+                else if (ka == 2) R[a][2] = T(0);
+                else if (ka == 3) R[a][3] = T(0);
+                else R[a][4] = T(0);
+        }
 #pragma unroll
-            for (int b = 0; b < 5; ++b) {
-                const bool colk = (tx + 32 * b) == k;
-                R[a][b] = rowk ? rn[b] : (colk ? T(0) : R[a][b]) - co[a] * rn[b];
-            }
+        for (int a = 0; a < 5; ++a)
+#pragma unroll
+            for (int b = 0; b < 5; ++b) R[a][b] = fma(-co[a], rn[b], R[a][b]);
+        // the pivot row is the scaled old row
+        if (ty == kr) {
+#pragma unroll
+            for (int b = 0; b < 5; ++b)
+                if (ka == 0) R[0][b] = rn[b];
+                else if (ka == 1) R[1][b] = rn[b];
+                else if (ka == 2) R[2][b] = rn[b];
+                else if (ka == 3) R[3][b] = rn[b];
+                else R[4][b] = rn[b];
         }
     }
 #pragma unroll
@@ -372,6 +387,10 @@ int mg_build(to_problem* P) {
         return fail(TO_ERR_ARG, "coarsest multigrid grid too large for the dense solve (" + std::to_string(n) +
                                     " DOFs > " + std::to_string(kMaxCoarseDof) + "): use a grid that halves more often");
     P->n_coarse = n;
+    if (cudaStreamCreateWithFlags(&P->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming) != cudaSuccess)
+        return fail(TO_ERR_CUDA, "multigrid stream / event creation failed");
     if (cudaMalloc(&P->coarse_A, (size_t)n * n * es) != cudaSuccess ||
         cudaMalloc(&P->coarse_L, (size_t)n * n * es + (size_t)n * es) != cudaSuccess)
         return fail(TO_ERR_CUDA, "coarse allocation");
@@ -409,6 +428,11 @@ static int refresh_t(to_problem* P, cudaStream_t s) {
     TO_CUDA(cudaGetLastError());
     const size_t smem = (size_t)n * n * sizeof(T);
     T* inv = (T*)P->coarse_L;
+    // the inverse runs on a branch; the first coarse solve joins it (it is needed only there)
+    TO_CUDA(cudaEventRecord(P->ev_fork, s));
+    TO_CUDA(cudaStreamWaitEvent(P->side, P->ev_fork, 0));
+    cudaStream_t main_s = s;
+    s = P->side;
     if (n <= kRegDof)
         k_dense_invert_reg<T><<<1, dim3(32, 32), 0, s>>>((const T*)P->coarse_A, inv, inv + (size_t)n * n, n, &P->sc->err);
     else if (smem <= smem_cap<T>())
@@ -416,6 +440,8 @@ static int refresh_t(to_problem* P, cudaStream_t s) {
     else
         k_dense_invert<T, false><<<1, dim3(32, 32), 0, s>>>((const T*)P->coarse_A, inv, inv + (size_t)n * n, n, &P->sc->err);
     TO_CUDA(cudaGetLastError());
+    TO_CUDA(cudaEventRecord(P->ev_join, s));
+    (void)main_s;
     return TO_OK;
 }
 
@@ -426,6 +452,7 @@ int mg_refresh(to_problem* P, cudaStream_t s) {
 template <typename T>
 static int coarse_solve_t(to_problem* P, const void* b, void* x, cudaStream_t s) {
     const int n = P->n_coarse;
+    TO_CUDA(cudaStreamWaitEvent(s, P->ev_join, 0));   // the inverse of this design is ready
     const T* inv = (const T*)P->coarse_L;
     k_dense_solve<T><<<(n + 7) / 8, dim3(32, 8), 0, s>>>(inv, inv + (size_t)n * n, (const T*)b, (T*)x, n);
     TO_CUDA(cudaGetLastError());
@@ -459,7 +486,9 @@ static int vcycle_t(to_problem* P, int l, const void* b, void* x, void* t, cudaS
     k_prolong_add<T><<<grid3(F.nx + 1, F.ny + 1, F.nz + 1), block3(), 0, s>>>(C.nx, C.ny, C.nz, (const T*)C.x, C.mask, F.mask, (T*)cur);
     TO_CUDA(cudaGetLastError());
     for (int it = 0; it < nu2; ++it) {
-        if ((rc = launch_operator(P, l, OP_SMOOTH, cur, oth, b, s, om))) return rc;
+        // on the fine level the last sweep also reduces b^T x (= r^T z of the lower-level step)
+        const int flag = (l == 0 && it == nu2 - 1) ? 2 : 0;
+        if ((rc = launch_operator(P, l, OP_SMOOTH, cur, oth, b, s, om, flag))) return rc;
         std::swap(cur, oth);
     }
     if (cur != x) return fail(TO_ERR_STATE, "V-cycle buffer parity");

@@ -383,7 +383,10 @@ __global__ void __launch_bounds__(TX * TY) k_operator(const OpArgs<T> a) {
                 } else if (MODE == OP_BMINUS) {
                     a.y[dof] = sm.eb[s_bot][ty][tx][c] - Kx;
                 } else if (MODE == OP_SMOOTH) {
-                    a.y[dof] = xv + a.omega * (sm.eb[s_bot][ty][tx][c] - Kx) / sm.ed[s_bot][ty][tx][c];
+                    const T bv = sm.eb[s_bot][ty][tx][c];
+                    const T yv = xv + a.omega * (bv - Kx) / sm.ed[s_bot][ty][tx][c];
+                    a.y[dof] = yv;
+                    acc0 = fma(bv, yv, acc0);
                 } else if (MODE == OP_RESID) {
                     const T bv = sm.eb[s_bot][ty][tx][c];
                     const T rv2 = bv - Kx;
@@ -406,6 +409,17 @@ __global__ void __launch_bounds__(TX * TY) k_operator(const OpArgs<T> a) {
     cp_wait<0>();
     double* sh_red = sm.red;
 
+    if (MODE == OP_SMOOTH && a.first_step == 2) {
+        // last fine-level sweep of a V-cycle: r^T z with r the cycle's right-hand side
+        double v[1] = {(double)acc0};
+        const int kind[1] = {0};
+        double tot[1];
+        block_reduce<1>(v, kind, sh_red);
+        if (finish_reduction<1>(v, kind, a.red, a.counter, tot, sh_red) && tid == 0) {
+            a.sc->rz = tot[0];
+            if (!isfinite(tot[0])) set_err(&a.sc->err, TO_ERR_NONFINITE);
+        }
+    }
     if (MODE == OP_Q) {
         double v[1] = {(double)acc0};
         const int kind[1] = {0};
@@ -473,6 +487,8 @@ static int launch_t(to_problem* P, int level, int mode, const void* x, void* y, 
         a.gt = (T*)P->gt;
     } else if (mode == OP_Q) {
         a.counter = P->counters + 1;
+    } else if (mode == OP_SMOOTH) {
+        a.counter = P->counters + 6;
     }
     const int gx = (L.nx + 1 + TX - 2) / (TX - 1);
     const int gy = (L.ny + 1 + TY - 2) / (TY - 1);
@@ -488,7 +504,7 @@ static int launch_t(to_problem* P, int level, int mode, const void* x, void* y, 
     if (kchunk > L.nz + 1) kchunk = L.nz + 1;
     a.kchunk = kchunk;
     const int gz = (L.nz + 1 + kchunk - 1) / kchunk;
-    if ((long long)gx * gy * gz > kMaxRedBlocks && (mode == OP_RESID || mode == OP_Q))
+    if ((long long)gx * gy * gz > kMaxRedBlocks && (mode == OP_RESID || mode == OP_Q || mode == OP_SMOOTH))
         return fail(TO_ERR_ARG, "operator grid exceeds the reduction scratch; raise tile_z");
     dim3 grid(gx, gy, gz), block(TX, TY);
     const size_t smem = sizeof(OpSmem<T, TX, TY, kRing>);
