@@ -38,6 +38,7 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=None)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-diff", action="store_true")
     ap.add_argument("--precond", default="auto", choices=["auto", "mg", "jacobi"])
     ap.add_argument("--apply-only", nargs=3, type=int, metavar=("NX", "NY", "NZ"),
                     help="time only K(rho)u on a cantilever of this size (random design), FP32-mixed")
@@ -285,6 +286,31 @@ def main():
         rho_h.copy_(rho_o)
     t_e2e = time.perf_counter() - t0
 
+    # --- differentiable compliance: forward + backward through T = 5 Jacobi steps, 256x128x128, FP32
+    diff = None
+    if not args.no_diff:
+        pbd = W.cantilever_random_256x128x128()
+        Pd = fb.Problem.from_workload(pbd, fb.to_default_params(precision=fb.TO_FP32_MIXED), device=local)
+        rho_d = torch.tensor(pbd.rho0, dtype=torch.float32, device=dev)
+        gd = Pd.elem()
+        for _ in range(2):
+            fb.to_compliance_truncated(Pd, rho_d, 5, 0.5, want_J=False)
+            fb.to_compliance_truncated_grad(Pd, 1.0, gd)
+        torch.cuda.synchronize()
+        a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        nrep = 5
+        a_.record(stream)
+        for _ in range(nrep):
+            fb.to_compliance_truncated(Pd, rho_d, 5, 0.5, want_J=False)
+            fb.to_compliance_truncated_grad(Pd, 1.0, gd)
+        b_.record(stream)
+        torch.cuda.synchronize()
+        td = a_.elapsed_time(b_) / 1000.0 / nrep
+        diff = {"workload": "cantilever 256x128x128, rho ~ U[0.2,1], T = 5, beta = 0.5, FP32",
+                "fwd_bwd_per_s": 1.0 / td, "ms": td * 1e3}
+        Pd.close()
+        del rho_d, gd
+
     # --- plain FP64
     res64 = None
     if not args.no_fp64:
@@ -336,6 +362,7 @@ def main():
                     "fp64_us": res64["apply_ms"] * 1e3 if res64 else None},
         "fp64_plain": res64,
         "fp32_over_fp64_iters": (ips32 / res64["outer_iters_per_s"]) if res64 else None,
+        "differentiable_compliance": diff,
         "roofline": {"kernel": "k_operator (K(rho)u, FP32)", "bound": "hbm", "achieved": ach, "peak": hbm,
                      "unit": "GB/s", "frac": ach / hbm, "traffic": None,
                      "algorithmic_bytes": apply_bytes(s_el),

@@ -202,6 +202,25 @@ int to_step(to_problem* P, int32_t n_outer, to_stats* stats_out, void* stream);
 int to_get_state(to_problem* P, void* rho_dev, void* u_dev, int64_t* k_out, double* alpha0_out, void* stream);
 int to_set_state(to_problem* P, const void* rho_dev, const void* u_dev, int64_t k, double alpha0, void* stream);
 
+/* Differentiable compliance through a truncated lower-level solve.
+ * J(rho) = f^T u_T where u_0 = 0 and u_{j+1} = u_j + beta D^-1 (f - K^(rho~) u_j),
+ * D = diag K^ (the literal constant-beta step of Algorithms 1 / 3 with the Jacobi M),
+ * j < T_steps.  Sets the problem's design to rho (as to_set_design), keeps
+ * u_0 .. u_T for the reverse sweep (the problem allocates (T_steps + 1) n_dof
+ * entries on the first call with this T) and, if J_out is not NULL, returns J
+ * (synchronises).  Requires precond = TO_PRECOND_JACOBI (TO_ERR_STATE otherwise).
+ * As T grows the gradient tends to the exact sensitivity of Sec. III. */
+int to_compliance_truncated(to_problem* P, const void* rho_dev, int32_t T_steps, double beta,
+                            double* J_out, void* stream);
+
+/* g = scale * dJ/drho for the last to_compliance_truncated call: a reverse sweep
+ * over the kept iterates (adjoint lambda_T = f, lambda_j = lambda_{j+1} - K^ s_j,
+ * s_j = beta D^-1 lambda_{j+1}) with the element terms
+ * -E'_e [ s_e^T k_e u_j,e + sum_{d in e} k_dd s_d z_j,d ] (z_j = D^-1 r_j, the
+ * dependence of D on rho included), chained through the filter transpose.
+ * g: n_elem entries.  TO_ERR_STATE if no forward call preceded. */
+int to_compliance_truncated_grad(to_problem* P, double scale, void* g_dev, void* stream);
+
 /* Allocation-free projection.  The paper has no counterpart: this entry point
  * exists for callers that may not allocate device memory, for instance code
  * running inside a host framework that owns every device byte through its own

@@ -18,7 +18,8 @@ from ._abi import (TO_FP32_MIXED, TO_FP64, TO_INNER_RICHARDSON, TO_INNER_SD, TO_
 
 __all__ = ["to_default_params", "to_create", "to_destroy", "to_sizes", "to_set_design", "to_apply_K",
            "to_inner_solve", "to_sensitivity", "to_filter", "to_project", "to_step", "to_get_state",
-           "to_set_state", "to_check", "to_last_error", "to_project_noalloc", "Problem", "ToError",
+           "to_set_state", "to_check", "to_last_error", "to_project_noalloc", "to_compliance_truncated",
+           "to_compliance_truncated_grad", "Problem", "ToError",
            "TO_FP64", "TO_FP32_MIXED", "TO_PRECOND_JACOBI", "TO_PRECOND_MG", "TO_PRECOND_NONE",
            "TO_INNER_SD", "TO_INNER_RICHARDSON"]
 
@@ -232,6 +233,18 @@ def to_set_state(P, rho=None, u=None, k=1, alpha0=0.0):
 
 def to_check(P):
     _abi.check(_lib().to_check(_h(P), _stream(P.device)))
+
+
+def to_compliance_truncated(P, rho, T, beta, want_J=True):
+    J = C.c_double()
+    _abi.check(_lib().to_compliance_truncated(_h(P), _ptr(rho, _dt(P), P.n_elem, "rho"), int(T), float(beta),
+                                              C.byref(J) if want_J else None, _stream(P.device)))
+    return J.value if want_J else None
+
+
+def to_compliance_truncated_grad(P, scale, g):
+    _abi.check(_lib().to_compliance_truncated_grad(_h(P), float(scale), _ptr(g, _dt(P), P.n_elem, "g"),
+                                                   _stream(P.device)))
 
 
 def to_project_noalloc(w, rho, vbar, lo=0.0, hi=1.0, want_lambda=True):

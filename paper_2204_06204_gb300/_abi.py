@@ -68,6 +68,8 @@ SIGNATURES = {
     "to_get_state": (C.c_int, [P, P, P, C.POINTER(C.c_int64), C.POINTER(C.c_double), P]),
     "to_set_state": (C.c_int, [P, P, P, C.c_int64, C.c_double, P]),
     "to_check": (C.c_int, [P, P]),
+    "to_compliance_truncated": (C.c_int, [P, P, C.c_int32, C.c_double, C.POINTER(C.c_double), P]),
+    "to_compliance_truncated_grad": (C.c_int, [P, C.c_double, P, P]),
     "to_project_noalloc": (C.c_int, [P, P, C.c_int64, C.c_int32, C.c_double, C.c_double, C.c_double,
                                      C.POINTER(C.c_double), P]),
     "to_last_error": (C.c_char_p, []),

@@ -1,0 +1,269 @@
+// Compliance through a truncated lower-level solve, and its gradient.
+//
+// J(rho) = f^T u_T with u_0 = 0 and T constant-beta Jacobi steps (the literal
+// lower-level step of Algorithms 1 / 3 with M = diag K):
+//     r_j = f - K^ u_j,   z_j = r_j / D,   u_{j+1} = u_j + beta z_j.
+// Reverse mode over the stored iterates (z_j = (u_{j+1} - u_j) / beta, so the
+// residuals need not be kept):
+//     lambda_T = f;  for j = T-1 .. 0:
+//         s = beta lambda / D
+//         dJ/drho~_e += -E'_e [ s_e^T k_e u_j,e + sum_{d in e} k_dd s_d z_j,d ]
+//         lambda <- lambda - K^ s
+//     dJ/drho = C^T dJ/drho~
+// (u_j, s and z_j vanish on fixed DOFs; the element terms are evaluated in the
+// sum/difference basis, where x^T y = (T x)^T (T y) / 8.)  As T grows, u_T tends
+// to K^-1 f and the gradient to the exact sensitivity of Sec. III.
+#include <cstring>
+
+#include "device.cuh"
+
+namespace to {
+
+int launch_filter_prescaled_T(to_problem* P, const void* x, void* y, cudaStream_t s);
+
+// Haar coefficients (sum / difference basis) of one element's 24 nodal values
+template <typename T>
+__device__ __forceinline__ void element_haar(const T nv[2][2][2][3], T uh[24]) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        T F[2][4];
+#pragma unroll
+        for (int c2 = 0; c2 < 2; ++c2) {
+            const T sx0 = nv[c2][0][1][c] + nv[c2][0][0][c], dx0 = nv[c2][0][1][c] - nv[c2][0][0][c];
+            const T sx1 = nv[c2][1][1][c] + nv[c2][1][0][c], dx1 = nv[c2][1][1][c] - nv[c2][1][0][c];
+            F[c2][0] = sx1 + sx0;
+            F[c2][1] = dx1 + dx0;
+            F[c2][2] = sx1 - sx0;
+            F[c2][3] = dx1 - dx0;
+        }
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            uh[3 * f + c] = F[1][f] + F[0][f];
+            uh[12 + 3 * f + c] = F[1][f] - F[0][f];
+        }
+    }
+}
+
+// a^T K^ b in the sum/difference basis (45 non-zeros, order of kHaarRow / kHaarCol)
+template <typename T>
+__device__ __forceinline__ T haar_bilinear(const T* k, const T a[24], const T b[24]) {
+    T r = T(0);
+    r += a[3] * (k[0] * b[3] + k[1] * b[7] + k[2] * b[14]);
+    r += a[7] * (k[3] * b[3] + k[4] * b[7] + k[5] * b[14]);
+    r += a[14] * (k[6] * b[3] + k[7] * b[7] + k[8] * b[14]);
+    r += a[4] * (k[9] * b[4] + k[10] * b[6]) + a[6] * (k[11] * b[4] + k[12] * b[6]);
+    r += a[5] * (k[13] * b[5] + k[14] * b[12]) + a[12] * (k[15] * b[5] + k[16] * b[12]);
+    r += a[8] * (k[17] * b[8] + k[18] * b[13]) + a[13] * (k[19] * b[8] + k[20] * b[13]);
+    r += a[9] * (k[21] * b[9] + k[22] * b[20]) + a[20] * (k[23] * b[9] + k[24] * b[20]);
+    r += a[10] * (k[25] * b[10] + k[26] * b[17]) + a[17] * (k[27] * b[10] + k[28] * b[17]);
+    r += a[15] * (k[29] * b[15] + k[30] * b[19]) + a[19] * (k[31] * b[15] + k[32] * b[19]);
+    r += a[11] * (k[33] * b[11] + k[34] * b[16] + k[35] * b[18]);
+    r += a[16] * (k[36] * b[11] + k[37] * b[16] + k[38] * b[18]);
+    r += a[18] * (k[39] * b[11] + k[40] * b[16] + k[41] * b[18]);
+    r += a[21] * k[42] * b[21] + a[22] * k[43] * b[22] + a[23] * k[44] * b[23];
+    return r;
+}
+
+// gt_e (+)= -scale E'_e [ s_e^T k_e u_e + kdiag sum_d s_d z_d ],  z = (u1 - u0) / beta
+template <typename T>
+__global__ void __launch_bounds__(256) k_adjoint_elem(int nx, int ny, int nz, const T* __restrict__ svec,
+                                                      const T* __restrict__ u0, const T* __restrict__ u1,
+                                                      const uint8_t* __restrict__ mask, const T* __restrict__ Ed,
+                                                      T* __restrict__ gt, HaarK<T> kh, T kdiag, T inv_beta,
+                                                      T scale, int accumulate) {
+    const Idx3 t = idx3(nx, ny, nz);
+    if (!t.ok) return;
+    const int i = t.i, j = t.j, k = t.k;
+    const long long e = i + (long long)nx * (j + (long long)ny * k);
+    const int nxn = nx + 1, nyn = ny + 1;
+    T sv[2][2][2][3], uv[2][2][2][3], zv[2][2][2][3];
+#pragma unroll
+    for (int c2 = 0; c2 < 2; ++c2)
+#pragma unroll
+        for (int b2 = 0; b2 < 2; ++b2)
+#pragma unroll
+            for (int a2 = 0; a2 < 2; ++a2) {
+                const long long node = (i + a2) + (long long)nxn * ((j + b2) + (long long)nyn * (k + c2));
+                const uint8_t mk = mask[node];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const bool fx = (mk >> c) & 1;
+                    const long long d = 3 * node + c;
+                    const T a = u0[d];
+                    sv[c2][b2][a2][c] = fx ? T(0) : svec[d];
+                    uv[c2][b2][a2][c] = fx ? T(0) : a;
+                    zv[c2][b2][a2][c] = fx ? T(0) : (u1[d] - a) * inv_beta;
+                }
+            }
+    T sh[24], uh[24], zh[24];
+    element_haar<T>(sv, sh);
+    element_haar<T>(uv, uh);
+    element_haar<T>(zv, zh);
+    T dz = T(0);
+#pragma unroll
+    for (int q = 0; q < 24; ++q) dz = fma(sh[q], zh[q], dz);
+    const T term = haar_bilinear<T>(kh.v, sh, uh) + kdiag * dz * T(0.125);
+    const T v = -scale * Ed[e] * term;
+    gt[e] = accumulate ? gt[e] + v : v;
+}
+
+// out = u + beta z
+template <typename T>
+__global__ void k_axpy_out(long long n, const T* __restrict__ u, const T* __restrict__ z, T beta, T* __restrict__ out) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = u[i] + beta * z[i];
+}
+
+// s = beta lambda / d
+template <typename T>
+__global__ void k_adj_s(long long n, const T* __restrict__ lam, const T* __restrict__ d, T beta, T* __restrict__ s) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        s[i] = beta * lam[i] / d[i];
+}
+
+// lambda -= q
+template <typename T>
+__global__ void k_sub_inplace(long long n, T* __restrict__ lam, const T* __restrict__ q) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        lam[i] -= q[i];
+}
+
+// J = f^T u
+template <typename T>
+__global__ void __launch_bounds__(256) k_dot_J(long long n, const T* __restrict__ f, const T* __restrict__ u, double* red,
+                                               unsigned* counter, DevScalars* sc) {
+    __shared__ double sh[32 * kRedQ];
+    double acc = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const T fv = f[i];
+        if (fv != T(0)) acc += (double)fv * (double)u[i];
+    }
+    double v[1] = {acc};
+    const int kind[1] = {0};
+    double tot[1];
+    block_reduce<1>(v, kind, sh);
+    if (finish_reduction<1>(v, kind, red, counter, tot, sh) && threadIdx.x == 0) sc->J = tot[0];
+}
+
+static int grid_n(long long n, int num_sms) {
+    long long b = (n + 255) / 256;
+    if (b > 8LL * num_sms) b = 8LL * num_sms;
+    return (int)(b < 1 ? 1 : b);
+}
+
+template <typename T>
+static T* iterate(to_problem* P, int j) {
+    return (T*)P->iters + (size_t)j * (size_t)P->n_dof;
+}
+
+template <typename T>
+static int forward_t(to_problem* P, const void* rho, int Tn, double beta, cudaStream_t s) {
+    const size_t bytes = (size_t)P->n_dof * sizeof(T);
+    if (Tn + 1 > P->iters_cap) {
+        TO_CUDA(cudaStreamSynchronize(s));
+        if (P->iters) cudaFree(P->iters);
+        P->iters = nullptr;
+        P->iters_cap = 0;
+        TO_CUDA(cudaMalloc(&P->iters, bytes * (size_t)(Tn + 1)));
+        P->iters_cap = Tn + 1;
+    }
+    TO_CUDA(cudaMemcpyAsync(P->rho, rho, P->n_elem * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    int rc = launch_moduli(P, s);
+    if (rc) return rc;
+    if ((rc = launch_diag(P, 0, s))) return rc;
+    TO_CUDA(cudaMemsetAsync(iterate<T>(P, 0), 0, bytes, s));
+    void* gt = P->gt;
+    P->gt = nullptr;   // no fused sensitivity in these residuals
+    const int nb = grid_n(P->n_dof, P->num_sms);
+    for (int j = 0; j < Tn; ++j) {
+        // r_j = f - K^ u_j and z_j = r_j / D (fused Jacobi epilogue), then u_{j+1} = u_j + beta z_j
+        rc = launch_operator(P, 0, OP_RESID, iterate<T>(P, j), P->r, P->f, s, 0.0, 0);
+        if (rc) break;
+        k_axpy_out<T><<<nb, 256, 0, s>>>(P->n_dof, iterate<T>(P, j), (const T*)P->z, (T)beta, iterate<T>(P, j + 1));
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) {
+            rc = fail(TO_ERR_CUDA, std::string("axpy: ") + cudaGetErrorString(e));
+            break;
+        }
+    }
+    P->gt = gt;
+    if (rc) return rc;
+    k_dot_J<T><<<nb, 256, 0, s>>>(P->n_dof, (const T*)P->f, iterate<T>(P, Tn), P->red, P->counters + 7, P->sc);
+    TO_CUDA(cudaGetLastError());
+    P->iters_T = Tn;
+    P->iters_beta = beta;
+    return TO_OK;
+}
+
+template <typename T>
+static int backward_t(to_problem* P, double scale, void* g, cudaStream_t s) {
+    const int Tn = P->iters_T;
+    const double beta = P->iters_beta;
+    const int nb = grid_n(P->n_dof, P->num_sms);
+    T* lam = (T*)P->tmp_v;
+    T* sv = (T*)P->z;
+    T* q = (T*)P->q;
+    TO_CUDA(cudaMemcpyAsync(lam, P->f, P->n_dof * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    HaarK<T> kh;
+    for (int n = 0; n < kHaarNnz; ++n) kh.v[n] = (T)P->haar[n];
+    const dim3 eg = grid3(P->g.nx, P->g.ny, P->g.nz);
+    if (Tn == 0) TO_CUDA(cudaMemsetAsync(P->gt, 0, P->n_elem * sizeof(T), s));
+    for (int j = Tn - 1; j >= 0; --j) {
+        k_adj_s<T><<<nb, 256, 0, s>>>(P->n_dof, lam, (const T*)P->lv[0].d, (T)beta, sv);
+        TO_CUDA(cudaGetLastError());
+        k_adjoint_elem<T><<<eg, block3(), 0, s>>>(P->g.nx, P->g.ny, P->g.nz, sv, iterate<T>(P, j), iterate<T>(P, j + 1),
+                                                  P->lv[0].mask, (const T*)P->Ed, (T*)P->gt, kh, (T)P->kdiag,
+                                                  (T)(1.0 / beta), (T)scale, j < Tn - 1);
+        TO_CUDA(cudaGetLastError());
+        if (j > 0) {
+            int rc = launch_operator(P, 0, OP_APPLY, sv, q, nullptr, s);
+            if (rc) return rc;
+            k_sub_inplace<T><<<nb, 256, 0, s>>>(P->n_dof, lam, q);
+            TO_CUDA(cudaGetLastError());
+        }
+    }
+    return launch_filter_prescaled_T(P, P->gt, g, s);
+}
+
+}  // namespace to
+
+using namespace to;
+
+extern "C" int to_compliance_truncated(to_problem* P, const void* rho_dev, int32_t T_steps, double beta,
+                                       double* J_out, void* stream) {
+    if (!P) return fail(TO_ERR_ARG, "null problem");
+    if (!rho_dev || T_steps < 0 || !(beta > 0.0)) return fail(TO_ERR_ARG, "need rho, T >= 0 and beta > 0");
+    if (P->prm.precond != TO_PRECOND_JACOBI)
+        return fail(TO_ERR_STATE, "the truncated compliance is defined with the Jacobi preconditioner");
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (cudaSetDevice(P->device) != cudaSuccess) return fail(TO_ERR_CUDA, "cudaSetDevice failed");
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = P->prec == TO_FP64 ? forward_t<double>(P, rho_dev, T_steps, beta, s)
+                                : forward_t<float>(P, rho_dev, T_steps, beta, s);
+    if (!rc && J_out) {
+        DevScalars h;
+        if (cudaMemcpyAsync(&h, P->sc, sizeof h, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            rc = fail(TO_ERR_CUDA, "reading J failed");
+        else {
+            *J_out = h.J;
+            if (h.err) rc = fail(h.err, "device-side error in the truncated solve");
+        }
+    }
+    if (prev >= 0) cudaSetDevice(prev);
+    return rc;
+}
+
+extern "C" int to_compliance_truncated_grad(to_problem* P, double scale, void* g_dev, void* stream) {
+    if (!P) return fail(TO_ERR_ARG, "null problem");
+    if (!g_dev) return fail(TO_ERR_ARG, "null gradient");
+    if (P->iters_T < 0) return fail(TO_ERR_STATE, "call to_compliance_truncated first");
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (cudaSetDevice(P->device) != cudaSuccess) return fail(TO_ERR_CUDA, "cudaSetDevice failed");
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = P->prec == TO_FP64 ? backward_t<double>(P, scale, g_dev, s) : backward_t<float>(P, scale, g_dev, s);
+    if (prev >= 0) cudaSetDevice(prev);
+    return rc;
+}

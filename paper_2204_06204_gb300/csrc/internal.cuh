@@ -127,6 +127,12 @@ struct to_problem {
     to_stats* dstats = nullptr;    // device stats ring
     int dstats_cap = 0;
 
+    // truncated-solve iterates u_0 .. u_T kept for the reverse sweep
+    void* iters = nullptr;
+    int iters_cap = 0;
+    int iters_T = -1;
+    double iters_beta = 0.0;
+
     // captured outer iteration (replayed by to_step) on a library-owned stream
     cudaStream_t gstream = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
