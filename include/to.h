@@ -68,6 +68,7 @@ enum { TO_PRECOND_JACOBI = 0, TO_PRECOND_MG = 1, TO_PRECOND_NONE = 2 };
 enum { TO_INNER_SD = 0, TO_INNER_RICHARDSON = 1 };
 
 typedef struct to_problem to_problem;      /* opaque */
+typedef struct to_batch to_batch;          /* opaque: many problems advanced together */
 
 /* Voxel grid: element counts and edge length h (> 0). */
 typedef struct {
@@ -201,6 +202,21 @@ int to_step(to_problem* P, int32_t n_outer, to_stats* stats_out, void* stream);
  * skip that part.  to_set_state recomputes rho~ and the moduli. */
 int to_get_state(to_problem* P, void* rho_dev, void* u_dev, int64_t* k_out, double* alpha0_out, void* stream);
 int to_set_state(to_problem* P, const void* rho_dev, const void* u_dev, int64_t k, double alpha0, void* stream);
+
+/* Batches of independent design problems (each advanced exactly as to_step
+ * advances it: Algorithms 1 / 3 with its own lambda, beta, alpha and state).
+ * to_batch_create groups existing problems (not copied, not owned: destroy the
+ * batch before its problems).  They must share precision, device, element
+ * size h, E0 / Emin / p / nu and n_inner, and use TO_PRECOND_JACOBI with
+ * TO_INNER_SD; grids, loads, fixtures, volume fractions and filter radii may
+ * differ.  to_batch_step runs n_outer outer iterations of every problem with
+ * one kernel launch per phase for the whole batch (captured once as a CUDA
+ * graph); stats_out (may be NULL) receives n problems x n_outer records,
+ * problem-major, and then the call synchronises.  n_outer must not exceed any
+ * problem's stats ring (256 after to_create; a longer to_step grows it). */
+int to_batch_create(to_problem* const* problems, int32_t n, to_batch** out);
+void to_batch_destroy(to_batch* batch);
+int to_batch_step(to_batch* batch, int32_t n_outer, to_stats* stats_out, void* stream);
 
 /* Differentiable compliance through a truncated lower-level solve.
  * J(rho) = f^T u_T where u_0 = 0 and u_{j+1} = u_j + beta D^-1 (f - K^(rho~) u_j),

@@ -19,7 +19,8 @@ from ._abi import (TO_FP32_MIXED, TO_FP64, TO_INNER_RICHARDSON, TO_INNER_SD, TO_
 __all__ = ["to_default_params", "to_create", "to_destroy", "to_sizes", "to_set_design", "to_apply_K",
            "to_inner_solve", "to_sensitivity", "to_filter", "to_project", "to_step", "to_get_state",
            "to_set_state", "to_check", "to_last_error", "to_project_noalloc", "to_compliance_truncated",
-           "to_compliance_truncated_grad", "Problem", "ToError",
+           "to_compliance_truncated_grad", "to_batch_create", "to_batch_destroy", "to_batch_step", "Batch",
+           "Problem", "ToError",
            "TO_FP64", "TO_FP32_MIXED", "TO_PRECOND_JACOBI", "TO_PRECOND_MG", "TO_PRECOND_NONE",
            "TO_INNER_SD", "TO_INNER_RICHARDSON"]
 
@@ -245,6 +246,55 @@ def to_compliance_truncated(P, rho, T, beta, want_J=True):
 def to_compliance_truncated_grad(P, scale, g):
     _abi.check(_lib().to_compliance_truncated_grad(_h(P), float(scale), _ptr(g, _dt(P), P.n_elem, "g"),
                                                    _stream(P.device)))
+
+
+def to_batch_create(problems):
+    arr = (C.c_void_p * len(problems))(*[_h(p).value for p in problems])
+    out = C.c_void_p()
+    _abi.check(_lib().to_batch_create(arr, len(problems), C.byref(out)))
+    return out
+
+
+def to_batch_destroy(B):
+    _lib().to_batch_destroy(B)
+
+
+def to_batch_step(B, n_problems, n_outer, device, want_stats=True):
+    if want_stats:
+        arr = (to_stats * (n_problems * max(int(n_outer), 1)))()
+        _abi.check(_lib().to_batch_step(B, int(n_outer), arr, _stream(device)))
+        return [[arr[p * n_outer + i].as_dict() for i in range(n_outer)] for p in range(n_problems)]
+    _abi.check(_lib().to_batch_step(B, int(n_outer), None, _stream(device)))
+    return None
+
+
+class Batch:
+    """Many Problems advanced together (one launch per phase); keeps them alive."""
+
+    def __init__(self, problems):
+        self.problems = list(problems)
+        self.device = self.problems[0].device
+        self.handle = to_batch_create(self.problems)
+
+    def step(self, n_outer=1, want_stats=True):
+        return to_batch_step(self.handle, len(self.problems), n_outer, self.device, want_stats)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            to_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 def to_project_noalloc(w, rho, vbar, lo=0.0, hi=1.0, want_lambda=True):

@@ -68,6 +68,9 @@ SIGNATURES = {
     "to_get_state": (C.c_int, [P, P, P, C.POINTER(C.c_int64), C.POINTER(C.c_double), P]),
     "to_set_state": (C.c_int, [P, P, P, C.c_int64, C.c_double, P]),
     "to_check": (C.c_int, [P, P]),
+    "to_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(C.c_void_p)]),
+    "to_batch_destroy": (None, [P]),
+    "to_batch_step": (C.c_int, [P, C.c_int32, C.POINTER(to_stats), P]),
     "to_compliance_truncated": (C.c_int, [P, P, C.c_int32, C.c_double, C.POINTER(C.c_double), P]),
     "to_compliance_truncated_grad": (C.c_int, [P, C.c_double, P, P]),
     "to_project_noalloc": (C.c_int, [P, P, C.c_int64, C.c_int32, C.c_double, C.c_double, C.c_double,

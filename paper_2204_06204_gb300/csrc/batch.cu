@@ -1,0 +1,608 @@
+// Many independent design problems advanced together: one kernel launch per
+// phase of the outer iteration (Algorithms 1 / 3) covers every problem, and
+// the whole batched iteration is captured once as a CUDA graph.
+//
+// Each problem keeps its own buffers, scalars, reduction slots and stats ring
+// (it is an ordinary to_problem); the batched kernels read a device table of
+// per-problem arguments indexed by blockIdx.y (blockIdx.x for the projection's
+// clusters).  Phases, per outer iteration:
+//   design   rho -> rho~ -> E, E'/Hs            k_b_design
+//   diag     Jacobi diagonal                     k_b_diag
+//   resid    r = f - K u, z = r/d, sensitivity   k_operator_batch<OP_RESID>
+//   n_inner x (Q apply, update)                  k_operator_batch<OP_Q>, k_b_update
+//   filterT  g = C^T g~, ||g||_inf, alpha_k      k_b_filter_T
+//   project  one thread-block cluster per problem (distributed shared memory
+//            for the pass totals: no grid-wide barrier between problems)
+//   record   per-problem stats                    k_b_record
+// Requirements: every problem uses the Jacobi preconditioner and steepest
+// descent with the same n_inner, the same precision, device, element size and
+// material moduli (the element matrix constants are common to the launch).
+#include <cooperative_groups.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "device.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace to {
+
+int batch_operator_launch(int prec, int mode, const void* tab, const void* kh, int max_tiles, int n, cudaStream_t s);
+int op_tables_build(to_problem* const* probs, int n, void** resid, void** q_first, void** q, void** kh_host,
+                    int* max_tiles);
+
+template <typename T>
+struct BProb {
+    int nx, ny, nz, ns, R;
+    long long n_elem, n_dof;
+    const T* rho;
+    T* rhot;
+    const T* Hs;
+    T* E;
+    T* Ed;
+    const int4* st;
+    const T* stw;
+    const T* gt;
+    T* grad;
+    const uint8_t* mask;
+    T* d;
+    double kdiag;
+    T* u;
+    T* r;
+    T* z;
+    const T* q;
+    T* wbuf;
+    double* red;
+    unsigned* counters;
+    DevScalars* sc;
+    to_stats* dstats;
+    int dstats_cap;
+    double vbar, lo, hi, alpha0_param, alpha_scale, m_exp;
+    int mean_proj;
+};
+
+// rho~ = C(rho), E = Emin + rho~^p (E0 - Emin), E'/Hs  (grid-stride over each problem's elements)
+template <typename T>
+__global__ void __launch_bounds__(256) k_b_design(const BProb<T>* __restrict__ tab, double E0, double Emin, double p) {
+    const BProb<T>& P = tab[blockIdx.y];
+    const int nx = P.nx, ny = P.ny, nz = P.nz;
+    const T dE = (T)(E0 - Emin);
+    for (long long e = blockIdx.x * 256LL + threadIdx.x; e < P.n_elem; e += (long long)gridDim.x * 256) {
+        const int i = (int)(e % nx), j = (int)((e / nx) % ny), k = (int)(e / ((long long)nx * ny));
+        T acc = T(0);
+        for (int s = 0; s < P.ns; ++s) {
+            const int4 o = P.st[s];
+            const int ii = i + o.x, jj = j + o.y, kk = k + o.z;
+            if (ii < 0 || ii >= nx || jj < 0 || jj >= ny || kk < 0 || kk >= nz) continue;
+            acc += P.stw[s] * P.rho[ii + (long long)nx * (jj + (long long)ny * kk)];
+        }
+        const T hs = P.Hs[e];
+        const T rt = acc / hs;
+        P.rhot[e] = rt;
+        if (!isfinite((double)rt)) set_err(&P.sc->err, TO_ERR_NONFINITE);
+        T pw, pw1;
+        if (p == 3.0) {
+            pw1 = rt * rt;
+            pw = pw1 * rt;
+        } else {
+            pw1 = (T)pow((double)rt, p - 1.0);
+            pw = pw1 * rt;
+        }
+        P.E[e] = (T)Emin + pw * dE;
+        P.Ed[e] = (T)p * pw1 * dE / hs;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_b_diag(const BProb<T>* __restrict__ tab) {
+    const BProb<T>& P = tab[blockIdx.y];
+    const int nx = P.nx, ny = P.ny, nz = P.nz;
+    const long long nn = P.n_dof / 3;
+    for (long long n = blockIdx.x * 256LL + threadIdx.x; n < nn; n += (long long)gridDim.x * 256) {
+        const int i = (int)(n % (nx + 1)), j = (int)((n / (nx + 1)) % (ny + 1)), k = (int)(n / ((long long)(nx + 1) * (ny + 1)));
+        T s = T(0);
+        for (int dk = -1; dk <= 0; ++dk)
+            for (int dj = -1; dj <= 0; ++dj)
+                for (int di = -1; di <= 0; ++di) {
+                    const int ei = i + di, ej = j + dj, ek = k + dk;
+                    if (ei < 0 || ei >= nx || ej < 0 || ej >= ny || ek < 0 || ek >= nz) continue;
+                    s += P.E[ei + (long long)nx * (ej + (long long)ny * ek)];
+                }
+        const uint8_t mk = P.mask[n];
+        const T v = (T)P.kdiag * s;
+        for (int c = 0; c < 3; ++c) P.d[3 * n + c] = ((mk >> c) & 1) ? T(1) : v;
+    }
+}
+
+// u += beta z, r -= beta q, z = r / d, and r^T z per problem
+template <typename T>
+__global__ void __launch_bounds__(256) k_b_update(const BProb<T>* __restrict__ tab) {
+    __shared__ double sh[32 * kRedQ];
+    const BProb<T>& P = tab[blockIdx.y];
+    const T beta = (T)P.sc->beta;
+    T acc = T(0);
+    for (long long i = blockIdx.x * 256LL + threadIdx.x; i < P.n_dof; i += (long long)gridDim.x * 256) {
+        P.u[i] += beta * P.z[i];
+        const T ri = P.r[i] - beta * P.q[i];
+        P.r[i] = ri;
+        const T zn = ri / P.d[i];
+        P.z[i] = zn;
+        acc += ri * zn;
+    }
+    double v[1] = {(double)acc};
+    const int kind[1] = {0};
+    double tot[1];
+    block_reduce<1>(v, kind, sh);
+    if (finish_reduction<1>(v, kind, P.red, P.counters + 4, tot, sh, blockIdx.x, gridDim.x) && threadIdx.x == 0)
+        P.sc->rz = tot[0];
+}
+
+// g = C^T (g~ / Hs) (prescaled), ||g||_inf, 1^T g, and the step size alpha_k per problem
+template <typename T>
+__global__ void __launch_bounds__(256) k_b_filter_T(const BProb<T>* __restrict__ tab) {
+    __shared__ double sh[32 * kRedQ];
+    const BProb<T>& P = tab[blockIdx.y];
+    const int nx = P.nx, ny = P.ny, nz = P.nz;
+    double amax = 0.0, sum = 0.0;
+    for (long long e = blockIdx.x * 256LL + threadIdx.x; e < P.n_elem; e += (long long)gridDim.x * 256) {
+        const int i = (int)(e % nx), j = (int)((e / nx) % ny), k = (int)(e / ((long long)nx * ny));
+        T acc = T(0);
+        for (int s = 0; s < P.ns; ++s) {
+            const int4 o = P.st[s];
+            const int ii = i + o.x, jj = j + o.y, kk = k + o.z;
+            if (ii < 0 || ii >= nx || jj < 0 || jj >= ny || kk < 0 || kk >= nz) continue;
+            acc += P.stw[s] * P.gt[ii + (long long)nx * (jj + (long long)ny * kk)];
+        }
+        P.grad[e] = acc;
+        amax = fmax(amax, fabs((double)acc));
+        sum += (double)acc;
+    }
+    double v[2] = {amax, sum};
+    const int kind[2] = {1, 0};
+    double tot[2];
+    block_reduce<2>(v, kind, sh);
+    if (finish_reduction<2>(v, kind, P.red, P.counters + 2, tot, sh, blockIdx.x, gridDim.x) && threadIdx.x == 0) {
+        DevScalars* sc = P.sc;
+        sc->gmax = tot[0];
+        sc->gsum = tot[1];
+        if (!isfinite(tot[0]) || !isfinite(tot[1])) set_err(&sc->err, TO_ERR_NONFINITE);
+        double a0 = P.alpha0_param > 0.0 ? P.alpha0_param : sc->alpha0;
+        if (!(a0 > 0.0) && tot[0] > 0.0) a0 = P.alpha_scale / tot[0];
+        sc->alpha0 = a0 > 0.0 ? a0 : 0.0;
+        sc->alpha = a0 > 0.0 ? a0 * pow((double)sc->k, -P.m_exp) : 0.0;
+    }
+}
+
+// ----------------------------------------------------------------------------- projection, one cluster per problem
+constexpr int kClusterCTAs = 8;
+
+__device__ __forceinline__ float proj_ru(double t) {
+    float f = (float)t;
+    if ((double)f < t) f = nextafterf(f, INFINITY);
+    return f;
+}
+__device__ __forceinline__ float proj_rd(double t) {
+    float f = (float)t;
+    if ((double)f > t) f = nextafterf(f, -INFINITY);
+    return f;
+}
+template <typename T> struct BThresh;
+template <> struct BThresh<float> {
+    float tu, tl;
+    __device__ BThresh(double lam, double lo, double hi) : tu(proj_ru(lam + hi)), tl(proj_rd(lam + lo)) {}
+    __device__ int cls(float w) const { return w >= tu ? 0 : (w <= tl ? 1 : 2); }
+};
+template <> struct BThresh<double> {
+    double tu, tl;
+    __device__ BThresh(double lam, double lo, double hi) : tu(lam + hi), tl(lam + lo) {}
+    __device__ int cls(double w) const { return w >= tu ? 0 : (w <= tl ? 1 : 2); }
+};
+
+// Totals over the cluster: every CTA folds the CTAs' slots in rank order
+// through distributed shared memory (identical totals in every CTA).
+template <int NQ>
+__device__ __forceinline__ void cluster_totals(cg::cluster_group& cl, double (*slots)[8], int parity, const int (&kind)[NQ],
+                                               double (&tot)[NQ]) {
+    cl.sync();
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) tot[q] = kind[q] ? -INFINITY : 0.0;
+    for (unsigned r = 0; r < cl.num_blocks(); ++r) {
+        const double* rs = cl.map_shared_rank(&slots[parity][0], r);
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) tot[q] = kind[q] ? fmax(tot[q], rs[q]) : tot[q] + rs[q];
+    }
+}
+
+template <typename T, bool CACHE>
+__global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(256)
+    k_b_project(const BProb<T>* __restrict__ tab) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* wloc = reinterpret_cast<T*>(smem_raw);
+    __shared__ double slots[2][8];
+    __shared__ double sh8[32 * 8];
+    cg::cluster_group cl = cg::this_cluster();
+    const unsigned rank = cl.block_rank();
+    const BProb<T>& P = tab[blockIdx.x / kClusterCTAs];
+    const long long n = P.n_elem;
+    const long long chunk = (n + kClusterCTAs - 1) / kClusterCTAs;
+    const long long b0 = (long long)rank * chunk, b1 = min(b0 + chunk, n);
+    const int tid = threadIdx.x;
+    DevScalars* sc = P.sc;
+    const double alpha = sc->alpha;
+    const double gmean = P.mean_proj ? sc->gsum / (double)n : 0.0;
+    const T alpha_t = (T)alpha, gmean_t = (T)gmean;
+    auto wat = [&](long long e) -> T { return CACHE ? wloc[e - b0] : P.wbuf[e]; };
+    int parity = 0;
+
+    // pass 0
+    double tot6[6];
+    {
+        double v[6] = {0.0, 0.0, 0.0, 0.0, INFINITY, -INFINITY};
+        T sF = T(0), wmn = T(INFINITY), wmx = T(-INFINITY);
+        const BThresh<T> th(0.0, P.lo, P.hi);
+        for (long long e = b0 + tid; e < b1; e += blockDim.x) {
+            const T w = P.rho[e] - alpha_t * (P.grad[e] - gmean_t);
+            if (CACHE) wloc[e - b0] = w;
+            else P.wbuf[e] = w;
+            const int c = th.cls(w);
+            if (c == 0) v[0] += 1.0;
+            else if (c == 1) v[1] += 1.0;
+            else { v[2] += 1.0; sF += w; }
+            wmn = fmin(wmn, w);
+            wmx = fmax(wmx, w);
+        }
+        double mv[6] = {v[0], v[1], v[2], (double)sF, -(double)wmn, (double)wmx};
+        const int kind[6] = {0, 0, 0, 0, 1, 1};
+        block_reduce<6>(mv, kind, sh8);
+        if (tid == 0)
+            for (int q = 0; q < 6; ++q) slots[parity][q] = mv[q];
+        cluster_totals<6>(cl, slots, parity, kind, tot6);
+        parity ^= 1;
+    }
+    const double wmin = -tot6[4], wmax = tot6[5];
+    double S = tot6[0] * P.hi + tot6[1] * P.lo + tot6[3];
+    double lambda = 0.0, lam_lo = 0.0, lam_hi = 0.0;
+    int iters = 0;
+    bool done = !(S > P.vbar) || !isfinite(S);
+    if (!isfinite(S)) set_err(&sc->err, TO_ERR_NONFINITE);
+    if (!done) {
+        lam_lo = fmax(0.0, wmin - P.hi);
+        lam_hi = wmax - P.lo;
+        const double nF = tot6[2];
+        const double ln = nF > 0.0 ? (S - P.vbar) / nF : NAN;
+        lambda = (ln > lam_lo && ln < lam_hi) ? ln : 0.5 * (lam_lo + lam_hi);
+    }
+    while (!done && iters < 100) {
+        ++iters;
+        const BThresh<T> th(lambda, P.lo, P.hi);
+        double v[4] = {0.0, 0.0, 0.0, 0.0};
+        T sF = T(0);
+        for (long long e = b0 + tid; e < b1; e += blockDim.x) {
+            const T w = wat(e);
+            const int c = th.cls(w);
+            if (c == 0) v[0] += 1.0;
+            else if (c == 1) v[1] += 1.0;
+            else { v[2] += 1.0; sF += w; }
+        }
+        v[3] = (double)sF;
+        const int kind[4] = {0, 0, 0, 0};
+        block_reduce<4>(v, kind, sh8);
+        if (tid == 0)
+            for (int q = 0; q < 4; ++q) slots[parity][q] = v[q];
+        double t4[4];
+        cluster_totals<4>(cl, slots, parity, kind, t4);
+        parity ^= 1;
+        const double nF = t4[2];
+        S = t4[0] * P.hi + t4[1] * P.lo + t4[3] - lambda * nF;
+        if (S == P.vbar) break;
+        if (S > P.vbar) lam_lo = lambda;
+        else lam_hi = lambda;
+        const double ln = nF > 0.0 ? lambda + (S - P.vbar) / nF : NAN;
+        const double next = (ln > lam_lo && ln < lam_hi) ? ln : 0.5 * (lam_lo + lam_hi);
+        if (next == lambda || fabs(next - lambda) <= 1e-15 * fmax(1.0, fabs(lambda)) ||
+            lam_hi - lam_lo <= 1e-15 * fmax(1.0, fabs(lambda))) {
+            lambda = next;
+            break;
+        }
+        lambda = next;
+    }
+    double dmax = 0.0, vol = 0.0;
+    for (long long e = b0 + tid; e < b1; e += blockDim.x) {
+        const double wd = (double)wat(e);
+        const T rt = (T)fmin(fmax(wd - lambda, P.lo), P.hi);
+        T* rho = const_cast<T*>(P.rho);
+        dmax = fmax(dmax, fabs((double)rt - (double)rho[e]));
+        vol += (double)rt;
+        rho[e] = rt;
+    }
+    double v2[2] = {dmax, vol};
+    const int kind2[2] = {1, 0};
+    block_reduce<2>(v2, kind2, sh8);
+    if (tid == 0) {
+        slots[parity][0] = v2[0];
+        slots[parity][1] = v2[1];
+    }
+    double t2[2];
+    cluster_totals<2>(cl, slots, parity, kind2, t2);
+    if (rank == 0 && tid == 0) {
+        sc->lambda = lambda;
+        sc->drho_inf = t2[0];
+        sc->volume = t2[1];
+        sc->proj_iters = iters;
+        sc->alpha = alpha;
+    }
+    cl.sync();   // no CTA leaves while another may still read its slots
+}
+
+template <typename T>
+__global__ void k_b_record(const BProb<T>* __restrict__ tab, int n, int reset) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    DevScalars* sc = tab[p].sc;
+    if (reset) {
+        sc->rec = 0;
+        return;
+    }
+    to_stats s;
+    s.k = sc->k;
+    s.J = sc->J;
+    s.res_inf = sc->res_inf;
+    s.res2 = sc->res2;
+    s.drho_inf = sc->drho_inf;
+    s.volume = sc->volume;
+    s.lambda = sc->lambda;
+    s.alpha = sc->alpha;
+    s.gmax = sc->gmax;
+    s.beta_first = sc->beta_first;
+    s.beta_last = sc->beta;
+    s.proj_iters = sc->proj_iters;
+    s.status = sc->err;
+    const int slot = sc->rec;
+    if (slot >= 0 && slot < tab[p].dstats_cap) tab[p].dstats[slot] = s;
+    sc->rec = slot + 1;
+    sc->k += 1;
+    sc->beta_first = 0.0;
+    sc->beta = 0.0;
+}
+
+}  // namespace to
+
+// ----------------------------------------------------------------------------- host side
+struct to_batch {
+    std::vector<to_problem*> probs;
+    int n = 0, prec = TO_FP32_MIXED, n_inner = 0, device = 0;
+    void* btab = nullptr;                 // BProb<T>[n]
+    void* tab_resid = nullptr;            // OpArgs<T>[n]
+    void* tab_q_first = nullptr;
+    void* tab_q = nullptr;
+    void* kh = nullptr;                   // host copy of HaarK<T>
+    int max_tiles = 0, grid_x = 0;
+    size_t proj_smem = 0;
+    bool proj_cache = true;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    int graph_state = 0;
+};
+
+using namespace to;
+
+namespace {
+
+template <typename T>
+int build_tables_t(to_batch* B) {
+    std::vector<BProb<T>> h(B->n);
+    long long max_elem = 0, max_dof = 0;
+    for (int i = 0; i < B->n; ++i) {
+        to_problem* P = B->probs[i];
+        BProb<T>& b = h[i];
+        b.nx = P->g.nx;
+        b.ny = P->g.ny;
+        b.nz = P->g.nz;
+        b.ns = P->n_stencil;
+        b.R = (int)std::ceil(P->mat.rmin);
+        b.n_elem = P->n_elem;
+        b.n_dof = P->n_dof;
+        b.rho = (const T*)P->rho;
+        b.rhot = (T*)P->rhot;
+        b.Hs = (const T*)P->Hs;
+        b.E = (T*)P->lv[0].E;
+        b.Ed = (T*)P->Ed;
+        b.st = P->stencil;
+        b.stw = (const T*)P->stencil_w;
+        b.gt = (const T*)P->gt;
+        b.grad = (T*)P->grad;
+        b.mask = P->lv[0].mask;
+        b.d = (T*)P->lv[0].d;
+        b.kdiag = P->kdiag;
+        b.u = (T*)P->u;
+        b.r = (T*)P->r;
+        b.z = (T*)P->z;
+        b.q = (const T*)P->q;
+        b.wbuf = (T*)P->tmp_e;
+        b.red = P->red;
+        b.counters = P->counters;
+        b.sc = P->sc;
+        b.dstats = P->dstats;
+        b.dstats_cap = P->dstats_cap;
+        b.vbar = P->mat.volfrac * (double)P->n_elem;
+        b.lo = P->mat.rho_min;
+        b.hi = P->mat.rho_max;
+        b.alpha0_param = P->prm.alpha0;
+        b.alpha_scale = P->prm.alpha_scale;
+        b.m_exp = P->prm.m;
+        b.mean_proj = P->prm.mean_proj;
+        max_elem = std::max<long long>(max_elem, (long long)P->n_elem);
+        max_dof = std::max<long long>(max_dof, (long long)P->n_dof);
+    }
+    if (!B->btab && cudaMalloc(&B->btab, sizeof(BProb<T>) * (size_t)B->n) != cudaSuccess)
+        return fail(TO_ERR_CUDA, "batch table allocation");
+    if (cudaMemcpy(B->btab, h.data(), sizeof(BProb<T>) * (size_t)B->n, cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(TO_ERR_CUDA, "batch table upload");
+    // grid-stride width for the elementwise phases: enough blocks for the largest problem
+    B->grid_x = (int)std::min<long long>((max_dof + 255) / 256, 64);
+    const long long chunk = (max_elem + kClusterCTAs - 1) / kClusterCTAs;
+    B->proj_smem = (size_t)chunk * sizeof(T);
+    B->proj_cache = B->proj_smem <= 96 * 1024;
+    if (B->proj_cache) {
+        if (cudaFuncSetAttribute(k_b_project<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B->proj_smem) !=
+            cudaSuccess)
+            return fail(TO_ERR_CUDA, "projection shared-memory opt-in");
+    } else {
+        B->proj_smem = 0;
+    }
+    return TO_OK;
+}
+
+template <typename T>
+int iteration_t(to_batch* B, cudaStream_t s) {
+    const BProb<T>* tab = (const BProb<T>*)B->btab;
+    const to_problem* P0 = B->probs[0];
+    const dim3 g2(B->grid_x, B->n);
+    k_b_design<T><<<g2, 256, 0, s>>>(tab, P0->mat.E0, P0->mat.Emin, P0->mat.p);
+    k_b_diag<T><<<g2, 256, 0, s>>>(tab);
+    TO_CUDA(cudaGetLastError());
+    int rc = batch_operator_launch(B->prec, OP_RESID, B->tab_resid, B->kh, B->max_tiles, B->n, s);
+    if (rc) return rc;
+    for (int it = 0; it < B->n_inner; ++it) {
+        rc = batch_operator_launch(B->prec, OP_Q, it == 0 ? B->tab_q_first : B->tab_q, B->kh, B->max_tiles, B->n, s);
+        if (rc) return rc;
+        k_b_update<T><<<g2, 256, 0, s>>>(tab);
+        TO_CUDA(cudaGetLastError());
+    }
+    k_b_filter_T<T><<<g2, 256, 0, s>>>(tab);
+    if (B->proj_cache)
+        k_b_project<T, true><<<B->n * kClusterCTAs, 256, B->proj_smem, s>>>(tab);
+    else
+        k_b_project<T, false><<<B->n * kClusterCTAs, 256, 0, s>>>(tab);
+    k_b_record<T><<<(B->n + 63) / 64, 64, 0, s>>>(tab, B->n, 0);
+    TO_CUDA(cudaGetLastError());
+    return TO_OK;
+}
+
+void destroy_batch(to_batch* B) {
+    if (!B) return;
+    if (B->stream) cudaStreamSynchronize(B->stream);
+    if (B->gexec) cudaGraphExecDestroy(B->gexec);
+    if (B->ev_in) cudaEventDestroy(B->ev_in);
+    if (B->ev_out) cudaEventDestroy(B->ev_out);
+    if (B->stream) cudaStreamDestroy(B->stream);
+    void* ps[] = {B->btab, B->tab_resid, B->tab_q_first, B->tab_q};
+    for (void* p : ps)
+        if (p) cudaFree(p);
+    free(B->kh);
+    delete B;
+}
+
+}  // namespace
+
+extern "C" int to_batch_create(to_problem* const* problems, int32_t n, to_batch** out) {
+    if (!out) return fail(TO_ERR_ARG, "out is null");
+    *out = nullptr;
+    if (!problems || n < 1) return fail(TO_ERR_ARG, "need at least one problem");
+    const to_problem* P0 = problems[0];
+    if (!P0) return fail(TO_ERR_ARG, "null problem");
+    for (int i = 0; i < n; ++i) {
+        const to_problem* P = problems[i];
+        if (!P) return fail(TO_ERR_ARG, "null problem");
+        if (P->prec != P0->prec || P->device != P0->device || P->prm.precond != TO_PRECOND_JACOBI ||
+            P->prm.inner_mode != TO_INNER_SD || P->prm.n_inner != P0->prm.n_inner || P->g.h != P0->g.h ||
+            P->mat.E0 != P0->mat.E0 || P->mat.Emin != P0->mat.Emin || P->mat.p != P0->mat.p || P->mat.nu != P0->mat.nu)
+            return fail(TO_ERR_ARG,
+                        "batched problems must share precision, device, element size, material moduli and n_inner, "
+                        "and use the Jacobi preconditioner with steepest descent");
+    }
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (cudaSetDevice(P0->device) != cudaSuccess) return fail(TO_ERR_CUDA, "cudaSetDevice failed");
+    to_batch* B = new to_batch();
+    B->probs.assign(problems, problems + n);
+    B->n = n;
+    B->prec = P0->prec;
+    B->n_inner = P0->prm.n_inner;
+    B->device = P0->device;
+    int rc = P0->prec == TO_FP64 ? build_tables_t<double>(B) : build_tables_t<float>(B);
+    if (!rc) rc = op_tables_build(B->probs.data(), n, &B->tab_resid, &B->tab_q_first, &B->tab_q, &B->kh, &B->max_tiles);
+    if (!rc && (cudaStreamCreateWithFlags(&B->stream, cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&B->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&B->ev_out, cudaEventDisableTiming) != cudaSuccess))
+        rc = fail(TO_ERR_CUDA, "batch stream / event creation failed");
+    if (prev >= 0) cudaSetDevice(prev);
+    if (rc) {
+        destroy_batch(B);
+        return rc;
+    }
+    *out = B;
+    return TO_OK;
+}
+
+extern "C" void to_batch_destroy(to_batch* B) {
+    if (!B) return;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(B->device);
+    destroy_batch(B);
+    if (prev >= 0) cudaSetDevice(prev);
+}
+
+extern "C" int to_batch_step(to_batch* B, int32_t n_outer, to_stats* stats_out, void* stream) {
+    if (!B) return fail(TO_ERR_ARG, "null batch");
+    if (n_outer < 0) return fail(TO_ERR_ARG, "n_outer must be >= 0");
+    if (n_outer == 0) return TO_OK;
+    for (to_problem* P : B->probs)
+        if (n_outer > P->dstats_cap)
+            return fail(TO_ERR_ARG, "n_outer exceeds a problem's stats ring (run to_step once with that many iterations "
+                                    "to grow it, or use fewer outer iterations per call)");
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (cudaSetDevice(B->device) != cudaSuccess) return fail(TO_ERR_CUDA, "cudaSetDevice failed");
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = TO_OK;
+    auto body = [&]() -> int {
+        TO_CUDA(cudaEventRecord(B->ev_in, s));
+        TO_CUDA(cudaStreamWaitEvent(B->stream, B->ev_in, 0));
+        if (B->prec == TO_FP64)
+            k_b_record<double><<<(B->n + 63) / 64, 64, 0, B->stream>>>((const BProb<double>*)B->btab, B->n, 1);
+        else
+            k_b_record<float><<<(B->n + 63) / 64, 64, 0, B->stream>>>((const BProb<float>*)B->btab, B->n, 1);
+        TO_CUDA(cudaGetLastError());
+        if (B->graph_state == 0) {
+            cudaGraph_t g = nullptr;
+            B->graph_state = -1;
+            if (cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+                const int r2 = B->prec == TO_FP64 ? iteration_t<double>(B, B->stream) : iteration_t<float>(B, B->stream);
+                if (cudaStreamEndCapture(B->stream, &g) == cudaSuccess && g && r2 == TO_OK &&
+                    cudaGraphInstantiate(&B->gexec, g, 0) == cudaSuccess)
+                    B->graph_state = 1;
+                if (g) cudaGraphDestroy(g);
+            }
+            cudaGetLastError();
+        }
+        for (int i = 0; i < n_outer; ++i) {
+            if (B->graph_state == 1) {
+                TO_CUDA(cudaGraphLaunch(B->gexec, B->stream));
+            } else {
+                const int r2 = B->prec == TO_FP64 ? iteration_t<double>(B, B->stream) : iteration_t<float>(B, B->stream);
+                if (r2) return r2;
+            }
+        }
+        TO_CUDA(cudaEventRecord(B->ev_out, B->stream));
+        TO_CUDA(cudaStreamWaitEvent(s, B->ev_out, 0));
+        if (stats_out) {
+            for (int p = 0; p < B->n; ++p)
+                TO_CUDA(cudaMemcpyAsync(stats_out + (size_t)p * n_outer, B->probs[p]->dstats,
+                                        sizeof(to_stats) * (size_t)n_outer, cudaMemcpyDeviceToHost, s));
+            TO_CUDA(cudaStreamSynchronize(s));
+            for (int p = 0; p < B->n; ++p)
+                for (int i = 0; i < n_outer; ++i)
+                    if (stats_out[(size_t)p * n_outer + i].status)
+                        return fail(stats_out[(size_t)p * n_outer + i].status, "device-side error in a batched problem");
+        }
+        return TO_OK;
+    };
+    rc = body();
+    if (prev >= 0) cudaSetDevice(prev);
+    return rc;
+}

@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(256) k_filter(int nx, int ny, int nz, const T*
         const int kind[2] = {1, 0};
         double tot[2];
         block_reduce<2>(v, kind, sh);
-        if (finish_reduction<2>(v, kind, red, counter, tot, sh) && threadIdx.x == 0 && threadIdx.y == 0) {
+        if (finish_reduction<2>(v, kind, red, counter, tot, sh, linear_block(), grid_blocks()) && threadIdx.x == 0 && threadIdx.y == 0) {
             sc->gmax = tot[0];
             sc->gsum = tot[1];
             if (!isfinite(tot[0]) || !isfinite(tot[1])) set_err(&sc->err, TO_ERR_NONFINITE);

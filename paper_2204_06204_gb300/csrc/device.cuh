@@ -40,16 +40,15 @@ __device__ __forceinline__ void block_reduce(double (&v)[NQ], const int (&kind)[
     __syncthreads();
 }
 
-// Write this block's partials, then let the last block to finish combine all
-// partials in block order.  Returns true (in every thread) only in that block,
+// Write this block's partials (slot `bid` of `nblocks` taking part), then let the
+// last block to finish combine all partials in block order.  Returns true (in every thread) only in that block,
 // with the totals in `tot` valid in all its threads.
 template <int NQ>
 __device__ __forceinline__ bool finish_reduction(const double (&v)[NQ], const int (&kind)[NQ], double* partials,
-                                                 unsigned* counter, double (&tot)[NQ], double* sh) {
+                                                 unsigned* counter, double (&tot)[NQ], double* sh, unsigned bid,
+                                                 unsigned nblocks) {
     __shared__ int s_last;
     const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
-    const unsigned nblocks = gridDim.x * gridDim.y * gridDim.z;
-    const unsigned bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
     if (tid == 0) {
 #pragma unroll
         for (int q = 0; q < NQ; ++q) partials[bid * kRedQ + q] = v[q];
@@ -118,6 +117,9 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err) {
 }
 
 __device__ __forceinline__ void set_err(int* err, int code) { atomicCAS(err, 0, code); }
+
+__device__ __forceinline__ unsigned linear_block() { return blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z); }
+__device__ __forceinline__ unsigned grid_blocks() { return gridDim.x * gridDim.y * gridDim.z; }
 
 // 3-D lattice launches: block (32, 8), grid (ceil(X/32), ceil(Y/8), Z); no divisions per thread.
 inline dim3 grid3(int X, int Y, int Z) { return dim3((unsigned)((X + 31) / 32), (unsigned)((Y + 7) / 8), (unsigned)Z); }

@@ -19,6 +19,8 @@
 //      to node plane k, brought back to nodes by the inverse face butterflies;
 //   5. the four columns around each owned node add their corner contributions
 //      in a fixed order (no atomics: bitwise reproducible).
+#include <vector>
+
 #include "device.cuh"
 
 namespace to {
@@ -166,8 +168,11 @@ struct OpSmem {
 constexpr int kDepth = 2;                  // planes in flight ahead of the one being consumed
 constexpr int kRing = kDepth + 2;
 
+// The operator for one CTA tile (bx, by, bz) of one problem; `bid` / `nblocks` place
+// the tile among the problem's tiles for the fused reductions.
 template <typename T, int TX, int TY, int MODE>
-__global__ void __launch_bounds__(TX * TY) k_operator(const OpArgs<T> a) {
+__device__ __forceinline__ void op_body(const OpArgs<T>& a, const HaarK<T>& kh, int bx, int by, int bz, unsigned bid,
+                                        unsigned nblocks) {
     static_assert(TX == 32, "one warp per row of element columns");
     using P = typename PairT<T>::t;
     using N4 = typename Node4<T>::t;
@@ -182,8 +187,8 @@ __global__ void __launch_bounds__(TX * TY) k_operator(const OpArgs<T> a) {
 
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = tx + TX * ty;
-    const int X0 = blockIdx.x * (TX - 1), Y0 = blockIdx.y * (TY - 1);
-    const int kb = blockIdx.z * a.kchunk;
+    const int X0 = bx * (TX - 1), Y0 = by * (TY - 1);
+    const int kb = bz * a.kchunk;
     const int ke = min(kb + a.kchunk, a.nz + 1);
     const int nxn = a.nx + 1, nyn = a.ny + 1;
     const long long nplane = (long long)nxn * nyn;
@@ -305,7 +310,7 @@ __global__ void __launch_bounds__(TX * TY) k_operator(const OpArgs<T> a) {
                 uh[12 + 3 * f + 2] = Ft.z[f] - Fb.z[f];
             }
             T v[24];
-            haar_apply(a.kh.v, uh, v);
+            haar_apply(kh.v, uh, v);
             if (MODE == OP_RESID) {
                 if (a.gt && owner && k + 1 >= kb && k + 1 < ke) {
                     T en = T(0);
@@ -415,7 +420,7 @@ __global__ void __launch_bounds__(TX * TY) k_operator(const OpArgs<T> a) {
         const int kind[1] = {0};
         double tot[1];
         block_reduce<1>(v, kind, sh_red);
-        if (finish_reduction<1>(v, kind, a.red, a.counter, tot, sh_red) && tid == 0) {
+        if (finish_reduction<1>(v, kind, a.red, a.counter, tot, sh_red, bid, nblocks) && tid == 0) {
             a.sc->rz = tot[0];
             if (!isfinite(tot[0])) set_err(&a.sc->err, TO_ERR_NONFINITE);
         }
@@ -425,7 +430,7 @@ __global__ void __launch_bounds__(TX * TY) k_operator(const OpArgs<T> a) {
         const int kind[1] = {0};
         double tot[1];
         block_reduce<1>(v, kind, sh_red);
-        if (finish_reduction<1>(v, kind, a.red, a.counter, tot, sh_red) && tid == 0) {
+        if (finish_reduction<1>(v, kind, a.red, a.counter, tot, sh_red, bid, nblocks) && tid == 0) {
             DevScalars* sc = a.sc;
             sc->zq = tot[0];
             const double rz = sc->rz;
@@ -443,7 +448,7 @@ __global__ void __launch_bounds__(TX * TY) k_operator(const OpArgs<T> a) {
         const int kind[4] = {0, 0, 1, 0};
         double tot[4];
         block_reduce<4>(v, kind, sh_red);
-        if (finish_reduction<4>(v, kind, a.red, a.counter, tot, sh_red) && tid == 0) {
+        if (finish_reduction<4>(v, kind, a.red, a.counter, tot, sh_red, bid, nblocks) && tid == 0) {
             DevScalars* sc = a.sc;
             sc->rz = tot[0];
             if (a.first_step) {   // the residual at u_k: tracking error and compliance estimate
@@ -454,6 +459,24 @@ __global__ void __launch_bounds__(TX * TY) k_operator(const OpArgs<T> a) {
             if (!isfinite(tot[1]) || !isfinite(tot[0])) set_err(&sc->err, TO_ERR_NONFINITE);
         }
     }
+}
+
+template <typename T, int TX, int TY, int MODE>
+__global__ void __launch_bounds__(TX * TY) k_operator(const OpArgs<T> a) {
+    op_body<T, TX, TY, MODE>(a, a.kh, blockIdx.x, blockIdx.y, blockIdx.z, linear_block(), grid_blocks());
+}
+
+// Many problems in one launch: blockIdx.y selects the problem (its arguments come
+// from a device table), blockIdx.x enumerates that problem's tiles; the element
+// matrix constants are common to the batch.
+template <typename T, int TX, int TY, int MODE>
+__global__ void __launch_bounds__(TX * TY) k_operator_batch(const OpArgs<T>* __restrict__ tab, const HaarK<T> kh) {
+    const OpArgs<T> a = tab[blockIdx.y];
+    const int gx = (a.nx + 1 + TX - 2) / (TX - 1), gy = (a.ny + 1 + TY - 2) / (TY - 1);
+    const int gz = (a.nz + 1 + a.kchunk - 1) / a.kchunk;
+    const int t = blockIdx.x;
+    if (t >= gx * gy * gz) return;
+    op_body<T, TX, TY, MODE>(a, kh, t % gx, (t / gx) % gy, t / (gx * gy), (unsigned)t, (unsigned)(gx * gy * gz));
 }
 
 template <typename T>
@@ -539,6 +562,115 @@ int launch_operator(to_problem* P, int level, int mode, const void* x, void* y, 
                     cudaStream_t s, double omega, int first) {
     if (P->prec == TO_FP64) return launch_t<double, 32, 8>(P, level, mode, x, y, b, s, omega, first);
     return launch_t<float, 32, 8>(P, level, mode, x, y, b, s, omega, first);
+}
+
+}  // namespace to
+
+// ----------------------------------------------------------------------------- batched launches
+namespace to {
+
+template <typename T>
+static OpArgs<T> batch_args(to_problem* P, int mode, int first) {
+    const Level& L = P->lv[0];
+    OpArgs<T> a{};
+    a.nx = L.nx;
+    a.ny = L.ny;
+    a.nz = L.nz;
+    a.kchunk = L.nz + 1 < 8 ? L.nz + 1 : 8;
+    a.E = (const T*)L.E;
+    a.mask = L.mask;
+    a.d = (const T*)L.d;
+    a.red = P->red;
+    a.sc = P->sc;
+    a.first_step = first;
+    fill_haar<T>(P, 1.0, a.kh);
+    if (mode == OP_RESID) {
+        a.x = (const T*)P->u;
+        a.y = (T*)P->r;
+        a.b = (const T*)P->f;
+        a.z = (T*)P->z;
+        a.Ed = (const T*)P->Ed;
+        a.gt = (T*)P->gt;
+        a.counter = P->counters + 0;
+    } else {
+        a.x = (const T*)P->z;
+        a.y = (T*)P->q;
+        a.counter = P->counters + 1;
+    }
+    return a;
+}
+
+template <typename T>
+static int op_table_t(to_problem* const* probs, int n, int mode, int first, void** dev, int* max_tiles) {
+    std::vector<OpArgs<T>> h(n);
+    int mt = 0;
+    for (int i = 0; i < n; ++i) {
+        h[i] = batch_args<T>(probs[i], mode, first);
+        const int gx = (h[i].nx + 1 + 30) / 31, gy = (h[i].ny + 1 + 6) / 7, gz = (h[i].nz + 1 + h[i].kchunk - 1) / h[i].kchunk;
+        if ((long long)gx * gy * gz > kMaxRedBlocks) return fail(TO_ERR_ARG, "batched problem too large for the reduction slots");
+        mt = mt > gx * gy * gz ? mt : gx * gy * gz;
+    }
+    if (!*dev && cudaMalloc(dev, sizeof(OpArgs<T>) * (size_t)n) != cudaSuccess) return fail(TO_ERR_CUDA, "table allocation");
+    if (cudaMemcpy(*dev, h.data(), sizeof(OpArgs<T>) * (size_t)n, cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(TO_ERR_CUDA, "table upload");
+    *max_tiles = mt;
+    return TO_OK;
+}
+
+// device tables of operator arguments for a list of problems, and the common element constants
+int op_tables_build(to_problem* const* probs, int n, void** resid, void** q_first, void** q, void** kh_host,
+                    int* max_tiles) {
+    const int prec = probs[0]->prec;
+    int mt = 0, rc;
+    if (prec == TO_FP64) {
+        if ((rc = op_table_t<double>(probs, n, OP_RESID, 1, resid, &mt)) || (rc = op_table_t<double>(probs, n, OP_Q, 1, q_first, &mt)) ||
+            (rc = op_table_t<double>(probs, n, OP_Q, 0, q, &mt)))
+            return rc;
+        HaarK<double>* kh = (HaarK<double>*)malloc(sizeof(HaarK<double>));
+        fill_haar<double>(probs[0], 1.0, *kh);
+        *kh_host = kh;
+    } else {
+        if ((rc = op_table_t<float>(probs, n, OP_RESID, 1, resid, &mt)) || (rc = op_table_t<float>(probs, n, OP_Q, 1, q_first, &mt)) ||
+            (rc = op_table_t<float>(probs, n, OP_Q, 0, q, &mt)))
+            return rc;
+        HaarK<float>* kh = (HaarK<float>*)malloc(sizeof(HaarK<float>));
+        fill_haar<float>(probs[0], 1.0, *kh);
+        *kh_host = kh;
+    }
+    *max_tiles = mt;
+    // shared-memory opt-in of the batched kernels
+    const size_t smem = prec == TO_FP64 ? sizeof(OpSmem<double, 32, 8, kRing>) : sizeof(OpSmem<float, 32, 8, kRing>);
+    const void* fns[2];
+    if (prec == TO_FP64) {
+        fns[0] = (const void*)k_operator_batch<double, 32, 8, OP_RESID>;
+        fns[1] = (const void*)k_operator_batch<double, 32, 8, OP_Q>;
+    } else {
+        fns[0] = (const void*)k_operator_batch<float, 32, 8, OP_RESID>;
+        fns[1] = (const void*)k_operator_batch<float, 32, 8, OP_Q>;
+    }
+    for (const void* f : fns) TO_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    return TO_OK;
+}
+
+int batch_operator_launch(int prec, int mode, const void* tab, const void* kh, int max_tiles, int n, cudaStream_t s) {
+    const dim3 grid(max_tiles, n), block(32, 8);
+    if (prec == TO_FP64) {
+        const size_t smem = sizeof(OpSmem<double, 32, 8, kRing>);
+        const HaarK<double>& k = *(const HaarK<double>*)kh;
+        if (mode == OP_RESID)
+            k_operator_batch<double, 32, 8, OP_RESID><<<grid, block, smem, s>>>((const OpArgs<double>*)tab, k);
+        else
+            k_operator_batch<double, 32, 8, OP_Q><<<grid, block, smem, s>>>((const OpArgs<double>*)tab, k);
+    } else {
+        const size_t smem = sizeof(OpSmem<float, 32, 8, kRing>);
+        const HaarK<float>& k = *(const HaarK<float>*)kh;
+        if (mode == OP_RESID)
+            k_operator_batch<float, 32, 8, OP_RESID><<<grid, block, smem, s>>>((const OpArgs<float>*)tab, k);
+        else
+            k_operator_batch<float, 32, 8, OP_Q><<<grid, block, smem, s>>>((const OpArgs<float>*)tab, k);
+    }
+    TO_CUDA(cudaGetLastError());
+    return TO_OK;
 }
 
 }  // namespace to

@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(256) k_project(const ProjArgs<T> a) {
     const int kind2[2] = {1, 0};
     double tot2[2];
     block_reduce<2>(v2, kind2, sh);
-    if (finish_reduction<2>(v2, kind2, a.red, a.counter, tot2, sh) && tid == 0) {
+    if (finish_reduction<2>(v2, kind2, a.red, a.counter, tot2, sh, linear_block(), grid_blocks()) && tid == 0) {
         sc->lambda = lambda;
         sc->drho_inf = tot2[0];
         sc->volume = tot2[1];

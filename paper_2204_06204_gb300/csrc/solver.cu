@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(256) k_update_sd(long long n, T* __restrict__ 
         const int kind[1] = {0};
         double tot[1];
         block_reduce<1>(v, kind, sh);
-        if (finish_reduction<1>(v, kind, red, counter, tot, sh) && threadIdx.x == 0) sc->rz = tot[0];
+        if (finish_reduction<1>(v, kind, red, counter, tot, sh, linear_block(), grid_blocks()) && threadIdx.x == 0) sc->rz = tot[0];
     }
 }
 
@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(256) k_dot_rz(long long n, const T* __restrict
     const int kind[1] = {0};
     double tot[1];
     block_reduce<1>(v, kind, sh);
-    if (finish_reduction<1>(v, kind, red, counter, tot, sh) && threadIdx.x == 0) sc->rz = tot[0];
+    if (finish_reduction<1>(v, kind, red, counter, tot, sh, linear_block(), grid_blocks()) && threadIdx.x == 0) sc->rz = tot[0];
 }
 
 // u += beta z  (Richardson)
