@@ -117,6 +117,8 @@ extern "C" void to_destroy(to_problem* P) {
         dfree(L.d);
         void* mk = L.mask;
         dfree(mk);
+        void* tm = L.tmask;
+        dfree(tm);
         dfree(L.x);
         dfree(L.b);
         dfree(L.t);
@@ -249,6 +251,7 @@ extern "C" int to_create(const to_grid* g, const to_material* m, const to_loads*
     for (size_t i = 0; i < nd; ++i)
         if ((hmask[i / 3] >> (i % 3)) & 1) hf[i] = 0.0;
 
+    if ((rc = build_tile_mask(F, hmask.data()))) return bail(rc);
     cudaStream_t s = nullptr;
     if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return bail(fail(TO_ERR_CUDA, "stream"));
     auto upload = [&](void* dst, const void* src, size_t bytes) {

@@ -71,6 +71,7 @@ struct Level {
     void* E = nullptr;        // element moduli (T)
     void* d = nullptr;        // diag(K^) (T)
     uint8_t* mask = nullptr;  // per node: bit c set = DOF c fixed
+    uint8_t* tmask = nullptr; // per operator tile column: any fixed node in its footprint
     void* x = nullptr;        // V-cycle vectors (T)
     void* b = nullptr;
     void* t = nullptr;
@@ -169,6 +170,7 @@ int launch_sens_filter_T(to_problem* P, cudaStream_t s);
 int launch_energy(to_problem* P, const void* u, cudaStream_t s);
 int launch_record(to_problem* P, cudaStream_t s);
 int operator_init(to_problem* P);
+int build_tile_mask(Level& L, const uint8_t* mask_host);
 int launch_richardson(to_problem* P, cudaStream_t s);
 
 // multigrid

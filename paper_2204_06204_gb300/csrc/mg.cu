@@ -379,6 +379,7 @@ int mg_build(to_problem* P) {
         if (e != cudaSuccess) return fail(TO_ERR_CUDA, std::string("multigrid allocation: ") + cudaGetErrorString(e));
         if (cudaMemcpy(mk, mc.data(), mc.size(), cudaMemcpyHostToDevice) != cudaSuccess)
             return fail(TO_ERR_CUDA, "mask upload");
+        if (int rc2 = build_tile_mask(P->lv.back(), mc.data())) return rc2;
         mf.swap(mc);
     }
     const Level& Cst = P->lv.back();

@@ -19,6 +19,8 @@
 //      to node plane k, brought back to nodes by the inverse face butterflies;
 //   5. the four columns around each owned node add their corner contributions
 //      in a fixed order (no atomics: bitwise reproducible).
+#include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "device.cuh"
@@ -42,6 +44,7 @@ struct OpArgs {
     double* red;
     unsigned* counter;
     DevScalars* sc;
+    const uint8_t* tmask;   // per CTA tile column: any fixed node in its footprint (nullptr = assume yes)
     int first_step;   // Q: record beta as the first step size of the iteration;
                       // RESID: this is the residual at u_k (record norms and J)
 };
@@ -174,6 +177,7 @@ template <typename T, int TX, int TY, int MODE>
 __device__ __forceinline__ void op_body(const OpArgs<T>& a, const HaarK<T>& kh, int bx, int by, int bz, unsigned bid,
                                         unsigned nblocks) {
     static_assert(TX == 32, "one warp per row of element columns");
+    static_assert(kRing == 4, "the ring phase is dispatched at compile time");
     using P = typename PairT<T>::t;
     using N4 = typename Node4<T>::t;
     using SM = OpSmem<T, TX, TY, kRing>;
@@ -200,8 +204,12 @@ __device__ __forceinline__ void op_body(const OpArgs<T>& a, const HaarK<T>& kh, 
     const long long own_base = (long long)ni + (long long)nxn * nj;
     const long long elem_base = col_in ? (long long)ie + (long long)a.nx * je : 0;
     const bool dz = NEED_D && a.d != nullptr && (MODE != OP_RESID || a.z != nullptr);
+    // tiles whose footprint holds no fixed node skip every mask operation
+    const bool hm = a.tmask == nullptr || a.tmask[bx + ((a.nx + 1 + TX - 2) / (TX - 1)) * by] != 0;
 
-    long long st_base[SR];
+    // per-thread staging pointers (advanced by whole planes)
+    const T* st_x[SR];
+    long long st_node[SR];
     bool st_ok[SR];
 #pragma unroll
     for (int r = 0; r < SR; ++r) {
@@ -209,53 +217,59 @@ __device__ __forceinline__ void op_body(const OpArgs<T>& a, const HaarK<T>& kh, 
         const int px = sidx % (TX + 1), py = sidx / (TX + 1);
         const int gi = X0 - 1 + px, gj = Y0 - 1 + py;
         st_ok[r] = sidx < PN && gi >= 0 && gi < nxn && gj >= 0 && gj < nyn;
-        st_base[r] = st_ok[r] ? (long long)gi + (long long)nxn * gj : 0;
+        st_node[r] = st_ok[r] ? (long long)gi + (long long)nxn * gj : 0;
+        st_x[r] = a.x + 3 * st_node[r];
     }
-    auto slot = [](int p) { return (p + kRing) % kRing; };
+    const T* e_src = a.E + elem_base;
+    const T* b_src = NEED_B ? a.b + 3 * own_base : nullptr;
+    const T* d_src = dz ? a.d + 3 * own_base : nullptr;
 
-    // issue every asynchronous copy that plane p (and element layer p-1) needs
-    auto issue = [&](int p) {
-        const int sp = slot(p);
+    // all asynchronous copies that plane p (and element layer p-1) needs, into ring slot SP
+    auto issue = [&](int p, auto SPc) {
+        constexpr int SP = decltype(SPc)::value;
         const bool pin = p >= 0 && p <= a.nz;
+        const long long pn = (long long)p * nplane;
 #pragma unroll
         for (int r = 0; r < SR; ++r) {
             const int sidx = tid + r * NT;
             if (sidx < PN) {
                 const bool v = st_ok[r] && pin;
-                const long long node = v ? st_base[r] + p * nplane : 0;
-                T* dst = reinterpret_cast<T*>(&sm.plane[sp][sidx]);
-                cp_async_t<T>(dst + 0, a.x + 3 * node + 0, v);
-                cp_async_t<T>(dst + 1, a.x + 3 * node + 1, v);
-                cp_async_t<T>(dst + 2, a.x + 3 * node + 2, v);
-                cp_async_4(&sm.mword[sp][sidx], reinterpret_cast<const uint32_t*>(a.mask) + (node >> 2), v);
+                const T* src = v ? st_x[r] + 3 * pn : a.x;
+                T* dst = reinterpret_cast<T*>(&sm.plane[SP][sidx]);
+                cp_async_t<T>(dst + 0, src + 0, v);
+                cp_async_t<T>(dst + 1, src + 1, v);
+                cp_async_t<T>(dst + 2, src + 2, v);
+                if (hm)
+                    cp_async_4(&sm.mword[SP][sidx],
+                               reinterpret_cast<const uint32_t*>(a.mask) + (v ? (st_node[r] + pn) >> 2 : 0), v);
             }
         }
-        const int L = p - 1;   // element layer whose top face is plane p
+        const int L = p - 1;
         const bool ev = col_in && L >= 0 && L < a.nz;
-        cp_async_t<T>(&sm.ebuf[sp][ty][tx], ev ? a.E + (elem_base + (long long)L * eplane) : a.E, ev);
+        cp_async_t<T>(&sm.ebuf[SP][ty][tx], ev ? e_src + (long long)L * eplane : a.E, ev);
         if (NEED_B || dz) {
             const bool ov = owner && p >= kb && p < ke;
-            const long long node = ov ? own_base + p * nplane : 0;
             if (NEED_B)
 #pragma unroll
-                for (int c = 0; c < 3; ++c) cp_async_t<T>(&sm.eb[sp][ty][tx][c], a.b + 3 * node + c, ov);
+                for (int c = 0; c < 3; ++c) cp_async_t<T>(&sm.eb[SP][ty][tx][c], ov ? b_src + 3 * pn + c : a.b, ov);
             if (dz)
 #pragma unroll
-                for (int c = 0; c < 3; ++c) cp_async_t<T>(&sm.ed[sp][ty][tx][c], a.d + 3 * node + c, ov);
+                for (int c = 0; c < 3; ++c) cp_async_t<T>(&sm.ed[SP][ty][tx][c], ov ? d_src + 3 * pn + c : a.d, ov);
         }
         cp_commit();
     };
-    // zero the fixed components of the nodes this thread staged for plane p (after they landed)
-    auto patch = [&](int p) {
-        const int sp = slot(p);
+    auto patch = [&](int p, auto SPc) {
+        constexpr int SP = decltype(SPc)::value;
+        if (!hm || p < 0 || p > a.nz) return;
+        const long long pn = (long long)p * nplane;
 #pragma unroll
         for (int r = 0; r < SR; ++r) {
             const int sidx = tid + r * NT;
-            if (sidx < PN && st_ok[r] && p >= 0 && p <= a.nz) {
-                const long long node = st_base[r] + p * nplane;
-                const uint32_t m = (sm.mword[sp][sidx] >> (8 * (int)(node & 3))) & 0xffu;
+            if (sidx < PN && st_ok[r]) {
+                const long long node = st_node[r] + pn;
+                const uint32_t m = (sm.mword[SP][sidx] >> (8 * (int)(node & 3))) & 0xffu;
                 if (m) {
-                    T* dst = reinterpret_cast<T*>(&sm.plane[sp][sidx]);
+                    T* dst = reinterpret_cast<T*>(&sm.plane[SP][sidx]);
                     if (m & 1) dst[0] = T(0);
                     if (m & 2) dst[1] = T(0);
                     if (m & 4) dst[2] = T(0);
@@ -263,41 +277,66 @@ __device__ __forceinline__ void op_body(const OpArgs<T>& a, const HaarK<T>& kh, 
             }
         }
     };
+    using I0 = std::integral_constant<int, 0>;
+    using I1 = std::integral_constant<int, 1>;
+    using I2 = std::integral_constant<int, 2>;
+    using I3 = std::integral_constant<int, 3>;
+    // ring slot of plane p is p & 3 (p >= -1, so use (p + 4) & 3)
+    auto issue_p = [&](int p) {
+        switch ((p + 4) & 3) {
+            case 0: issue(p, I0{}); break;
+            case 1: issue(p, I1{}); break;
+            case 2: issue(p, I2{}); break;
+            default: issue(p, I3{}); break;
+        }
+    };
+    auto patch_p = [&](int p) {
+        switch ((p + 4) & 3) {
+            case 0: patch(p, I0{}); break;
+            case 1: patch(p, I1{}); break;
+            case 2: patch(p, I2{}); break;
+            default: patch(p, I3{}); break;
+        }
+    };
 
     T acc0 = T(0), acc1 = T(0), acc3 = T(0), accmax = T(0);
 
-    // prologue: planes kb-1 .. kb+kDepth-1 in flight; wait for kb-1 and kb
 #pragma unroll
-    for (int q = 0; q <= kDepth; ++q) issue(kb - 1 + q);
+    for (int q = 0; q <= kDepth; ++q) issue_p(kb - 1 + q);
     cp_wait<kDepth - 1>();
-    patch(kb - 1);
-    patch(kb);
+    patch_p(kb - 1);
+    patch_p(kb);
     __syncthreads();
-    Face<T> Fb;
+    Face<T> Fb, Gc;
     {
-        const N4* bp = sm.plane[slot(kb - 1)];
+        const N4* bp = sm.plane[(kb - 1 + 4) & 3];
         face_forward4<T>(bp[ty * (TX + 1) + tx], bp[ty * (TX + 1) + tx + 1], bp[(ty + 1) * (TX + 1) + tx],
                          bp[(ty + 1) * (TX + 1) + tx + 1], Fb);
     }
-    Face<T> Gc;
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
         Gc.p[f] = P{T(0), T(0)};
         Gc.z[f] = T(0);
     }
+    T* y_own = a.y + 3 * own_base;
+    const T* x_own = a.x + 3 * own_base;
 
-    for (int k = kb - 1; k < ke; ++k) {
-        issue(k + 1 + kDepth);
-        const int s_top = slot(k + 1), s_bot = slot(k);
+    // one element layer with compile-time ring slots: top plane k+1 in slot ST, bottom plane k in SB
+    auto layer = [&](int k, auto STc) {
+        constexpr int ST = decltype(STc)::value;
+        constexpr int SB = (ST + 3) & 3;
+        constexpr int SI = (ST + 2) & 3;   // plane k+3 is issued into the slot of plane k-1
+        constexpr int SN = (ST + 1) & 3;   // plane k+2, patched at the end of this layer
+        issue(k + 1 + kDepth, std::integral_constant<int, SI>{});
 
-        const N4* tp = sm.plane[s_top];
+        const N4* tp = sm.plane[ST];
         Face<T> Ft;
         face_forward4<T>(tp[ty * (TX + 1) + tx], tp[ty * (TX + 1) + tx + 1], tp[(ty + 1) * (TX + 1) + tx],
                          tp[(ty + 1) * (TX + 1) + tx + 1], Ft);
         Face<T> S;
         const bool elem_in = col_in && k >= 0 && k < a.nz;
         if (elem_in) {
-            const T Ee = sm.ebuf[s_top][ty][tx];
+            const T Ee = sm.ebuf[ST][ty][tx];
             T uh[24];
 #pragma unroll
             for (int f = 0; f < 4; ++f) {
@@ -367,38 +406,39 @@ __device__ __forceinline__ void op_body(const OpArgs<T>& a, const HaarK<T>& kh, 
         if (out_plane && owner) {
             const N4 yb = sm.ybuf[ty + 1][tx];
             const T Kx3[3] = {Xp.x + yb.x, Xp.y + yb.y, Xz + yb.z};
-            const long long node = own_base + (long long)k * nplane;
+            const long long pofs = 3 * (long long)k * nplane;
             const int oidx = (ty + 1) * (TX + 1) + tx + 1;
-            const N4 xs = sm.plane[s_bot][oidx];
+            const N4 xs = sm.plane[SB][oidx];
             const T xv3[3] = {xs.x, xs.y, xs.z};
-            const uint32_t mk = (sm.mword[s_bot][oidx] >> (8 * (int)(node & 3))) & 0xffu;
+            uint32_t mk = 0;
+            if (hm) mk = (sm.mword[SB][oidx] >> (8 * (int)((own_base + (long long)k * nplane) & 3))) & 0xffu;
+            T* yo = y_own + pofs;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                const long long dof = 3 * node + c;
                 T Kx = Kx3[c], xv = xv3[c];
                 if ((mk >> c) & 1) {               // K^ is the identity on fixed DOFs
-                    xv = a.x[dof];
+                    xv = x_own[pofs + c];
                     Kx = xv;
                 }
                 if (MODE == OP_APPLY) {
-                    a.y[dof] = Kx;
+                    yo[c] = Kx;
                 } else if (MODE == OP_Q) {
-                    a.y[dof] = Kx;
+                    yo[c] = Kx;
                     acc0 = fma(xv, Kx, acc0);
                 } else if (MODE == OP_BMINUS) {
-                    a.y[dof] = sm.eb[s_bot][ty][tx][c] - Kx;
+                    yo[c] = sm.eb[SB][ty][tx][c] - Kx;
                 } else if (MODE == OP_SMOOTH) {
-                    const T bv = sm.eb[s_bot][ty][tx][c];
-                    const T yv = xv + a.omega * (bv - Kx) / sm.ed[s_bot][ty][tx][c];
-                    a.y[dof] = yv;
+                    const T bv = sm.eb[SB][ty][tx][c];
+                    const T yv = xv + a.omega * (bv - Kx) / sm.ed[SB][ty][tx][c];
+                    yo[c] = yv;
                     acc0 = fma(bv, yv, acc0);
                 } else if (MODE == OP_RESID) {
-                    const T bv = sm.eb[s_bot][ty][tx][c];
+                    const T bv = sm.eb[SB][ty][tx][c];
                     const T rv2 = bv - Kx;
-                    a.y[dof] = rv2;
+                    yo[c] = rv2;
                     if (a.z) {
-                        const T zv = rv2 / sm.ed[s_bot][ty][tx][c];
-                        a.z[dof] = zv;
+                        const T zv = rv2 / sm.ed[SB][ty][tx][c];
+                        a.z[3 * (own_base + (long long)k * nplane) + c] = zv;
                         acc0 = fma(rv2, zv, acc0);
                     }
                     acc1 = fma(rv2, rv2, acc1);
@@ -408,8 +448,17 @@ __device__ __forceinline__ void op_body(const OpArgs<T>& a, const HaarK<T>& kh, 
             }
         }
         cp_wait<kDepth - 1>();     // plane k+2 (and its layer, operands) landed
-        patch(k + 2);
+        patch(k + 2, std::integral_constant<int, SN>{});
         __syncthreads();   // (B)
+    };
+
+    for (int k = kb - 1; k < ke; ++k) {
+        switch ((k + 1 + 4) & 3) {
+            case 0: layer(k, I0{}); break;
+            case 1: layer(k, I1{}); break;
+            case 2: layer(k, I2{}); break;
+            default: layer(k, I3{}); break;
+        }
     }
     cp_wait<0>();
     double* sh_red = sm.red;
@@ -462,7 +511,7 @@ __device__ __forceinline__ void op_body(const OpArgs<T>& a, const HaarK<T>& kh, 
 }
 
 template <typename T, int TX, int TY, int MODE>
-__global__ void __launch_bounds__(TX * TY) k_operator(const OpArgs<T> a) {
+__global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 ? (MODE == OP_RESID ? 2 : 3) : 1)) k_operator(const OpArgs<T> a) {
     op_body<T, TX, TY, MODE>(a, a.kh, blockIdx.x, blockIdx.y, blockIdx.z, linear_block(), grid_blocks());
 }
 
@@ -470,7 +519,7 @@ __global__ void __launch_bounds__(TX * TY) k_operator(const OpArgs<T> a) {
 // from a device table), blockIdx.x enumerates that problem's tiles; the element
 // matrix constants are common to the batch.
 template <typename T, int TX, int TY, int MODE>
-__global__ void __launch_bounds__(TX * TY) k_operator_batch(const OpArgs<T>* __restrict__ tab, const HaarK<T> kh) {
+__global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 ? (MODE == OP_RESID ? 2 : 3) : 1)) k_operator_batch(const OpArgs<T>* __restrict__ tab, const HaarK<T> kh) {
     const OpArgs<T> a = tab[blockIdx.y];
     const int gx = (a.nx + 1 + TX - 2) / (TX - 1), gy = (a.ny + 1 + TY - 2) / (TY - 1);
     const int gz = (a.nz + 1 + a.kchunk - 1) / a.kchunk;
@@ -498,6 +547,7 @@ static int launch_t(to_problem* P, int level, int mode, const void* x, void* y, 
     a.d = (const T*)L.d;
     a.E = (const T*)L.E;
     a.mask = L.mask;
+    a.tmask = L.tmask;
     fill_haar<T>(P, L.h / P->g.h, a.kh);
     a.omega = (T)omega;
     a.red = P->red;
@@ -558,6 +608,37 @@ int operator_init(to_problem* P) {
     return P->prec == TO_FP64 ? init_t<double, 32, 8>() : init_t<float, 32, 8>();
 }
 
+// Per CTA tile column of the operator's 32 x 8 tiling: does its node footprint
+// (x from 31 bx - 1 to 31 bx + 31, y from 7 by - 1 to 7 by + 7, every z) hold a
+// fixed DOF?  Tiles without one skip all mask handling.
+int build_tile_mask(Level& L, const uint8_t* mask_host) {
+    const int nxn = L.nx + 1, nyn = L.ny + 1, nzn = L.nz + 1;
+    std::vector<uint8_t> col((size_t)nxn * nyn, 0);
+    for (int k = 0; k < nzn; ++k)
+        for (int j = 0; j < nyn; ++j)
+            for (int i = 0; i < nxn; ++i)
+                if (mask_host[(size_t)i + (size_t)nxn * ((size_t)j + (size_t)nyn * k)]) col[(size_t)i + (size_t)nxn * j] = 1;
+    const int gx = (nxn + 29) / 31 + 1, gy = (nyn + 5) / 7 + 1;   // generous: covers (n + 1 + 30) / 31 tiles
+    std::vector<uint8_t> t((size_t)gx * gy, 0);
+    const int gxk = (L.nx + 1 + 32 - 2) / 31;
+    for (int by = 0; by < gy; ++by)
+        for (int bx = 0; bx < gxk; ++bx) {
+            uint8_t f = 0;
+            for (int j = std::max(7 * by - 1, 0); j <= std::min(7 * by + 7, nyn - 1) && !f; ++j)
+                for (int i = std::max(31 * bx - 1, 0); i <= std::min(31 * bx + 31, nxn - 1); ++i)
+                    if (col[(size_t)i + (size_t)nxn * j]) {
+                        f = 1;
+                        break;
+                    }
+            t[(size_t)bx + (size_t)gxk * by] = f;
+        }
+    void* d = nullptr;
+    TO_CUDA(cudaMalloc(&d, t.size()));
+    TO_CUDA(cudaMemcpy(d, t.data(), t.size(), cudaMemcpyHostToDevice));
+    L.tmask = (uint8_t*)d;
+    return TO_OK;
+}
+
 int launch_operator(to_problem* P, int level, int mode, const void* x, void* y, const void* b,
                     cudaStream_t s, double omega, int first) {
     if (P->prec == TO_FP64) return launch_t<double, 32, 8>(P, level, mode, x, y, b, s, omega, first);
@@ -579,6 +660,7 @@ static OpArgs<T> batch_args(to_problem* P, int mode, int first) {
     a.kchunk = L.nz + 1 < 8 ? L.nz + 1 : 8;
     a.E = (const T*)L.E;
     a.mask = L.mask;
+    a.tmask = L.tmask;
     a.d = (const T*)L.d;
     a.red = P->red;
     a.sc = P->sc;
