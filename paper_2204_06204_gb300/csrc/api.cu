@@ -235,7 +235,7 @@ extern "C" int to_create(const to_grid* g, const to_material* m, const to_loads*
     void* p = nullptr;
     if ((rc = dalloc(&p, sizeof(DevScalars)))) return bail(rc);
     P->sc = (DevScalars*)p;
-    if ((rc = dalloc(&p, sizeof(double) * (size_t)kMaxRedBlocks * (kRedQ + 2 * 8)))) return bail(rc);
+    if ((rc = dalloc(&p, sizeof(double) * (size_t)kMaxRedBlocks * (kRedQ + 2 * 12)))) return bail(rc);
     P->red = (double*)p;
     if ((rc = dalloc(&p, sizeof(unsigned) * 64))) return bail(rc);
     P->counters = (unsigned*)p;

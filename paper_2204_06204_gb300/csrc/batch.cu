@@ -177,6 +177,7 @@ __global__ void __launch_bounds__(256) k_b_filter_T(const BProb<T>* __restrict__
 
 // ----------------------------------------------------------------------------- projection, one cluster per problem
 constexpr int kClusterCTAs = 8;
+constexpr int kProjMaxIter = 100;
 
 __device__ __forceinline__ float proj_ru(double t) {
     float f = (float)t;
@@ -203,7 +204,7 @@ template <> struct BThresh<double> {
 // Totals over the cluster: every CTA folds the CTAs' slots in rank order
 // through distributed shared memory (identical totals in every CTA).
 template <int NQ>
-__device__ __forceinline__ void cluster_totals(cg::cluster_group& cl, double (*slots)[8], int parity, const int (&kind)[NQ],
+__device__ __forceinline__ void cluster_totals(cg::cluster_group& cl, double (*slots)[12], int parity, const int (&kind)[NQ],
                                                double (&tot)[NQ]) {
     cl.sync();
 #pragma unroll
@@ -220,8 +221,8 @@ __global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(256)
     k_b_project(const BProb<T>* __restrict__ tab) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* wloc = reinterpret_cast<T*>(smem_raw);
-    __shared__ double slots[2][8];
-    __shared__ double sh8[32 * 8];
+    __shared__ double slots[2][12];
+    __shared__ double sh10[32 * 10];
     cg::cluster_group cl = cg::this_cluster();
     const unsigned rank = cl.block_rank();
     const BProb<T>& P = tab[blockIdx.x / kClusterCTAs];
@@ -234,49 +235,64 @@ __global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(256)
     const double gmean = P.mean_proj ? sc->gsum / (double)n : 0.0;
     const T alpha_t = (T)alpha, gmean_t = (T)gmean;
     auto wat = [&](long long e) -> T { return CACHE ? wloc[e - b0] : P.wbuf[e]; };
-    int parity = 0;
 
-    // pass 0
-    double tot6[6];
+    // pass 0: w; the piece at lambda = 0 (box-clamp volume), the piece at the warm
+    // start lambda_s (the previous multiplier), min / max of w
+    const double lam_s = sc->lambda;
+    double tot[10];
+    int parity = 0;
     {
-        double v[6] = {0.0, 0.0, 0.0, 0.0, INFINITY, -INFINITY};
-        T sF = T(0), wmn = T(INFINITY), wmx = T(-INFINITY);
-        const BThresh<T> th(0.0, P.lo, P.hi);
+        double v[10] = {0.0, 0.0, 0.0, 0.0, INFINITY, -INFINITY, 0.0, 0.0, 0.0, 0.0};
+        T sF = T(0), sFs = T(0), wmn = T(INFINITY), wmx = T(-INFINITY);
+        const BThresh<T> th0(0.0, P.lo, P.hi), ths(lam_s > 0.0 ? lam_s : 0.0, P.lo, P.hi);
         for (long long e = b0 + tid; e < b1; e += blockDim.x) {
             const T w = P.rho[e] - alpha_t * (P.grad[e] - gmean_t);
             if (CACHE) wloc[e - b0] = w;
             else P.wbuf[e] = w;
-            const int c = th.cls(w);
+            int c = th0.cls(w);
             if (c == 0) v[0] += 1.0;
             else if (c == 1) v[1] += 1.0;
             else { v[2] += 1.0; sF += w; }
+            c = ths.cls(w);
+            if (c == 0) v[6] += 1.0;
+            else if (c == 1) v[7] += 1.0;
+            else { v[8] += 1.0; sFs += w; }
             wmn = fmin(wmn, w);
             wmx = fmax(wmx, w);
         }
-        double mv[6] = {v[0], v[1], v[2], (double)sF, -(double)wmn, (double)wmx};
-        const int kind[6] = {0, 0, 0, 0, 1, 1};
-        block_reduce<6>(mv, kind, sh8);
+        double mv[10] = {v[0], v[1], v[2], (double)sF, -(double)wmn, (double)wmx, v[6], v[7], v[8], (double)sFs};
+        const int kind[10] = {0, 0, 0, 0, 1, 1, 0, 0, 0, 0};
+        block_reduce<10>(mv, kind, sh10);
         if (tid == 0)
-            for (int q = 0; q < 6; ++q) slots[parity][q] = mv[q];
-        cluster_totals<6>(cl, slots, parity, kind, tot6);
+            for (int q = 0; q < 10; ++q) slots[parity][q] = mv[q];
+        cluster_totals<10>(cl, slots, parity, kind, tot);
         parity ^= 1;
     }
-    const double wmin = -tot6[4], wmax = tot6[5];
-    double S = tot6[0] * P.hi + tot6[1] * P.lo + tot6[3];
-    double lambda = 0.0, lam_lo = 0.0, lam_hi = 0.0;
+    const double wmin = -tot[4], wmax = tot[5];
+    const double S0 = tot[0] * P.hi + tot[1] * P.lo + tot[3];
+    double lambda = 0.0;
     int iters = 0;
-    bool done = !(S > P.vbar) || !isfinite(S);
-    if (!isfinite(S)) set_err(&sc->err, TO_ERR_NONFINITE);
-    if (!done) {
-        lam_lo = fmax(0.0, wmin - P.hi);
-        lam_hi = wmax - P.lo;
-        const double nF = tot6[2];
-        const double ln = nF > 0.0 ? (S - P.vbar) / nF : NAN;
-        lambda = (ln > lam_lo && ln < lam_hi) ? ln : 0.5 * (lam_lo + lam_hi);
+    if (!isfinite(S0)) set_err(&sc->err, TO_ERR_NONFINITE);
+    ProjSearch st;
+    st.done = !(S0 > P.vbar) || !isfinite(S0);
+    st.have_prev = false;
+    st.pU = st.pL = st.pF = 0.0;
+    if (!st.done) {
+        st.lo_b = fmax(0.0, wmin - P.hi);
+        st.hi_b = wmax - P.lo;
+        const double t0[4] = {tot[0], tot[1], tot[2], tot[3]};
+        st.lam = 0.0;
+        proj_search_step(st, t0, P.vbar, P.lo, P.hi);          // Newton from lambda = 0
+        if (!st.done && lam_s > st.lo_b && lam_s < st.hi_b) {           // the warm start tightens it
+            const double ts[4] = {tot[6], tot[7], tot[8], tot[9]};
+            st.lam = lam_s;
+            st.have_prev = false;
+            proj_search_step(st, ts, P.vbar, P.lo, P.hi);
+        }
     }
-    while (!done && iters < 100) {
+    while (!st.done && iters < kProjMaxIter) {
         ++iters;
-        const BThresh<T> th(lambda, P.lo, P.hi);
+        const BThresh<T> th(st.lam, P.lo, P.hi);
         double v[4] = {0.0, 0.0, 0.0, 0.0};
         T sF = T(0);
         for (long long e = b0 + tid; e < b1; e += blockDim.x) {
@@ -288,26 +304,16 @@ __global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(256)
         }
         v[3] = (double)sF;
         const int kind[4] = {0, 0, 0, 0};
-        block_reduce<4>(v, kind, sh8);
+        block_reduce<4>(v, kind, sh10);
         if (tid == 0)
             for (int q = 0; q < 4; ++q) slots[parity][q] = v[q];
         double t4[4];
         cluster_totals<4>(cl, slots, parity, kind, t4);
         parity ^= 1;
-        const double nF = t4[2];
-        S = t4[0] * P.hi + t4[1] * P.lo + t4[3] - lambda * nF;
-        if (S == P.vbar) break;
-        if (S > P.vbar) lam_lo = lambda;
-        else lam_hi = lambda;
-        const double ln = nF > 0.0 ? lambda + (S - P.vbar) / nF : NAN;
-        const double next = (ln > lam_lo && ln < lam_hi) ? ln : 0.5 * (lam_lo + lam_hi);
-        if (next == lambda || fabs(next - lambda) <= 1e-15 * fmax(1.0, fabs(lambda)) ||
-            lam_hi - lam_lo <= 1e-15 * fmax(1.0, fabs(lambda))) {
-            lambda = next;
-            break;
-        }
-        lambda = next;
+        proj_search_step(st, t4, P.vbar, P.lo, P.hi);
     }
+    lambda = st.done && !(S0 > P.vbar) ? 0.0 : st.lam;
+
     double dmax = 0.0, vol = 0.0;
     for (long long e = b0 + tid; e < b1; e += blockDim.x) {
         const double wd = (double)wat(e);
@@ -319,7 +325,7 @@ __global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(256)
     }
     double v2[2] = {dmax, vol};
     const int kind2[2] = {1, 0};
-    block_reduce<2>(v2, kind2, sh8);
+    block_reduce<2>(v2, kind2, sh10);
     if (tid == 0) {
         slots[parity][0] = v2[0];
         slots[parity][1] = v2[1];
@@ -331,7 +337,6 @@ __global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(256)
         sc->drho_inf = t2[0];
         sc->volume = t2[1];
         sc->proj_iters = iters;
-        sc->alpha = alpha;
     }
     cl.sync();   // no CTA leaves while another may still read its slots
 }

@@ -15,11 +15,13 @@ constexpr int kMaxStencil = 1024;   // cone of radius < 6 voxels
 // PRESCALED: the input already carries the 1 / Hs factor (the fused sensitivity
 // writes g~ / Hs), so the transpose is a plain weighted sum.
 // STATS also reports max |y| and sum y and fixes the step size alpha_k.
-template <typename T, bool TRANSPOSE, bool STATS, bool PRESCALED>
+template <typename T, bool TRANSPOSE, bool STATS, bool PRESCALED, bool MODULI = false>
 __global__ void __launch_bounds__(256) k_filter(int nx, int ny, int nz, const T* __restrict__ x, T* __restrict__ y,
                                                 const T* __restrict__ Hs, const int4* __restrict__ st,
                                                 const T* __restrict__ w, int ns, int R, double* red, unsigned* counter,
-                                                DevScalars* sc, double alpha0_param, double alpha_scale, double m_exp) {
+                                                DevScalars* sc, double alpha0_param, double alpha_scale, double m_exp,
+                                                T* Eout = nullptr, T* Edout = nullptr, double E0 = 1.0, double Emin = 0.0,
+                                                double pexp = 3.0) {
     __shared__ double sh[32 * kRedQ];
     __shared__ int4 s_st[kMaxStencil];
     __shared__ T s_w[kMaxStencil];
@@ -34,18 +36,47 @@ __global__ void __launch_bounds__(256) k_filter(int nx, int ny, int nz, const T*
         const long long e = i + (long long)nx * (j + (long long)ny * k);
         const bool interior = i >= R && i < nx - R && j >= R && j < ny - R && k >= R && k < nz - R;
         T acc = T(0);
-        for (int s = 0; s < ns; ++s) {
-            const int4 o = s_st[s];
-            const int ii = i + o.x, jj = j + o.y, kk = k + o.z;
-            if (!interior && (ii < 0 || ii >= nx || jj < 0 || jj >= ny || kk < 0 || kk >= nz)) continue;
-            const long long m = e + o.w;   // precomputed linear offset
-            if (TRANSPOSE && !PRESCALED)
-                acc += s_w[s] * x[m] / Hs[m];
-            else
-                acc += s_w[s] * x[m];
+        // eight stencil points per round, all loads issued before the sums
+        for (int s0 = 0; s0 < ns; s0 += 8) {
+            T xv[8], hv[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int s = s0 + q;
+                bool ok = s < ns;
+                const int4 o = s_st[ok ? s : 0];
+                const int ii = i + o.x, jj = j + o.y, kk = k + o.z;
+                ok = ok && (interior || (ii >= 0 && ii < nx && jj >= 0 && jj < ny && kk >= 0 && kk < nz));
+                const long long m = e + o.w;   // precomputed linear offset
+                xv[q] = ok ? x[m] : T(0);
+                hv[q] = (TRANSPOSE && !PRESCALED) ? (ok ? Hs[m] : T(1)) : T(1);
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int s = s0 + q;
+                const T wq = s < ns ? s_w[s] : T(0);
+                if (TRANSPOSE && !PRESCALED)
+                    acc += wq * xv[q] / hv[q];
+                else
+                    acc += wq * xv[q];
+            }
         }
-        const T out = TRANSPOSE ? acc : acc / Hs[e];
+        const T hs_e = TRANSPOSE ? T(1) : Hs[e];
+        const T out = TRANSPOSE ? acc : acc / hs_e;
         y[e] = out;
+        if (MODULI) {   // E = Emin + rho~^p (E0 - Emin) and E' / Hs (the sensitivity's prescaled factor)
+            const T dE = (T)(E0 - Emin);
+            T pw, pw1;
+            if (pexp == 3.0) {
+                pw1 = out * out;
+                pw = pw1 * out;
+            } else {
+                pw1 = (T)pow((double)out, pexp - 1.0);
+                pw = pw1 * out;
+            }
+            Eout[e] = (T)Emin + pw * dE;
+            Edout[e] = (T)pexp * pw1 * dE / hs_e;
+            if (!isfinite((double)out)) set_err(&sc->err, TO_ERR_NONFINITE);
+        }
         if (STATS) {
             amax = fmax(amax, fabs((double)out));
             sum += (double)out;
@@ -196,11 +227,12 @@ int launch_sens_filter_T(to_problem* P, cudaStream_t s) {
 
 template <typename T>
 static int moduli_t(to_problem* P, cudaStream_t s) {
-    int rc = filter_t<T>(P, P->rho, P->rhot, 0, 0, 0, s);
-    if (rc) return rc;
-    const int nb = grid_for(P->n_elem, 256, P->num_sms);
-    k_moduli<T><<<nb, 256, 0, s>>>(P->n_elem, (const T*)P->rhot, (const T*)P->Hs, (T*)P->lv[0].E, (T*)P->Ed,
-                                   P->mat.E0, P->mat.Emin, P->mat.p, &P->sc->err);
+    // rho~ = C(rho) and the moduli in one pass
+    const int nx = P->g.nx, ny = P->g.ny, nz = P->g.nz;
+    k_filter<T, false, false, false, true><<<grid3(nx, ny, nz), block3(), 0, s>>>(
+        nx, ny, nz, (const T*)P->rho, (T*)P->rhot, (const T*)P->Hs, P->stencil, (const T*)P->stencil_w, P->n_stencil,
+        (int)std::ceil(P->mat.rmin), nullptr, nullptr, P->sc, 0.0, 0.0, 0.0, (T*)P->lv[0].E, (T*)P->Ed, P->mat.E0,
+        P->mat.Emin, P->mat.p);
     TO_CUDA(cudaGetLastError());
     return TO_OK;
 }

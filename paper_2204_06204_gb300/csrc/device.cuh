@@ -121,6 +121,45 @@ __device__ __forceinline__ void set_err(int* err, int code) { atomicCAS(err, 0, 
 __device__ __forceinline__ unsigned linear_block() { return blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z); }
 __device__ __forceinline__ unsigned grid_blocks() { return gridDim.x * gridDim.y * gridDim.z; }
 
+// Multiplier search of the projection onto X (Eq. piecewiseLinearEQ).  Each pass
+// classifies the elements at lambda into n_U (at hi), n_L (at lo) and the free
+// set (count n_F, sum s_F of w).  On that piece the volume is
+// S = n_U hi + n_L lo + s_F - lambda n_F, whose root is
+// lambda_N = (n_U hi + n_L lo + s_F - vbar) / n_F: a function of the sets alone.
+// The search moves to lambda_N (or bisects the bracket when lambda_N leaves it)
+// and stops when the sets at lambda_N are the sets lambda_N came from; the
+// result is then lambda_N of the final sets, independent of the starting point
+// (so a warm start from the previous multiplier changes the pass count only).
+struct ProjSearch {
+    double lam, lo_b, hi_b;
+    double pU, pL, pF;   // sets that produced lam (when have_prev)
+    bool have_prev, done;
+};
+
+__device__ __forceinline__ void proj_search_step(ProjSearch& st, const double (&t)[4], double vbar, double lo,
+                                                 double hi) {
+    if (st.have_prev && t[0] == st.pU && t[1] == st.pL && t[2] == st.pF) {
+        st.done = true;          // lam = lambda_N of these very sets
+        return;
+    }
+    const double S = t[0] * hi + t[1] * lo + t[3] - st.lam * t[2];
+    if (S > vbar) st.lo_b = fmax(st.lo_b, st.lam);
+    else st.hi_b = fmin(st.hi_b, st.lam);
+    const double ln = t[2] > 0.0 ? (t[0] * hi + t[1] * lo + t[3] - vbar) / t[2] : NAN;
+    const bool newton = ln >= st.lo_b && ln <= st.hi_b;
+    const double next = newton ? ln : 0.5 * (st.lo_b + st.hi_b);
+    if (!newton && !(st.hi_b - st.lo_b > 1e-15 * fmax(1.0, fabs(st.lam)))) {
+        st.lam = next;
+        st.done = true;
+        return;
+    }
+    st.pU = t[0];
+    st.pL = t[1];
+    st.pF = t[2];
+    st.have_prev = newton;
+    st.lam = next;
+}
+
 // 3-D lattice launches: block (32, 8), grid (ceil(X/32), ceil(Y/8), Z); no divisions per thread.
 inline dim3 grid3(int X, int Y, int Z) { return dim3((unsigned)((X + 31) / 32), (unsigned)((Y + 7) / 8), (unsigned)Z); }
 inline dim3 block3() { return dim3(32, 8, 1); }

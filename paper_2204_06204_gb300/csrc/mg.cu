@@ -58,22 +58,26 @@ __global__ void k_restrict(int cx, int cy, int cz, const T* __restrict__ tf, con
         const int I = t.i, J = t.j, K = t.k;
         const long long n = I + (long long)(cx + 1) * (J + (long long)(cy + 1) * K);
         T acc[3] = {T(0), T(0), T(0)};
+#pragma unroll
         for (int dk = -1; dk <= 1; ++dk) {
             const int k = 2 * K + dk;
-            if (k < 0 || k > fz) continue;
             const T wk = dk ? T(0.5) : T(1);
+#pragma unroll
             for (int dj = -1; dj <= 1; ++dj) {
                 const int j = 2 * J + dj;
-                if (j < 0 || j > fy) continue;
                 const T wj = dj ? T(0.5) : T(1);
+#pragma unroll
                 for (int di = -1; di <= 1; ++di) {
                     const int i = 2 * I + di;
-                    if (i < 0 || i > fx) continue;
+                    const bool in = k >= 0 && k <= fz && j >= 0 && j <= fy && i >= 0 && i <= fx;
+                    const long long fnode = in ? i + (long long)(fx + 1) * (j + (long long)(fy + 1) * k) : 0;
                     const T w = (di ? T(0.5) : T(1)) * wj * wk;
-                    const long long fnode = i + (long long)(fx + 1) * (j + (long long)(fy + 1) * k);
-                    const uint8_t m = mf[fnode];
-                    for (int c = 0; c < 3; ++c)
-                        if (!((m >> c) & 1)) acc[c] += w * tf[3 * fnode + c];
+                    const uint8_t m = in ? mf[fnode] : 7;
+                    const T v0 = in ? tf[3 * fnode + 0] : T(0), v1 = in ? tf[3 * fnode + 1] : T(0),
+                            v2 = in ? tf[3 * fnode + 2] : T(0);
+                    acc[0] += (m & 1) ? T(0) : w * v0;
+                    acc[1] += (m & 2) ? T(0) : w * v1;
+                    acc[2] += (m & 4) ? T(0) : w * v2;
                 }
             }
         }
@@ -95,15 +99,19 @@ __global__ void k_prolong_add(int cx, int cy, int cz, const T* __restrict__ xc, 
         if (m == 7) return;
         const int i0 = i >> 1, i1 = (i + 1) >> 1, j0 = j >> 1, j1 = (j + 1) >> 1, k0 = k >> 1, k1 = (k + 1) >> 1;
         T acc[3] = {T(0), T(0), T(0)};
-        for (int kc = k0; kc <= k1; ++kc)
-            for (int jc = j0; jc <= j1; ++jc)
-                for (int ic = i0; ic <= i1; ++ic) {
-                    const T w = ((i & 1) ? T(0.5) : T(1)) * ((j & 1) ? T(0.5) : T(1)) * ((k & 1) ? T(0.5) : T(1));
-                    const long long cn = ic + (long long)(cx + 1) * (jc + (long long)(cy + 1) * kc);
-                    const uint8_t mcn = mc[cn];
-                    for (int c = 0; c < 3; ++c)
-                        if (!((mcn >> c) & 1)) acc[c] += w * xc[3 * cn + c];
-                }
+        const T w = ((i & 1) ? T(0.5) : T(1)) * ((j & 1) ? T(0.5) : T(1)) * ((k & 1) ? T(0.5) : T(1));
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int ic = (q & 1) ? i1 : i0, jc = (q & 2) ? j1 : j0, kc = (q & 4) ? k1 : k0;
+            // a coordinate with an even fine index has one parent: count it once
+            const bool use = (!(q & 1) || i1 != i0) && (!(q & 2) || j1 != j0) && (!(q & 4) || k1 != k0);
+            const long long cn = ic + (long long)(cx + 1) * (jc + (long long)(cy + 1) * kc);
+            const uint8_t mcn = use ? mc[cn] : 7;
+            const T v0 = use ? xc[3 * cn + 0] : T(0), v1 = use ? xc[3 * cn + 1] : T(0), v2 = use ? xc[3 * cn + 2] : T(0);
+            acc[0] += (mcn & 1) ? T(0) : w * v0;
+            acc[1] += (mcn & 2) ? T(0) : w * v1;
+            acc[2] += (mcn & 4) ? T(0) : w * v2;
+        }
         for (int c = 0; c < 3; ++c)
             if (!((m >> c) & 1)) xf[3 * n + c] += acc[c];
     }

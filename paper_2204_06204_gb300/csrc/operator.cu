@@ -572,7 +572,7 @@ static int launch_t(to_problem* P, int level, int mode, const void* x, void* y, 
         const long long want = 3LL * P->num_sms;
         long long gz = (want + per_plane - 1) / per_plane;
         kchunk = (int)((L.nz + 1 + gz - 1) / gz);
-        if (kchunk < 4) kchunk = 4;
+        if (kchunk < 1) kchunk = 1;
     }
     if (kchunk > L.nz + 1) kchunk = L.nz + 1;
     a.kchunk = kchunk;

@@ -23,7 +23,7 @@
 
 namespace to {
 
-constexpr int kProjSlot = 8;      // doubles per block per pass in the projection scratch
+constexpr int kProjSlot = 12;     // doubles per block per pass in the projection scratch
 constexpr int kProjMaxIter = 100;
 
 template <typename T>
@@ -102,8 +102,8 @@ __global__ void __launch_bounds__(256) k_project(const ProjArgs<T> a) {
     extern __shared__ unsigned char smem_raw[];
     T* wloc = reinterpret_cast<T*>(smem_raw);
     __shared__ double sh[32 * kRedQ];
-    __shared__ double sh8[32 * 8];
-    __shared__ double shb[8];
+    __shared__ double sh10[32 * 10];
+    __shared__ double shb[10];
     const unsigned nb = gridDim.x, bid = blockIdx.x;
     const long long b0 = (long long)bid * a.chunk;
     const long long b1 = min(b0 + a.chunk, a.n);
@@ -115,52 +115,64 @@ __global__ void __launch_bounds__(256) k_project(const ProjArgs<T> a) {
     const T alpha_t = (T)alpha, gmean_t = (T)gmean;
     auto wat = [&](long long e) -> T { return CACHE ? wloc[e - b0] : a.wbuf[e]; };
 
-    // pass 0: w, the box-clamp volume (the piece at lambda = 0), min / max of w
-    double tot[6];
+    // pass 0: w; the piece at lambda = 0 (box-clamp volume), the piece at the warm
+    // start lambda_s (the previous multiplier), min / max of w
+    const double lam_s = sc->lambda;
+    double tot[10];
     int parity = 0;
     {
-        double v[6] = {0.0, 0.0, 0.0, 0.0, INFINITY, -INFINITY};
-        T sF = T(0), wmn = T(INFINITY), wmx = T(-INFINITY);
-        const Thresh<T> th(0.0, a.lo, a.hi);
+        double v[10] = {0.0, 0.0, 0.0, 0.0, INFINITY, -INFINITY, 0.0, 0.0, 0.0, 0.0};
+        T sF = T(0), sFs = T(0), wmn = T(INFINITY), wmx = T(-INFINITY);
+        const Thresh<T> th0(0.0, a.lo, a.hi), ths(lam_s > 0.0 ? lam_s : 0.0, a.lo, a.hi);
         for (long long e = b0 + tid; e < b1; e += blockDim.x) {
             const T w = a.fused ? a.rho_in[e] - alpha_t * (a.g[e] - gmean_t) : a.w_in[e];
             if (CACHE) wloc[e - b0] = w;
             else a.wbuf[e] = w;
-            const int c = th.cls(w);
+            int c = th0.cls(w);
             if (c == 0) v[0] += 1.0;
             else if (c == 1) v[1] += 1.0;
             else { v[2] += 1.0; sF += w; }
+            c = ths.cls(w);
+            if (c == 0) v[6] += 1.0;
+            else if (c == 1) v[7] += 1.0;
+            else { v[8] += 1.0; sFs += w; }
             wmn = fmin(wmn, w);
             wmx = fmax(wmx, w);
         }
-        double mv[6] = {v[0], v[1], v[2], (double)sF, -(double)wmn, (double)wmx};
-        const int kind[6] = {0, 0, 0, 0, 1, 1};
-        block_reduce<6>(mv, kind, sh8);
+        double mv[10] = {v[0], v[1], v[2], (double)sF, -(double)wmn, (double)wmx, v[6], v[7], v[8], (double)sFs};
+        const int kind[10] = {0, 0, 0, 0, 1, 1, 0, 0, 0, 0};
+        block_reduce<10>(mv, kind, sh10);
         if (tid == 0)
-            for (int q = 0; q < 6; ++q) a.part[(parity * nb + bid) * kProjSlot + q] = mv[q];
+            for (int q = 0; q < 10; ++q) a.part[(parity * nb + bid) * kProjSlot + q] = mv[q];
         if (!grid_barrier(a.bar, &sc->err)) return;
-        combine_partials<6>(a.part + parity * nb * kProjSlot, nb, kind, tot, shb);
+        combine_partials<10>(a.part + parity * nb * kProjSlot, nb, kind, tot, shb);
         parity ^= 1;
     }
     const double wmin = -tot[4], wmax = tot[5];
-    double S = tot[0] * a.hi + tot[1] * a.lo + tot[3];
-    double lambda = 0.0, lam_lo = 0.0, lam_hi = 0.0;
+    const double S0 = tot[0] * a.hi + tot[1] * a.lo + tot[3];
+    double lambda = 0.0;
     int iters = 0;
-    bool done = false;
-    if (!isfinite(S)) set_err(&sc->err, TO_ERR_NONFINITE);
-    if (S <= a.vbar || !isfinite(S)) {
-        done = true;
-    } else {
-        lam_lo = fmax(0.0, wmin - a.hi);
-        lam_hi = wmax - a.lo;
-        const double nF = tot[2];
-        const double ln = nF > 0.0 ? (S - a.vbar) / nF : NAN;
-        lambda = (ln > lam_lo && ln < lam_hi) ? ln : 0.5 * (lam_lo + lam_hi);
+    if (!isfinite(S0)) set_err(&sc->err, TO_ERR_NONFINITE);
+    ProjSearch st;
+    st.done = !(S0 > a.vbar) || !isfinite(S0);
+    st.have_prev = false;
+    st.pU = st.pL = st.pF = 0.0;
+    if (!st.done) {
+        st.lo_b = fmax(0.0, wmin - a.hi);
+        st.hi_b = wmax - a.lo;
+        const double t0[4] = {tot[0], tot[1], tot[2], tot[3]};
+        st.lam = 0.0;
+        proj_search_step(st, t0, a.vbar, a.lo, a.hi);          // Newton from lambda = 0
+        if (!st.done && lam_s > st.lo_b && lam_s < st.hi_b) {           // the warm start tightens it
+            const double ts[4] = {tot[6], tot[7], tot[8], tot[9]};
+            st.lam = lam_s;
+            st.have_prev = false;
+            proj_search_step(st, ts, a.vbar, a.lo, a.hi);
+        }
     }
-
-    while (!done && iters < kProjMaxIter) {
+    while (!st.done && iters < kProjMaxIter) {
         ++iters;
-        const Thresh<T> th(lambda, a.lo, a.hi);
+        const Thresh<T> th(st.lam, a.lo, a.hi);
         double v[4] = {0.0, 0.0, 0.0, 0.0};
         T sF = T(0);
         for (long long e = b0 + tid; e < b1; e += blockDim.x) {
@@ -179,20 +191,9 @@ __global__ void __launch_bounds__(256) k_project(const ProjArgs<T> a) {
         double t4[4];
         combine_partials<4>(a.part + parity * nb * kProjSlot, nb, kind, t4, shb);
         parity ^= 1;
-        const double nF = t4[2];
-        S = t4[0] * a.hi + t4[1] * a.lo + t4[3] - lambda * nF;
-        if (S == a.vbar) break;
-        if (S > a.vbar) lam_lo = lambda;
-        else lam_hi = lambda;
-        const double ln = nF > 0.0 ? lambda + (S - a.vbar) / nF : NAN;
-        const double next = (ln > lam_lo && ln < lam_hi) ? ln : 0.5 * (lam_lo + lam_hi);
-        if (next == lambda || fabs(next - lambda) <= 1e-15 * fmax(1.0, fabs(lambda)) ||
-            lam_hi - lam_lo <= 1e-15 * fmax(1.0, fabs(lambda))) {
-            lambda = next;
-            break;
-        }
-        lambda = next;
+        proj_search_step(st, t4, a.vbar, a.lo, a.hi);
     }
+    lambda = st.done && !(S0 > a.vbar) ? 0.0 : st.lam;
 
     // final pass: rho = clamp(w - lambda), ||drho||_inf, volume
     double dmax = 0.0, vol = 0.0;
@@ -286,7 +287,7 @@ int project_coop_blocks(int prec, int num_sms, int* out) {
 // The same projection kernel, for callers that must not allocate device
 // memory: its reduction slots, barrier words and result scalars live in one
 // file-scope device array instead of a problem's buffers.  Every GPU that
-// loads this library holds the array (about 170 KB) until the process exits.
+// loads this library holds the array (about 230 KB) until the process exits.
 namespace to {
 namespace {
 
