@@ -425,16 +425,24 @@ def _mg_levels(nx, ny, nz):
 
 
 def _launches_per_step(mg, n_inner, dims=(128, 64, 64), nu1=2, nu2=2):
-    """Kernel launches of one outer iteration, as issued by the library."""
-    # filter + moduli, diag, residual, (Q + update) per step, filter^T, projection, record
-    base = 2 + 1 + 1 + 2 * n_inner + 1 + 1 + 1
+    """Kernel launches of one outer iteration (one to_step(1) call), as issued by the library."""
+    # stats-slot reset (once per to_step call), filter + moduli, diag, residual with the fused
+    # sensitivity, (Q + update) per step, filter^T with the step-size statistics, projection, record
+    base = 1 + 1 + 1 + 1 + 2 * n_inner + 1 + 1 + 1
     if not mg:
         return base
     L = _mg_levels(*dims)
-    refresh = 2 * (L - 1) + 2                       # coarsen + diag per level, dense assemble + invert
-    vcycle = (L - 1) * (1 + (nu1 - 1) + 1 + 1 + 1 + nu2) + 1
-    precond = vcycle + 1                            # V-cycle + r^T z
-    return base + refresh + precond * n_inner       # one V-cycle per step (before each Q apply)
+    if L == 1:
+        return base + 2 + n_inner                   # dense assemble + invert, one dense solve per step
+    refresh = 2 * (L - 1) + 2                       # coarsen + diag per coarse level, dense assemble + invert
+    # levels from the first one (>= 1, above the coarsest) with at most 1024 elements run as one kernel
+    elems = [(dims[0] >> l) * (dims[1] >> l) * (dims[2] >> l) for l in range(L)]
+    tail = next((l for l in range(1, L - 1) if elems[l] <= 1024), 0)
+    host_levels = tail if tail else L - 1
+    # first sweep on the finest level (coarser ones come out of the restriction), per host level:
+    # nu1 - 1 sweeps, b - K x, restriction, prolongation, nu2 sweeps; the dense solve or the tail kernel
+    vcycle = 1 + host_levels * ((nu1 - 1) + 1 + 1 + 1 + nu2) + 1
+    return base + refresh + vcycle * n_inner        # one V-cycle per step (r^T z fused into the last sweep)
 
 
 if __name__ == "__main__":

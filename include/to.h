@@ -245,7 +245,7 @@ int to_compliance_truncated_grad(to_problem* P, double scale, void* g_dev, void*
  * what to_project computes for a problem with n_elem = n, vbar, rho_min = lo and
  * rho_max = hi, without a to_problem and without allocating: its scratch (block
  * partials, barrier words, result scalars) is one static device array of about
- * 230 KB that every GPU loading this library holds until the process exits.
+ * 200 KB that every GPU loading this library holds until the process exits.
  *   w_dev, rho_dev  n entries on the current device (double for TO_FP64, float for
  *                   TO_FP32_MIXED); they may alias.
  *   n               1 <= n <= 2,097,152; larger n returns TO_ERR_ARG (also when the

@@ -141,8 +141,8 @@ __global__ void __launch_bounds__(256) k_dot_J(long long n, const T* __restrict_
     double v[1] = {acc};
     const int kind[1] = {0};
     double tot[1];
-    block_reduce<1>(v, kind, sh);
-    if (finish_reduction<1>(v, kind, red, counter, tot, sh, linear_block(), grid_blocks()) && threadIdx.x == 0) sc->J = tot[0];
+    block_reduce<double, 1>(v, kind, sh);
+    if (finish_reduction<double, 1>(v, kind, red, counter, tot, sh, linear_block(), grid_blocks()) && threadIdx.x == 0) sc->J = tot[0];
 }
 
 static int grid_n(long long n, int num_sms) {

@@ -286,6 +286,10 @@ extern "C" int to_create(const to_grid* g, const to_material* m, const to_loads*
         cudaStreamDestroy(s);
         return bail(rc);
     }
+    if ((rc = project_cluster_setup(P))) {
+        cudaStreamDestroy(s);
+        return bail(rc);
+    }
     if ((rc = launch_moduli(P, s)) || (rc = refresh_preconditioner(P, s))) {
         cudaStreamDestroy(s);
         return bail(rc);

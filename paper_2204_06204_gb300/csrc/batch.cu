@@ -23,11 +23,13 @@
 #include <cmath>
 #include <vector>
 
-#include "device.cuh"
+#include "projection.cuh"
 
 namespace cg = cooperative_groups;
 
 namespace to {
+template <typename T>
+SimpT<T> simp_params(const to_material& m);
 
 int batch_operator_launch(int prec, int mode, const void* tab, const void* kh, int max_tiles, int n, cudaStream_t s);
 int op_tables_build(to_problem* const* probs, int n, void** resid, void** q_first, void** q, void** kh_host,
@@ -65,10 +67,9 @@ struct BProb {
 
 // rho~ = C(rho), E = Emin + rho~^p (E0 - Emin), E'/Hs  (grid-stride over each problem's elements)
 template <typename T>
-__global__ void __launch_bounds__(256) k_b_design(const BProb<T>* __restrict__ tab, double E0, double Emin, double p) {
+__global__ void __launch_bounds__(256) k_b_design(const BProb<T>* __restrict__ tab, const SimpT<T> simp) {
     const BProb<T>& P = tab[blockIdx.y];
     const int nx = P.nx, ny = P.ny, nz = P.nz;
-    const T dE = (T)(E0 - Emin);
     for (long long e = blockIdx.x * 256LL + threadIdx.x; e < P.n_elem; e += (long long)gridDim.x * 256) {
         const int i = (int)(e % nx), j = (int)((e / nx) % ny), k = (int)(e / ((long long)nx * ny));
         T acc = T(0);
@@ -81,17 +82,11 @@ __global__ void __launch_bounds__(256) k_b_design(const BProb<T>* __restrict__ t
         const T hs = P.Hs[e];
         const T rt = acc / hs;
         P.rhot[e] = rt;
-        if (!isfinite((double)rt)) set_err(&P.sc->err, TO_ERR_NONFINITE);
-        T pw, pw1;
-        if (p == 3.0) {
-            pw1 = rt * rt;
-            pw = pw1 * rt;
-        } else {
-            pw1 = (T)pow((double)rt, p - 1.0);
-            pw = pw1 * rt;
-        }
-        P.E[e] = (T)Emin + pw * dE;
-        P.Ed[e] = (T)p * pw1 * dE / hs;
+        if (!tfinite(rt)) set_err(&P.sc->err, TO_ERR_NONFINITE);
+        T Ee, Ed;
+        simp_moduli(simp, rt, Ee, Ed);
+        P.E[e] = Ee;
+        P.Ed[e] = Ed / hs;
     }
 }
 
@@ -121,7 +116,10 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_b_update(const BProb<T>* __restrict__ tab) {
     __shared__ double sh[32 * kRedQ];
     const BProb<T>& P = tab[blockIdx.y];
-    const T beta = (T)P.sc->beta;
+    __shared__ T s_beta;
+    if (threadIdx.x == 0) s_beta = (T)P.sc->beta;   // one conversion per block
+    __syncthreads();
+    const T beta = s_beta;
     T acc = T(0);
     for (long long i = blockIdx.x * 256LL + threadIdx.x; i < P.n_dof; i += (long long)gridDim.x * 256) {
         P.u[i] += beta * P.z[i];
@@ -131,11 +129,11 @@ __global__ void __launch_bounds__(256) k_b_update(const BProb<T>* __restrict__ t
         P.z[i] = zn;
         acc += ri * zn;
     }
-    double v[1] = {(double)acc};
+    T v[1] = {acc};
     const int kind[1] = {0};
     double tot[1];
-    block_reduce<1>(v, kind, sh);
-    if (finish_reduction<1>(v, kind, P.red, P.counters + 4, tot, sh, blockIdx.x, gridDim.x) && threadIdx.x == 0)
+    block_reduce<T, 1>(v, kind, reinterpret_cast<T*>(sh));
+    if (finish_reduction<T, 1>(v, kind, P.red, P.counters + 4, tot, sh, blockIdx.x, gridDim.x) && threadIdx.x == 0)
         P.sc->rz = tot[0];
 }
 
@@ -145,7 +143,7 @@ __global__ void __launch_bounds__(256) k_b_filter_T(const BProb<T>* __restrict__
     __shared__ double sh[32 * kRedQ];
     const BProb<T>& P = tab[blockIdx.y];
     const int nx = P.nx, ny = P.ny, nz = P.nz;
-    double amax = 0.0, sum = 0.0;
+    T amax = T(0), sum = T(0);
     for (long long e = blockIdx.x * 256LL + threadIdx.x; e < P.n_elem; e += (long long)gridDim.x * 256) {
         const int i = (int)(e % nx), j = (int)((e / nx) % ny), k = (int)(e / ((long long)nx * ny));
         T acc = T(0);
@@ -156,14 +154,14 @@ __global__ void __launch_bounds__(256) k_b_filter_T(const BProb<T>* __restrict__
             acc += P.stw[s] * P.gt[ii + (long long)nx * (jj + (long long)ny * kk)];
         }
         P.grad[e] = acc;
-        amax = fmax(amax, fabs((double)acc));
-        sum += (double)acc;
+        amax = tmax(amax, tabs(acc));
+        sum += acc;
     }
-    double v[2] = {amax, sum};
+    T v[2] = {amax, sum};
     const int kind[2] = {1, 0};
     double tot[2];
-    block_reduce<2>(v, kind, sh);
-    if (finish_reduction<2>(v, kind, P.red, P.counters + 2, tot, sh, blockIdx.x, gridDim.x) && threadIdx.x == 0) {
+    block_reduce<T, 2>(v, kind, reinterpret_cast<T*>(sh));
+    if (finish_reduction<T, 2>(v, kind, P.red, P.counters + 2, tot, sh, blockIdx.x, gridDim.x) && threadIdx.x == 0) {
         DevScalars* sc = P.sc;
         sc->gmax = tot[0];
         sc->gsum = tot[1];
@@ -177,168 +175,62 @@ __global__ void __launch_bounds__(256) k_b_filter_T(const BProb<T>* __restrict__
 
 // ----------------------------------------------------------------------------- projection, one cluster per problem
 constexpr int kClusterCTAs = 8;
-constexpr int kProjMaxIter = 100;
 
-__device__ __forceinline__ float proj_ru(double t) {
-    float f = (float)t;
-    if ((double)f < t) f = nextafterf(f, INFINITY);
-    return f;
-}
-__device__ __forceinline__ float proj_rd(double t) {
-    float f = (float)t;
-    if ((double)f > t) f = nextafterf(f, -INFINITY);
-    return f;
-}
-template <typename T> struct BThresh;
-template <> struct BThresh<float> {
-    float tu, tl;
-    __device__ BThresh(double lam, double lo, double hi) : tu(proj_ru(lam + hi)), tl(proj_rd(lam + lo)) {}
-    __device__ int cls(float w) const { return w >= tu ? 0 : (w <= tl ? 1 : 2); }
-};
-template <> struct BThresh<double> {
-    double tu, tl;
-    __device__ BThresh(double lam, double lo, double hi) : tu(lam + hi), tl(lam + lo) {}
-    __device__ int cls(double w) const { return w >= tu ? 0 : (w <= tl ? 1 : 2); }
-};
-
-// Totals over the cluster: every CTA folds the CTAs' slots in rank order
-// through distributed shared memory (identical totals in every CTA).
-template <int NQ>
-__device__ __forceinline__ void cluster_totals(cg::cluster_group& cl, double (*slots)[12], int parity, const int (&kind)[NQ],
-                                               double (&tot)[NQ]) {
-    cl.sync();
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) tot[q] = kind[q] ? -INFINITY : 0.0;
-    for (unsigned r = 0; r < cl.num_blocks(); ++r) {
-        const double* rs = cl.map_shared_rank(&slots[parity][0], r);
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) tot[q] = kind[q] ? fmax(tot[q], rs[q]) : tot[q] + rs[q];
-    }
-}
-
+// Cluster size (CTAs per problem) and CTA size are launch parameters: the
+// batched path launches 8 CTAs of 256 threads per problem, a single problem
+// 16 CTAs of 1024 threads.  Each CTA takes a contiguous chunk of its problem.
 template <typename T, bool CACHE>
-__global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(256)
-    k_b_project(const BProb<T>* __restrict__ tab) {
+__global__ void __launch_bounds__(1024) k_b_project(const BProb<T>* __restrict__ tab) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* wloc = reinterpret_cast<T*>(smem_raw);
-    __shared__ double slots[2][12];
-    __shared__ double sh10[32 * 10];
+    __shared__ ProjPart slots[2];
     cg::cluster_group cl = cg::this_cluster();
-    const unsigned rank = cl.block_rank();
-    const BProb<T>& P = tab[blockIdx.x / kClusterCTAs];
+    const unsigned rank = cl.block_rank(), csize = cl.num_blocks();
+    const BProb<T>& P = tab[blockIdx.x / csize];
     const long long n = P.n_elem;
-    const long long chunk = (n + kClusterCTAs - 1) / kClusterCTAs;
-    const long long b0 = (long long)rank * chunk, b1 = min(b0 + chunk, n);
-    const int tid = threadIdx.x;
-    DevScalars* sc = P.sc;
-    const double alpha = sc->alpha;
-    const double gmean = P.mean_proj ? sc->gsum / (double)n : 0.0;
-    const T alpha_t = (T)alpha, gmean_t = (T)gmean;
-    auto wat = [&](long long e) -> T { return CACHE ? wloc[e - b0] : P.wbuf[e]; };
-
-    // pass 0: w; the piece at lambda = 0 (box-clamp volume), the piece at the warm
-    // start lambda_s (the previous multiplier), min / max of w
-    const double lam_s = sc->lambda;
-    double tot[10];
-    int parity = 0;
-    {
-        double v[10] = {0.0, 0.0, 0.0, 0.0, INFINITY, -INFINITY, 0.0, 0.0, 0.0, 0.0};
-        T sF = T(0), sFs = T(0), wmn = T(INFINITY), wmx = T(-INFINITY);
-        const BThresh<T> th0(0.0, P.lo, P.hi), ths(lam_s > 0.0 ? lam_s : 0.0, P.lo, P.hi);
-        for (long long e = b0 + tid; e < b1; e += blockDim.x) {
-            const T w = P.rho[e] - alpha_t * (P.grad[e] - gmean_t);
-            if (CACHE) wloc[e - b0] = w;
-            else P.wbuf[e] = w;
-            int c = th0.cls(w);
-            if (c == 0) v[0] += 1.0;
-            else if (c == 1) v[1] += 1.0;
-            else { v[2] += 1.0; sF += w; }
-            c = ths.cls(w);
-            if (c == 0) v[6] += 1.0;
-            else if (c == 1) v[7] += 1.0;
-            else { v[8] += 1.0; sFs += w; }
-            wmn = fmin(wmn, w);
-            wmx = fmax(wmx, w);
-        }
-        double mv[10] = {v[0], v[1], v[2], (double)sF, -(double)wmn, (double)wmx, v[6], v[7], v[8], (double)sFs};
-        const int kind[10] = {0, 0, 0, 0, 1, 1, 0, 0, 0, 0};
-        block_reduce<10>(mv, kind, sh10);
-        if (tid == 0)
-            for (int q = 0; q < 10; ++q) slots[parity][q] = mv[q];
-        cluster_totals<10>(cl, slots, parity, kind, tot);
-        parity ^= 1;
-    }
-    const double wmin = -tot[4], wmax = tot[5];
-    const double S0 = tot[0] * P.hi + tot[1] * P.lo + tot[3];
-    double lambda = 0.0;
-    int iters = 0;
-    if (!isfinite(S0)) set_err(&sc->err, TO_ERR_NONFINITE);
-    ProjSearch st;
-    st.done = !(S0 > P.vbar) || !isfinite(S0);
-    st.have_prev = false;
-    st.pU = st.pL = st.pF = 0.0;
-    if (!st.done) {
-        st.lo_b = fmax(0.0, wmin - P.hi);
-        st.hi_b = wmax - P.lo;
-        const double t0[4] = {tot[0], tot[1], tot[2], tot[3]};
-        st.lam = 0.0;
-        proj_search_step(st, t0, P.vbar, P.lo, P.hi);          // Newton from lambda = 0
-        if (!st.done && lam_s > st.lo_b && lam_s < st.hi_b) {           // the warm start tightens it
-            const double ts[4] = {tot[6], tot[7], tot[8], tot[9]};
-            st.lam = lam_s;
-            st.have_prev = false;
-            proj_search_step(st, ts, P.vbar, P.lo, P.hi);
-        }
-    }
-    while (!st.done && iters < kProjMaxIter) {
-        ++iters;
-        const BThresh<T> th(st.lam, P.lo, P.hi);
-        double v[4] = {0.0, 0.0, 0.0, 0.0};
-        T sF = T(0);
-        for (long long e = b0 + tid; e < b1; e += blockDim.x) {
-            const T w = wat(e);
-            const int c = th.cls(w);
-            if (c == 0) v[0] += 1.0;
-            else if (c == 1) v[1] += 1.0;
-            else { v[2] += 1.0; sF += w; }
-        }
-        v[3] = (double)sF;
-        const int kind[4] = {0, 0, 0, 0};
-        block_reduce<4>(v, kind, sh10);
-        if (tid == 0)
-            for (int q = 0; q < 4; ++q) slots[parity][q] = v[q];
-        double t4[4];
-        cluster_totals<4>(cl, slots, parity, kind, t4);
-        parity ^= 1;
-        proj_search_step(st, t4, P.vbar, P.lo, P.hi);
-    }
-    lambda = st.done && !(S0 > P.vbar) ? 0.0 : st.lam;
-
-    double dmax = 0.0, vol = 0.0;
-    for (long long e = b0 + tid; e < b1; e += blockDim.x) {
-        const double wd = (double)wat(e);
-        const T rt = (T)fmin(fmax(wd - lambda, P.lo), P.hi);
-        T* rho = const_cast<T*>(P.rho);
-        dmax = fmax(dmax, fabs((double)rt - (double)rho[e]));
-        vol += (double)rt;
-        rho[e] = rt;
-    }
-    double v2[2] = {dmax, vol};
-    const int kind2[2] = {1, 0};
-    block_reduce<2>(v2, kind2, sh10);
-    if (tid == 0) {
-        slots[parity][0] = v2[0];
-        slots[parity][1] = v2[1];
-    }
-    double t2[2];
-    cluster_totals<2>(cl, slots, parity, kind2, t2);
-    if (rank == 0 && tid == 0) {
-        sc->lambda = lambda;
-        sc->drho_inf = t2[0];
-        sc->volume = t2[1];
-        sc->proj_iters = iters;
-    }
+    const long long chunk = (n + csize - 1) / csize;
+    ProjIO io;
+    io.n = n;
+    io.b0 = (long long)rank * chunk;
+    io.b1 = min(io.b0 + chunk, n);
+    io.vbar = P.vbar;
+    io.lo = P.lo;
+    io.hi = P.hi;
+    io.fused = 1;
+    io.mean_proj = P.mean_proj;
+    io.writer = rank == 0;
+    ClusterComm comm{slots};
+    T* rho = const_cast<T*>(P.rho);
+    projection_body<T, CACHE>(comm, io, nullptr, P.rho, P.grad, reinterpret_cast<T*>(smem_raw), P.wbuf, rho, P.sc);
     cl.sync();   // no CTA leaves while another may still read its slots
+}
+
+template <typename T>
+int launch_cluster_project(const BProb<T>* tab, int n_problems, int csize, int threads, bool cache, size_t smem,
+                           cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(n_problems * csize));
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)csize;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    if (cache) TO_CUDA(cudaLaunchKernelEx(&cfg, k_b_project<T, true>, tab));
+    else TO_CUDA(cudaLaunchKernelEx(&cfg, k_b_project<T, false>, tab));
+    return TO_OK;
+}
+
+// shared-memory and non-portable cluster-size opt-in of the cluster projection
+template <typename T>
+int cluster_project_attrs(size_t smem) {
+    TO_CUDA(cudaFuncSetAttribute(k_b_project<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    TO_CUDA(cudaFuncSetAttribute(k_b_project<T, true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    TO_CUDA(cudaFuncSetAttribute(k_b_project<T, false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    return TO_OK;
 }
 
 template <typename T>
@@ -451,13 +343,8 @@ int build_tables_t(to_batch* B) {
     const long long chunk = (max_elem + kClusterCTAs - 1) / kClusterCTAs;
     B->proj_smem = (size_t)chunk * sizeof(T);
     B->proj_cache = B->proj_smem <= 96 * 1024;
-    if (B->proj_cache) {
-        if (cudaFuncSetAttribute(k_b_project<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B->proj_smem) !=
-            cudaSuccess)
-            return fail(TO_ERR_CUDA, "projection shared-memory opt-in");
-    } else {
-        B->proj_smem = 0;
-    }
+    if (!B->proj_cache) B->proj_smem = 0;
+    if (int rc = cluster_project_attrs<T>(160 * 1024)) return rc;
     return TO_OK;
 }
 
@@ -466,7 +353,7 @@ int iteration_t(to_batch* B, cudaStream_t s) {
     const BProb<T>* tab = (const BProb<T>*)B->btab;
     const to_problem* P0 = B->probs[0];
     const dim3 g2(B->grid_x, B->n);
-    k_b_design<T><<<g2, 256, 0, s>>>(tab, P0->mat.E0, P0->mat.Emin, P0->mat.p);
+    k_b_design<T><<<g2, 256, 0, s>>>(tab, simp_params<T>(P0->mat));
     k_b_diag<T><<<g2, 256, 0, s>>>(tab);
     TO_CUDA(cudaGetLastError());
     int rc = batch_operator_launch(B->prec, OP_RESID, B->tab_resid, B->kh, B->max_tiles, B->n, s);
@@ -478,10 +365,7 @@ int iteration_t(to_batch* B, cudaStream_t s) {
         TO_CUDA(cudaGetLastError());
     }
     k_b_filter_T<T><<<g2, 256, 0, s>>>(tab);
-    if (B->proj_cache)
-        k_b_project<T, true><<<B->n * kClusterCTAs, 256, B->proj_smem, s>>>(tab);
-    else
-        k_b_project<T, false><<<B->n * kClusterCTAs, 256, 0, s>>>(tab);
+    if ((rc = launch_cluster_project<T>(tab, B->n, kClusterCTAs, 256, B->proj_cache, B->proj_smem, s))) return rc;
     k_b_record<T><<<(B->n + 63) / 64, 64, 0, s>>>(tab, B->n, 0);
     TO_CUDA(cudaGetLastError());
     return TO_OK;
@@ -502,6 +386,7 @@ void destroy_batch(to_batch* B) {
 }
 
 }  // namespace
+
 
 extern "C" int to_batch_create(to_problem* const* problems, int32_t n, to_batch** out) {
     if (!out) return fail(TO_ERR_ARG, "out is null");

@@ -7,8 +7,6 @@
 
 namespace to {
 
-constexpr int kMaxStencil = 1024;   // cone of radius < 6 voxels
-
 // ----------------------------------------------------------------------------- filter
 // forward:   y_e = sum_s w_s x_{e+s} / Hs_e
 // transpose: y_i = sum_s w_s x_{i+s} / Hs_{i+s}   (the stencil is symmetric)
@@ -20,40 +18,49 @@ __global__ void __launch_bounds__(256) k_filter(int nx, int ny, int nz, const T*
                                                 const T* __restrict__ Hs, const int4* __restrict__ st,
                                                 const T* __restrict__ w, int ns, int R, double* red, unsigned* counter,
                                                 DevScalars* sc, double alpha0_param, double alpha_scale, double m_exp,
-                                                T* Eout = nullptr, T* Edout = nullptr, double E0 = 1.0, double Emin = 0.0,
-                                                double pexp = 3.0) {
+                                                T* Eout = nullptr, T* Edout = nullptr, SimpT<T> simp = SimpT<T>{}) {
     __shared__ double sh[32 * kRedQ];
-    __shared__ int4 s_st[kMaxStencil];
-    __shared__ T s_w[kMaxStencil];
-    for (int q = threadIdx.x + 32 * threadIdx.y; q < ns; q += 256) {
-        s_st[q] = st[q];
-        s_w[q] = w[q];
+    // the stencil, padded to a multiple of 8 with zero-weight copies of the centre
+    extern __shared__ __align__(16) unsigned char fsm[];
+    const int nsp = (ns + 7) & ~7;
+    int4* s_st = reinterpret_cast<int4*>(fsm);
+    T* s_w = reinterpret_cast<T*>(fsm + (size_t)nsp * sizeof(int4));
+    for (int q = threadIdx.x + 32 * threadIdx.y; q < nsp; q += 256) {
+        s_st[q] = q < ns ? st[q] : make_int4(0, 0, 0, 0);
+        s_w[q] = q < ns ? w[q] : T(0);
     }
     __syncthreads();
-    double amax = 0.0, sum = 0.0;
+    T amax = T(0), sum = T(0);   // per-thread partials in the element precision
     const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y;
+    const bool ij_in = i >= R && i < nx - R && j >= R && j < ny - R;
     for (int k = blockIdx.z; k < nz && i < nx && j < ny; k += gridDim.z) {
         const long long e = i + (long long)nx * (j + (long long)ny * k);
-        const bool interior = i >= R && i < nx - R && j >= R && j < ny - R && k >= R && k < nz - R;
+        const bool interior = ij_in && k >= R && k < nz - R;
         T acc = T(0);
         // eight stencil points per round, all loads issued before the sums
-        for (int s0 = 0; s0 < ns; s0 += 8) {
+        for (int s0 = 0; s0 < nsp; s0 += 8) {
             T xv[8], hv[8];
+            if (interior) {   // no bounds checks: the linear offsets stay inside the grid
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int s = s0 + q;
-                bool ok = s < ns;
-                const int4 o = s_st[ok ? s : 0];
-                const int ii = i + o.x, jj = j + o.y, kk = k + o.z;
-                ok = ok && (interior || (ii >= 0 && ii < nx && jj >= 0 && jj < ny && kk >= 0 && kk < nz));
-                const long long m = e + o.w;   // precomputed linear offset
-                xv[q] = ok ? x[m] : T(0);
-                hv[q] = (TRANSPOSE && !PRESCALED) ? (ok ? Hs[m] : T(1)) : T(1);
+                for (int q = 0; q < 8; ++q) {
+                    const long long m = e + s_st[s0 + q].w;
+                    xv[q] = x[m];
+                    hv[q] = (TRANSPOSE && !PRESCALED) ? Hs[m] : T(1);
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int4 o = s_st[s0 + q];
+                    const int ii = i + o.x, jj = j + o.y, kk = k + o.z;
+                    const bool ok = ii >= 0 && ii < nx && jj >= 0 && jj < ny && kk >= 0 && kk < nz;
+                    const long long m = e + o.w;
+                    xv[q] = ok ? x[m] : T(0);
+                    hv[q] = (TRANSPOSE && !PRESCALED) ? (ok ? Hs[m] : T(1)) : T(1);
+                }
             }
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
-                const int s = s0 + q;
-                const T wq = s < ns ? s_w[s] : T(0);
+                const T wq = s_w[s0 + q];
                 if (TRANSPOSE && !PRESCALED)
                     acc += wq * xv[q] / hv[q];
                 else
@@ -63,31 +70,24 @@ __global__ void __launch_bounds__(256) k_filter(int nx, int ny, int nz, const T*
         const T hs_e = TRANSPOSE ? T(1) : Hs[e];
         const T out = TRANSPOSE ? acc : acc / hs_e;
         y[e] = out;
-        if (MODULI) {   // E = Emin + rho~^p (E0 - Emin) and E' / Hs (the sensitivity's prescaled factor)
-            const T dE = (T)(E0 - Emin);
-            T pw, pw1;
-            if (pexp == 3.0) {
-                pw1 = out * out;
-                pw = pw1 * out;
-            } else {
-                pw1 = (T)pow((double)out, pexp - 1.0);
-                pw = pw1 * out;
-            }
-            Eout[e] = (T)Emin + pw * dE;
-            Edout[e] = (T)pexp * pw1 * dE / hs_e;
-            if (!isfinite((double)out)) set_err(&sc->err, TO_ERR_NONFINITE);
+        if (MODULI) {   // E and E' / Hs (the sensitivity's prescaled factor)
+            T Ee, Ed;
+            simp_moduli(simp, out, Ee, Ed);
+            Eout[e] = Ee;
+            Edout[e] = Ed / hs_e;
+            if (!tfinite(out)) set_err(&sc->err, TO_ERR_NONFINITE);
         }
         if (STATS) {
-            amax = fmax(amax, fabs((double)out));
-            sum += (double)out;
+            amax = tmax(amax, tabs(out));
+            sum += out;
         }
     }
     if (STATS) {
-        double v[2] = {amax, sum};
+        T v[2] = {amax, sum};
         const int kind[2] = {1, 0};
         double tot[2];
-        block_reduce<2>(v, kind, sh);
-        if (finish_reduction<2>(v, kind, red, counter, tot, sh, linear_block(), grid_blocks()) && threadIdx.x == 0 && threadIdx.y == 0) {
+        block_reduce<T, 2>(v, kind, reinterpret_cast<T*>(sh));
+        if (finish_reduction<T, 2>(v, kind, red, counter, tot, sh, linear_block(), grid_blocks()) && threadIdx.x == 0 && threadIdx.y == 0) {
             sc->gmax = tot[0];
             sc->gsum = tot[1];
             if (!isfinite(tot[0]) || !isfinite(tot[1])) set_err(&sc->err, TO_ERR_NONFINITE);
@@ -99,6 +99,25 @@ __global__ void __launch_bounds__(256) k_filter(int nx, int ny, int nz, const T*
         }
     }
 }
+
+// dynamic shared memory of k_filter: the padded stencil
+template <typename T>
+static size_t filter_smem(int ns) {
+    const int nsp = (ns + 7) & ~7;
+    return (size_t)nsp * (sizeof(int4) + sizeof(T));
+}
+
+template <typename T>
+SimpT<T> simp_params(const to_material& m) {
+    SimpT<T> s;
+    s.emin = (T)m.Emin;
+    s.dE = (T)(m.E0 - m.Emin);
+    s.p = (T)m.p;
+    s.cubic = m.p == 3.0;
+    return s;
+}
+template SimpT<float> simp_params<float>(const to_material&);
+template SimpT<double> simp_params<double>(const to_material&);
 
 template <typename T>
 __global__ void k_filter_rowsum(int nx, int ny, int nz, T* Hs, const int4* st, const T* w, int ns) {
@@ -114,42 +133,6 @@ __global__ void k_filter_rowsum(int nx, int ny, int nz, T* Hs, const int4* st, c
             acc += w[s];
         }
         Hs[e] = acc;
-    }
-}
-
-// E = Emin + rho~^p (E0 - Emin),  E' = p rho~^(p-1) (E0 - Emin)
-template <typename T>
-__device__ __forceinline__ void simp(T rt, double E0, double Emin, double p, T& E, T& Ed) {
-    const T dE = (T)(E0 - Emin);
-    T pw, pw1;
-    if (p == 3.0) {
-        pw1 = rt * rt;
-        pw = pw1 * rt;
-    } else if (p == 1.0) {
-        pw1 = T(1);
-        pw = rt;
-    } else if (p == 2.0) {
-        pw1 = rt;
-        pw = rt * rt;
-    } else {
-        pw1 = (T)pow((double)rt, p - 1.0);
-        pw = pw1 * rt;
-    }
-    E = (T)Emin + pw * dE;
-    Ed = (T)p * pw1 * dE;
-}
-
-// E and E' / Hs (the filter row sum is folded into E' so that the fused
-// sensitivity writes g~ / Hs, the input the filter transpose needs)
-template <typename T>
-__global__ void k_moduli(long long n, const T* rt, const T* Hs, T* E, T* Ed, double E0, double Emin, double p, int* err) {
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-        const T r = rt[e];
-        if (!isfinite((double)r)) set_err(err, TO_ERR_NONFINITE);
-        T a, b;
-        simp<T>(r, E0, Emin, p, a, b);
-        E[e] = a;
-        Ed[e] = b / Hs[e];
     }
 }
 
@@ -197,15 +180,16 @@ static int filter_t(to_problem* P, const void* x, void* y, int transpose, int st
         if (gz < nz) grid.z = (unsigned)gz;
     }
 #define TO_FILTER_ARGS nx, ny, nz, (const T*)x, (T*)y, Hs, P->stencil, w, P->n_stencil, R
+    const size_t fs = filter_smem<T>(P->n_stencil);
     if (transpose && stats && prescaled)
-        k_filter<T, true, true, true><<<grid, block3(), 0, s>>>(TO_FILTER_ARGS, P->red, P->counters + 2, P->sc,
-                                                                 P->prm.alpha0, P->prm.alpha_scale, P->prm.m);
+        k_filter<T, true, true, true><<<grid, block3(), fs, s>>>(TO_FILTER_ARGS, P->red, P->counters + 2, P->sc,
+                                                                  P->prm.alpha0, P->prm.alpha_scale, P->prm.m);
     else if (transpose && prescaled)
-        k_filter<T, true, false, true><<<grid, block3(), 0, s>>>(TO_FILTER_ARGS, nullptr, nullptr, nullptr, 0.0, 0.0, 0.0);
+        k_filter<T, true, false, true><<<grid, block3(), fs, s>>>(TO_FILTER_ARGS, nullptr, nullptr, nullptr, 0.0, 0.0, 0.0);
     else if (transpose)
-        k_filter<T, true, false, false><<<grid, block3(), 0, s>>>(TO_FILTER_ARGS, nullptr, nullptr, nullptr, 0.0, 0.0, 0.0);
+        k_filter<T, true, false, false><<<grid, block3(), fs, s>>>(TO_FILTER_ARGS, nullptr, nullptr, nullptr, 0.0, 0.0, 0.0);
     else
-        k_filter<T, false, false, false><<<grid, block3(), 0, s>>>(TO_FILTER_ARGS, nullptr, nullptr, nullptr, 0.0, 0.0, 0.0);
+        k_filter<T, false, false, false><<<grid, block3(), fs, s>>>(TO_FILTER_ARGS, nullptr, nullptr, nullptr, 0.0, 0.0, 0.0);
 #undef TO_FILTER_ARGS
     TO_CUDA(cudaGetLastError());
     return TO_OK;
@@ -229,10 +213,10 @@ template <typename T>
 static int moduli_t(to_problem* P, cudaStream_t s) {
     // rho~ = C(rho) and the moduli in one pass
     const int nx = P->g.nx, ny = P->g.ny, nz = P->g.nz;
-    k_filter<T, false, false, false, true><<<grid3(nx, ny, nz), block3(), 0, s>>>(
+    k_filter<T, false, false, false, true><<<grid3(nx, ny, nz), block3(), filter_smem<T>(P->n_stencil), s>>>(
         nx, ny, nz, (const T*)P->rho, (T*)P->rhot, (const T*)P->Hs, P->stencil, (const T*)P->stencil_w, P->n_stencil,
-        (int)std::ceil(P->mat.rmin), nullptr, nullptr, P->sc, 0.0, 0.0, 0.0, (T*)P->lv[0].E, (T*)P->Ed, P->mat.E0,
-        P->mat.Emin, P->mat.p);
+        (int)std::ceil(P->mat.rmin), nullptr, nullptr, P->sc, 0.0, 0.0, 0.0, (T*)P->lv[0].E, (T*)P->Ed,
+        simp_params<T>(P->mat));
     TO_CUDA(cudaGetLastError());
     return TO_OK;
 }

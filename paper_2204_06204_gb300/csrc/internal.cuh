@@ -25,6 +25,13 @@ int fail(int code, const std::string& msg);
 // ----------------------------------------------------------------------------- device scalars
 // Device-resident scalars of the outer loop; read by kernels, never copied to
 // the host except through to_stats / to_get_state / to_check.
+// State of the projection's multiplier search (device.cuh: proj_search_step)
+struct ProjSearch {
+    double lam, lo_b, hi_b;
+    double pU, pL, pF;   // sets that produced lam (when have_prev)
+    bool have_prev, done;
+};
+
 struct DevScalars {
     double rz, zq, beta, beta_first;   // lower-level step sizes (Algorithm 1 / 3, line 1)
     double J, res_inf, res2;           // f^T u_k, residual norms at u_k
@@ -36,6 +43,7 @@ struct DevScalars {
     int proj_iters;
     int n_inner_done;
     int rec;                           // next stats slot written by the record kernel
+    ProjSearch ps;                     // the projection's search, carried between its kernels
 };
 
 // Reduction scratch: one slot of up to kRedQ doubles per block, plus a
@@ -119,12 +127,16 @@ struct to_problem {
     void* coarse_A = nullptr;      // dense coarsest operator (T), n_c x n_c
     void* coarse_L = nullptr;      // scaled inverse (T), n_c x n_c, then the n_c scale factors
     int n_coarse = 0;
+    int mg_tail = 0;               // first level of the one-CTA coarse tail (0: none)
     double* ke_dev = nullptr;      // 24x24 unit element matrix (device, double)
 
     // device scalars, reductions, stats
     to::DevScalars* sc = nullptr;
     double* red = nullptr;         // kMaxRedBlocks * kRedQ doubles
-    unsigned* counters = nullptr;  // completion counters / barrier words
+    // completion counters / barrier words (64): [0] residual, [1] z^T q, [2] filter^T statistics,
+    // [4] update, [5] r^T z, [6] smoother r^T z, [7] f^T u, [8..9] grid barrier,
+    // [10..11] projection first / final pass
+    unsigned* counters = nullptr;
     to_stats* dstats = nullptr;    // device stats ring
     int dstats_cap = 0;
 
@@ -134,6 +146,9 @@ struct to_problem {
     int iters_T = -1;
     double iters_beta = 0.0;
 
+    // can one 16-CTA cluster run the projection's search passes
+    int cluster16 = 0;
+
     // captured outer iteration (replayed by to_step) on a library-owned stream
     cudaStream_t gstream = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
@@ -142,8 +157,9 @@ struct to_problem {
     cudaStream_t side = nullptr;   // branch for the coarsest inverse (overlaps the fine-level work)
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 
-    // launch configuration of the operator kernel
+    // launch configuration of the operator kernel; resident CTAs per SM of each mode
     int tile_x = 32, tile_y = 8, tile_z = 8;
+    int op_occ[5] = {0, 0, 0, 0, 0};
     int num_sms = 0;
     int coop_blocks = 0;           // co-resident blocks for the projection kernel
 };
@@ -171,6 +187,7 @@ int launch_energy(to_problem* P, const void* u, cudaStream_t s);
 int launch_record(to_problem* P, cudaStream_t s);
 int operator_init(to_problem* P);
 int build_tile_mask(Level& L, const uint8_t* mask_host);
+int project_cluster_setup(to_problem* P);
 int launch_richardson(to_problem* P, cudaStream_t s);
 
 // multigrid

@@ -18,6 +18,8 @@
 #include <cmath>
 
 #include "device.cuh"
+#include "haar.cuh"
+#include "transfer.cuh"
 
 namespace to {
 
@@ -48,73 +50,21 @@ __global__ void k_coarsen_E(int cx, int cy, int cz, const T* __restrict__ Ef, T*
     }
 }
 
-// b_c = m_c P^T (m_f t)
+// b_c = m_c P^T (m_f t), optionally with the coarse level's first sweep
 template <typename T>
 __global__ void k_restrict(int cx, int cy, int cz, const T* __restrict__ tf, const uint8_t* __restrict__ mf,
-                           const uint8_t* __restrict__ mc, T* __restrict__ bc) {
-    const int fx = 2 * cx, fy = 2 * cy, fz = 2 * cz;
+                           const uint8_t* __restrict__ mc, T* __restrict__ bc, const T* __restrict__ dc,
+                           T* __restrict__ xc, T omega) {
     const Idx3 t = idx3(cx + 1, cy + 1, cz + 1);
-    if (t.ok) {
-        const int I = t.i, J = t.j, K = t.k;
-        const long long n = I + (long long)(cx + 1) * (J + (long long)(cy + 1) * K);
-        T acc[3] = {T(0), T(0), T(0)};
-#pragma unroll
-        for (int dk = -1; dk <= 1; ++dk) {
-            const int k = 2 * K + dk;
-            const T wk = dk ? T(0.5) : T(1);
-#pragma unroll
-            for (int dj = -1; dj <= 1; ++dj) {
-                const int j = 2 * J + dj;
-                const T wj = dj ? T(0.5) : T(1);
-#pragma unroll
-                for (int di = -1; di <= 1; ++di) {
-                    const int i = 2 * I + di;
-                    const bool in = k >= 0 && k <= fz && j >= 0 && j <= fy && i >= 0 && i <= fx;
-                    const long long fnode = in ? i + (long long)(fx + 1) * (j + (long long)(fy + 1) * k) : 0;
-                    const T w = (di ? T(0.5) : T(1)) * wj * wk;
-                    const uint8_t m = in ? mf[fnode] : 7;
-                    const T v0 = in ? tf[3 * fnode + 0] : T(0), v1 = in ? tf[3 * fnode + 1] : T(0),
-                            v2 = in ? tf[3 * fnode + 2] : T(0);
-                    acc[0] += (m & 1) ? T(0) : w * v0;
-                    acc[1] += (m & 2) ? T(0) : w * v1;
-                    acc[2] += (m & 4) ? T(0) : w * v2;
-                }
-            }
-        }
-        const uint8_t m = mc[n];
-        for (int c = 0; c < 3; ++c) bc[3 * n + c] = ((m >> c) & 1) ? T(0) : acc[c];
-    }
+    if (t.ok) restrict_node<T>(cx, cy, cz, t.i, t.j, t.k, tf, mf, mc, bc, dc, xc, omega);
 }
 
 // x_f += m_f P (m_c x_c)
 template <typename T>
 __global__ void k_prolong_add(int cx, int cy, int cz, const T* __restrict__ xc, const uint8_t* __restrict__ mc,
                               const uint8_t* __restrict__ mf, T* __restrict__ xf) {
-    const int fx = 2 * cx, fy = 2 * cy, fz = 2 * cz;
-    const Idx3 t = idx3(fx + 1, fy + 1, fz + 1);
-    if (t.ok) {
-        const int i = t.i, j = t.j, k = t.k;
-        const long long n = i + (long long)(fx + 1) * (j + (long long)(fy + 1) * k);
-        const uint8_t m = mf[n];
-        if (m == 7) return;
-        const int i0 = i >> 1, i1 = (i + 1) >> 1, j0 = j >> 1, j1 = (j + 1) >> 1, k0 = k >> 1, k1 = (k + 1) >> 1;
-        T acc[3] = {T(0), T(0), T(0)};
-        const T w = ((i & 1) ? T(0.5) : T(1)) * ((j & 1) ? T(0.5) : T(1)) * ((k & 1) ? T(0.5) : T(1));
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int ic = (q & 1) ? i1 : i0, jc = (q & 2) ? j1 : j0, kc = (q & 4) ? k1 : k0;
-            // a coordinate with an even fine index has one parent: count it once
-            const bool use = (!(q & 1) || i1 != i0) && (!(q & 2) || j1 != j0) && (!(q & 4) || k1 != k0);
-            const long long cn = ic + (long long)(cx + 1) * (jc + (long long)(cy + 1) * kc);
-            const uint8_t mcn = use ? mc[cn] : 7;
-            const T v0 = use ? xc[3 * cn + 0] : T(0), v1 = use ? xc[3 * cn + 1] : T(0), v2 = use ? xc[3 * cn + 2] : T(0);
-            acc[0] += (mcn & 1) ? T(0) : w * v0;
-            acc[1] += (mcn & 2) ? T(0) : w * v1;
-            acc[2] += (mcn & 4) ? T(0) : w * v2;
-        }
-        for (int c = 0; c < 3; ++c)
-            if (!((m >> c) & 1)) xf[3 * n + c] += acc[c];
-    }
+    const Idx3 t = idx3(2 * cx + 1, 2 * cy + 1, 2 * cz + 1);
+    if (t.ok) prolong_node<T>(cx, cy, cz, t.i, t.j, t.k, xc, mc, mf, xf);
 }
 
 // x = omega D^-1 b  (first Jacobi sweep from x = 0)
@@ -176,7 +126,7 @@ __global__ void __launch_bounds__(1024) k_dense_invert(const T* __restrict__ A, 
     __syncthreads();
     for (int i = tid; i < n; i += nt) {
         const T d = A[(long long)i * n + i];
-        s[i] = d > T(0) ? T(1) / sqrt(d) : T(0);
+        s[i] = d > T(0) ? T(1) / tsqrt(d) : T(0);
         if (!(d > T(0))) bad = 1;
     }
     __syncthreads();
@@ -235,7 +185,7 @@ __global__ void __launch_bounds__(1024) k_dense_invert_reg(const T* __restrict__
     __syncthreads();
     for (int i = tid; i < n; i += 1024) {
         const T d = A[(long long)i * n + i];
-        s[i] = d > T(0) ? T(1) / sqrt(d) : T(0);
+        s[i] = d > T(0) ? T(1) / tsqrt(d) : T(0);
         if (!(d > T(0))) bad = 1;
     }
     __syncthreads();
@@ -334,7 +284,252 @@ __global__ void k_dense_solve(const T* __restrict__ Ainv, const T* __restrict__ 
     if (threadIdx.x == 0) x[i] = sc[i] * acc;
 }
 
+// ----------------------------------------------------------------------------- the coarse tail on one CTA
+// Below about a thousand elements a level's sweep costs far less than a kernel
+// launch.  The V-cycle from the first such level down (its smoothing, residual,
+// restriction, the dense coarsest solve, prolongation and post-smoothing) then
+// runs in one CTA, with a barrier between steps.  Its operator is element-
+// parallel: each thread applies the element matrix of its elements (the same
+// Haar factorisation as the operator kernel) into shared memory, then each node
+// adds the contributions of its (up to 8) elements in a fixed order.
+constexpr int kTailMaxLevels = 8;
+constexpr int kTailThreads = 512;
+constexpr int kTailMaxElems = 1024;
+constexpr size_t kTailSmem = 220 * 1024;
+
+// one level of the tail: its arrays live in shared memory for the whole kernel
+template <typename T>
+struct TailLevel {
+    int nx, ny, nz;
+    const T* E;
+    const T* d;
+    const uint8_t* mask;
+    T* x;
+    T* b;
+    T* t;
+    T escale;   // h_level / h_0 = 2^level (exact): the level's K_e is escale times the finest one
+};
+
+// global arrays of a level and the byte offsets of its shared-memory copies
+template <typename T>
+struct TailGlobal {
+    int nx, ny, nz;
+    const T* E;
+    const T* d;
+    const uint8_t* mask;
+    T* x;              // level 0 of the tail: the result goes back here
+    const T* b;        // level 0: the right-hand side
+    const T* first;    // level 0: its first sweep (written with the restriction)
+    unsigned oE, od, omask, ox, ot, ob;
+    T escale;
+};
+
+template <typename T>
+struct TailArgs {
+    int nlev;            // levels in the tail, the last one the coarsest (dense solve)
+    int nu1, nu2;
+    T omega;
+    const T* inv;        // n_c x n_c scaled inverse, then the n_c scale factors
+    int n_c;
+    unsigned ocontrib;   // byte offset of the element contributions
+    TailGlobal<T> lv[kTailMaxLevels];
+};
+
+// y = x + omega D^-1 (b - K x) (smooth) or y = b - K x on one level; `contrib`
+// holds 24 values per element (component-major: [24][ne])
+template <typename T>
+__device__ __forceinline__ void tail_operator(const TailLevel<T>& Lv, const HaarK<T>& kh, const T* x, T* y, bool smooth,
+                                              T omega, T* contrib) {
+    const int nx = Lv.nx, ny = Lv.ny, nz = Lv.nz, nxn = nx + 1, nyn = ny + 1;
+    const int ne = nx * ny * nz, nn = nxn * nyn * (nz + 1);
+    constexpr int kOff[8][3] = {{0, 0, 0}, {1, 0, 0}, {1, 1, 0}, {0, 1, 0}, {0, 0, 1}, {1, 0, 1}, {1, 1, 1}, {0, 1, 1}};
+    constexpr int kNode[2][2][2] = {{{0, 4}, {3, 7}}, {{1, 5}, {2, 6}}};
+    for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+        const int i = e % nx, j = (e / nx) % ny, k = e / (nx * ny);
+        T u[24];
+#pragma unroll
+        for (int l = 0; l < 8; ++l) {
+            const int n = (i + kOff[l][0]) + nxn * ((j + kOff[l][1]) + nyn * (k + kOff[l][2]));
+            const uint8_t m = Lv.mask[n];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) u[3 * l + c] = ((m >> c) & 1) ? T(0) : x[3 * n + c];
+        }
+        T yv[24];
+        elem_apply_haar(kh.v, Lv.E[e] * Lv.escale, u, yv);
+#pragma unroll
+        for (int q = 0; q < 24; ++q) contrib[q * ne + e] = yv[q];
+    }
+    __syncthreads();
+    for (int n = threadIdx.x; n < nn; n += blockDim.x) {
+        const int i = n % nxn, j = (n / nxn) % nyn, k = n / (nxn * nyn);
+        T kx[3] = {T(0), T(0), T(0)};
+#pragma unroll
+        for (int dk = -1; dk <= 0; ++dk)
+#pragma unroll
+            for (int dj = -1; dj <= 0; ++dj)
+#pragma unroll
+                for (int di = -1; di <= 0; ++di) {
+                    const int ei = i + di, ej = j + dj, ek = k + dk;
+                    if (ei < 0 || ei >= nx || ej < 0 || ej >= ny || ek < 0 || ek >= nz) continue;
+                    const int e = ei + nx * (ej + ny * ek);
+                    const int l = kNode[-di][-dj][-dk];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) kx[c] += contrib[(3 * l + c) * ne + e];
+                }
+        const uint8_t m = Lv.mask[n];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const T xv = x[3 * n + c], bv = Lv.b[3 * n + c];
+            const T K = ((m >> c) & 1) ? xv : kx[c];   // K^ is the identity on fixed DOFs
+            y[3 * n + c] = smooth ? xv + omega * (bv - K) / Lv.d[3 * n + c] : bv - K;
+        }
+    }
+    __syncthreads();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTailThreads) k_mg_tail(const TailArgs<T> a, const HaarK<T> kh) {
+    extern __shared__ __align__(16) unsigned char tsm[];
+    T* contrib = reinterpret_cast<T*>(tsm + a.ocontrib);
+    TailLevel<T> lv[kTailMaxLevels];
+    T* cur[kTailMaxLevels];
+    // stage every level's moduli, diagonal and mask (and the top level's right-hand side
+    // and first sweep) in shared memory
+    for (int t = 0; t < a.nlev; ++t) {
+        const TailGlobal<T>& G = a.lv[t];
+        TailLevel<T>& L = lv[t];
+        L.nx = G.nx;
+        L.ny = G.ny;
+        L.nz = G.nz;
+        L.escale = G.escale;
+        T* E = reinterpret_cast<T*>(tsm + G.oE);
+        T* d = reinterpret_cast<T*>(tsm + G.od);
+        uint8_t* m = tsm + G.omask;
+        L.E = E;
+        L.d = d;
+        L.mask = m;
+        L.x = reinterpret_cast<T*>(tsm + G.ox);
+        L.t = reinterpret_cast<T*>(tsm + G.ot);
+        L.b = reinterpret_cast<T*>(tsm + G.ob);
+        const int ne = G.nx * G.ny * G.nz, nn = (G.nx + 1) * (G.ny + 1) * (G.nz + 1);
+        if (t + 1 < a.nlev) {
+            for (int q = threadIdx.x; q < ne; q += blockDim.x) E[q] = G.E[q];
+            for (int q = threadIdx.x; q < 3 * nn; q += blockDim.x) d[q] = G.d[q];
+        }
+        for (int q = threadIdx.x; q < nn; q += blockDim.x) m[q] = G.mask[q];
+    }
+    const bool even = (a.nu1 - 1 + a.nu2) % 2 == 0;   // the first target, so that the last sweep writes x
+    {
+        const TailGlobal<T>& G = a.lv[0];
+        const int nn = (G.nx + 1) * (G.ny + 1) * (G.nz + 1);
+        T* c0 = even ? lv[0].x : lv[0].t;
+        for (int q = threadIdx.x; q < 3 * nn; q += blockDim.x) {
+            lv[0].b[q] = G.b[q];
+            c0[q] = G.first[q];
+        }
+    }
+    __syncthreads();
+    const TailLevel<T>* tl = lv;
+    // down: the first sweep of lv[0] came with its restriction, later ones come from ours
+    for (int t = 0; t + 1 < a.nlev; ++t) {
+        const TailLevel<T>& F = tl[t];
+        const TailLevel<T>& C = tl[t + 1];
+        T* c = even ? F.x : F.t;
+        T* o = even ? F.t : F.x;
+        for (int it = 1; it < a.nu1; ++it) {
+            tail_operator<T>(F, kh, c, o, true, a.omega, contrib);
+            T* sw = c;
+            c = o;
+            o = sw;
+        }
+        tail_operator<T>(F, kh, c, o, false, a.omega, contrib);
+        T* xc = t + 2 < a.nlev ? (even ? C.x : C.t) : nullptr;
+        const int X = C.nx + 1, Y = C.ny + 1, Z = C.nz + 1;
+        for (int n = threadIdx.x; n < X * Y * Z; n += blockDim.x)
+            restrict_node<T>(C.nx, C.ny, C.nz, n % X, (n / X) % Y, n / (X * Y), o, F.mask, C.mask, C.b, C.d, xc, a.omega);
+        __syncthreads();
+        cur[t] = c;
+    }
+    // the coarsest level: x = S A^-1 S b, one warp per row (lane-strided sums, shuffle tree)
+    {
+        const TailLevel<T>& Cst = tl[a.nlev - 1];
+        const int n = a.n_c, lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        const T* sc = a.inv + (size_t)n * n;
+        for (int i = wid; i < n; i += nw) {
+            T acc = T(0);
+            for (int j = lane; j < n; j += 32) acc += a.inv[(long long)i * n + j] * sc[j] * Cst.b[j];
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) Cst.x[i] = sc[i] * acc;
+        }
+        __syncthreads();
+    }
+    // up
+    for (int t = a.nlev - 2; t >= 0; --t) {
+        const TailLevel<T>& F = tl[t];
+        const TailLevel<T>& C = tl[t + 1];
+        T* c = cur[t];
+        T* o = c == F.x ? F.t : F.x;
+        const int X = 2 * C.nx + 1, Y = 2 * C.ny + 1, Z = 2 * C.nz + 1;
+        for (int n = threadIdx.x; n < X * Y * Z; n += blockDim.x)
+            prolong_node<T>(C.nx, C.ny, C.nz, n % X, (n / X) % Y, n / (X * Y), C.x, C.mask, F.mask, c);
+        __syncthreads();
+        for (int it = 0; it < a.nu2; ++it) {
+            tail_operator<T>(F, kh, c, o, true, a.omega, contrib);
+            T* sw = c;
+            c = o;
+            o = sw;
+        }
+    }
+    // the top level's correction back to global memory
+    const TailGlobal<T>& G = a.lv[0];
+    const int nn = (G.nx + 1) * (G.ny + 1) * (G.nz + 1);
+    for (int q = threadIdx.x; q < 3 * nn; q += blockDim.x) G.x[q] = tl[0].x[q];
+}
+
 // ----------------------------------------------------------------------------- host side
+
+// shared-memory layout of the tail from level l0: per level E, d, mask, x, t, b, then
+// the element contributions of level l0; returns the total bytes
+template <typename T>
+static size_t tail_layout(const to_problem* P, int l0, TailArgs<T>* a) {
+    const int L = (int)P->lv.size();
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off += (bytes + 15) & ~(size_t)15;
+        return (unsigned)o;
+    };
+    for (int t = 0; t < L - l0 && t < kTailMaxLevels; ++t) {
+        const Level& F = P->lv[l0 + t];
+        const size_t nn = (size_t)F.n_node, ne = (size_t)F.n_elem;
+        const unsigned oE = take(ne * sizeof(T)), od = take(3 * nn * sizeof(T)), om = take(nn),
+                       ox = take(3 * nn * sizeof(T)), ot = take(3 * nn * sizeof(T)), ob = take(3 * nn * sizeof(T));
+        if (a) {
+            TailGlobal<T>& g = a->lv[t];
+            g.nx = F.nx;
+            g.ny = F.ny;
+            g.nz = F.nz;
+            g.E = (const T*)F.E;
+            g.d = (const T*)F.d;
+            g.mask = F.mask;
+            g.x = (T*)F.x;
+            g.b = (const T*)F.b;
+            g.first = (const T*)((((P->prm.mg_nu_pre - 1 + P->prm.mg_nu_post) % 2) == 0) ? F.x : F.t);
+            g.oE = oE;
+            g.od = od;
+            g.omask = om;
+            g.ox = ox;
+            g.ot = ot;
+            g.ob = ob;
+            g.escale = (T)(F.h / P->g.h);
+        }
+    }
+    const unsigned oc = take((size_t)24 * P->lv[l0].n_elem * sizeof(T));
+    if (a) a->ocontrib = oc;
+    return off;
+}
+
+
 
 static int auto_levels(int nx, int ny, int nz) {
     int t = 0;
@@ -417,6 +612,20 @@ int mg_build(to_problem* P) {
                             : cudaFuncSetAttribute(k_dense_invert<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return fail(TO_ERR_CUDA, std::string("shared memory opt-in: ") + cudaGetErrorString(e));
     }
+    // the coarse tail: from the first level (>= 1, above the coarsest) with at most
+    // kTailMaxElems elements, when its levels fit in shared memory
+    P->mg_tail = 0;
+    for (int l = 1; l + 1 < L && L - l <= kTailMaxLevels; ++l) {
+        if (P->lv[l].n_elem > kTailMaxElems) continue;
+        const size_t tsm = P->prec == TO_FP64 ? tail_layout<double>(P, l, nullptr) : tail_layout<float>(P, l, nullptr);
+        if (tsm > kTailSmem) break;
+        cudaError_t e = P->prec == TO_FP64
+                            ? cudaFuncSetAttribute(k_mg_tail<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm)
+                            : cudaFuncSetAttribute(k_mg_tail<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm);
+        if (e != cudaSuccess) return fail(TO_ERR_CUDA, std::string("shared memory opt-in: ") + cudaGetErrorString(e));
+        P->mg_tail = l;
+        break;
+    }
     return TO_OK;
 }
 
@@ -458,6 +667,26 @@ int mg_refresh(to_problem* P, cudaStream_t s) {
     return P->prec == TO_FP64 ? refresh_t<double>(P, s) : refresh_t<float>(P, s);
 }
 
+// levels mg_tail .. L-1 in one launch (after the coarsest inverse is ready)
+template <typename T>
+static int tail_t(to_problem* P, cudaStream_t s) {
+    const int L = (int)P->lv.size(), l0 = P->mg_tail;
+    TailArgs<T> a{};
+    a.nlev = L - l0;
+    a.nu1 = P->prm.mg_nu_pre;
+    a.nu2 = P->prm.mg_nu_post;
+    a.omega = (T)P->prm.mg_omega;
+    a.inv = (const T*)P->coarse_L;
+    a.n_c = P->n_coarse;
+    const size_t tsm = tail_layout<T>(P, l0, &a);
+    HaarK<T> kh;
+    for (int q = 0; q < kHaarNnz; ++q) kh.v[q] = (T)P->haar[q];
+    TO_CUDA(cudaStreamWaitEvent(s, P->ev_join, 0));   // the inverse of this design is ready
+    k_mg_tail<T><<<1, kTailThreads, tsm, s>>>(a, kh);
+    TO_CUDA(cudaGetLastError());
+    return TO_OK;
+}
+
 template <typename T>
 static int coarse_solve_t(to_problem* P, const void* b, void* x, cudaStream_t s) {
     const int n = P->n_coarse;
@@ -470,7 +699,7 @@ static int coarse_solve_t(to_problem* P, const void* b, void* x, cudaStream_t s)
 
 // x_l = V(l, b_l); the result lands in `x`, `t` is scratch of the same size
 template <typename T>
-static int vcycle_t(to_problem* P, int l, const void* b, void* x, void* t, cudaStream_t s) {
+static int vcycle_t(to_problem* P, int l, const void* b, void* x, void* t, cudaStream_t s, bool first_done = false) {
     const int L = (int)P->lv.size();
     const Level& F = P->lv[l];
     if (l == L - 1) return coarse_solve_t<T>(P, b, x, s);
@@ -480,8 +709,10 @@ static int vcycle_t(to_problem* P, int l, const void* b, void* x, void* t, cudaS
     // choose the first target so that the last sweep writes into x
     void* cur = ((nu1 - 1 + nu2) % 2 == 0) ? x : t;
     void* oth = cur == x ? t : x;
-    k_jacobi_first<T><<<grid1(F.n_dof, P->num_sms), 256, 0, s>>>(F.n_dof, (const T*)b, (const T*)F.d, (T*)cur, (T)om);
-    TO_CUDA(cudaGetLastError());
+    if (!first_done) {
+        k_jacobi_first<T><<<grid1(F.n_dof, P->num_sms), 256, 0, s>>>(F.n_dof, (const T*)b, (const T*)F.d, (T*)cur, (T)om);
+        TO_CUDA(cudaGetLastError());
+    }
     for (int it = 1; it < nu1; ++it) {
         if ((rc = launch_operator(P, l, OP_SMOOTH, cur, oth, b, s, om))) return rc;
         std::swap(cur, oth);
@@ -489,9 +720,17 @@ static int vcycle_t(to_problem* P, int l, const void* b, void* x, void* t, cudaS
     // residual into oth, restrict to the coarse right-hand side
     if ((rc = launch_operator(P, l, OP_BMINUS, cur, oth, b, s))) return rc;
     const Level& C = P->lv[l + 1];
-    k_restrict<T><<<grid3(C.nx + 1, C.ny + 1, C.nz + 1), block3(), 0, s>>>(C.nx, C.ny, C.nz, (const T*)oth, F.mask, C.mask, (T*)C.b);
+    // above the coarsest level the restriction also takes the coarse level's first sweep
+    const bool fuse = l + 1 < L - 1;
+    void* cfirst = ((nu1 - 1 + nu2) % 2 == 0) ? C.x : C.t;
+    k_restrict<T><<<grid3(C.nx + 1, C.ny + 1, C.nz + 1), block3(), 0, s>>>(
+        C.nx, C.ny, C.nz, (const T*)oth, F.mask, C.mask, (T*)C.b, (const T*)C.d, fuse ? (T*)cfirst : nullptr, (T)om);
     TO_CUDA(cudaGetLastError());
-    if ((rc = vcycle_t<T>(P, l + 1, C.b, C.x, C.t, s))) return rc;
+    if (P->mg_tail == l + 1) {
+        if ((rc = tail_t<T>(P, s))) return rc;   // levels l+1 .. L-1 in one CTA
+    } else if ((rc = vcycle_t<T>(P, l + 1, C.b, C.x, C.t, s, fuse))) {
+        return rc;
+    }
     k_prolong_add<T><<<grid3(F.nx + 1, F.ny + 1, F.nz + 1), block3(), 0, s>>>(C.nx, C.ny, C.nz, (const T*)C.x, C.mask, F.mask, (T*)cur);
     TO_CUDA(cudaGetLastError());
     for (int it = 0; it < nu2; ++it) {
@@ -513,7 +752,9 @@ int mg_vcycle(to_problem* P, const void* r, void* z, cudaStream_t s) {
 int mg_launches(const to_problem* P) {
     const int L = (int)P->lv.size();
     const int nu1 = P->prm.mg_nu_pre, nu2 = P->prm.mg_nu_post;
-    return (L - 1) * (1 + (nu1 - 1) + 1 + 1 + 1 + nu2) + 1;
+    if (L == 1) return 1;
+    const int host_levels = P->mg_tail > 0 ? P->mg_tail : L - 1;
+    return 1 + host_levels * ((nu1 - 1) + 1 + 1 + 1 + nu2) + 1;   // + the dense solve or the tail kernel
 }
 
 }  // namespace to

@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "device.cuh"
+#include "haar.cuh"
 
 namespace to {
 
@@ -61,33 +62,6 @@ __device__ __forceinline__ void face_forward(const T* p00, const T* p10, const T
         F[6 + c] = sx1 - sx0;
         F[9 + c] = dx1 - dx0;
     }
-}
-
-// v = K^ u in the sum/difference basis (45 non-zeros, order of kHaarRow/kHaarCol)
-template <typename T>
-__device__ __forceinline__ void haar_apply(const T* __restrict__ k, const T u[24], T v[24]) {
-    v[0] = v[1] = v[2] = T(0);
-    v[3] = k[0] * u[3] + k[1] * u[7] + k[2] * u[14];
-    v[7] = k[3] * u[3] + k[4] * u[7] + k[5] * u[14];
-    v[14] = k[6] * u[3] + k[7] * u[7] + k[8] * u[14];
-    v[4] = k[9] * u[4] + k[10] * u[6];
-    v[6] = k[11] * u[4] + k[12] * u[6];
-    v[5] = k[13] * u[5] + k[14] * u[12];
-    v[12] = k[15] * u[5] + k[16] * u[12];
-    v[8] = k[17] * u[8] + k[18] * u[13];
-    v[13] = k[19] * u[8] + k[20] * u[13];
-    v[9] = k[21] * u[9] + k[22] * u[20];
-    v[20] = k[23] * u[9] + k[24] * u[20];
-    v[10] = k[25] * u[10] + k[26] * u[17];
-    v[17] = k[27] * u[10] + k[28] * u[17];
-    v[15] = k[29] * u[15] + k[30] * u[19];
-    v[19] = k[31] * u[15] + k[32] * u[19];
-    v[11] = k[33] * u[11] + k[34] * u[16] + k[35] * u[18];
-    v[16] = k[36] * u[11] + k[37] * u[16] + k[38] * u[18];
-    v[18] = k[39] * u[11] + k[40] * u[16] + k[41] * u[18];
-    v[21] = k[42] * u[21];
-    v[22] = k[43] * u[22];
-    v[23] = k[44] * u[23];
 }
 
 // ----------------------------------------------------------------------------- pairs
@@ -442,7 +416,7 @@ __device__ __forceinline__ void op_body(const OpArgs<T>& a, const HaarK<T>& kh, 
                         acc0 = fma(rv2, zv, acc0);
                     }
                     acc1 = fma(rv2, rv2, acc1);
-                    accmax = fmax(accmax, fabs(rv2));
+                    accmax = tmax(accmax, tabs(rv2));
                     acc3 = fma(bv, xv, acc3);
                 }
             }
@@ -465,21 +439,21 @@ __device__ __forceinline__ void op_body(const OpArgs<T>& a, const HaarK<T>& kh, 
 
     if (MODE == OP_SMOOTH && a.first_step == 2) {
         // last fine-level sweep of a V-cycle: r^T z with r the cycle's right-hand side
-        double v[1] = {(double)acc0};
+        T v[1] = {acc0};
         const int kind[1] = {0};
         double tot[1];
-        block_reduce<1>(v, kind, sh_red);
-        if (finish_reduction<1>(v, kind, a.red, a.counter, tot, sh_red, bid, nblocks) && tid == 0) {
+        block_reduce<T, 1>(v, kind, reinterpret_cast<T*>(sh_red));
+        if (finish_reduction<T, 1>(v, kind, a.red, a.counter, tot, sh_red, bid, nblocks) && tid == 0) {
             a.sc->rz = tot[0];
             if (!isfinite(tot[0])) set_err(&a.sc->err, TO_ERR_NONFINITE);
         }
     }
     if (MODE == OP_Q) {
-        double v[1] = {(double)acc0};
+        T v[1] = {acc0};
         const int kind[1] = {0};
         double tot[1];
-        block_reduce<1>(v, kind, sh_red);
-        if (finish_reduction<1>(v, kind, a.red, a.counter, tot, sh_red, bid, nblocks) && tid == 0) {
+        block_reduce<T, 1>(v, kind, reinterpret_cast<T*>(sh_red));
+        if (finish_reduction<T, 1>(v, kind, a.red, a.counter, tot, sh_red, bid, nblocks) && tid == 0) {
             DevScalars* sc = a.sc;
             sc->zq = tot[0];
             const double rz = sc->rz;
@@ -493,11 +467,11 @@ __device__ __forceinline__ void op_body(const OpArgs<T>& a, const HaarK<T>& kh, 
             sc->n_inner_done += 1;
         }
     } else if (MODE == OP_RESID) {
-        double v[4] = {(double)acc0, (double)acc1, (double)accmax, (double)acc3};
+        T v[4] = {acc0, acc1, accmax, acc3};
         const int kind[4] = {0, 0, 1, 0};
         double tot[4];
-        block_reduce<4>(v, kind, sh_red);
-        if (finish_reduction<4>(v, kind, a.red, a.counter, tot, sh_red, bid, nblocks) && tid == 0) {
+        block_reduce<T, 4>(v, kind, reinterpret_cast<T*>(sh_red));
+        if (finish_reduction<T, 4>(v, kind, a.red, a.counter, tot, sh_red, bid, nblocks) && tid == 0) {
             DevScalars* sc = a.sc;
             sc->rz = tot[0];
             if (a.first_step) {   // the residual at u_k: tracking error and compliance estimate
@@ -527,6 +501,8 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 ? (MODE == OP_RESID ?
     if (t >= gx * gy * gz) return;
     op_body<T, TX, TY, MODE>(a, kh, t % gx, (t / gx) % gy, t / (gx * gy), (unsigned)t, (unsigned)(gx * gy * gz));
 }
+
+int choose_kchunk(long long columns, int planes, long long slots);
 
 template <typename T>
 static void fill_haar(const to_problem* P, double scale_h, HaarK<T>& kh) {
@@ -566,14 +542,7 @@ static int launch_t(to_problem* P, int level, int mode, const void* x, void* y, 
     const int gx = (L.nx + 1 + TX - 2) / (TX - 1);
     const int gy = (L.ny + 1 + TY - 2) / (TY - 1);
     int kchunk = P->tile_z;
-    if (kchunk <= 0) {
-        // enough CTAs for two per SM, at least 4 planes per walk
-        const long long per_plane = (long long)gx * gy;
-        const long long want = 3LL * P->num_sms;
-        long long gz = (want + per_plane - 1) / per_plane;
-        kchunk = (int)((L.nz + 1 + gz - 1) / gz);
-        if (kchunk < 1) kchunk = 1;
-    }
+    if (kchunk <= 0) kchunk = choose_kchunk((long long)gx * gy, L.nz + 1, (long long)P->op_occ[mode] * P->num_sms);
     if (kchunk > L.nz + 1) kchunk = L.nz + 1;
     a.kchunk = kchunk;
     const int gz = (L.nz + 1 + kchunk - 1) / kchunk;
@@ -594,18 +563,44 @@ static int launch_t(to_problem* P, int level, int mode, const void* x, void* y, 
 }
 
 template <typename T, int TX, int TY>
-static int init_t() {
+static int init_t(to_problem* P) {
     const size_t smem = sizeof(OpSmem<T, TX, TY, kRing>);
     const void* fns[5] = {(const void*)k_operator<T, TX, TY, OP_APPLY>, (const void*)k_operator<T, TX, TY, OP_RESID>,
                           (const void*)k_operator<T, TX, TY, OP_Q>, (const void*)k_operator<T, TX, TY, OP_SMOOTH>,
                           (const void*)k_operator<T, TX, TY, OP_BMINUS>};
-    for (const void* f : fns) TO_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    for (int m = 0; m < 5; ++m) {
+        TO_CUDA(cudaFuncSetAttribute(fns[m], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int occ = 0;
+        TO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fns[m], TX * TY, smem));
+        P->op_occ[m] = occ > 0 ? occ : 1;
+    }
     return TO_OK;
 }
 
-// shared-memory opt-in of the operator kernels (on the problem's device, before any capture)
+// shared-memory opt-in and residency of the operator kernels (on the problem's device, before any capture)
 int operator_init(to_problem* P) {
-    return P->prec == TO_FP64 ? init_t<double, 32, 8>() : init_t<float, 32, 8>();
+    return P->prec == TO_FP64 ? init_t<double, 32, 8>(P) : init_t<float, 32, 8>(P);
+}
+
+// Node planes per CTA tile for one launch: the CTA count is gx * gy * ceil(planes / kchunk)
+// and a CTA walks kchunk + 1 planes (one recomputed halo layer).  With `slots` CTAs
+// resident at once the launch takes about ceil(CTAs / slots) rounds of the longest
+// walk; pick the chunk that minimises rounds x walk (the fewest CTAs on ties).
+int choose_kchunk(long long columns, int planes, long long slots) {
+    long long best_cost = -1, best_ctas = 0;
+    int best = planes;
+    for (int kc = 1; kc <= planes; ++kc) {
+        const long long gz = (planes + kc - 1) / kc;
+        if (kc > 1 && (planes + kc - 2) / (kc - 1) == gz) continue;   // same split as a shorter chunk
+        const long long ctas = columns * gz;
+        const long long cost = ((ctas + slots - 1) / slots) * (kc + 1);
+        if (best_cost < 0 || cost < best_cost || (cost == best_cost && ctas < best_ctas)) {
+            best_cost = cost;
+            best_ctas = ctas;
+            best = kc;
+        }
+    }
+    return best;
 }
 
 // Per CTA tile column of the operator's 32 x 8 tiling: does its node footprint

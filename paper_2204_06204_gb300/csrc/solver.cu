@@ -32,7 +32,10 @@ __global__ void __launch_bounds__(256) k_update_sd(long long n, T* __restrict__ 
                                                    const T* __restrict__ q, const T* __restrict__ d, double* red,
                                                    unsigned* counter, DevScalars* sc) {
     __shared__ double sh[32 * kRedQ];
-    const T beta = (T)sc->beta;
+    __shared__ T s_beta;
+    if (threadIdx.x == 0) s_beta = (T)sc->beta;   // one conversion per block
+    __syncthreads();
+    const T beta = s_beta;
     T acc = T(0);
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const T zi = z[i];
@@ -46,11 +49,11 @@ __global__ void __launch_bounds__(256) k_update_sd(long long n, T* __restrict__ 
         }
     }
     if (JACOBI) {
-        double v[1] = {(double)acc};
+        T v[1] = {acc};
         const int kind[1] = {0};
         double tot[1];
-        block_reduce<1>(v, kind, sh);
-        if (finish_reduction<1>(v, kind, red, counter, tot, sh, linear_block(), grid_blocks()) && threadIdx.x == 0) sc->rz = tot[0];
+        block_reduce<T, 1>(v, kind, reinterpret_cast<T*>(sh));
+        if (finish_reduction<T, 1>(v, kind, red, counter, tot, sh, linear_block(), grid_blocks()) && threadIdx.x == 0) sc->rz = tot[0];
     }
 }
 
@@ -62,11 +65,11 @@ __global__ void __launch_bounds__(256) k_dot_rz(long long n, const T* __restrict
     T acc = T(0);
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         acc += r[i] * z[i];
-    double v[1] = {(double)acc};
+    T v[1] = {acc};
     const int kind[1] = {0};
     double tot[1];
-    block_reduce<1>(v, kind, sh);
-    if (finish_reduction<1>(v, kind, red, counter, tot, sh, linear_block(), grid_blocks()) && threadIdx.x == 0) sc->rz = tot[0];
+    block_reduce<T, 1>(v, kind, reinterpret_cast<T*>(sh));
+    if (finish_reduction<T, 1>(v, kind, red, counter, tot, sh, linear_block(), grid_blocks()) && threadIdx.x == 0) sc->rz = tot[0];
 }
 
 // u += beta z  (Richardson)
