@@ -27,6 +27,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 L2_FLUSH_BYTES = 512 << 20       # > 129 MB L2: written between timed steps
+# DRAM bytes (read + written) of one K(rho)u launch at 128x64x64, FP32, from one ncu capture of the current
+# operator kernel (dram__bytes_read.sum + dram__bytes_write.sum); below the algorithmic bytes because the
+# working set stays in L2.  Set to None whenever the operator kernel changes until it is measured again.
+APPLY_TRAFFIC_128 = 9238528
 
 
 def parse():
@@ -40,6 +44,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-diff", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-mbb", action="store_true", help="skip the 512x256x256 MBB line")
+    ap.add_argument("--quality-steps", type=int, default=200,
+                    help="outer iterations of the FP32-mixed vs FP64 compliance comparison (0: skip)")
     ap.add_argument("--precond", default="auto", choices=["auto", "mg", "jacobi"])
     ap.add_argument("--apply-only", nargs=3, type=int, metavar=("NX", "NY", "NZ"),
                     help="time only K(rho)u on a cantilever of this size (random design), FP32-mixed")
@@ -348,6 +355,60 @@ def main():
                  "apply_gdofs": pb.n_dof / t_apply64 / 1e9, "steps": k64}
         P64.close()
 
+    # --- FP32-mixed vs FP64 plain from the same start: compliance after the same iterations
+    quality = None
+    if not args.no_fp64 and args.quality_steps > 0:
+        nq = args.quality_steps
+        res = {}
+        for name, prec in (("fp32", fb.TO_FP32_MIXED), ("fp64", fb.TO_FP64)):
+            Pq = make(prec)
+            st = Pq.step(nq, want_stats=True)
+            rho_q = Pq.get_state()[0].double().cpu().numpy()
+            res[name] = (st[-1] if isinstance(st[-1], dict) else st[-1].as_dict(), rho_q)
+            Pq.close()
+        J32, J64 = res["fp32"][0]["J"], res["fp64"][0]["J"]
+        quality = {"workload": f"cantilever 128x64x64, {nq} outer iterations from rho = 0.3, u = 0",
+                   "J_fp32": J32, "J_fp64": J64, "J_rel_diff": abs(J32 - J64) / abs(J64),
+                   "mean_abs_drho": float(np.mean(np.abs(res["fp32"][1] - res["fp64"][1]))),
+                   "volume_fp32": res["fp32"][0]["volume"], "volume_fp64": res["fp64"][0]["volume"]}
+
+    # --- large single problem: MBB half model 512x256x256 (101.6M DOFs), filter radius 2.5, MG, FP32-mixed
+    mbb = None
+    if not args.no_mbb:
+        pbm = W.mbb_512x256x256()
+        prm_m = fb.to_default_params(precision=fb.TO_FP32_MIXED, precond=fb.TO_PRECOND_MG, n_inner=2)
+        Pm = fb.Problem.from_workload(pbm, prm_m, device=local)
+        Pm.step(2, want_stats=False)
+        torch.cuda.synchronize()
+        km = 5
+        evm = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(km)]
+        for a, b in evm:
+            a.record(stream)
+            Pm.step(1, want_stats=False)
+            b.record(stream)
+        torch.cuda.synchronize()
+        Pm.check()
+        tm = sum(a.elapsed_time(b) for a, b in evm) / 1000.0
+        um = Pm.get_state()[1]
+        ym = Pm.dof()
+        for _ in range(3):
+            Pm.apply_K(um, ym)
+        a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a_.record(stream)
+        for _ in range(10):
+            Pm.apply_K(um, ym)
+        b_.record(stream)
+        torch.cuda.synchronize()
+        tam = a_.elapsed_time(b_) / 1000.0 / 10
+        bytes_m = 2 * 3 * pbm.n_node * 4 + pbm.n_elem * 4 + pbm.n_node
+        mbb = {"workload": "MBB half model 512x256x256 (101,649,411 DOFs), volfrac 0.15, r = 2.5, FP32-mixed, "
+                           "MG-preconditioned steepest descent x2 (inputs far larger than L2)",
+               "outer_iters_per_s": km / tm, "ms_per_iter": tm * 1e3 / km,
+               "apply_K_us": tam * 1e6, "apply_gdofs": pbm.n_dof / tam / 1e9,
+               "apply_GBs": bytes_m / tam / 1e9, "apply_frac_of_hbm": bytes_m / tam / 1e9 / hbm}
+        Pm.close()
+        del um, ym
+
     # max over ranks
     if dist:
         tt = torch.tensor([t32], device=dev, dtype=torch.float64)
@@ -388,10 +449,12 @@ def main():
                     "fp64_us": res64["apply_ms"] * 1e3 if res64 else None},
         "fp64_plain": res64,
         "fp32_over_fp64_iters": (ips32 / res64["outer_iters_per_s"]) if res64 else None,
+        "fp32_vs_fp64_quality": quality,
         "differentiable_compliance": diff,
         "batched": batch,
+        "mbb_large": mbb,
         "roofline": {"kernel": "k_operator (K(rho)u, FP32)", "bound": "hbm", "achieved": ach, "peak": hbm,
-                     "unit": "GB/s", "frac": ach / hbm, "traffic": None,
+                     "unit": "GB/s", "frac": ach / hbm, "traffic": APPLY_TRAFFIC_128,
                      "algorithmic_bytes": apply_bytes(s_el),
                      "peak_source": "MEASURED_PEAKS.json hbm_gbs" if pk else "fallback 6800"},
         "e2e": {"value": ke / t_e2e, "unit": "outer_iters/s", "h2d_bytes_per_step": pb.n_elem * 4,
