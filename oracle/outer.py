@@ -57,7 +57,7 @@ class Setup:
 
 def run(pb, n_outer, precond="jacobi", n_inner=5, inner_mode="sd", beta=0.5,
         alpha0=None, alpha_scale=0.2, m=0.75, mean_proj=False,
-        mg_levels=None, mg_omega=0.5, nu1=2, nu2=2, setup=None, rho=None, u=None, k0=1):
+        mg_levels=None, mg_omega=0.5, nu1=2, nu2=2, setup=None, rho=None, u=None, k0=1, krylov_dim=20):
     """Run ``n_outer`` outer iterations; returns (rho, u, history, alpha0)."""
     S = setup or Setup(pb)
     rho = pb.rho0.copy() if rho is None else rho.copy()
@@ -83,6 +83,8 @@ def run(pb, n_outer, precond="jacobi", n_inner=5, inner_mode="sd", beta=0.5,
                 Minv = mg
             elif precond == "none":
                 Minv = lambda r: r
+            elif precond == "krylov":   # Eq. (LSP); with inner_mode "richardson", beta = 1: CPFBTO
+                Minv = lambda r: solve.krylov_apply(A, r, krylov_dim)
             else:
                 raise ValueError(precond)
             if inner_mode == "sd":

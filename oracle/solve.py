@@ -7,6 +7,11 @@
   beta = r^T z / z^T K z, the minimiser of P_f on that line.
 * ``inner_richardson`` -- the literal constant-beta step of Algorithms 1 / 3,
   u <- u - beta M^-1 (K u - f).
+* ``krylov_apply``     -- the Krylov preconditioner of Eq. (LSP) (Sec. IV-C):
+  M^-1 b = sum_{i=0}^{D} c_i K^i b, with c minimising ||b - sum_{i=1}^{D+1}
+  c_{i-1} K^i b||, on an orthonormal Arnoldi basis of that Krylov space
+  (``krylov_apply_power``: the paper's Householder QR of the power basis).
+  With beta = 1 in ``inner_richardson`` this is Algorithm CPFBTO.
 * ``solve_exact``      -- K^-1 f for the nested exact method (PGD, Sec. V):
   dense Cholesky when small, sparse LU otherwise.
 * ``Multigrid``        -- a geometric-multigrid V-cycle used as M^-1.  The paper
@@ -56,6 +61,61 @@ def inner_richardson(A, f: np.ndarray, u: np.ndarray, Minv, n: int, beta: float)
             r0 = r.copy()
         u = u + beta * Minv(r)
     return u, r0
+
+
+def krylov_apply(A, b: np.ndarray, D: int) -> np.ndarray:
+    """M^-1 b of Eq. (LSP) (Sec. IV-C) for the operator ``A`` (a callable).
+
+    Eq. (LSP) defines M^-1 b = sum_{i=0}^{D} c_i K^i b with c the minimiser of
+    ||b - sum_{i=1}^{D+1} c_{i-1} K^i b||: the vector x of the Krylov space
+    span{b, K b, ..., K^D b} whose K x is closest to b.  That space is spanned
+    here by an orthonormal basis q_0 .. q_D built by the Arnoldi process
+    (modified Gram-Schmidt; K q_j = sum_{i<=j+1} H_ij q_i), so that
+    ||b - K Q y|| = || ||b|| e_1 - H y || and the minimiser is the small
+    least-squares solution y.  (The paper solves the same least-squares problem
+    on the power basis b, K b, ... with a Householder QR; in double precision
+    that basis loses rank beyond D of about 8 on these problems, see
+    ``krylov_apply_power``.)
+    """
+    beta0 = float(np.linalg.norm(b))
+    if beta0 == 0.0:
+        return np.zeros_like(b)
+    Q = [b / beta0]
+    H = np.zeros((D + 2, D + 1))
+    m = D + 1
+    for j in range(D + 1):
+        w = A(Q[j])
+        for i in range(j + 1):
+            H[i, j] = float(Q[i] @ w)
+            w = w - H[i, j] * Q[i]
+        H[j + 1, j] = float(np.linalg.norm(w))
+        if H[j + 1, j] <= 1e-14 * beta0:     # the space is invariant: K^-1 b lies in it
+            m = j + 1
+            break
+        Q.append(w / H[j + 1, j])
+    e1 = np.zeros(m + 1)
+    e1[0] = beta0
+    y = np.linalg.lstsq(H[:m + 1, :m], e1, rcond=None)[0]
+    return np.stack(Q[:m], axis=1) @ y
+
+
+def krylov_apply_power(A, b: np.ndarray, D: int) -> np.ndarray:
+    """The same least-squares problem as ``krylov_apply`` posed on the power basis,
+    as the paper does: s_0 = b, s_i = K s_{i-1} / ||K s_{i-1}|| (normalising changes
+    neither the span nor the minimiser), min_c ||b - [K s_0 ... K s_D] c|| by a
+    Householder QR (numpy.linalg.qr: LAPACK geqrf), M^-1 b = [s_0 ... s_D] c.
+    Agrees with ``krylov_apply`` while the power basis keeps full numerical rank."""
+    S = [b.copy()]
+    KS = []
+    for i in range(D + 1):
+        w = A(S[i])
+        KS.append(w)
+        if i < D:
+            nw = float(np.linalg.norm(w))
+            S.append(w / nw if nw > 0.0 else np.zeros_like(w))
+    Q, R = np.linalg.qr(np.stack(KS, axis=1))
+    c = np.linalg.lstsq(R, Q.T @ b, rcond=None)[0]
+    return np.stack(S, axis=1) @ c
 
 
 def solve_exact(K: sp.spmatrix, f: np.ndarray) -> np.ndarray:

@@ -117,3 +117,73 @@ def test_truncated_gradient_tends_to_exact_sensitivity():
     JT, gT = adjoint.gradient(S, pb.rho0, 10000, 0.5)
     assert abs(JT - J) < 1e-8 * J
     assert np.abs(gT - g_exact).max() < 1e-9 * np.abs(g_exact).max()
+
+
+# ----------------------------------------------------------------------------- Krylov preconditioner, Eq. (LSP)
+def test_krylov_preconditioner_is_the_gmres_minimal_residual_vector():
+    """Eq. (LSP) minimises ||b - K x|| over x in span{b, ..., K^D b}: the vector one
+    restart cycle of GMRES(D + 1) from x = 0 returns (scipy's implementation)."""
+    import scipy.sparse.linalg as spla
+    pb, S, Ee = _setup(rho=lambda n: W.random_rho(n))
+    K = S.K(Ee).tocsr()
+    b = W.random_u(pb.n_dof)
+    for D in (0, 1, 4, 20):
+        x = solve.krylov_apply(lambda v: K @ v, b, D)
+        xg, _ = spla.gmres(K, b, x0=np.zeros_like(b), rtol=1e-300, atol=0.0, restart=D + 1, maxiter=1)
+        assert np.linalg.norm(x - xg) <= 1e-6 * np.linalg.norm(xg)
+        rx, rg = np.linalg.norm(b - K @ x), np.linalg.norm(b - K @ xg)
+        assert abs(rx - rg) <= 1e-10 * np.linalg.norm(b)
+
+
+def test_krylov_preconditioner_power_basis_agrees_for_small_D():
+    """The paper's Householder QR of the power basis solves the same problem."""
+    pb, S, Ee = _setup(rho=lambda n: W.random_rho(n))
+    K = S.K(Ee)
+    b = W.random_u(pb.n_dof)
+    for D in (0, 1, 2, 4):
+        x = solve.krylov_apply(lambda v: K @ v, b, D)
+        xp = solve.krylov_apply_power(lambda v: K @ v, b, D)
+        assert np.linalg.norm(x - xp) <= 1e-9 * np.linalg.norm(x)
+
+
+def test_krylov_residual_never_grows_with_D():
+    """Nested Krylov spaces: the minimal residual is non-increasing in D."""
+    pb, S, Ee = _setup(rho=lambda n: W.random_rho(n))
+    K = S.K(Ee)
+    b = W.random_u(pb.n_dof)
+    last = np.linalg.norm(b)
+    for D in range(0, 21):
+        res = np.linalg.norm(b - K @ solve.krylov_apply(lambda v: K @ v, b, D))
+        assert res <= last * (1 + 1e-10)
+        last = res
+
+
+def test_krylov_preconditioner_is_the_exact_inverse_on_a_complete_space():
+    """One element (24 DOFs, 12 fixed): the Krylov space of dimension 24 holds K^-1 b."""
+    pb = W.cantilever(1, 1, 1)
+    S = outer.Setup(pb)
+    _, Ee, _ = S.moduli(np.full(1, 0.7))
+    K = S.K(Ee).toarray()
+    b = W.random_u(pb.n_dof)
+    x = solve.krylov_apply(lambda v: K @ v, b, 23)
+    assert np.linalg.norm(x - np.linalg.solve(K, b)) <= 1e-8 * np.linalg.norm(np.linalg.solve(K, b))
+
+
+def test_cpfbto_step_contracts_the_tracking_error():
+    """Eq. (contractXi): with the Krylov preconditioner and beta = 1,
+    ||K(v_k) u_{k+1} - f|| < ||K(v_k) u_k - f|| at every outer iteration
+    (Algorithm CPFBTO, line 1)."""
+    pb = W.cantilever(16, 8, 8)
+    S = outer.Setup(pb)
+    rho, u = pb.rho0.copy(), np.zeros(pb.n_dof)
+    a0 = None
+    for k in range(1, 9):
+        _, Ee, _ = S.moduli(rho)
+        K = S.K(Ee)
+        before = np.linalg.norm(K @ u - S.f)
+        u_next, _ = solve.inner_richardson(lambda v: K @ v, S.f, u, lambda r: solve.krylov_apply(lambda v: K @ v, r, 20), 1, 1.0)
+        after = np.linalg.norm(K @ u_next - S.f)
+        assert after < before
+        rho, _, _, a0 = outer.run(pb, 1, precond="krylov", n_inner=1, inner_mode="richardson", beta=1.0,
+                                  krylov_dim=20, setup=S, rho=rho, u=u, k0=k, alpha0=a0)
+        u = u_next
