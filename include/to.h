@@ -64,7 +64,7 @@ enum {
 };
 
 enum { TO_FP64 = 0, TO_FP32_MIXED = 1 };
-enum { TO_PRECOND_JACOBI = 0, TO_PRECOND_MG = 1, TO_PRECOND_NONE = 2 };
+enum { TO_PRECOND_JACOBI = 0, TO_PRECOND_MG = 1, TO_PRECOND_NONE = 2, TO_PRECOND_KRYLOV = 3 };
 enum { TO_INNER_SD = 0, TO_INNER_RICHARDSON = 1 };
 
 typedef struct to_problem to_problem;      /* opaque */
@@ -101,7 +101,11 @@ typedef struct {
 
 /* Solver parameters.
  *   precision   TO_FP64 | TO_FP32_MIXED
- *   precond     M of the lower-level step: Jacobi diagonal, multigrid V-cycle, or none
+ *   precond     M of the lower-level step: Jacobi diagonal, multigrid V-cycle, none,
+ *               or the Krylov preconditioner of Eq. (LSP) (Sec. IV-C): M^-1 b is the
+ *               vector of span{b, K b, ..., K^D b} whose K-image is closest to b;
+ *               with inner_mode TO_INNER_RICHARDSON and beta = 1 this is
+ *               Algorithm CPFBTO
  *   inner_mode  TO_INNER_SD: steepest descent with the exact line search
  *               beta = r^T z / z^T K z; TO_INNER_RICHARDSON: constant beta
  *               (the literal step of Algorithms 1 / 3)
@@ -115,13 +119,16 @@ typedef struct {
  *               mg_omega damped-Jacobi weight
  *   tile_x, tile_y, tile_z   0 = automatic tile choice for the operator kernel
  *   no_graph    0: to_step replays one captured CUDA graph per outer iteration;
- *               1: to_step launches the kernels one by one */
+ *               1: to_step launches the kernels one by one
+ *   krylov_dim  D of Eq. (LSP), 0 <= D <= 30 (the paper uses 20); it costs D + 1
+ *               operator applications and (D + 2) vectors of n_dof per application */
 typedef struct {
     int32_t precision, precond, inner_mode, n_inner;
     double beta, alpha0, alpha_scale, m;
     int32_t mean_proj, mg_levels, mg_nu_pre, mg_nu_post;
     double mg_omega;
     int32_t tile_x, tile_y, tile_z, no_graph;
+    int32_t krylov_dim, reserved;
 } to_params;
 
 /* Per-outer-iteration record (host copy). */

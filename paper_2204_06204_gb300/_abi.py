@@ -9,7 +9,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libfbto.so")
 
 TO_OK, TO_ERR_ARG, TO_ERR_CUDA, TO_ERR_NONFINITE, TO_ERR_INFEASIBLE, TO_ERR_TIMEOUT, TO_ERR_SINGULAR, TO_ERR_STATE = range(8)
 TO_FP64, TO_FP32_MIXED = 0, 1
-TO_PRECOND_JACOBI, TO_PRECOND_MG, TO_PRECOND_NONE = 0, 1, 2
+TO_PRECOND_JACOBI, TO_PRECOND_MG, TO_PRECOND_NONE, TO_PRECOND_KRYLOV = 0, 1, 2, 3
 TO_INNER_SD, TO_INNER_RICHARDSON = 0, 1
 
 ERROR_NAMES = {0: "TO_OK", 1: "TO_ERR_ARG", 2: "TO_ERR_CUDA", 3: "TO_ERR_NONFINITE", 4: "TO_ERR_INFEASIBLE",
@@ -37,7 +37,8 @@ class to_params(C.Structure):
                 ("beta", C.c_double), ("alpha0", C.c_double), ("alpha_scale", C.c_double), ("m", C.c_double),
                 ("mean_proj", C.c_int32), ("mg_levels", C.c_int32), ("mg_nu_pre", C.c_int32), ("mg_nu_post", C.c_int32),
                 ("mg_omega", C.c_double),
-                ("tile_x", C.c_int32), ("tile_y", C.c_int32), ("tile_z", C.c_int32), ("no_graph", C.c_int32)]
+                ("tile_x", C.c_int32), ("tile_y", C.c_int32), ("tile_z", C.c_int32), ("no_graph", C.c_int32),
+                ("krylov_dim", C.c_int32), ("reserved", C.c_int32)]
 
 
 class to_stats(C.Structure):

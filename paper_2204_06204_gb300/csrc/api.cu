@@ -74,6 +74,7 @@ extern "C" void to_default_params(to_params* o) {
     o->mg_nu_pre = 2;
     o->mg_nu_post = 2;
     o->mg_omega = 0.5;
+    o->krylov_dim = 20;
 }
 
 static int validate(const to_grid* g, const to_material* m, const to_loads* L, const to_bcs* B, const to_params* p) {
@@ -91,7 +92,9 @@ static int validate(const to_grid* g, const to_material* m, const to_loads* L, c
     if (L->n < 0 || (L->n > 0 && (!L->dof || !L->val))) return fail(TO_ERR_ARG, "bad load list");
     if (B->n < 0 || (B->n > 0 && !B->dof)) return fail(TO_ERR_ARG, "bad fixture list");
     if (p->precision != TO_FP64 && p->precision != TO_FP32_MIXED) return fail(TO_ERR_ARG, "bad precision");
-    if (p->precond < 0 || p->precond > 2) return fail(TO_ERR_ARG, "bad preconditioner");
+    if (p->precond < 0 || p->precond > 3) return fail(TO_ERR_ARG, "bad preconditioner");
+    if (p->precond == TO_PRECOND_KRYLOV && (p->krylov_dim < 0 || p->krylov_dim > 30))
+        return fail(TO_ERR_ARG, "krylov_dim must lie in [0, 30]");
     if (p->inner_mode != TO_INNER_SD && p->inner_mode != TO_INNER_RICHARDSON) return fail(TO_ERR_ARG, "bad inner mode");
     if (p->n_inner < 0) return fail(TO_ERR_ARG, "n_inner must be >= 0");
     if (!(p->m >= 0.0)) return fail(TO_ERR_ARG, "alpha exponent m must be >= 0");
@@ -134,6 +137,9 @@ extern "C" void to_destroy(to_problem* P) {
     if (P->gstream) cudaStreamDestroy(P->gstream);
     void* p;
     p = P->ke_dev; dfree(p);
+    p = P->kry_q; dfree(p);
+    p = P->kry_s; dfree(p);
+    p = P->kry_part; dfree(p);
     p = P->sc; dfree(p);
     p = P->red; dfree(p);
     p = P->counters; dfree(p);
@@ -279,6 +285,10 @@ extern "C" int to_create(const to_grid* g, const to_material* m, const to_loads*
     }
     if ((rc = fill_scalar(P, P->rho, P->n_elem, m->volfrac > m->rho_max ? m->rho_max : m->volfrac, s)) ||
         (rc = launch_rowsum(P, s))) {
+        cudaStreamDestroy(s);
+        return bail(rc);
+    }
+    if (prm->precond == TO_PRECOND_KRYLOV && (rc = krylov_build(P))) {
         cudaStreamDestroy(s);
         return bail(rc);
     }

@@ -128,6 +128,14 @@ struct to_problem {
     void* coarse_L = nullptr;      // scaled inverse (T), n_c x n_c, then the n_c scale factors
     int n_coarse = 0;
     int mg_tail = 0;               // first level of the one-CTA coarse tail (0: none)
+
+    // Krylov preconditioner (Eq. LSP): basis of D + 2 columns (leading dimension kry_ld),
+    // device coefficients, per-block partials of its streaming passes
+    void* kry_q = nullptr;
+    void* kry_s = nullptr;
+    double* kry_part = nullptr;
+    long long kry_ld = 0;
+    int kry_blocks = 0;
     double* ke_dev = nullptr;      // 24x24 unit element matrix (device, double)
 
     // device scalars, reductions, stats
@@ -135,7 +143,7 @@ struct to_problem {
     double* red = nullptr;         // kMaxRedBlocks * kRedQ doubles
     // completion counters / barrier words (64): [0] residual, [1] z^T q, [2] filter^T statistics,
     // [4] update, [5] r^T z, [6] smoother r^T z, [7] f^T u, [8..9] grid barrier,
-    // [10..11] projection first / final pass
+    // [10..11] projection first / final pass, [12] Krylov passes
     unsigned* counters = nullptr;
     to_stats* dstats = nullptr;    // device stats ring
     int dstats_cap = 0;
@@ -188,6 +196,8 @@ int launch_record(to_problem* P, cudaStream_t s);
 int operator_init(to_problem* P);
 int build_tile_mask(Level& L, const uint8_t* mask_host);
 int project_cluster_setup(to_problem* P);
+int krylov_build(to_problem* P);
+int krylov_apply(to_problem* P, const void* b, void* x, cudaStream_t s);
 int launch_richardson(to_problem* P, cudaStream_t s);
 
 // multigrid

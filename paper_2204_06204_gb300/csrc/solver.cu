@@ -134,6 +134,9 @@ static int precond_t(to_problem* P, cudaStream_t s) {
         int rc = mg_vcycle(P, P->r, P->z, s);
         if (rc) return rc;
         if (P->prm.mg_nu_post > 0 && P->lv.size() > 1) return TO_OK;   // r^T z fused into the last sweep
+    } else if (P->prm.precond == TO_PRECOND_KRYLOV) {
+        int rc = krylov_apply(P, P->r, P->z, s);
+        if (rc) return rc;
     } else if (P->prm.precond == TO_PRECOND_NONE) {
         TO_CUDA(cudaMemcpyAsync(P->z, P->r, P->n_dof * sizeof(T), cudaMemcpyDeviceToDevice, s));
     } else {
