@@ -89,7 +89,9 @@ def krylov_apply(A, b: np.ndarray, D: int) -> np.ndarray:
             H[i, j] = float(Q[i] @ w)
             w = w - H[i, j] * Q[i]
         H[j + 1, j] = float(np.linalg.norm(w))
-        if H[j + 1, j] <= 1e-14 * beta0:     # the space is invariant: K^-1 b lies in it
+        # the space is invariant (K^-1 b lies in it) when the new direction vanishes
+        # relative to ||K q_j|| = ||H[0..j+1, j]||
+        if H[j + 1, j] <= 1e-12 * float(np.linalg.norm(H[:j + 2, j])):
             m = j + 1
             break
         Q.append(w / H[j + 1, j])

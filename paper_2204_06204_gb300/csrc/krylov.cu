@@ -12,10 +12,11 @@
 // Householder QR; the power basis loses rank in floating point well before
 // D = 20 on these problems, the Arnoldi basis does not.)
 //
-// Per basis vector j: w = K q_j (the operator kernel), then three streaming
-// passes over the basis: h = Q^T w; w -= Q h with the second Gram-Schmidt dots
+// Per basis vector j: w = K q_j (the operator kernel, on the still unnormalised
+// q_j), then three streaming passes over the basis: q_j and w scaled by the
+// previous column's norm, h = Q^T w; w -= Q h with the second Gram-Schmidt dots
 // fused in (h' = Q^T w, element by element on the updated w); w -= Q h' with
-// ||w||^2 fused in; then q_{j+1} = w / ||w||.  Dots: float products, float
+// ||w||^2 fused in.  Dots: float products, float
 // block trees, float-pair cross-block sums on the mixed path (double on the
 // FP64 path), delivered as doubles; the coefficients are double.
 #include <cmath>
@@ -43,63 +44,90 @@ struct KrylovScalars {
 constexpr int kHld = kKryMax + 2;
 
 // ----------------------------------------------------------------------------- streaming passes
-// MODE 0: out = Q^T w (the first m basis vectors)
-// MODE 1: w -= Q h_in, then out = Q^T w (fused second Gram-Schmidt dots)
-// MODE 2: w -= Q h_in, then out[0] = w^T w
-// MODE 3: out[0] = w^T w
-// Partials of each block (one per output) are combined by the last block; `add` adds the
-// totals to `dst` (dst[i] += t_i) instead of storing them.
+// One kernel, four passes over the basis (columns of Q, leading dimension ld):
+//   MODE 3 (start): beta0 = ||b||; one basis vector, H cleared.
+//   MODE 0 (column j, first Gram-Schmidt pass): the column's candidate q_j (b for j = 0)
+//          and w = K q_j are scaled by 1/sigma (sigma = beta0, or H[j, j-1]: the previous
+//          column left q_j and its image unnormalised), then h = Q^T w -> H[0..j, j].
+//   MODE 1 (second pass): w -= Q H[., j], then h' = Q^T w; H[., j] += h'.
+//   MODE 2 (norm): w -= Q h', then H[j+1, j] = ||w||; w stays unnormalised in column j+1.
+// Each thread loads the basis values of an element once (all loads in flight together);
+// the last block to finish folds the per-block partials and does the column's bookkeeping.
 template <typename T, int MODE>
-__global__ void __launch_bounds__(kKryThreads) k_kry_pass(const T* __restrict__ Q, long long n, long long ld, T* w,
-                                                          const double* h_in, double* part, unsigned* counter,
-                                                          double* dst, int add, KrylovScalars* ks) {
+__global__ void __launch_bounds__(kKryThreads) k_kry_pass(T* Q, long long n, long long ld, int j, const T* b,
+                                                          double* part, unsigned* counter, KrylovScalars* ks, int m_full) {
     __shared__ T s_h[kKryMax + 1];
     __shared__ T sh[32 * (kKryMax + 1)];
-    __shared__ int s_m, s_last;
+    __shared__ T s_inv;
+    __shared__ int s_skip, s_last;
     const int tid = threadIdx.x;
-    if (tid == 0) s_m = MODE == 3 ? 1 : (ks->breakdown ? 0 : ks->m);
-    __syncthreads();
-    const int m = s_m;
-    if (m == 0) return;   // every block reads the same flag: all leave together
-    if (MODE == 1 || MODE == 2) {
-        if (tid < m) s_h[tid] = (T)h_in[tid];
-        __syncthreads();
+    constexpr int NQ = kKryMax + 1;
+    const int m = MODE == 3 ? 0 : j + 1;   // basis vectors q_0 .. q_j
+    if (tid == 0) {
+        s_skip = MODE == 3 ? 0 : ks->breakdown;
+        if (MODE == 0) {
+            const double sg = j == 0 ? ks->beta0 : ks->H[j + kHld * (j - 1)];
+            s_inv = sg > 0.0 ? (T)(1.0 / sg) : T(0);
+        }
     }
-    constexpr int NQ = (MODE == 0 || MODE == 1) ? kKryMax + 1 : 1;
+    if (MODE == 1 && tid <= j) s_h[tid] = (T)ks->H[tid + kHld * j];
+    if (MODE == 2 && tid <= j) s_h[tid] = (T)ks->h[tid];
+    __syncthreads();
+    if (s_skip) return;   // every block reads the same flag: all leave together
+    T* w = Q + (size_t)(j + 1) * ld;
     T acc[NQ];
 #pragma unroll
     for (int i = 0; i < NQ; ++i) acc[i] = T(0);
     for (long long e = (long long)blockIdx.x * blockDim.x + tid; e < n; e += (long long)gridDim.x * blockDim.x) {
-        T we = w[e];
-        if (MODE == 1 || MODE == 2) {
+        if constexpr (MODE == 3) {
+            const T x = b[e];
+            acc[0] = fma(x, x, acc[0]);
+        } else {
+        T qv[NQ];
 #pragma unroll
-            for (int i = 0; i < kKryMax + 1; ++i)
-                if (i < m) we -= s_h[i] * Q[i * ld + e];
+        for (int i = 0; i < NQ; ++i) qv[i] = (i < m) ? Q[i * ld + e] : T(0);   // predicated, independent loads
+        T we = w[e];
+        if (MODE == 0) {
+            const T inv = s_inv;
+            T qraw = j == 0 ? b[e] : T(0);
+#pragma unroll
+            for (int i = 1; i < NQ; ++i)
+                if (i == j) qraw = qv[i];   // compile-time register index: no local memory
+            const T qj = qraw * inv;
+            Q[(size_t)j * ld + e] = qj;
+#pragma unroll
+            for (int i = 0; i < NQ; ++i)
+                if (i == j) qv[i] = qj;
+            we *= inv;
+            w[e] = we;
+        } else {
+#pragma unroll
+            for (int i = 0; i < NQ; ++i) we = fma(-s_h[i < m ? i : 0], qv[i], we);   // qv = 0 beyond m
             w[e] = we;
         }
         if (MODE == 0 || MODE == 1) {
 #pragma unroll
-            for (int i = 0; i < NQ; ++i)
-                if (i < m) acc[i] = fma(Q[i * ld + e], we, acc[i]);
+            for (int i = 0; i < NQ; ++i) acc[i] = fma(qv[i], we, acc[i]);
         } else {
             acc[0] = fma(we, we, acc[0]);
         }
+        }
     }
     const int nq = (MODE == 0 || MODE == 1) ? m : 1;
-    // block totals: a shuffle tree per warp, then one over the warps (fixed order)
+    // block totals: a shuffle tree per warp, then the warps in order
     const int lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
 #pragma unroll
     for (int i = 0; i < NQ; ++i)
         if (i < nq) {
             const T v = warp_sum(acc[i]);
-            if (lane == 0) sh[wid * (kKryMax + 1) + i] = v;
+            if (lane == 0) sh[wid * NQ + i] = v;
         }
     __syncthreads();
     if (tid < nq) {
         T t = T(0);
-        for (int q = 0; q < nw; ++q) t += sh[q * (kKryMax + 1) + tid];
-        if (sizeof(T) == 4) reinterpret_cast<float2*>(part)[(size_t)blockIdx.x * (kKryMax + 1) + tid] = make_float2((float)t, 0.f);
-        else part[(size_t)blockIdx.x * (kKryMax + 1) + tid] = (double)t;
+        for (int q = 0; q < nw; ++q) t += sh[q * NQ + tid];
+        if (sizeof(T) == 4) reinterpret_cast<float2*>(part)[(size_t)blockIdx.x * NQ + tid] = make_float2((float)t, 0.f);
+        else part[(size_t)blockIdx.x * NQ + tid] = (double)t;
     }
     __threadfence();
     __syncthreads();
@@ -111,10 +139,11 @@ __global__ void __launch_bounds__(kKryThreads) k_kry_pass(const T* __restrict__ 
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    // the last block: output i is folded by threads i, i + 32, ... over block chunks, then
-    // the chunks in order (fixed pattern)
-    __shared__ double s_chunk[16][kKryMax + 1];
-    const int i = tid & 31, c = tid >> 5;   // up to 16 chunks of the blocks
+    // the last block: output i folded by threads i, i + 32, ... over chunks of the blocks
+    // (loads batched), then the chunks in order
+    __shared__ double s_chunk[16][NQ];
+    __shared__ double s_tot[NQ];
+    const int i = tid & 31, c = tid >> 5;
     const int nchunk = blockDim.x >> 5;
     if (i < nq) {
         FF accf{0.f, 0.f};
@@ -124,12 +153,12 @@ __global__ void __launch_bounds__(kKryThreads) k_kry_pass(const T* __restrict__ 
             double td[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                const unsigned b = b0 + u * nchunk;
+                const unsigned bb = b0 + u * nchunk;
                 if (sizeof(T) == 4)
-                    tf[u] = b < gridDim.x ? __ldcg(reinterpret_cast<const float2*>(part) + (size_t)b * (kKryMax + 1) + i)
-                                          : make_float2(0.f, 0.f);
+                    tf[u] = bb < gridDim.x ? __ldcg(reinterpret_cast<const float2*>(part) + (size_t)bb * NQ + i)
+                                           : make_float2(0.f, 0.f);
                 else
-                    td[u] = b < gridDim.x ? __ldcg(part + (size_t)b * (kKryMax + 1) + i) : 0.0;
+                    td[u] = bb < gridDim.x ? __ldcg(part + (size_t)bb * NQ + i) : 0.0;
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
@@ -143,98 +172,79 @@ __global__ void __launch_bounds__(kKryThreads) k_kry_pass(const T* __restrict__ 
     if (tid < nq) {
         double t = 0.0;
         for (int q = 0; q < nchunk; ++q) t += s_chunk[q][tid];
-        if (add) dst[tid] += t;
-        else dst[tid] = t;
-    }
-}
-
-// beta0 = ||b||, q_0 = b / beta0 (the first column) -- the scale step of any column:
-// q_{j+1} = w / H[j+1, j]; a vanishing norm marks the space invariant
-template <typename T>
-__global__ void __launch_bounds__(256) k_kry_scale(const T* w, T* q, long long n, KrylovScalars* ks, int j) {
-    __shared__ T s_inv;
-    __shared__ int s_skip;
-    if (threadIdx.x == 0) {
-        double nrm;
-        if (j < 0) {
-            nrm = ks->beta0;
-        } else {
-            nrm = ks->H[(j + 1) + kHld * j];
-        }
-        const bool dead = ks->breakdown || !(nrm > 1e-30 * (ks->beta0 > 0.0 ? ks->beta0 : 1.0));
-        s_skip = dead;
-        s_inv = dead ? T(0) : (T)(1.0 / nrm);
+        s_tot[tid] = t;
     }
     __syncthreads();
-    if (s_skip) return;
-    const T inv = s_inv;
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
-        q[e] = w[e] * inv;
-}
-
-// one thread: bookkeeping between the passes of column j
-//   stage 0: beta0 = sqrt(w2) at the start of an application; one basis vector
-//   stage 1: H[0..j, j] = h (first Gram-Schmidt pass)
-//   stage 3: H[0..j, j] += h (second pass)
-//   stage 2: H[j+1, j] = sqrt(w2); the space is invariant when it vanishes relative
-//            to the column, else one more basis vector is in use
-__global__ void k_kry_book(KrylovScalars* ks, int j, int stage, int m_full) {
-    if (stage == 0) {
-        const double b2 = ks->w2;
+    if (tid != 0) return;
+    // the column's bookkeeping (one thread)
+    if (MODE == 3) {
+        const double b2 = s_tot[0];
         ks->beta0 = b2 > 0.0 ? sqrt(b2) : 0.0;
         ks->breakdown = !(ks->beta0 > 0.0);
-        ks->m = 1;
+        ks->m = ks->breakdown ? 0 : 1;
         for (int q = 0; q < kHld * (kKryMax + 1); ++q) ks->H[q] = 0.0;
-        return;
-    }
-    if (ks->breakdown) return;
-    if (stage == 1 || stage == 3) {
-        for (int i = 0; i <= j; ++i) ks->H[i + kHld * j] = (stage == 1 ? 0.0 : ks->H[i + kHld * j]) + ks->h[i];
-        return;
-    }
-    double colmax = 0.0;
-    for (int i = 0; i <= j; ++i) colmax = fmax(colmax, fabs(ks->H[i + kHld * j]));
-    const double w2 = ks->w2;
-    const double hn = w2 > 0.0 ? sqrt(w2) : 0.0;
-    ks->H[(j + 1) + kHld * j] = hn;
-    if (!(hn > 1e-12 * colmax)) {
-        ks->breakdown = 1;        // K q_j lies in the span of q_0 .. q_j: the space is complete
-        ks->m = j + 1;
+    } else if (MODE == 0) {
+        for (int q = 0; q <= j; ++q) ks->H[q + kHld * j] = s_tot[q];
+    } else if (MODE == 1) {
+        for (int q = 0; q <= j; ++q) {
+            ks->h[q] = s_tot[q];
+            ks->H[q + kHld * j] += s_tot[q];
+        }
     } else {
-        ks->m = (j + 2 < m_full) ? j + 2 : m_full;
+        const double w2 = s_tot[0];
+        const double hn = w2 > 0.0 ? sqrt(w2) : 0.0;
+        ks->H[(j + 1) + kHld * j] = hn;
+        double col2 = w2;   // ||K q_j||^2 = sum_i H[i, j]^2 + H[j+1, j]^2
+        for (int q = 0; q <= j; ++q) col2 += ks->H[q + kHld * j] * ks->H[q + kHld * j];
+        if (!(hn > 1e-12 * sqrt(col2))) {
+            ks->breakdown = 1;        // K q_j lies in span{q_0 .. q_j}: the space is complete
+            ks->m = j + 1;
+        } else {
+            ks->m = (j + 2 < m_full) ? j + 2 : m_full;
+        }
     }
 }
 
-// one thread: min || beta0 e_1 - H y || over the m columns in use, by Givens rotations
-__global__ void k_kry_lsq(KrylovScalars* ks, int m_full) {
+// one warp: min || beta0 e_1 - H y || over the m columns in use, by Givens rotations
+__global__ void __launch_bounds__(32) k_kry_lsq(KrylovScalars* ks, int m_full) {
+    __shared__ double R[kKryMax + 2][kKryMax + 1];
+    __shared__ double g[kKryMax + 2];
+    __shared__ double y[kKryMax + 1];
+    const int lane = threadIdx.x;
     const int m = ks->breakdown ? ks->m : m_full;
-    double R[kKryMax + 2][kKryMax + 1];
-    double g[kKryMax + 2];
-    for (int i = 0; i <= m; ++i) {
-        g[i] = i == 0 ? ks->beta0 : 0.0;
-        for (int j = 0; j < m; ++j) R[i][j] = ks->H[i + kHld * j];
-    }
+    for (int i = 0; i <= m; ++i)
+        for (int k = lane; k < m; k += 32) R[i][k] = ks->H[i + kHld * k];
+    if (lane <= m) g[lane] = lane == 0 ? ks->beta0 : 0.0;
+    __syncwarp();
     for (int j = 0; j < m; ++j) {   // annihilate R[j+1][j]
-        const double a = R[j][j], b = R[j + 1][j];
-        const double r = hypot(a, b);
-        const double c = r > 0.0 ? a / r : 1.0, s = r > 0.0 ? b / r : 0.0;
-        for (int k = j; k < m; ++k) {
-            const double x = R[j][k], y = R[j + 1][k];
-            R[j][k] = c * x + s * y;
-            R[j + 1][k] = -s * x + c * y;
+        const double a = R[j][j], bb = R[j + 1][j];
+        const double r = hypot(a, bb);
+        const double c = r > 0.0 ? a / r : 1.0, s = r > 0.0 ? bb / r : 0.0;
+        __syncwarp();
+        for (int k = j + lane; k < m; k += 32) {
+            const double x = R[j][k], yv = R[j + 1][k];
+            R[j][k] = c * x + s * yv;
+            R[j + 1][k] = -s * x + c * yv;
         }
-        const double x = g[j], y = g[j + 1];
-        g[j] = c * x + s * y;
-        g[j + 1] = -s * x + c * y;
+        if (lane == 0) {
+            const double x = g[j], yv = g[j + 1];
+            g[j] = c * x + s * yv;
+            g[j + 1] = -s * x + c * yv;
+        }
+        __syncwarp();
     }
     for (int j = m - 1; j >= 0; --j) {
-        double t = g[j];
-        for (int k = j + 1; k < m; ++k) t -= R[j][k] * ks->y[k];
-        ks->y[j] = R[j][j] != 0.0 ? t / R[j][j] : 0.0;
+        double t = 0.0;
+        for (int k = j + 1 + lane; k < m; k += 32) t += R[j][k] * y[k];
+        t = warp_sum(t);
+        if (lane == 0) y[j] = R[j][j] != 0.0 ? (g[j] - t) / R[j][j] : 0.0;
+        __syncwarp();
     }
-    for (int j = m; j <= kKryMax; ++j) ks->y[j] = 0.0;
-    ks->m = m;
-    ks->breakdown = 0;   // the combination uses all m columns
+    if (lane <= kKryMax) ks->y[lane] = lane < m ? y[lane] : 0.0;
+    if (lane == 0) {
+        ks->m = m;
+        ks->breakdown = 0;   // the combination uses all m columns
+    }
 }
 
 // x = Q y over the m columns in use
@@ -248,10 +258,12 @@ __global__ void __launch_bounds__(256) k_kry_combine(const T* __restrict__ Q, lo
     __syncthreads();
     const int m = s_m;
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        T qv[kKryMax + 1];
+#pragma unroll
+        for (int i = 0; i < kKryMax + 1; ++i) qv[i] = (i < m) ? Q[i * ld + e] : T(0);
         T t = T(0);
 #pragma unroll
-        for (int i = 0; i < kKryMax + 1; ++i)
-            if (i < m) t = fma(s_y[i], Q[i * ld + e], t);
+        for (int i = 0; i < kKryMax + 1; ++i) t = fma(s_y[i], qv[i], t);
         x[e] = t;
     }
 }
@@ -267,27 +279,17 @@ static int krylov_t(to_problem* P, const void* b, void* x, cudaStream_t s) {
     unsigned* cnt = P->counters + 12;
     const int nb = P->kry_blocks;
     const int nbs = (int)std::min<long long>((n + 255) / 256, 4LL * P->num_sms);
-    // beta0 = ||b||, q_0 = b / beta0
-    k_kry_pass<T, 3><<<nb, kKryThreads, 0, s>>>(Q, n, ld, (T*)b, nullptr, part, cnt, &ks->w2, 0, ks);
-    k_kry_book<<<1, 1, 0, s>>>(ks, 0, 0, m_full);
-    k_kry_scale<T><<<nbs, 256, 0, s>>>((const T*)b, Q, n, ks, -1);
+    k_kry_pass<T, 3><<<nb, kKryThreads, 0, s>>>(Q, n, ld, -1, (const T*)b, part, cnt, ks, m_full);   // beta0
     for (int j = 0; j <= D; ++j) {
-        T* qj = Q + (size_t)j * ld;
-        T* w = Q + (size_t)(j + 1) * ld;
-        int rc = launch_operator(P, 0, 0 /* OP_APPLY */, qj, w, nullptr, s, 0.0, 0);
+        // w = K q_j with q_j still unnormalised (b itself for j = 0): the next pass scales both
+        const void* qj = j == 0 ? b : (const void*)(Q + (size_t)j * ld);
+        int rc = launch_operator(P, 0, 0 /* OP_APPLY */, qj, Q + (size_t)(j + 1) * ld, nullptr, s, 0.0, 0);
         if (rc) return rc;
-        // h = Q^T w over the j+1 basis vectors (ks->m = j + 1 here)
-        k_kry_pass<T, 0><<<nb, kKryThreads, 0, s>>>(Q, n, ld, w, nullptr, part, cnt, ks->h, 0, ks);
-        k_kry_book<<<1, 1, 0, s>>>(ks, j, 1, m_full);
-        // w -= Q h, then the second pass's h' = Q^T w
-        k_kry_pass<T, 1><<<nb, kKryThreads, 0, s>>>(Q, n, ld, w, ks->h, part, cnt, ks->h, 0, ks);
-        k_kry_book<<<1, 1, 0, s>>>(ks, j, 3, m_full);
-        // w -= Q h', then ||w||^2
-        k_kry_pass<T, 2><<<nb, kKryThreads, 0, s>>>(Q, n, ld, w, ks->h, part, cnt, &ks->w2, 0, ks);
-        k_kry_book<<<1, 1, 0, s>>>(ks, j, 2, m_full);
-        if (j < D) k_kry_scale<T><<<nbs, 256, 0, s>>>(w, w, n, ks, j);
+        k_kry_pass<T, 0><<<nb, kKryThreads, 0, s>>>(Q, n, ld, j, (const T*)b, part, cnt, ks, m_full);
+        k_kry_pass<T, 1><<<nb, kKryThreads, 0, s>>>(Q, n, ld, j, (const T*)b, part, cnt, ks, m_full);
+        k_kry_pass<T, 2><<<nb, kKryThreads, 0, s>>>(Q, n, ld, j, (const T*)b, part, cnt, ks, m_full);
     }
-    k_kry_lsq<<<1, 1, 0, s>>>(ks, m_full);
+    k_kry_lsq<<<1, 32, 0, s>>>(ks, m_full);
     k_kry_combine<T><<<nbs, 256, 0, s>>>(Q, n, ld, (T*)x, ks);
     TO_CUDA(cudaGetLastError());
     return TO_OK;
