@@ -331,6 +331,7 @@ def main():
         prm_b = fb.to_default_params(precision=fb.TO_FP32_MIXED, n_inner=5)
         probs = [fb.Problem.from_workload(pb_, prm_b, device=local) for pb_ in pbs]
         with fb.Batch(probs) as Bt:
+            tile_kc, tile_us = Bt.tile()
             Bt.step(3, want_stats=False)
             torch.cuda.synchronize()
             kb = 20
@@ -345,7 +346,8 @@ def main():
                  "problems": 64, "total_dofs": ndof_b, "batched_iterations": kb,
                  "ms_per_batched_iteration": tb * 1e3 / kb,
                  "outer_iters_per_s_aggregate": 64 * kb / tb,
-                 "apply_gdofs_effective": ndof_b * 6 * kb / tb / 1e9}
+                 "apply_gdofs_effective": ndof_b * 6 * kb / tb / 1e9,
+                 "autotuned_tile_planes": tile_kc, "autotuned_batched_apply_us": tile_us}
         for P_ in probs:
             P_.close()
 

@@ -225,6 +225,13 @@ int to_batch_create(to_problem* const* problems, int32_t n, to_batch** out);
 void to_batch_destroy(to_batch* batch);
 int to_batch_step(to_batch* batch, int32_t n_outer, to_stats* stats_out, void* stream);
 
+/* The batched operator's tile shape chosen by the autotuner at to_batch_create:
+ * to_batch_create times the batch's K u (into scratch, no state change) for tiles
+ * of 2, 4, 8, 16 and 32 node planes and keeps the fastest.  kchunk_out receives
+ * the planes per tile, us_out the measured microseconds of one batched K u at that
+ * choice; either pointer may be NULL.  No counterpart in the paper. */
+int to_batch_tile(const to_batch* batch, int32_t* kchunk_out, double* us_out);
+
 /* Differentiable compliance through a truncated lower-level solve.
  * J(rho) = f^T u_T where u_0 = 0 and u_{j+1} = u_j + beta D^-1 (f - K^(rho~) u_j),
  * D = diag K^ (the literal constant-beta step of Algorithms 1 / 3 with the Jacobi M),

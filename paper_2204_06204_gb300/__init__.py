@@ -19,7 +19,7 @@ from ._abi import (TO_FP32_MIXED, TO_FP64, TO_INNER_RICHARDSON, TO_INNER_SD, TO_
 __all__ = ["to_default_params", "to_create", "to_destroy", "to_sizes", "to_set_design", "to_apply_K",
            "to_inner_solve", "to_sensitivity", "to_filter", "to_project", "to_step", "to_get_state",
            "to_set_state", "to_check", "to_last_error", "to_project_noalloc", "to_compliance_truncated",
-           "to_compliance_truncated_grad", "to_batch_create", "to_batch_destroy", "to_batch_step", "Batch",
+           "to_compliance_truncated_grad", "to_batch_create", "to_batch_destroy", "to_batch_step", "to_batch_tile", "Batch",
            "Problem", "ToError",
            "TO_FP64", "TO_FP32_MIXED", "TO_PRECOND_JACOBI", "TO_PRECOND_MG", "TO_PRECOND_NONE", "TO_PRECOND_KRYLOV",
            "TO_INNER_SD", "TO_INNER_RICHARDSON"]
@@ -259,6 +259,12 @@ def to_batch_destroy(B):
     _lib().to_batch_destroy(B)
 
 
+def to_batch_tile(B):
+    kc, us = C.c_int32(), C.c_double()
+    _abi.check(_lib().to_batch_tile(B, C.byref(kc), C.byref(us)))
+    return kc.value, us.value
+
+
 def to_batch_step(B, n_problems, n_outer, device, want_stats=True):
     if want_stats:
         arr = (to_stats * (n_problems * max(int(n_outer), 1)))()
@@ -278,6 +284,10 @@ class Batch:
 
     def step(self, n_outer=1, want_stats=True):
         return to_batch_step(self.handle, len(self.problems), n_outer, self.device, want_stats)
+
+    def tile(self):
+        """(planes per operator tile, microseconds of one batched K u) picked by the autotuner."""
+        return to_batch_tile(self.handle)
 
     def close(self):
         if getattr(self, "handle", None):

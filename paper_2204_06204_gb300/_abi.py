@@ -72,6 +72,7 @@ SIGNATURES = {
     "to_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(C.c_void_p)]),
     "to_batch_destroy": (None, [P]),
     "to_batch_step": (C.c_int, [P, C.c_int32, C.POINTER(to_stats), P]),
+    "to_batch_tile": (C.c_int, [P, C.POINTER(C.c_int32), C.POINTER(C.c_double)]),
     "to_compliance_truncated": (C.c_int, [P, P, C.c_int32, C.c_double, C.POINTER(C.c_double), P]),
     "to_compliance_truncated_grad": (C.c_int, [P, C.c_double, P, P]),
     "to_project_noalloc": (C.c_int, [P, P, C.c_int64, C.c_int32, C.c_double, C.c_double, C.c_double,

@@ -32,8 +32,9 @@ template <typename T>
 SimpT<T> simp_params(const to_material& m);
 
 int batch_operator_launch(int prec, int mode, const void* tab, const void* kh, int max_tiles, int n, cudaStream_t s);
+int batch_autotune_kchunk(to_problem* const* probs, int n, const void* kh, cudaStream_t s, int* best_out, float* us_out);
 int op_tables_build(to_problem* const* probs, int n, void** resid, void** q_first, void** q, void** kh_host,
-                    int* max_tiles);
+                    int* max_tiles, int kchunk);
 
 template <typename T>
 struct BProb {
@@ -276,6 +277,8 @@ struct to_batch {
     void* tab_q = nullptr;
     void* kh = nullptr;                   // host copy of HaarK<T>
     int max_tiles = 0, grid_x = 0;
+    int kchunk = 8;                       // node planes per operator tile, picked by the autotuner
+    float tune_us = 0.f;                  // the batch's K u at that choice
     size_t proj_smem = 0;
     bool proj_cache = true;
     cudaStream_t stream = nullptr;
@@ -414,17 +417,27 @@ extern "C" int to_batch_create(to_problem* const* problems, int32_t n, to_batch*
     B->n_inner = P0->prm.n_inner;
     B->device = P0->device;
     int rc = P0->prec == TO_FP64 ? build_tables_t<double>(B) : build_tables_t<float>(B);
-    if (!rc) rc = op_tables_build(B->probs.data(), n, &B->tab_resid, &B->tab_q_first, &B->tab_q, &B->kh, &B->max_tiles);
     if (!rc && (cudaStreamCreateWithFlags(&B->stream, cudaStreamNonBlocking) != cudaSuccess ||
                 cudaEventCreateWithFlags(&B->ev_in, cudaEventDisableTiming) != cudaSuccess ||
                 cudaEventCreateWithFlags(&B->ev_out, cudaEventDisableTiming) != cudaSuccess))
         rc = fail(TO_ERR_CUDA, "batch stream / event creation failed");
+    // tile shapes: time the batched operator for each candidate depth, keep the fastest
+    if (!rc) rc = op_tables_build(B->probs.data(), n, &B->tab_resid, &B->tab_q_first, &B->tab_q, &B->kh, &B->max_tiles, 8);
+    if (!rc) rc = batch_autotune_kchunk(B->probs.data(), n, B->kh, B->stream, &B->kchunk, &B->tune_us);
+    if (!rc) rc = op_tables_build(B->probs.data(), n, &B->tab_resid, &B->tab_q_first, &B->tab_q, &B->kh, &B->max_tiles, B->kchunk);
     if (prev >= 0) cudaSetDevice(prev);
     if (rc) {
         destroy_batch(B);
         return rc;
     }
     *out = B;
+    return TO_OK;
+}
+
+extern "C" int to_batch_tile(const to_batch* B, int32_t* kchunk_out, double* us_out) {
+    if (!B) return fail(TO_ERR_ARG, "null batch");
+    if (kchunk_out) *kchunk_out = B->kchunk;
+    if (us_out) *us_out = (double)B->tune_us;
     return TO_OK;
 }
 

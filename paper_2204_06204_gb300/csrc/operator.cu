@@ -646,13 +646,13 @@ int launch_operator(to_problem* P, int level, int mode, const void* x, void* y, 
 namespace to {
 
 template <typename T>
-static OpArgs<T> batch_args(to_problem* P, int mode, int first) {
+static OpArgs<T> batch_args(to_problem* P, int mode, int first, int kchunk) {
     const Level& L = P->lv[0];
     OpArgs<T> a{};
     a.nx = L.nx;
     a.ny = L.ny;
     a.nz = L.nz;
-    a.kchunk = L.nz + 1 < 8 ? L.nz + 1 : 8;
+    a.kchunk = L.nz + 1 < kchunk ? L.nz + 1 : kchunk;
     a.E = (const T*)L.E;
     a.mask = L.mask;
     a.tmask = L.tmask;
@@ -669,20 +669,23 @@ static OpArgs<T> batch_args(to_problem* P, int mode, int first) {
         a.Ed = (const T*)P->Ed;
         a.gt = (T*)P->gt;
         a.counter = P->counters + 0;
-    } else {
+    } else if (mode == OP_Q) {
         a.x = (const T*)P->z;
         a.y = (T*)P->q;
         a.counter = P->counters + 1;
+    } else {   // OP_APPLY into scratch: the tile autotuner's timing runs
+        a.x = (const T*)P->u;
+        a.y = (T*)P->tmp_v;
     }
     return a;
 }
 
 template <typename T>
-static int op_table_t(to_problem* const* probs, int n, int mode, int first, void** dev, int* max_tiles) {
+static int op_table_t(to_problem* const* probs, int n, int mode, int first, void** dev, int* max_tiles, int kchunk) {
     std::vector<OpArgs<T>> h(n);
     int mt = 0;
     for (int i = 0; i < n; ++i) {
-        h[i] = batch_args<T>(probs[i], mode, first);
+        h[i] = batch_args<T>(probs[i], mode, first, kchunk);
         const int gx = (h[i].nx + 1 + 30) / 31, gy = (h[i].ny + 1 + 6) / 7, gz = (h[i].nz + 1 + h[i].kchunk - 1) / h[i].kchunk;
         if ((long long)gx * gy * gz > kMaxRedBlocks) return fail(TO_ERR_ARG, "batched problem too large for the reduction slots");
         mt = mt > gx * gy * gz ? mt : gx * gy * gz;
@@ -694,38 +697,90 @@ static int op_table_t(to_problem* const* probs, int n, int mode, int first, void
     return TO_OK;
 }
 
-// device tables of operator arguments for a list of problems, and the common element constants
+// device tables of operator arguments for a list of problems (node planes per tile:
+// kchunk), and the common element constants
 int op_tables_build(to_problem* const* probs, int n, void** resid, void** q_first, void** q, void** kh_host,
-                    int* max_tiles) {
+                    int* max_tiles, int kchunk) {
     const int prec = probs[0]->prec;
     int mt = 0, rc;
     if (prec == TO_FP64) {
-        if ((rc = op_table_t<double>(probs, n, OP_RESID, 1, resid, &mt)) || (rc = op_table_t<double>(probs, n, OP_Q, 1, q_first, &mt)) ||
-            (rc = op_table_t<double>(probs, n, OP_Q, 0, q, &mt)))
+        if ((rc = op_table_t<double>(probs, n, OP_RESID, 1, resid, &mt, kchunk)) ||
+            (rc = op_table_t<double>(probs, n, OP_Q, 1, q_first, &mt, kchunk)) || (rc = op_table_t<double>(probs, n, OP_Q, 0, q, &mt, kchunk)))
             return rc;
-        HaarK<double>* kh = (HaarK<double>*)malloc(sizeof(HaarK<double>));
-        fill_haar<double>(probs[0], 1.0, *kh);
-        *kh_host = kh;
+        if (!*kh_host) {
+            HaarK<double>* kh = (HaarK<double>*)malloc(sizeof(HaarK<double>));
+            fill_haar<double>(probs[0], 1.0, *kh);
+            *kh_host = kh;
+        }
     } else {
-        if ((rc = op_table_t<float>(probs, n, OP_RESID, 1, resid, &mt)) || (rc = op_table_t<float>(probs, n, OP_Q, 1, q_first, &mt)) ||
-            (rc = op_table_t<float>(probs, n, OP_Q, 0, q, &mt)))
+        if ((rc = op_table_t<float>(probs, n, OP_RESID, 1, resid, &mt, kchunk)) ||
+            (rc = op_table_t<float>(probs, n, OP_Q, 1, q_first, &mt, kchunk)) || (rc = op_table_t<float>(probs, n, OP_Q, 0, q, &mt, kchunk)))
             return rc;
-        HaarK<float>* kh = (HaarK<float>*)malloc(sizeof(HaarK<float>));
-        fill_haar<float>(probs[0], 1.0, *kh);
-        *kh_host = kh;
+        if (!*kh_host) {
+            HaarK<float>* kh = (HaarK<float>*)malloc(sizeof(HaarK<float>));
+            fill_haar<float>(probs[0], 1.0, *kh);
+            *kh_host = kh;
+        }
     }
     *max_tiles = mt;
     // shared-memory opt-in of the batched kernels
     const size_t smem = prec == TO_FP64 ? sizeof(OpSmem<double, 32, 8, kRing>) : sizeof(OpSmem<float, 32, 8, kRing>);
-    const void* fns[2];
+    const void* fns[3];
     if (prec == TO_FP64) {
         fns[0] = (const void*)k_operator_batch<double, 32, 8, OP_RESID>;
         fns[1] = (const void*)k_operator_batch<double, 32, 8, OP_Q>;
+        fns[2] = (const void*)k_operator_batch<double, 32, 8, OP_APPLY>;
     } else {
         fns[0] = (const void*)k_operator_batch<float, 32, 8, OP_RESID>;
         fns[1] = (const void*)k_operator_batch<float, 32, 8, OP_Q>;
+        fns[2] = (const void*)k_operator_batch<float, 32, 8, OP_APPLY>;
     }
     for (const void* f : fns) TO_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    return TO_OK;
+}
+
+int batch_operator_launch(int prec, int mode, const void* tab, const void* kh, int max_tiles, int n, cudaStream_t s);
+
+// Tile autotuner of the batched operator: time the batch's K u into scratch (no scalar
+// side effects) for each candidate number of node planes per tile and return the fastest.
+int batch_autotune_kchunk(to_problem* const* probs, int n, const void* kh, cudaStream_t s, int* best_out, float* us_out) {
+    const int prec = probs[0]->prec;
+    static const int cand[] = {2, 4, 8, 16, 32};
+    void* tab = nullptr;
+    cudaEvent_t e0, e1;
+    TO_CUDA(cudaEventCreate(&e0));
+    TO_CUDA(cudaEventCreate(&e1));
+    int best = 8;
+    float best_t = -1.f;
+    int rc = TO_OK;
+    for (int kc : cand) {
+        int mt = 0;
+        rc = prec == TO_FP64 ? op_table_t<double>(probs, n, OP_APPLY, 0, &tab, &mt, kc)
+                             : op_table_t<float>(probs, n, OP_APPLY, 0, &tab, &mt, kc);
+        if (rc) break;
+        for (int r = 0; r < 2 && !rc; ++r) rc = batch_operator_launch(prec, OP_APPLY, tab, kh, mt, n, s);
+        if (rc) break;
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < 5 && !rc; ++r) rc = batch_operator_launch(prec, OP_APPLY, tab, kh, mt, n, s);
+        cudaEventRecord(e1, s);
+        if (rc) break;
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            rc = fail(TO_ERR_CUDA, "autotune timing");
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (best_t < 0.f || ms < best_t) {
+            best_t = ms;
+            best = kc;
+        }
+    }
+    if (tab) cudaFree(tab);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    *best_out = best;
+    if (us_out) *us_out = best_t * 1000.f / 5.f;
     return TO_OK;
 }
 
@@ -736,15 +791,19 @@ int batch_operator_launch(int prec, int mode, const void* tab, const void* kh, i
         const HaarK<double>& k = *(const HaarK<double>*)kh;
         if (mode == OP_RESID)
             k_operator_batch<double, 32, 8, OP_RESID><<<grid, block, smem, s>>>((const OpArgs<double>*)tab, k);
-        else
+        else if (mode == OP_Q)
             k_operator_batch<double, 32, 8, OP_Q><<<grid, block, smem, s>>>((const OpArgs<double>*)tab, k);
+        else
+            k_operator_batch<double, 32, 8, OP_APPLY><<<grid, block, smem, s>>>((const OpArgs<double>*)tab, k);
     } else {
         const size_t smem = sizeof(OpSmem<float, 32, 8, kRing>);
         const HaarK<float>& k = *(const HaarK<float>*)kh;
         if (mode == OP_RESID)
             k_operator_batch<float, 32, 8, OP_RESID><<<grid, block, smem, s>>>((const OpArgs<float>*)tab, k);
-        else
+        else if (mode == OP_Q)
             k_operator_batch<float, 32, 8, OP_Q><<<grid, block, smem, s>>>((const OpArgs<float>*)tab, k);
+        else
+            k_operator_batch<float, 32, 8, OP_APPLY><<<grid, block, smem, s>>>((const OpArgs<float>*)tab, k);
     }
     TO_CUDA(cudaGetLastError());
     return TO_OK;

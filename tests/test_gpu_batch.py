@@ -68,3 +68,17 @@ def test_batch_rejects_mixed_settings():
         fb.Batch([a, b])
     a.close()
     b.close()
+
+
+def test_batch_tile_autotuner_picks_a_candidate():
+    fb = _fb()
+    pbs = W.batch_cantilevers(4)
+    probs = [fb.Problem.from_workload(p, fb.to_default_params(precision=fb.TO_FP32_MIXED)) for p in pbs]
+    try:
+        with fb.Batch(probs) as B:
+            kc, us = B.tile()
+            assert kc in (2, 4, 8, 16, 32) and us > 0.0
+            B.step(2, want_stats=False)
+    finally:
+        for P in probs:
+            P.close()
