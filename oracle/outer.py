@@ -89,6 +89,8 @@ def run(pb, n_outer, precond="jacobi", n_inner=5, inner_mode="sd", beta=0.5,
                 raise ValueError(precond)
             if inner_mode == "sd":
                 u_new, _, betas, r0 = solve.inner_sd(A, S.f, u, Minv, n_inner)
+            elif inner_mode == "pfbto":
+                u_new, r0 = solve.inner_pfbto(A, S.f, u, Minv, n_inner, beta)
             else:
                 u_new, r0 = solve.inner_richardson(A, S.f, u, Minv, n_inner, beta)
         g = filt.filter_transpose(S.H, S.Hs, gt)

@@ -12,6 +12,8 @@
   c_{i-1} K^i b||, on an orthonormal Arnoldi basis of that Krylov space
   (``krylov_apply_power``: the paper's Householder QR of the power basis).
   With beta = 1 in ``inner_richardson`` this is Algorithm CPFBTO.
+* ``inner_pfbto``      -- Algorithm 2 (PFBTO): u <- u - beta K M^-1 M^-1 (K u - f),
+  the preconditioned gradient step on the squared lower-level problem.
 * ``solve_exact``      -- K^-1 f for the nested exact method (PGD, Sec. V):
   dense Cholesky when small, sparse LU otherwise.
 * ``Multigrid``        -- a geometric-multigrid V-cycle used as M^-1.  The paper
@@ -118,6 +120,21 @@ def krylov_apply_power(A, b: np.ndarray, D: int) -> np.ndarray:
     Q, R = np.linalg.qr(np.stack(KS, axis=1))
     c = np.linalg.lstsq(R, Q.T @ b, rcond=None)[0]
     return np.stack(S, axis=1) @ c
+
+
+def inner_pfbto(A, f: np.ndarray, u: np.ndarray, Minv, n: int, beta: float):
+    """Return (u_n, r_0): n steps of Algorithm PFBTO (Algorithm 2, lines 1-2):
+    delta = M^-1 (K u - f), u <- u - beta K M^-1 delta, i.e. preconditioned gradient
+    steps on the squared lower-level problem (1/2) ||K u - f||^2 (Eq. optBilevelSqr)."""
+    u = u.copy()
+    r0 = None
+    for _ in range(n):
+        b = A(u) - f
+        if r0 is None:
+            r0 = -b
+        delta = Minv(b)
+        u = u - beta * A(Minv(delta))
+    return u, r0
 
 
 def solve_exact(K: sp.spmatrix, f: np.ndarray) -> np.ndarray:

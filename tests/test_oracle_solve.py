@@ -187,3 +187,31 @@ def test_cpfbto_step_contracts_the_tracking_error():
         rho, _, _, a0 = outer.run(pb, 1, precond="krylov", n_inner=1, inner_mode="richardson", beta=1.0,
                                   krylov_dim=20, setup=S, rho=rho, u=u, k0=k, alpha0=a0)
         u = u_next
+
+
+# ----------------------------------------------------------------------------- PFBTO (Algorithm 2)
+def test_pfbto_step_with_the_exact_preconditioner_solves_the_system():
+    """M = K, beta = 1: u - K K^-1 K^-1 (K u - f) = K^-1 f in one step."""
+    pb, S, Ee = _setup(rho=lambda n: W.random_rho(n))
+    K = S.K(Ee).tocsc()
+    lu = sp.linalg.splu(K)
+    u0 = W.random_u(pb.n_dof)
+    u0[pb.fixed_dof] = 0.0
+    u1, _ = solve.inner_pfbto(lambda v: K @ v, S.f, u0, lu.solve, 1, 1.0)
+    assert np.linalg.norm(u1 - lu.solve(S.f)) <= 1e-10 * np.linalg.norm(lu.solve(S.f))
+
+
+def test_pfbto_squared_residual_decreases_with_a_small_step():
+    """With M = I the step is gradient descent on (1/2)||K u - f||^2 (Eq. optBilevelSqr):
+    every step with beta < 2 / lambda_max(K^2) lowers ||K u - f||."""
+    pb, S, Ee = _setup(rho=lambda n: W.random_rho(n))
+    K = S.K(Ee)
+    lmax = float(sp.linalg.eigsh(K, k=1, which="LA", return_eigenvectors=False)[0])
+    beta = 1.0 / lmax ** 2
+    u = np.zeros(pb.n_dof)
+    last = np.linalg.norm(K @ u - S.f)
+    for _ in range(10):
+        u, _ = solve.inner_pfbto(lambda v: K @ v, S.f, u, lambda r: r, 1, beta)
+        now = np.linalg.norm(K @ u - S.f)
+        assert now < last
+        last = now
