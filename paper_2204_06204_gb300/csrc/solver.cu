@@ -151,6 +151,31 @@ int launch_precond(to_problem* P, const void*, void*, cudaStream_t s) {
     return P->prec == TO_FP64 ? precond_t<double>(P, s) : precond_t<float>(P, s);
 }
 
+// out = in / d (the Jacobi M^-1 as a separate pass)
+template <typename T>
+__global__ void __launch_bounds__(256) k_div_diag(long long n, const T* __restrict__ in, const T* __restrict__ d,
+                                                  T* __restrict__ out) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = in[i] / d[i];
+}
+
+// out = M^-1 in for any preconditioner (in and out distinct)
+template <typename T>
+static int apply_M_t(to_problem* P, const void* in, void* out, cudaStream_t s) {
+    const int nb = grid_1d(P->n_dof, 256, P->num_sms);
+    switch (P->prm.precond) {
+        case TO_PRECOND_MG: return mg_vcycle(P, in, out, s);
+        case TO_PRECOND_KRYLOV: return krylov_apply(P, in, out, s);
+        case TO_PRECOND_NONE:
+            TO_CUDA(cudaMemcpyAsync(out, in, P->n_dof * sizeof(T), cudaMemcpyDeviceToDevice, s));
+            return TO_OK;
+        default:
+            k_div_diag<T><<<nb, 256, 0, s>>>(P->n_dof, (const T*)in, (const T*)P->lv[0].d, (T*)out);
+            TO_CUDA(cudaGetLastError());
+            return TO_OK;
+    }
+}
+
 // Residual at u (with the fused sensitivity when `primary`), then nsteps steps.
 int run_inner(to_problem* P, void* u, int nsteps, int primary, cudaStream_t s) {
     int rc;
@@ -159,7 +184,27 @@ int run_inner(to_problem* P, void* u, int nsteps, int primary, cudaStream_t s) {
     rc = launch_operator(P, 0, OP_RESID, u, P->r, P->f, s, 0.0, 1);
     P->gt = gt_save;
     if (rc) return rc;
-    if (P->prm.inner_mode == TO_INNER_SD) {
+    if (P->prm.inner_mode == TO_INNER_PFBTO) {
+        // Algorithm 2: u <- u - beta K M^-1 M^-1 (K u - f) = u + beta K M^-1 M^-1 r
+        const int nb = grid_1d(P->n_dof, 256, P->num_sms);
+        for (int it = 0; it < nsteps; ++it) {
+            if (it > 0) {
+                P->gt = nullptr;
+                rc = launch_operator(P, 0, OP_RESID, u, P->r, P->f, s, 0.0, 0);
+                P->gt = gt_save;
+                if (rc) return rc;
+            }
+            if ((rc = P->prec == TO_FP64 ? apply_M_t<double>(P, P->r, P->z, s) : apply_M_t<float>(P, P->r, P->z, s)) ||
+                (rc = P->prec == TO_FP64 ? apply_M_t<double>(P, P->z, P->tmp_v, s) : apply_M_t<float>(P, P->z, P->tmp_v, s)) ||
+                (rc = launch_operator(P, 0, OP_APPLY, P->tmp_v, P->q, nullptr, s, 0.0, 0)))
+                return rc;
+            if (P->prec == TO_FP64)
+                k_axpy<double><<<nb, 256, 0, s>>>(P->n_dof, (double*)u, (const double*)P->q, P->prm.beta);
+            else
+                k_axpy<float><<<nb, 256, 0, s>>>(P->n_dof, (float*)u, (const float*)P->q, (float)P->prm.beta);
+            TO_CUDA(cudaGetLastError());
+        }
+    } else if (P->prm.inner_mode == TO_INNER_SD) {
         if ((rc = launch_precond(P, P->r, P->z, s))) return rc;
         for (int it = 0; it < nsteps; ++it) {
             if ((rc = launch_operator(P, 0, OP_Q, P->z, P->q, nullptr, s, 0.0, it == 0))) return rc;
