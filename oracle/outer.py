@@ -91,6 +91,9 @@ def run(pb, n_outer, precond="jacobi", n_inner=5, inner_mode="sd", beta=0.5,
                 u_new, _, betas, r0 = solve.inner_sd(A, S.f, u, Minv, n_inner)
             elif inner_mode == "pfbto":
                 u_new, r0 = solve.inner_pfbto(A, S.f, u, Minv, n_inner, beta)
+            elif inner_mode == "pcg":   # n_inner conjugate-gradient iterations (the nested method's solve)
+                r0 = S.f - A(u)
+                u_new, _ = solve.pcg(A, S.f, Minv, tol=0.0, maxit=n_inner, x0=u)
             else:
                 u_new, r0 = solve.inner_richardson(A, S.f, u, Minv, n_inner, beta)
         g = filt.filter_transpose(S.H, S.Hs, gt)

@@ -215,3 +215,17 @@ def test_pfbto_squared_residual_decreases_with_a_small_step():
         now = np.linalg.norm(K @ u - S.f)
         assert now < last
         last = now
+
+
+def test_pcg_matches_scipy_cg():
+    """The oracle's preconditioned CG = scipy's CG with the same Jacobi preconditioner and
+    iteration count (an independent implementation of the same recurrence)."""
+    import scipy.sparse.linalg as spla
+    pb, S, Ee = _setup(rho=lambda n: W.random_rho(n))
+    K = S.K(Ee).tocsr()
+    D = fem.jacobi_diagonal(pb.nx, pb.ny, pb.nz, Ee, S.ke, pb.fixed_dof)
+    for it in (1, 5, 30):
+        x, _ = solve.pcg(lambda v: K @ v, S.f, lambda r: r / D, tol=0.0, maxit=it)
+        xs, _ = spla.cg(K, S.f, x0=np.zeros_like(S.f), rtol=1e-300, atol=0.0, maxiter=it,
+                        M=spla.LinearOperator(K.shape, matvec=lambda r: r / D))
+        assert np.linalg.norm(x - xs) <= 1e-9 * np.linalg.norm(xs)
