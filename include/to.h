@@ -65,7 +65,7 @@ enum {
 
 enum { TO_FP64 = 0, TO_FP32_MIXED = 1 };
 enum { TO_PRECOND_JACOBI = 0, TO_PRECOND_MG = 1, TO_PRECOND_NONE = 2, TO_PRECOND_KRYLOV = 3 };
-enum { TO_INNER_SD = 0, TO_INNER_RICHARDSON = 1, TO_INNER_PFBTO = 2 };
+enum { TO_INNER_SD = 0, TO_INNER_RICHARDSON = 1, TO_INNER_PFBTO = 2, TO_INNER_PCG = 3 };
 
 typedef struct to_problem to_problem;      /* opaque */
 typedef struct to_batch to_batch;          /* opaque: many problems advanced together */
@@ -110,7 +110,9 @@ typedef struct {
  *               beta = r^T z / z^T K z; TO_INNER_RICHARDSON: constant beta
  *               (the literal step of Algorithms 1 / 3); TO_INNER_PFBTO: the step of
  *               Algorithm 2, u <- u - beta K M^-1 M^-1 (K u - f) (two applications
- *               of M and one of K per step)
+ *               of M and one of K per step); TO_INNER_PCG: n_inner iterations of
+ *               preconditioned conjugate gradients from u (the near-exact solve of
+ *               the nested method, PGD, Sec. V)
  *   n_inner     lower-level steps per outer iteration (>= 0)
  *   beta        step of TO_INNER_RICHARDSON and TO_INNER_PFBTO
  *   alpha0      > 0: alpha_k = alpha0 k^-m.  <= 0: alpha0 = alpha_scale / ||g||_inf

@@ -13,7 +13,8 @@ import ctypes as C
 import numpy as np
 
 from . import _abi
-from ._abi import (TO_FP32_MIXED, TO_FP64, TO_INNER_PFBTO, TO_INNER_RICHARDSON, TO_INNER_SD, TO_PRECOND_JACOBI,
+from ._abi import (TO_FP32_MIXED, TO_FP64, TO_INNER_PCG, TO_INNER_PFBTO, TO_INNER_RICHARDSON, TO_INNER_SD,
+                   TO_PRECOND_JACOBI,
                    TO_PRECOND_KRYLOV,
                    TO_PRECOND_MG, TO_PRECOND_NONE, ToError, to_stats)
 
@@ -23,7 +24,7 @@ __all__ = ["to_default_params", "to_create", "to_destroy", "to_sizes", "to_set_d
            "to_compliance_truncated_grad", "to_batch_create", "to_batch_destroy", "to_batch_step", "to_batch_tile", "Batch",
            "Problem", "ToError",
            "TO_FP64", "TO_FP32_MIXED", "TO_PRECOND_JACOBI", "TO_PRECOND_MG", "TO_PRECOND_NONE", "TO_PRECOND_KRYLOV",
-           "TO_INNER_SD", "TO_INNER_RICHARDSON", "TO_INNER_PFBTO"]
+           "TO_INNER_SD", "TO_INNER_RICHARDSON", "TO_INNER_PFBTO", "TO_INNER_PCG"]
 
 
 def _lib():

@@ -10,7 +10,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libfbto.so")
 TO_OK, TO_ERR_ARG, TO_ERR_CUDA, TO_ERR_NONFINITE, TO_ERR_INFEASIBLE, TO_ERR_TIMEOUT, TO_ERR_SINGULAR, TO_ERR_STATE = range(8)
 TO_FP64, TO_FP32_MIXED = 0, 1
 TO_PRECOND_JACOBI, TO_PRECOND_MG, TO_PRECOND_NONE, TO_PRECOND_KRYLOV = 0, 1, 2, 3
-TO_INNER_SD, TO_INNER_RICHARDSON, TO_INNER_PFBTO = 0, 1, 2
+TO_INNER_SD, TO_INNER_RICHARDSON, TO_INNER_PFBTO, TO_INNER_PCG = 0, 1, 2, 3
 
 ERROR_NAMES = {0: "TO_OK", 1: "TO_ERR_ARG", 2: "TO_ERR_CUDA", 3: "TO_ERR_NONFINITE", 4: "TO_ERR_INFEASIBLE",
                5: "TO_ERR_TIMEOUT", 6: "TO_ERR_SINGULAR", 7: "TO_ERR_STATE"}

@@ -95,8 +95,7 @@ static int validate(const to_grid* g, const to_material* m, const to_loads* L, c
     if (p->precond < 0 || p->precond > 3) return fail(TO_ERR_ARG, "bad preconditioner");
     if (p->precond == TO_PRECOND_KRYLOV && (p->krylov_dim < 0 || p->krylov_dim > 30))
         return fail(TO_ERR_ARG, "krylov_dim must lie in [0, 30]");
-    if (p->inner_mode != TO_INNER_SD && p->inner_mode != TO_INNER_RICHARDSON && p->inner_mode != TO_INNER_PFBTO)
-        return fail(TO_ERR_ARG, "bad inner mode");
+    if (p->inner_mode < TO_INNER_SD || p->inner_mode > TO_INNER_PCG) return fail(TO_ERR_ARG, "bad inner mode");
     if (p->n_inner < 0) return fail(TO_ERR_ARG, "n_inner must be >= 0");
     if (!(p->m >= 0.0)) return fail(TO_ERR_ARG, "alpha exponent m must be >= 0");
     const long long ndof = 3LL * (long long)nn;

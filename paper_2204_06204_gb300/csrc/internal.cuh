@@ -34,6 +34,7 @@ struct ProjSearch {
 
 struct DevScalars {
     double rz, zq, beta, beta_first;   // lower-level step sizes (Algorithm 1 / 3, line 1)
+    double rz_old;                     // conjugate gradients: r^T z of the previous iteration
     double J, res_inf, res2;           // f^T u_k, residual norms at u_k
     double gmax, gsum;                 // ||g||_inf and 1^T g of dJ/drho
     double alpha0, alpha;              // high-level step size alpha_k = alpha0 k^-m

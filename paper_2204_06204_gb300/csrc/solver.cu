@@ -57,6 +57,52 @@ __global__ void __launch_bounds__(256) k_update_sd(long long n, T* __restrict__ 
     }
 }
 
+// Conjugate gradients: u += alpha p, r -= alpha q (alpha = r^T z / p^T q from the q = K p
+// pass); keeps the previous r^T z, and with the Jacobi M also z = r / d and the new r^T z
+template <typename T, bool JACOBI>
+__global__ void __launch_bounds__(256) k_cg_update(long long n, T* __restrict__ u, T* __restrict__ r, T* __restrict__ z,
+                                                   const T* __restrict__ p, const T* __restrict__ q, const T* __restrict__ d,
+                                                   double* red, unsigned* counter, DevScalars* sc) {
+    __shared__ double sh[32 * kRedQ];
+    __shared__ T s_alpha;
+    if (threadIdx.x == 0) {
+        s_alpha = (T)sc->beta;
+        if (blockIdx.x == 0) sc->rz_old = sc->rz;   // read before the new r^T z is written (by the last block,
+                                                    // or by the preconditioner that follows)
+    }
+    __syncthreads();
+    const T alpha = s_alpha;
+    T acc = T(0);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        u[i] += alpha * p[i];
+        const T ri = r[i] - alpha * q[i];
+        r[i] = ri;
+        if (JACOBI) {
+            const T zn = ri / d[i];
+            z[i] = zn;
+            acc += ri * zn;
+        }
+    }
+    if (JACOBI) {
+        T v[1] = {acc};
+        const int kind[1] = {0};
+        double tot[1];
+        block_reduce<T, 1>(v, kind, reinterpret_cast<T*>(sh));
+        if (finish_reduction<T, 1>(v, kind, red, counter, tot, sh, linear_block(), grid_blocks()) && threadIdx.x == 0) sc->rz = tot[0];
+    }
+}
+
+// p = z + (r^T z / previous r^T z) p
+template <typename T>
+__global__ void __launch_bounds__(256) k_cg_dir(long long n, const T* __restrict__ z, T* __restrict__ p, const DevScalars* sc) {
+    __shared__ T s_b;
+    if (threadIdx.x == 0) s_b = sc->rz_old != 0.0 ? (T)(sc->rz / sc->rz_old) : T(0);
+    __syncthreads();
+    const T b = s_b;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        p[i] = z[i] + b * p[i];
+}
+
 // r^T z (after a V-cycle)
 template <typename T>
 __global__ void __launch_bounds__(256) k_dot_rz(long long n, const T* __restrict__ r, const T* __restrict__ z, double* red,
@@ -184,7 +230,30 @@ int run_inner(to_problem* P, void* u, int nsteps, int primary, cudaStream_t s) {
     rc = launch_operator(P, 0, OP_RESID, u, P->r, P->f, s, 0.0, 1);
     P->gt = gt_save;
     if (rc) return rc;
-    if (P->prm.inner_mode == TO_INNER_PFBTO) {
+    if (P->prm.inner_mode == TO_INNER_PCG) {
+        // preconditioned conjugate gradients from u: p = z, then per iteration q = K p with
+        // alpha = r^T z / p^T q, the update, z = M^-1 r, p = z + beta p
+        const int nb = grid_1d(P->n_dof, 256, P->num_sms);
+        const bool jac = P->prm.precond == TO_PRECOND_JACOBI;
+        if ((rc = launch_precond(P, P->r, P->z, s))) return rc;
+        TO_CUDA(cudaMemcpyAsync(P->tmp_v, P->z, P->n_dof * P->esz, cudaMemcpyDeviceToDevice, s));
+        for (int it = 0; it < nsteps; ++it) {
+            if ((rc = launch_operator(P, 0, OP_Q, P->tmp_v, P->q, nullptr, s, 0.0, it == 0))) return rc;
+            if (P->prec == TO_FP64) {
+                if (jac) k_cg_update<double, true><<<nb, 256, 0, s>>>(P->n_dof, (double*)u, (double*)P->r, (double*)P->z, (const double*)P->tmp_v, (const double*)P->q, (const double*)P->lv[0].d, P->red, P->counters + 4, P->sc);
+                else k_cg_update<double, false><<<nb, 256, 0, s>>>(P->n_dof, (double*)u, (double*)P->r, (double*)P->z, (const double*)P->tmp_v, (const double*)P->q, (const double*)P->lv[0].d, P->red, P->counters + 4, P->sc);
+            } else {
+                if (jac) k_cg_update<float, true><<<nb, 256, 0, s>>>(P->n_dof, (float*)u, (float*)P->r, (float*)P->z, (const float*)P->tmp_v, (const float*)P->q, (const float*)P->lv[0].d, P->red, P->counters + 4, P->sc);
+                else k_cg_update<float, false><<<nb, 256, 0, s>>>(P->n_dof, (float*)u, (float*)P->r, (float*)P->z, (const float*)P->tmp_v, (const float*)P->q, (const float*)P->lv[0].d, P->red, P->counters + 4, P->sc);
+            }
+            TO_CUDA(cudaGetLastError());
+            if (it + 1 == nsteps) break;
+            if (!jac && (rc = launch_precond(P, P->r, P->z, s))) return rc;
+            if (P->prec == TO_FP64) k_cg_dir<double><<<nb, 256, 0, s>>>(P->n_dof, (const double*)P->z, (double*)P->tmp_v, P->sc);
+            else k_cg_dir<float><<<nb, 256, 0, s>>>(P->n_dof, (const float*)P->z, (float*)P->tmp_v, P->sc);
+            TO_CUDA(cudaGetLastError());
+        }
+    } else if (P->prm.inner_mode == TO_INNER_PFBTO) {
         // Algorithm 2: u <- u - beta K M^-1 M^-1 (K u - f) = u + beta K M^-1 M^-1 r
         const int nb = grid_1d(P->n_dof, 256, P->num_sms);
         for (int it = 0; it < nsteps; ++it) {
