@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-mbb", action="store_true", help="skip the 512x256x256 MBB line")
     ap.add_argument("--no-cpfbto", action="store_true", help="skip the CPFBTO (Krylov preconditioner) line")
+    ap.add_argument("--no-pgd", action="store_true", help="skip the FBTO vs nested-exact (PGD) time-to-quality line")
     ap.add_argument("--quality-steps", type=int, default=200,
                     help="outer iterations of the FP32-mixed vs FP64 compliance comparison (0: skip)")
     ap.add_argument("--precond", default="auto", choices=["auto", "mg", "jacobi"])
@@ -401,6 +402,51 @@ def main():
                   "tracking_residual_first_10": [x["res2"] for x in dk]}
         Pk.close()
 
+    # --- time to quality: FBTO (MG x2 steepest descent) against the nested method (PGD: the lower
+    # level re-solved by 30 MG-preconditioned CG iterations each outer iteration), same start
+    pgd = None
+    if not args.no_pgd:
+        f_dev = torch.zeros(pb.n_dof, dtype=torch.float32, device=dev)
+        f_dev[torch.as_tensor(pb.load_dof, device=dev)] = torch.as_tensor(pb.load_val, dtype=torch.float32, device=dev)
+
+        def exact_J(rho_t):
+            prm_e = fb.to_default_params(precision=fb.TO_FP32_MIXED, precond=fb.TO_PRECOND_MG,
+                                         inner_mode=fb.TO_INNER_PCG, n_inner=1)
+            Pe = fb.Problem.from_workload(pb, prm_e, device=local)
+            Pe.set_design(rho_t)
+            ue = Pe.dof()
+            ue.zero_()
+            Pe.inner_solve(ue, 100)
+            J = float(torch.dot(f_dev, ue).item())
+            Pe.close()
+            return J
+
+        def run(prm, n):
+            Pr = fb.Problem.from_workload(pb, prm, device=local)
+            torch.cuda.synchronize()
+            a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a_.record(stream)
+            st = Pr.step(n, want_stats=True)
+            b_.record(stream)
+            torch.cuda.synchronize()
+            rho_f = Pr.get_state()[0].clone()
+            Pr.close()
+            J = [x["J"] if isinstance(x, dict) else x.as_dict()["J"] for x in st]
+            return a_.elapsed_time(b_) / 1000.0, J, rho_f
+
+        n_f, n_p = 200, 30
+        tf, Jf, rho_fb = run(fb.to_default_params(precision=fb.TO_FP32_MIXED, precond=fb.TO_PRECOND_MG, n_inner=2), n_f)
+        tp, Jp, rho_pg = run(fb.to_default_params(precision=fb.TO_FP32_MIXED, precond=fb.TO_PRECOND_MG,
+                                                  inner_mode=fb.TO_INNER_PCG, n_inner=30), n_p)
+        k_same = max(1, min(n_f, int(round(n_f * tp / tf))))
+        pgd = {"workload": "cantilever 128x64x64 from rho = 0.3, FP32-mixed; compliance of each final design from "
+                           "100 MG-preconditioned CG iterations",
+               "fbto": {"iterations": n_f, "seconds": tf, "J_exact_final": exact_J(rho_fb),
+                        "J_tracked_every_20": Jf[::20]},
+               "pgd": {"iterations": n_p, "seconds": tp, "cg_iterations_per_outer": 30,
+                       "J_exact_final": exact_J(rho_pg), "J_every_5": Jp[::5]},
+               "fbto_iterations_in_pgd_time": k_same}
+
     # --- large single problem: MBB half model 512x256x256 (101.6M DOFs), filter radius 2.5, MG, FP32-mixed
     mbb = None
     if not args.no_mbb:
@@ -480,6 +526,7 @@ def main():
         "fp32_over_fp64_iters": (ips32 / res64["outer_iters_per_s"]) if res64 else None,
         "fp32_vs_fp64_quality": quality,
         "cpfbto": cpfbto,
+        "fbto_vs_pgd": pgd,
         "differentiable_compliance": diff,
         "batched": batch,
         "mbb_large": mbb,
