@@ -121,7 +121,11 @@ typedef struct {
  *   mean_proj   1: g <- g - mean(g) before the step (Sec. IV-B)
  *   mg_levels   0 = automatic; mg_nu_pre / mg_nu_post smoothing sweeps;
  *               mg_omega damped-Jacobi weight
- *   tile_x, tile_y, tile_z   0 = automatic tile choice for the operator kernel
+ *   tile_x, tile_y, tile_z   node planes per operator tile (tile_z): > 0 fixed; 0: picked
+ *               per multigrid level by an autotuner at to_create (the sweep is timed for
+ *               1 .. 32 planes and the cost model's choice); < 0 (the default): the cost
+ *               model alone (waves of resident CTAs x planes walked).  tile_x / tile_y are
+ *               reserved (the tile is 32 x 8 threads)
  *   no_graph    0: to_step replays one captured CUDA graph per outer iteration;
  *               1: to_step launches the kernels one by one
  *   krylov_dim  D of Eq. (LSP), 0 <= D <= 30 (the paper uses 20); it costs D + 1

@@ -75,6 +75,7 @@ extern "C" void to_default_params(to_params* o) {
     o->mg_nu_post = 2;
     o->mg_omega = 0.5;
     o->krylov_dim = 20;
+    o->tile_z = -1;   // the cost model: measured per level, the autotuner's isolated timings lost in the graph
 }
 
 static int validate(const to_grid* g, const to_material* m, const to_loads* L, const to_bcs* B, const to_params* p) {
@@ -170,8 +171,7 @@ extern "C" int to_create(const to_grid* g, const to_material* m, const to_loads*
     P->n_elem = (int64_t)g->nx * g->ny * g->nz;
     P->n_node = (int64_t)(g->nx + 1) * (g->ny + 1) * (g->nz + 1);
     P->n_dof = 3 * P->n_node;
-    if (prm->tile_z > 0) P->tile_z = prm->tile_z;
-    else P->tile_z = 0;
+    P->tile_z = prm->tile_z > 0 ? prm->tile_z : 0;
     auto bail = [&](int code) {
         to_destroy(P);
         return code;
@@ -300,7 +300,8 @@ extern "C" int to_create(const to_grid* g, const to_material* m, const to_loads*
         cudaStreamDestroy(s);
         return bail(rc);
     }
-    if ((rc = launch_moduli(P, s)) || (rc = refresh_preconditioner(P, s))) {
+    if ((rc = launch_moduli(P, s)) || (rc = refresh_preconditioner(P, s)) ||
+        (prm->tile_z == 0 && (rc = operator_autotune(P, s)))) {
         cudaStreamDestroy(s);
         return bail(rc);
     }

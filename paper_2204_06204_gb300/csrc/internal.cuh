@@ -85,6 +85,7 @@ struct Level {
     void* b = nullptr;
     void* t = nullptr;
     double kdiag = 0.0;       // k_e[ll] (all equal on a cube)
+    int kchunk = 0;           // node planes per operator tile picked by the autotuner (0: cost model)
 };
 
 struct to_problem_impl;
@@ -198,6 +199,7 @@ int operator_init(to_problem* P);
 int build_tile_mask(Level& L, const uint8_t* mask_host);
 int project_cluster_setup(to_problem* P);
 int krylov_build(to_problem* P);
+int operator_autotune(to_problem* P, cudaStream_t s);
 int krylov_apply(to_problem* P, const void* b, void* x, cudaStream_t s);
 int launch_richardson(to_problem* P, cudaStream_t s);
 

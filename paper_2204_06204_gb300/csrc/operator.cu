@@ -541,7 +541,7 @@ static int launch_t(to_problem* P, int level, int mode, const void* x, void* y, 
     }
     const int gx = (L.nx + 1 + TX - 2) / (TX - 1);
     const int gy = (L.ny + 1 + TY - 2) / (TY - 1);
-    int kchunk = P->tile_z;
+    int kchunk = P->tile_z > 0 ? P->tile_z : L.kchunk;
     if (kchunk <= 0) kchunk = choose_kchunk((long long)gx * gy, L.nz + 1, (long long)P->op_occ[mode] * P->num_sms);
     if (kchunk > L.nz + 1) kchunk = L.nz + 1;
     a.kchunk = kchunk;
@@ -580,6 +580,59 @@ static int init_t(to_problem* P) {
 // shared-memory opt-in and residency of the operator kernels (on the problem's device, before any capture)
 int operator_init(to_problem* P) {
     return P->prec == TO_FP64 ? init_t<double, 32, 8>(P) : init_t<float, 32, 8>(P);
+}
+
+// Tile autotuner of a problem's operator: for every multigrid level (or the fine grid
+// alone), time the damped-Jacobi sweep (the most frequent operator launch) for the
+// cost model's choice and 1, 2, 4, ..., 32 node planes per tile, and keep the fastest for
+// all of that level's operator launches.  Inputs and outputs are the level's scratch
+// vectors: timing only, no state the method reads is changed.
+int operator_autotune(to_problem* P, cudaStream_t s) {
+    cudaEvent_t e0, e1;
+    TO_CUDA(cudaEventCreate(&e0));
+    TO_CUDA(cudaEventCreate(&e1));
+    int rc = TO_OK;
+    const int L = (int)P->lv.size();
+    for (int l = 0; l < L && !rc; ++l) {
+        Level& Lv = P->lv[l];
+        if (l > 0 && l == P->mg_tail) break;   // the one-CTA tail takes over from here
+        if (l > 0 && l == L - 1) break;        // the dense coarsest solve
+        const void* x = l == 0 ? P->u : Lv.x;
+        void* y = l == 0 ? P->tmp_v : Lv.t;
+        const void* b = l == 0 ? P->r : Lv.b;
+        if (!x || !y || !b) continue;
+        const int gx = (Lv.nx + 1 + 30) / 31, gy = (Lv.ny + 1 + 6) / 7;
+        const int model = choose_kchunk((long long)gx * gy, Lv.nz + 1, (long long)P->op_occ[OP_SMOOTH] * P->num_sms);
+        int cand[8] = {model, 1, 2, 4, 8, 16, 32, 0};
+        int best = model;
+        float best_t = -1.f;
+        for (int c = 0; c < 7 && !rc; ++c) {
+            const int kc = cand[c];
+            if (kc > Lv.nz + 1 || (c > 0 && kc == model)) continue;
+            const long long ctas = (long long)gx * gy * ((Lv.nz + 1 + kc - 1) / kc);
+            if (ctas > kMaxRedBlocks) continue;
+            Lv.kchunk = kc;
+            for (int r = 0; r < 2 && !rc; ++r) rc = launch_operator(P, l, OP_SMOOTH, x, y, b, s, 0.5, 0);
+            cudaEventRecord(e0, s);
+            for (int r = 0; r < 5 && !rc; ++r) rc = launch_operator(P, l, OP_SMOOTH, x, y, b, s, 0.5, 0);
+            cudaEventRecord(e1, s);
+            if (rc) break;
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                rc = fail(TO_ERR_CUDA, "autotune timing");
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (best_t < 0.f || ms < best_t) {
+                best_t = ms;
+                best = kc;
+            }
+        }
+        Lv.kchunk = best;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
 }
 
 // Node planes per CTA tile for one launch: the CTA count is gx * gy * ceil(planes / kchunk)
