@@ -129,14 +129,17 @@ typedef struct {
  *   no_graph    0: to_step replays one captured CUDA graph per outer iteration;
  *               1: to_step launches the kernels one by one
  *   krylov_dim  D of Eq. (LSP), 0 <= D <= 30 (the paper uses 20); it costs D + 1
- *               operator applications and (D + 2) vectors of n_dof per application */
+ *               operator applications and (D + 2) vectors of n_dof per application
+ *   proj_sort   0: the projection's multiplier by the safeguarded Newton search;
+ *               1: by the paper's parallel form of Algorithm 4 (a radix sort of the
+ *               2E breakpoints and scans, Sec. IV-D); the same rho */
 typedef struct {
     int32_t precision, precond, inner_mode, n_inner;
     double beta, alpha0, alpha_scale, m;
     int32_t mean_proj, mg_levels, mg_nu_pre, mg_nu_post;
     double mg_omega;
     int32_t tile_x, tile_y, tile_z, no_graph;
-    int32_t krylov_dim, reserved;
+    int32_t krylov_dim, proj_sort;
 } to_params;
 
 /* Per-outer-iteration record (host copy). */

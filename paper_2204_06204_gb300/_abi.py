@@ -38,7 +38,7 @@ class to_params(C.Structure):
                 ("mean_proj", C.c_int32), ("mg_levels", C.c_int32), ("mg_nu_pre", C.c_int32), ("mg_nu_post", C.c_int32),
                 ("mg_omega", C.c_double),
                 ("tile_x", C.c_int32), ("tile_y", C.c_int32), ("tile_z", C.c_int32), ("no_graph", C.c_int32),
-                ("krylov_dim", C.c_int32), ("reserved", C.c_int32)]
+                ("krylov_dim", C.c_int32), ("proj_sort", C.c_int32)]
 
 
 class to_stats(C.Structure):

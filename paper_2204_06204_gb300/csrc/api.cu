@@ -141,6 +141,7 @@ extern "C" void to_destroy(to_problem* P) {
     p = P->kry_q; dfree(p);
     p = P->kry_s; dfree(p);
     p = P->kry_part; dfree(p);
+    p = P->ps_buf; dfree(p);
     p = P->sc; dfree(p);
     p = P->red; dfree(p);
     p = P->counters; dfree(p);
@@ -285,6 +286,10 @@ extern "C" int to_create(const to_grid* g, const to_material* m, const to_loads*
     }
     if ((rc = fill_scalar(P, P->rho, P->n_elem, m->volfrac > m->rho_max ? m->rho_max : m->volfrac, s)) ||
         (rc = launch_rowsum(P, s))) {
+        cudaStreamDestroy(s);
+        return bail(rc);
+    }
+    if (prm->proj_sort && (rc = dalloc(&P->ps_buf, projsort_bytes(P)))) {
         cudaStreamDestroy(s);
         return bail(rc);
     }

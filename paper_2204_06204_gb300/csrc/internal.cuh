@@ -45,6 +45,7 @@ struct DevScalars {
     int n_inner_done;
     int rec;                           // next stats slot written by the record kernel
     ProjSearch ps;                     // the projection's search, carried between its kernels
+    int proj_active;                   // the volume bound is active at this projection (lambda > 0)
 };
 
 // Reduction scratch: one slot of up to kRedQ doubles per block, plus a
@@ -158,6 +159,8 @@ struct to_problem {
 
     // can one 16-CTA cluster run the projection's search passes
     int cluster16 = 0;
+    // scratch of the sort-based multiplier (proj_sort)
+    void* ps_buf = nullptr;
 
     // captured outer iteration (replayed by to_step) on a library-owned stream
     cudaStream_t gstream = nullptr;
@@ -200,6 +203,8 @@ int build_tile_mask(Level& L, const uint8_t* mask_host);
 int project_cluster_setup(to_problem* P);
 int krylov_build(to_problem* P);
 int operator_autotune(to_problem* P, cudaStream_t s);
+int projsort_lambda(to_problem* P, const void* w, cudaStream_t s);
+size_t projsort_bytes(const to_problem* P);
 int krylov_apply(to_problem* P, const void* b, void* x, cudaStream_t s);
 int launch_richardson(to_problem* P, cudaStream_t s);
 

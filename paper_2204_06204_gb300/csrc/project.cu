@@ -108,6 +108,7 @@ __device__ __forceinline__ void proj_search_start(const ProjPart& tot, double la
     ProjSearch st;
     const double S0 = (double)tot.n[0] * hi + (double)tot.n[1] * lo + tot.s[0];
     if (!isfinite(S0)) set_err(&sc->err, TO_ERR_NONFINITE);
+    sc->proj_active = S0 > vbar && isfinite(S0);
     st.done = !(S0 > vbar) || !isfinite(S0);
     st.have_prev = false;
     st.pU = st.pL = st.pF = 0.0;
@@ -432,7 +433,10 @@ static int project_t(to_problem* P, const void* w, const void* rho_in, const voi
     const double vbar = a.vbar, lo = a.lo, hi = a.hi;
     long long n = a.n;
     DevScalars* sc = P->sc;
-    if (P->cluster16) {
+    if (P->prm.proj_sort) {
+        int rc = projsort_lambda(P, wsrc, s);   // the paper's sort-and-scan form of Algorithm 4
+        if (rc) return rc;
+    } else if (P->cluster16) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(16);
         cfg.blockDim = dim3(1024);
