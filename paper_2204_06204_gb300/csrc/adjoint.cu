@@ -114,11 +114,11 @@ __global__ void k_axpy_out(long long n, const T* __restrict__ u, const T* __rest
         out[i] = u[i] + beta * z[i];
 }
 
-// s = beta lambda / d
+// s = beta lambda / d (dinv = 1 / d)
 template <typename T>
-__global__ void k_adj_s(long long n, const T* __restrict__ lam, const T* __restrict__ d, T beta, T* __restrict__ s) {
+__global__ void k_adj_s(long long n, const T* __restrict__ lam, const T* __restrict__ dinv, T beta, T* __restrict__ s) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        s[i] = beta * lam[i] / d[i];
+        s[i] = beta * lam[i] * dinv[i];
 }
 
 // lambda -= q
@@ -209,7 +209,7 @@ static int backward_t(to_problem* P, double scale, void* g, cudaStream_t s) {
     const dim3 eg = grid3(P->g.nx, P->g.ny, P->g.nz);
     if (Tn == 0) TO_CUDA(cudaMemsetAsync(P->gt, 0, P->n_elem * sizeof(T), s));
     for (int j = Tn - 1; j >= 0; --j) {
-        k_adj_s<T><<<nb, 256, 0, s>>>(P->n_dof, lam, (const T*)P->lv[0].d, (T)beta, sv);
+        k_adj_s<T><<<nb, 256, 0, s>>>(P->n_dof, lam, (const T*)P->lv[0].dinv, (T)beta, sv);
         TO_CUDA(cudaGetLastError());
         k_adjoint_elem<T><<<eg, block3(), 0, s>>>(P->g.nx, P->g.ny, P->g.nz, sv, iterate<T>(P, j), iterate<T>(P, j + 1),
                                                   P->lv[0].mask, (const T*)P->Ed, (T*)P->gt, kh, (T)P->kdiag,

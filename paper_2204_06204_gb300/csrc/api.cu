@@ -1,6 +1,8 @@
 // C entry points (include/to.h): argument checks, device memory owned by the
 // problem, and stream-ordered calls into the kernels.
+#include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 
@@ -118,7 +120,7 @@ extern "C" void to_destroy(to_problem* P) {
     dfree(st);
     for (auto& L : P->lv) {
         dfree(L.E);
-        dfree(L.d);
+        dfree(L.dinv);
         void* mk = L.mask;
         dfree(mk);
         void* tm = L.tmask;
@@ -214,6 +216,8 @@ extern "C" int to_create(const to_grid* g, const to_material* m, const to_loads*
     }
     if (st.size() > 1024) return bail(fail(TO_ERR_ARG, "filter radius too large (more than 1024 stencil points)"));
     P->n_stencil = (int)st.size();
+    P->filter_ext = 0;
+    for (const int4& o : st) P->filter_ext = std::max(P->filter_ext, std::max(std::abs(o.x), std::max(std::abs(o.y), std::abs(o.z))));
 
     // level 0 (the fine grid)
     Level L0{};
@@ -230,7 +234,7 @@ extern "C" int to_create(const to_grid* g, const to_material* m, const to_loads*
         (rc = dalloc(&P->Ed, ne * es)) || (rc = dalloc(&P->Hs, ne * es)) || (rc = dalloc(&P->gt, ne * es)) ||
         (rc = dalloc(&P->grad, ne * es)) || (rc = dalloc(&P->tmp_e, ne * es)) || (rc = dalloc(&P->u, nd * es)) ||
         (rc = dalloc(&P->f, nd * es)) || (rc = dalloc(&P->r, nd * es)) || (rc = dalloc(&P->z, nd * es)) ||
-        (rc = dalloc(&P->q, nd * es)) || (rc = dalloc(&P->tmp_v, nd * es)) || (rc = dalloc(&F.d, nd * es)))
+        (rc = dalloc(&P->q, nd * es)) || (rc = dalloc(&P->tmp_v, nd * es)) || (rc = dalloc(&F.dinv, nd * es)))
         return bail(rc);
     void* mk = nullptr;
     // masks are read as aligned 4-byte words: round the allocation up

@@ -50,7 +50,7 @@ struct BProb {
     const T* gt;
     T* grad;
     const uint8_t* mask;
-    T* d;
+    T* dinv;   // 1 / diag(K^)
     double kdiag;
     T* u;
     T* r;
@@ -107,8 +107,8 @@ __global__ void __launch_bounds__(256) k_b_diag(const BProb<T>* __restrict__ tab
                     s += P.E[ei + (long long)nx * (ej + (long long)ny * ek)];
                 }
         const uint8_t mk = P.mask[n];
-        const T v = (T)P.kdiag * s;
-        for (int c = 0; c < 3; ++c) P.d[3 * n + c] = ((mk >> c) & 1) ? T(1) : v;
+        const T v = T(1) / ((T)P.kdiag * s);
+        for (int c = 0; c < 3; ++c) P.dinv[3 * n + c] = ((mk >> c) & 1) ? T(1) : v;
     }
 }
 
@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(256) k_b_update(const BProb<T>* __restrict__ t
         P.u[i] += beta * P.z[i];
         const T ri = P.r[i] - beta * P.q[i];
         P.r[i] = ri;
-        const T zn = ri / P.d[i];
+        const T zn = ri * P.dinv[i];
         P.z[i] = zn;
         acc += ri * zn;
     }
@@ -315,7 +315,7 @@ int build_tables_t(to_batch* B) {
         b.gt = (const T*)P->gt;
         b.grad = (T*)P->grad;
         b.mask = P->lv[0].mask;
-        b.d = (T*)P->lv[0].d;
+        b.dinv = (T*)P->lv[0].dinv;
         b.kdiag = P->kdiag;
         b.u = (T*)P->u;
         b.r = (T*)P->r;

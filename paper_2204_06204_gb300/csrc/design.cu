@@ -13,73 +13,114 @@ namespace to {
 // PRESCALED: the input already carries the 1 / Hs factor (the fused sensitivity
 // writes g~ / Hs), so the transpose is a plain weighted sum.
 // STATS also reports max |y| and sum y and fixes the step size alpha_k.
+// MODULI also writes E(y) and E'(y) / Hs (the forward filter of the design).
+//
+// A CTA of 32 x 8 threads owns a 32 x 8 column of elements over a chunk of kc z
+// planes.  Its whole input box, kc + 2R planes of (32 + 2R) x (8 + 2R) values
+// (R = the stencil's extent, zeros outside the grid), is copied to shared memory
+// in one asynchronous batch, so that a CTA waits for memory once.  Each tap is a
+// (weight, box offset) pair read as one shared-memory broadcast and applied to
+// four z planes of the thread's column at once; the taps keep the stencil's
+// order, so each output is summed in that order.  The transpose without
+// PRESCALED stages x / Hs.
+constexpr int kFilterPlanes = 4;     // z planes per thread and tap pass
+
+template <typename T>
+struct alignas(2 * sizeof(T)) FTap {
+    T w;
+    int off;   // dz * plane + dy * row + dx in the shared-memory box
+};
+
+// box planes a chunk of kc planes needs: kc rounded up to the tap pass, plus the halo
+__host__ __device__ inline int filter_box_planes(int kchunk, int R) {
+    return (kchunk + kFilterPlanes - 1) / kFilterPlanes * kFilterPlanes + 2 * R;
+}
+
 template <typename T, bool TRANSPOSE, bool STATS, bool PRESCALED, bool MODULI = false>
-__global__ void __launch_bounds__(256) k_filter(int nx, int ny, int nz, const T* __restrict__ x, T* __restrict__ y,
-                                                const T* __restrict__ Hs, const int4* __restrict__ st,
-                                                const T* __restrict__ w, int ns, int R, double* red, unsigned* counter,
-                                                DevScalars* sc, double alpha0_param, double alpha_scale, double m_exp,
-                                                T* Eout = nullptr, T* Edout = nullptr, SimpT<T> simp = SimpT<T>{}) {
+__global__ void __launch_bounds__(256) k_filter(int nx, int ny, int nz, int kchunk, const T* __restrict__ x,
+                                                T* __restrict__ y, const T* __restrict__ Hs,
+                                                const int4* __restrict__ st, const T* __restrict__ w, int ns, int R,
+                                                double* red, unsigned* counter, DevScalars* sc, double alpha0_param,
+                                                double alpha_scale, double m_exp, T* Eout, T* Edout, SimpT<T> simp) {
+    constexpr bool DIV = TRANSPOSE && !PRESCALED;   // the staged value is x / Hs
     __shared__ double sh[32 * kRedQ];
-    // the stencil, padded to a multiple of 8 with zero-weight copies of the centre
     extern __shared__ __align__(16) unsigned char fsm[];
-    const int nsp = (ns + 7) & ~7;
-    int4* s_st = reinterpret_cast<int4*>(fsm);
-    T* s_w = reinterpret_cast<T*>(fsm + (size_t)nsp * sizeof(int4));
-    for (int q = threadIdx.x + 32 * threadIdx.y; q < nsp; q += 256) {
-        s_st[q] = q < ns ? st[q] : make_int4(0, 0, 0, 0);
-        s_w[q] = q < ns ? w[q] : T(0);
+    const int TW = 32 + 2 * R, TH = 8 + 2 * R, PS = TW * TH, NS = filter_box_planes(kchunk, R);
+    FTap<T>* s_tap = reinterpret_cast<FTap<T>*>(fsm);
+    T* box = reinterpret_cast<T*>(fsm + (size_t)ns * sizeof(FTap<T>));   // NS planes of the input
+    T* hbox = box + (size_t)NS * PS;                                     // NS planes of Hs (DIV only)
+    const int tid = threadIdx.x + 32 * threadIdx.y;
+    const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 8;
+    const int k0 = blockIdx.z * kchunk, k1 = min(k0 + kchunk, nz);
+    const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
+    const bool ij_ok = i < nx && j < ny;
+    const long long plane = (long long)nx * ny;
+
+    // planes k0 - R .. k1 + R - 1 into box planes 0 .. k1 - k0 + 2R - 1 (zeros outside the grid)
+    for (int q = tid; q < PS; q += 256) {
+        const int gi = i0 - R + q % TW, gj = j0 - R + q / TW;
+        const bool okij = gi >= 0 && gi < nx && gj >= 0 && gj < ny;
+        const long long base = okij ? gi + (long long)nx * gj : 0;
+        for (int p = k0 - R, b = q; p < k1 + R; ++p, b += PS) {
+            const bool v = okij && p >= 0 && p < nz;
+            const long long e = v ? base + (long long)p * plane : 0;
+            cp_async_t<T>(box + b, x + e, v);
+            if (DIV) cp_async_t<T>(hbox + b, Hs + e, v);
+        }
     }
+    cp_commit();
+    for (int q = tid; q < ns; q += 256) {   // the taps, while the copies are in flight
+        const int4 o = st[q];
+        s_tap[q].w = w[q];
+        s_tap[q].off = o.z * PS + o.y * TW + o.x;
+    }
+    cp_wait<0>();
+    if (DIV)   // x / Hs in place for the words this thread copied
+        for (int q = tid; q < PS; q += 256) {
+            const int gi = i0 - R + q % TW, gj = j0 - R + q / TW;
+            const bool okij = gi >= 0 && gi < nx && gj >= 0 && gj < ny;
+            for (int p = k0 - R, b = q; p < k1 + R; ++p, b += PS)
+                if (okij && p >= 0 && p < nz) box[b] = box[b] / hbox[b];
+        }
     __syncthreads();
+
     T amax = T(0), sum = T(0);   // per-thread partials in the element precision
-    const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y;
-    const bool ij_in = i >= R && i < nx - R && j >= R && j < ny - R;
-    for (int k = blockIdx.z; k < nz && i < nx && j < ny; k += gridDim.z) {
-        const long long e = i + (long long)nx * (j + (long long)ny * k);
-        const bool interior = ij_in && k >= R && k < nz - R;
-        T acc = T(0);
-        // eight stencil points per round, all loads issued before the sums
-        for (int s0 = 0; s0 < nsp; s0 += 8) {
-            T xv[8], hv[8];
-            if (interior) {   // no bounds checks: the linear offsets stay inside the grid
+    const T* col = box + (size_t)R * PS + (threadIdx.y + R) * TW + threadIdx.x + R;   // (i, j, k0) in the box
+    for (int kb = k0; kb < k1; kb += kFilterPlanes) {
+        T acc[kFilterPlanes];
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const long long m = e + s_st[s0 + q].w;
-                    xv[q] = x[m];
-                    hv[q] = (TRANSPOSE && !PRESCALED) ? Hs[m] : T(1);
-                }
-            } else {
+        for (int c = 0; c < kFilterPlanes; ++c) acc[c] = T(0);
+        const T* b0 = col + (size_t)(kb - k0) * PS;
+        T hsv[kFilterPlanes];   // Hs of the outputs, loaded ahead of the taps
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const int4 o = s_st[s0 + q];
-                    const int ii = i + o.x, jj = j + o.y, kk = k + o.z;
-                    const bool ok = ii >= 0 && ii < nx && jj >= 0 && jj < ny && kk >= 0 && kk < nz;
-                    const long long m = e + o.w;
-                    xv[q] = ok ? x[m] : T(0);
-                    hv[q] = (TRANSPOSE && !PRESCALED) ? (ok ? Hs[m] : T(1)) : T(1);
-                }
-            }
+        for (int c = 0; c < kFilterPlanes; ++c)
+            hsv[c] = (!TRANSPOSE && ij_ok && kb + c < k1) ? Hs[i + (long long)nx * (j + (long long)ny * (kb + c))] : T(1);
+#pragma unroll 2
+        for (int q = 0; q < ns; ++q) {
+            const FTap<T> tp = s_tap[q];
+            const T* pp = b0 + tp.off;
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const T wq = s_w[s0 + q];
-                if (TRANSPOSE && !PRESCALED)
-                    acc += wq * xv[q] / hv[q];
-                else
-                    acc += wq * xv[q];
-            }
+            for (int c = 0; c < kFilterPlanes; ++c) acc[c] += tp.w * pp[c * PS];   // planes past k1: discarded
         }
-        const T hs_e = TRANSPOSE ? T(1) : Hs[e];
-        const T out = TRANSPOSE ? acc : acc / hs_e;
-        y[e] = out;
-        if (MODULI) {   // E and E' / Hs (the sensitivity's prescaled factor)
-            T Ee, Ed;
-            simp_moduli(simp, out, Ee, Ed);
-            Eout[e] = Ee;
-            Edout[e] = Ed / hs_e;
-            if (!tfinite(out)) set_err(&sc->err, TO_ERR_NONFINITE);
-        }
-        if (STATS) {
-            amax = tmax(amax, tabs(out));
-            sum += out;
+#pragma unroll
+        for (int c = 0; c < kFilterPlanes; ++c) {
+            const int k = kb + c;
+            if (!ij_ok || k >= k1) continue;
+            const long long e = i + (long long)nx * (j + (long long)ny * k);
+            const T hs_e = hsv[c];
+            const T out = TRANSPOSE ? acc[c] : acc[c] / hs_e;
+            y[e] = out;
+            if (MODULI) {   // E and E' / Hs (the sensitivity's prescaled factor)
+                T Ee, Ed;
+                simp_moduli(simp, out, Ee, Ed);
+                Eout[e] = Ee;
+                Edout[e] = Ed / hs_e;
+                if (!tfinite(out)) set_err(&sc->err, TO_ERR_NONFINITE);
+            }
+            if (STATS) {
+                amax = tmax(amax, tabs(out));
+                sum += out;
+            }
         }
     }
     if (STATS) {
@@ -87,7 +128,7 @@ __global__ void __launch_bounds__(256) k_filter(int nx, int ny, int nz, const T*
         const int kind[2] = {1, 0};
         double tot[2];
         block_reduce<T, 2>(v, kind, reinterpret_cast<T*>(sh));
-        if (finish_reduction<T, 2>(v, kind, red, counter, tot, sh, linear_block(), grid_blocks()) && threadIdx.x == 0 && threadIdx.y == 0) {
+        if (finish_reduction<T, 2>(v, kind, red, counter, tot, sh, linear_block(), grid_blocks()) && tid == 0) {
             sc->gmax = tot[0];
             sc->gsum = tot[1];
             if (!isfinite(tot[0]) || !isfinite(tot[1])) set_err(&sc->err, TO_ERR_NONFINITE);
@@ -100,11 +141,11 @@ __global__ void __launch_bounds__(256) k_filter(int nx, int ny, int nz, const T*
     }
 }
 
-// dynamic shared memory of k_filter: the padded stencil
+// dynamic shared memory of k_filter: the taps, the input box (and the Hs box)
 template <typename T>
-static size_t filter_smem(int ns) {
-    const int nsp = (ns + 7) & ~7;
-    return (size_t)nsp * (sizeof(int4) + sizeof(T));
+static size_t filter_smem(int ns, int R, int kchunk, bool div) {
+    const size_t PS = (size_t)(32 + 2 * R) * (8 + 2 * R), NS = filter_box_planes(kchunk, R);
+    return (size_t)ns * sizeof(FTap<T>) + (div ? 2 : 1) * NS * PS * sizeof(T);
 }
 
 template <typename T>
@@ -136,9 +177,10 @@ __global__ void k_filter_rowsum(int nx, int ny, int nz, T* Hs, const int4* st, c
     }
 }
 
-// diag(K^): kdiag * sum of the moduli of the (up to 8) elements around a node; 1 on fixed DOFs
+// 1 / diag(K^): diag(K^) is kdiag times the sum of the moduli of the (up to 8) elements
+// around a node, 1 on fixed DOFs; one divide per DOF here, multiplications where it is used
 template <typename T>
-__global__ void k_diag(int nx, int ny, int nz, const T* E, const uint8_t* mask, T* d, double kdiag) {
+__global__ void k_diag(int nx, int ny, int nz, const T* E, const uint8_t* mask, T* dinv, double kdiag) {
     const Idx3 t = idx3(nx + 1, ny + 1, nz + 1);
     if (t.ok) {
         const int i = t.i, j = t.j, k = t.k;
@@ -152,8 +194,8 @@ __global__ void k_diag(int nx, int ny, int nz, const T* E, const uint8_t* mask, 
                     s += E[ei + (long long)nx * (ej + (long long)ny * ek)];
                 }
         const uint8_t mk = mask[n];
-        const T v = (T)kdiag * s;
-        for (int c = 0; c < 3; ++c) d[3 * n + c] = ((mk >> c) & 1) ? T(1) : v;
+        const T v = T(1) / ((T)kdiag * s);
+        for (int c = 0; c < 3; ++c) dinv[3 * n + c] = ((mk >> c) & 1) ? T(1) : v;
     }
 }
 
@@ -165,34 +207,44 @@ static int grid_for(long long n, int threads, int num_sms) {
     return (int)b;
 }
 
-template <typename T>
-static int filter_t(to_problem* P, const void* x, void* y, int transpose, int stats, int prescaled, cudaStream_t s) {
-    const T* Hs = (const T*)P->Hs;
-    const T* w = (const T*)P->stencil_w;
-    const int nx = P->g.nx, ny = P->g.ny, nz = P->g.nz;
-    const int R = (int)std::ceil(P->mat.rmin);
-    dim3 grid = grid3(nx, ny, nz);
-    if (stats) {
-        // one reduction slot per block: fold z into the kernel's loop when the grid would exceed the slots
-        const long long per_z = (long long)grid.x * grid.y;
-        long long gz = kMaxRedBlocks / per_z;
-        if (gz < 1) return fail(TO_ERR_ARG, "filter grid exceeds the reduction scratch");
-        if (gz < nz) grid.z = (unsigned)gz;
+// the filter's launch shape: 32 x 8 element columns, each CTA a chunk of z planes
+// (about four CTAs per SM), and its shared memory
+template <typename T, bool TRANSPOSE, bool STATS, bool PRESCALED, bool MODULI>
+static int filter_launch(to_problem* P, const T* x, T* y, cudaStream_t s, T* Eout = nullptr, T* Edout = nullptr) {
+    const int nx = P->g.nx, ny = P->g.ny, nz = P->g.nz, R = P->filter_ext;
+    constexpr bool DIV = TRANSPOSE && !PRESCALED;
+    const int gx = (nx + 31) / 32, gy = (ny + 7) / 8;
+    long long chunks = (4LL * P->num_sms + (long long)gx * gy - 1) / ((long long)gx * gy);
+    if (chunks > nz) chunks = nz;
+    if (chunks < 1) chunks = 1;
+    int kchunk = (int)((nz + chunks - 1) / chunks);
+    while (kchunk > 1 && filter_smem<T>(P->n_stencil, R, kchunk, DIV) > 96 * 1024) --kchunk;   // the box fits
+    chunks = (nz + kchunk - 1) / kchunk;
+    if (STATS && (long long)gx * gy * chunks > kMaxRedBlocks) {
+        kchunk = (int)((nz + kMaxRedBlocks / ((long long)gx * gy) - 1) / (kMaxRedBlocks / ((long long)gx * gy)));
+        chunks = (nz + kchunk - 1) / kchunk;
+        if ((long long)gx * gy * chunks > kMaxRedBlocks) return fail(TO_ERR_ARG, "filter grid exceeds the reduction scratch");
     }
-#define TO_FILTER_ARGS nx, ny, nz, (const T*)x, (T*)y, Hs, P->stencil, w, P->n_stencil, R
-    const size_t fs = filter_smem<T>(P->n_stencil);
-    if (transpose && stats && prescaled)
-        k_filter<T, true, true, true><<<grid, block3(), fs, s>>>(TO_FILTER_ARGS, P->red, P->counters + 2, P->sc,
-                                                                  P->prm.alpha0, P->prm.alpha_scale, P->prm.m);
-    else if (transpose && prescaled)
-        k_filter<T, true, false, true><<<grid, block3(), fs, s>>>(TO_FILTER_ARGS, nullptr, nullptr, nullptr, 0.0, 0.0, 0.0);
-    else if (transpose)
-        k_filter<T, true, false, false><<<grid, block3(), fs, s>>>(TO_FILTER_ARGS, nullptr, nullptr, nullptr, 0.0, 0.0, 0.0);
-    else
-        k_filter<T, false, false, false><<<grid, block3(), fs, s>>>(TO_FILTER_ARGS, nullptr, nullptr, nullptr, 0.0, 0.0, 0.0);
-#undef TO_FILTER_ARGS
+    const size_t fs = filter_smem<T>(P->n_stencil, R, kchunk, DIV);
+    if (fs > 227 * 1024) return fail(TO_ERR_ARG, "filter tile exceeds shared memory (radius too large for this grid)");
+    auto kern = k_filter<T, TRANSPOSE, STATS, PRESCALED, MODULI>;
+    if (fs > 48 * 1024) TO_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fs));
+    const dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)chunks);
+    kern<<<grid, block3(), fs, s>>>(nx, ny, nz, kchunk, x, y, (const T*)P->Hs, P->stencil, (const T*)P->stencil_w,
+                                    P->n_stencil, R, STATS ? P->red : nullptr, STATS ? P->counters + 2 : nullptr, P->sc,
+                                    P->prm.alpha0, P->prm.alpha_scale, P->prm.m, Eout, Edout, simp_params<T>(P->mat));
     TO_CUDA(cudaGetLastError());
     return TO_OK;
+}
+
+template <typename T>
+static int filter_t(to_problem* P, const void* x, void* y, int transpose, int stats, int prescaled, cudaStream_t s) {
+    const T* xi = (const T*)x;
+    T* yo = (T*)y;
+    if (transpose && stats && prescaled) return filter_launch<T, true, true, true, false>(P, xi, yo, s);
+    if (transpose && prescaled) return filter_launch<T, true, false, true, false>(P, xi, yo, s);
+    if (transpose) return filter_launch<T, true, false, false, false>(P, xi, yo, s);
+    return filter_launch<T, false, false, false, false>(P, xi, yo, s);
 }
 
 int launch_filter(to_problem* P, const void* x, void* y, int transpose, cudaStream_t s) {
@@ -212,13 +264,7 @@ int launch_sens_filter_T(to_problem* P, cudaStream_t s) {
 template <typename T>
 static int moduli_t(to_problem* P, cudaStream_t s) {
     // rho~ = C(rho) and the moduli in one pass
-    const int nx = P->g.nx, ny = P->g.ny, nz = P->g.nz;
-    k_filter<T, false, false, false, true><<<grid3(nx, ny, nz), block3(), filter_smem<T>(P->n_stencil), s>>>(
-        nx, ny, nz, (const T*)P->rho, (T*)P->rhot, (const T*)P->Hs, P->stencil, (const T*)P->stencil_w, P->n_stencil,
-        (int)std::ceil(P->mat.rmin), nullptr, nullptr, P->sc, 0.0, 0.0, 0.0, (T*)P->lv[0].E, (T*)P->Ed,
-        simp_params<T>(P->mat));
-    TO_CUDA(cudaGetLastError());
-    return TO_OK;
+    return filter_launch<T, false, false, false, true>(P, (const T*)P->rho, (T*)P->rhot, s, (T*)P->lv[0].E, (T*)P->Ed);
 }
 
 int launch_moduli(to_problem* P, cudaStream_t s) {
@@ -231,7 +277,7 @@ static int diag_t(to_problem* P, int level, cudaStream_t s) {
     const int nb = grid_for(L.n_node, 256, P->num_sms);
     (void)nb;
     k_diag<T><<<grid3(L.nx + 1, L.ny + 1, L.nz + 1), block3(), 0, s>>>(L.nx, L.ny, L.nz, (const T*)L.E, L.mask,
-                                                                      (T*)L.d, L.kdiag);
+                                                                      (T*)L.dinv, L.kdiag);
     TO_CUDA(cudaGetLastError());
     return TO_OK;
 }

@@ -332,4 +332,22 @@ __device__ __forceinline__ Idx3 idx3(int X, int Y, int Z) {
     return r;
 }
 
+// ----------------------------------------------------------------------------- async copies
+__device__ __forceinline__ void cp_async_4(void* smem, const void* gmem, bool valid) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gmem), "r"(valid ? 4 : 0));
+}
+__device__ __forceinline__ void cp_async_8(void* smem, const void* gmem, bool valid) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(gmem), "r"(valid ? 8 : 0));
+}
+template <typename T>
+__device__ __forceinline__ void cp_async_t(T* smem, const T* gmem, bool valid) {
+    if (sizeof(T) == 8) cp_async_8(smem, gmem, valid);
+    else cp_async_4(smem, gmem, valid);
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
 }  // namespace to

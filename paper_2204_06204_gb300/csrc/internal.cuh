@@ -79,7 +79,7 @@ struct Level {
     int64_t n_elem, n_node, n_dof;
     double h;
     void* E = nullptr;        // element moduli (T)
-    void* d = nullptr;        // diag(K^) (T)
+    void* dinv = nullptr;     // 1 / diag(K^) (T): the Jacobi scaling, applied by multiplication
     uint8_t* mask = nullptr;  // per node: bit c set = DOF c fixed
     uint8_t* tmask = nullptr; // per operator tile column: any fixed node in its footprint
     void* x = nullptr;        // V-cycle vectors (T)
@@ -114,6 +114,7 @@ struct to_problem {
     void* grad = nullptr;          // dJ/drho
     void* tmp_e = nullptr;         // element scratch
     int n_stencil = 0;
+    int filter_ext = 0;            // largest |dx|, |dy|, |dz| of the stencil
     int4* stencil = nullptr;       // (dx, dy, dz, -) offsets
     void* stencil_w = nullptr;     // weights (T)
 

@@ -53,10 +53,10 @@ __global__ void k_coarsen_E(int cx, int cy, int cz, const T* __restrict__ Ef, T*
 // b_c = m_c P^T (m_f t), optionally with the coarse level's first sweep
 template <typename T>
 __global__ void k_restrict(int cx, int cy, int cz, const T* __restrict__ tf, const uint8_t* __restrict__ mf,
-                           const uint8_t* __restrict__ mc, T* __restrict__ bc, const T* __restrict__ dc,
+                           const uint8_t* __restrict__ mc, T* __restrict__ bc, const T* __restrict__ dinvc,
                            T* __restrict__ xc, T omega) {
     const Idx3 t = idx3(cx + 1, cy + 1, cz + 1);
-    if (t.ok) restrict_node<T>(cx, cy, cz, t.i, t.j, t.k, tf, mf, mc, bc, dc, xc, omega);
+    if (t.ok) restrict_node<T, long long, true>(cx, cy, cz, t.i, t.j, t.k, tf, mf, mc, bc, dinvc, xc, omega);
 }
 
 // x_f += m_f P (m_c x_c)
@@ -67,11 +67,11 @@ __global__ void k_prolong_add(int cx, int cy, int cz, const T* __restrict__ xc, 
     if (t.ok) prolong_node<T>(cx, cy, cz, t.i, t.j, t.k, xc, mc, mf, xf);
 }
 
-// x = omega D^-1 b  (first Jacobi sweep from x = 0)
+// x = omega D^-1 b  (first Jacobi sweep from x = 0; dinv = D^-1)
 template <typename T>
-__global__ void k_jacobi_first(long long n, const T* __restrict__ b, const T* __restrict__ d, T* __restrict__ x, T omega) {
+__global__ void k_jacobi_first(long long n, const T* __restrict__ b, const T* __restrict__ dinv, T* __restrict__ x, T omega) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        x[i] = omega * b[i] / d[i];
+        x[i] = omega * b[i] * dinv[i];
 }
 
 // dense coarsest operator (fixed rows / columns = identity)
@@ -293,16 +293,34 @@ __global__ void k_dense_solve(const T* __restrict__ Ainv, const T* __restrict__ 
 // Haar factorisation as the operator kernel) into shared memory, then each node
 // adds the contributions of its (up to 8) elements in a fixed order.
 constexpr int kTailMaxLevels = 8;
-constexpr int kTailThreads = 512;
+template <typename T>
+constexpr int tail_threads() { return 512; }   // measured: 1024 FP32 threads are no faster (longer start-up)
 constexpr int kTailMaxElems = 1024;
 constexpr size_t kTailSmem = 220 * 1024;
+
+// q = n / d without a divide: q = mulhi(n, m) with m = ceil(2^32 / d), exact
+// whenever n * d < 2^32 (division by invariant integers using multiplication,
+// Granlund and Montgomery 1994: with n = q d + r and m d = 2^32 + e, 0 <= e < d,
+// n m / 2^32 = q + (r + n e / 2^32) / d and r + n e / 2^32 < r + 1 <= d).
+// m = 0 stands for d = 1.
+struct FastDiv {
+    unsigned d, m;
+};
+inline FastDiv make_fast_div(unsigned d) {
+    FastDiv f;
+    f.d = d;
+    f.m = d > 1 ? (unsigned)(((1ull << 32) + d - 1) / d) : 0u;
+    return f;
+}
+__device__ __forceinline__ unsigned fdiv(unsigned n, FastDiv f) { return f.m ? __umulhi(n, f.m) : n; }
 
 // one level of the tail: its arrays live in shared memory for the whole kernel
 template <typename T>
 struct TailLevel {
     int nx, ny, nz;
+    FastDiv ex, exy, nxd, nxyd;   // element and node index divisors: nx, nx ny, nx+1, (nx+1)(ny+1)
     const T* E;
-    const T* d;
+    const T* dinv;   // 1 / diag(K^) of the level
     const uint8_t* mask;
     T* x;
     T* b;
@@ -314,8 +332,9 @@ struct TailLevel {
 template <typename T>
 struct TailGlobal {
     int nx, ny, nz;
+    FastDiv ex, exy, nxd, nxyd;
     const T* E;
-    const T* d;
+    const T* dinv;
     const uint8_t* mask;
     T* x;              // level 0 of the tail: the result goes back here
     const T* b;        // level 0: the right-hand side
@@ -331,48 +350,72 @@ struct TailArgs {
     T omega;
     const T* inv;        // n_c x n_c scaled inverse, then the n_c scale factors
     int n_c;
+    int inv_smem;        // the inverse (and scale factors) fit in the contribution buffer
     unsigned ocontrib;   // byte offset of the element contributions
     TailGlobal<T> lv[kTailMaxLevels];
 };
 
-// y = x + omega D^-1 (b - K x) (smooth) or y = b - K x on one level; `contrib`
-// holds 24 values per element (component-major: [24][ne])
+// copy `bytes` from global to shared memory: 16-byte asynchronous copies where
+// both ends allow, the rest by plain loads; completed by cp_async_wait_all()
+__device__ __forceinline__ void tail_stage(void* dst, const void* src, unsigned bytes) {
+    unsigned done = 0;
+    if (((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15) == 0) {
+        const unsigned n16 = bytes >> 4;
+        const unsigned base = (unsigned)__cvta_generic_to_shared(dst);
+        for (unsigned q = threadIdx.x; q < n16; q += blockDim.x)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(base + 16 * q),
+                         "l"(static_cast<const char*>(src) + 16 * (size_t)q));
+        done = n16 << 4;
+    }
+    for (unsigned q = done + threadIdx.x; q < bytes; q += blockDim.x)
+        static_cast<unsigned char*>(dst)[q] = static_cast<const unsigned char*>(src)[q];
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// y = x + omega D^-1 (b - K^ x) (smooth) or y = b - K^ x on one level; `contrib`
+// holds 24 values per element (component-major: [24][ne]).  Inside the tail x is
+// zero on every fixed DOF (the restricted right-hand sides are, each sweep maps
+// (x, b) = (0, 0) there to 0, and the prolongation skips those DOFs), so
+// K^ x = K x on the free DOFs and the element gather needs no mask.
 template <typename T>
 __device__ __forceinline__ void tail_operator(const TailLevel<T>& Lv, const HaarK<T>& kh, const T* x, T* y, bool smooth,
                                               T omega, T* contrib) {
     const int nx = Lv.nx, ny = Lv.ny, nz = Lv.nz, nxn = nx + 1, nyn = ny + 1;
     const int ne = nx * ny * nz, nn = nxn * nyn * (nz + 1);
-    constexpr int kOff[8][3] = {{0, 0, 0}, {1, 0, 0}, {1, 1, 0}, {0, 1, 0}, {0, 0, 1}, {1, 0, 1}, {1, 1, 1}, {0, 1, 1}};
-    constexpr int kNode[2][2][2] = {{{0, 4}, {3, 7}}, {{1, 5}, {2, 6}}};
+    const int pl = nxn * nyn;
+    const int off[8] = {0, 1, 1 + nxn, nxn, pl, 1 + pl, 1 + nxn + pl, nxn + pl};   // local node -> node offset
     for (int e = threadIdx.x; e < ne; e += blockDim.x) {
-        const int i = e % nx, j = (e / nx) % ny, k = e / (nx * ny);
+        const int q = (int)fdiv((unsigned)e, Lv.ex), k = (int)fdiv((unsigned)e, Lv.exy);
+        const int i = e - q * nx, j = q - k * ny;
+        const int n0 = i + nxn * (j + nyn * k);
         T u[24];
 #pragma unroll
-        for (int l = 0; l < 8; ++l) {
-            const int n = (i + kOff[l][0]) + nxn * ((j + kOff[l][1]) + nyn * (k + kOff[l][2]));
-            const uint8_t m = Lv.mask[n];
+        for (int l = 0; l < 8; ++l)
 #pragma unroll
-            for (int c = 0; c < 3; ++c) u[3 * l + c] = ((m >> c) & 1) ? T(0) : x[3 * n + c];
-        }
+            for (int c = 0; c < 3; ++c) u[3 * l + c] = x[3 * (n0 + off[l]) + c];
         T yv[24];
         elem_apply_haar(kh.v, Lv.E[e] * Lv.escale, u, yv);
 #pragma unroll
-        for (int q = 0; q < 24; ++q) contrib[q * ne + e] = yv[q];
+        for (int r = 0; r < 24; ++r) contrib[r * ne + e] = yv[r];
     }
     __syncthreads();
+    constexpr int kNode[2][2][2] = {{{0, 4}, {3, 7}}, {{1, 5}, {2, 6}}};
     for (int n = threadIdx.x; n < nn; n += blockDim.x) {
-        const int i = n % nxn, j = (n / nxn) % nyn, k = n / (nxn * nyn);
+        const int q = (int)fdiv((unsigned)n, Lv.nxd), k = (int)fdiv((unsigned)n, Lv.nxyd);
+        const int i = n - q * nxn, j = q - k * nyn;
+        const int e0 = (i - 1) + nx * ((j - 1) + ny * (k - 1));   // element (i-1, j-1, k-1)
         T kx[3] = {T(0), T(0), T(0)};
+        // the elements (i-1+a, j-1+b, k-1+c) around the node, in a fixed order
 #pragma unroll
-        for (int dk = -1; dk <= 0; ++dk)
+        for (int cc = 0; cc < 2; ++cc)
 #pragma unroll
-            for (int dj = -1; dj <= 0; ++dj)
+            for (int bb = 0; bb < 2; ++bb)
 #pragma unroll
-                for (int di = -1; di <= 0; ++di) {
-                    const int ei = i + di, ej = j + dj, ek = k + dk;
-                    if (ei < 0 || ei >= nx || ej < 0 || ej >= ny || ek < 0 || ek >= nz) continue;
-                    const int e = ei + nx * (ej + ny * ek);
-                    const int l = kNode[-di][-dj][-dk];
+                for (int aa = 0; aa < 2; ++aa) {
+                    const bool in = (aa ? i < nx : i > 0) && (bb ? j < ny : j > 0) && (cc ? k < nz : k > 0);
+                    if (!in) continue;
+                    const int e = e0 + aa + nx * (bb + ny * cc);
+                    const int l = kNode[1 - aa][1 - bb][1 - cc];
 #pragma unroll
                     for (int c = 0; c < 3; ++c) kx[c] += contrib[(3 * l + c) * ne + e];
                 }
@@ -381,53 +424,53 @@ __device__ __forceinline__ void tail_operator(const TailLevel<T>& Lv, const Haar
         for (int c = 0; c < 3; ++c) {
             const T xv = x[3 * n + c], bv = Lv.b[3 * n + c];
             const T K = ((m >> c) & 1) ? xv : kx[c];   // K^ is the identity on fixed DOFs
-            y[3 * n + c] = smooth ? xv + omega * (bv - K) / Lv.d[3 * n + c] : bv - K;
+            y[3 * n + c] = smooth ? xv + omega * (bv - K) * Lv.dinv[3 * n + c] : bv - K;
         }
     }
     __syncthreads();
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kTailThreads) k_mg_tail(const TailArgs<T> a, const HaarK<T> kh) {
+__global__ void __launch_bounds__(tail_threads<T>()) k_mg_tail(const TailArgs<T> a, const HaarK<T> kh) {
     extern __shared__ __align__(16) unsigned char tsm[];
     T* contrib = reinterpret_cast<T*>(tsm + a.ocontrib);
     TailLevel<T> lv[kTailMaxLevels];
     T* cur[kTailMaxLevels];
-    // stage every level's moduli, diagonal and mask (and the top level's right-hand side
-    // and first sweep) in shared memory
+    // stage every level's moduli, inverse diagonal and mask (and the top level's right-hand side
+    // and first sweep) in shared memory: all copies in flight at once
+    const bool even = (a.nu1 - 1 + a.nu2) % 2 == 0;   // the first target, so that the last sweep writes x
     for (int t = 0; t < a.nlev; ++t) {
         const TailGlobal<T>& G = a.lv[t];
         TailLevel<T>& L = lv[t];
         L.nx = G.nx;
         L.ny = G.ny;
         L.nz = G.nz;
+        L.ex = G.ex;
+        L.exy = G.exy;
+        L.nxd = G.nxd;
+        L.nxyd = G.nxyd;
         L.escale = G.escale;
         T* E = reinterpret_cast<T*>(tsm + G.oE);
         T* d = reinterpret_cast<T*>(tsm + G.od);
         uint8_t* m = tsm + G.omask;
         L.E = E;
-        L.d = d;
+        L.dinv = d;
         L.mask = m;
         L.x = reinterpret_cast<T*>(tsm + G.ox);
         L.t = reinterpret_cast<T*>(tsm + G.ot);
         L.b = reinterpret_cast<T*>(tsm + G.ob);
-        const int ne = G.nx * G.ny * G.nz, nn = (G.nx + 1) * (G.ny + 1) * (G.nz + 1);
+        const unsigned ne = G.nx * G.ny * G.nz, nn = (G.nx + 1) * (G.ny + 1) * (G.nz + 1);
         if (t + 1 < a.nlev) {
-            for (int q = threadIdx.x; q < ne; q += blockDim.x) E[q] = G.E[q];
-            for (int q = threadIdx.x; q < 3 * nn; q += blockDim.x) d[q] = G.d[q];
+            tail_stage(E, G.E, ne * sizeof(T));
+            tail_stage(d, G.dinv, 3 * nn * sizeof(T));
         }
-        for (int q = threadIdx.x; q < nn; q += blockDim.x) m[q] = G.mask[q];
-    }
-    const bool even = (a.nu1 - 1 + a.nu2) % 2 == 0;   // the first target, so that the last sweep writes x
-    {
-        const TailGlobal<T>& G = a.lv[0];
-        const int nn = (G.nx + 1) * (G.ny + 1) * (G.nz + 1);
-        T* c0 = even ? lv[0].x : lv[0].t;
-        for (int q = threadIdx.x; q < 3 * nn; q += blockDim.x) {
-            lv[0].b[q] = G.b[q];
-            c0[q] = G.first[q];
+        tail_stage(m, G.mask, nn);
+        if (t == 0) {
+            tail_stage(L.b, G.b, 3 * nn * sizeof(T));
+            tail_stage(even ? L.x : L.t, G.first, 3 * nn * sizeof(T));
         }
     }
+    cp_async_wait_all();
     __syncthreads();
     const TailLevel<T>* tl = lv;
     // down: the first sweep of lv[0] came with its restriction, later ones come from ours
@@ -443,21 +486,47 @@ __global__ void __launch_bounds__(kTailThreads) k_mg_tail(const TailArgs<T> a, c
             o = sw;
         }
         tail_operator<T>(F, kh, c, o, false, a.omega, contrib);
+        // before the last restriction: the coarsest inverse starts its way into the
+        // (now idle) contribution buffer
+        if (t + 2 == a.nlev && a.inv_smem) tail_stage(contrib, a.inv, (unsigned)((a.n_c + 1) * a.n_c * sizeof(T)));
         T* xc = t + 2 < a.nlev ? (even ? C.x : C.t) : nullptr;
-        const int X = C.nx + 1, Y = C.ny + 1, Z = C.nz + 1;
-        for (int n = threadIdx.x; n < X * Y * Z; n += blockDim.x)
-            restrict_node<T>(C.nx, C.ny, C.nz, n % X, (n / X) % Y, n / (X * Y), o, F.mask, C.mask, C.b, C.d, xc, a.omega);
+        const int X = C.nx + 1, nnc = X * (C.ny + 1) * (C.nz + 1);
+        for (int n = threadIdx.x; n < nnc; n += blockDim.x) {
+            const int q = (int)fdiv((unsigned)n, C.nxd), K = (int)fdiv((unsigned)n, C.nxyd);
+            restrict_node<T, int, true>(C.nx, C.ny, C.nz, n - q * X, q - K * (C.ny + 1), K, o, F.mask, C.mask, C.b, C.dinv,
+                                        xc, a.omega);
+        }
         __syncthreads();
         cur[t] = c;
     }
-    // the coarsest level: x = S A^-1 S b, one warp per row (lane-strided sums, shuffle tree)
+    // the coarsest level: x = S A^-1 S b, one warp per row (lane-strided sums, shuffle tree);
+    // s_j b_j first, then eight columns per lane in flight
     {
         const TailLevel<T>& Cst = tl[a.nlev - 1];
         const int n = a.n_c, lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-        const T* sc = a.inv + (size_t)n * n;
+        if (a.inv_smem) cp_async_wait_all();
+        const T* inv = a.inv_smem ? contrib : a.inv;
+        const T* sc = inv + (size_t)n * n;
+        T* sb = Cst.t;
+        __syncthreads();
+        for (int j = threadIdx.x; j < n; j += blockDim.x) sb[j] = sc[j] * Cst.b[j];
+        __syncthreads();
         for (int i = wid; i < n; i += nw) {
+            const T* row = inv + (size_t)i * n;
             T acc = T(0);
-            for (int j = lane; j < n; j += 32) acc += a.inv[(long long)i * n + j] * sc[j] * Cst.b[j];
+            for (int j0 = 0; j0 < n; j0 += 8 * 32) {
+                T v[8];
+#pragma unroll
+                for (int r = 0; r < 8; ++r) {
+                    const int j = j0 + 32 * r + lane;
+                    v[r] = j < n ? row[j] : T(0);
+                }
+#pragma unroll
+                for (int r = 0; r < 8; ++r) {
+                    const int j = j0 + 32 * r + lane;
+                    acc += j < n ? v[r] * sb[j] : T(0);
+                }
+            }
             for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
             if (lane == 0) Cst.x[i] = sc[i] * acc;
         }
@@ -469,9 +538,11 @@ __global__ void __launch_bounds__(kTailThreads) k_mg_tail(const TailArgs<T> a, c
         const TailLevel<T>& C = tl[t + 1];
         T* c = cur[t];
         T* o = c == F.x ? F.t : F.x;
-        const int X = 2 * C.nx + 1, Y = 2 * C.ny + 1, Z = 2 * C.nz + 1;
-        for (int n = threadIdx.x; n < X * Y * Z; n += blockDim.x)
-            prolong_node<T>(C.nx, C.ny, C.nz, n % X, (n / X) % Y, n / (X * Y), C.x, C.mask, F.mask, c);
+        const int X = F.nx + 1, nnf = X * (F.ny + 1) * (F.nz + 1);
+        for (int n = threadIdx.x; n < nnf; n += blockDim.x) {
+            const int q = (int)fdiv((unsigned)n, F.nxd), k = (int)fdiv((unsigned)n, F.nxyd);
+            prolong_node<T, int>(C.nx, C.ny, C.nz, n - q * X, q - k * (F.ny + 1), k, C.x, C.mask, F.mask, c);
+        }
         __syncthreads();
         for (int it = 0; it < a.nu2; ++it) {
             tail_operator<T>(F, kh, c, o, true, a.omega, contrib);
@@ -509,8 +580,12 @@ static size_t tail_layout(const to_problem* P, int l0, TailArgs<T>* a) {
             g.nx = F.nx;
             g.ny = F.ny;
             g.nz = F.nz;
+            g.ex = make_fast_div((unsigned)F.nx);
+            g.exy = make_fast_div((unsigned)(F.nx * F.ny));
+            g.nxd = make_fast_div((unsigned)(F.nx + 1));
+            g.nxyd = make_fast_div((unsigned)((F.nx + 1) * (F.ny + 1)));
             g.E = (const T*)F.E;
-            g.d = (const T*)F.d;
+            g.dinv = (const T*)F.dinv;
             g.mask = F.mask;
             g.x = (T*)F.x;
             g.b = (const T*)F.b;
@@ -577,7 +652,7 @@ int mg_build(to_problem* P) {
         if (e == cudaSuccess) e = cudaMalloc(&x, C.n_dof * es);
         if (e == cudaSuccess) e = cudaMalloc(&b, C.n_dof * es);
         if (e == cudaSuccess) e = cudaMalloc(&t, C.n_dof * es);
-        C.E = E; C.d = d; C.mask = (uint8_t*)mk; C.x = x; C.b = b; C.t = t;
+        C.E = E; C.dinv = d; C.mask = (uint8_t*)mk; C.x = x; C.b = b; C.t = t;
         P->lv.push_back(C);
         if (e != cudaSuccess) return fail(TO_ERR_CUDA, std::string("multigrid allocation: ") + cudaGetErrorString(e));
         if (cudaMemcpy(mk, mc.data(), mc.size(), cudaMemcpyHostToDevice) != cudaSuccess)
@@ -617,6 +692,7 @@ int mg_build(to_problem* P) {
     P->mg_tail = 0;
     for (int l = 1; l + 1 < L && L - l <= kTailMaxLevels; ++l) {
         if (P->lv[l].n_elem > kTailMaxElems) continue;
+        if ((unsigned long long)P->lv[l].n_node * (unsigned long long)P->lv[l].n_node >= (1ull << 32)) continue;   // FastDiv range
         const size_t tsm = P->prec == TO_FP64 ? tail_layout<double>(P, l, nullptr) : tail_layout<float>(P, l, nullptr);
         if (tsm > kTailSmem) break;
         cudaError_t e = P->prec == TO_FP64
@@ -678,11 +754,12 @@ static int tail_t(to_problem* P, cudaStream_t s) {
     a.omega = (T)P->prm.mg_omega;
     a.inv = (const T*)P->coarse_L;
     a.n_c = P->n_coarse;
+    a.inv_smem = (size_t)(a.n_c + 1) * a.n_c <= (size_t)24 * P->lv[l0].n_elem;
     const size_t tsm = tail_layout<T>(P, l0, &a);
     HaarK<T> kh;
     for (int q = 0; q < kHaarNnz; ++q) kh.v[q] = (T)P->haar[q];
     TO_CUDA(cudaStreamWaitEvent(s, P->ev_join, 0));   // the inverse of this design is ready
-    k_mg_tail<T><<<1, kTailThreads, tsm, s>>>(a, kh);
+    k_mg_tail<T><<<1, tail_threads<T>(), tsm, s>>>(a, kh);
     TO_CUDA(cudaGetLastError());
     return TO_OK;
 }
@@ -710,7 +787,7 @@ static int vcycle_t(to_problem* P, int l, const void* b, void* x, void* t, cudaS
     void* cur = ((nu1 - 1 + nu2) % 2 == 0) ? x : t;
     void* oth = cur == x ? t : x;
     if (!first_done) {
-        k_jacobi_first<T><<<grid1(F.n_dof, P->num_sms), 256, 0, s>>>(F.n_dof, (const T*)b, (const T*)F.d, (T*)cur, (T)om);
+        k_jacobi_first<T><<<grid1(F.n_dof, P->num_sms), 256, 0, s>>>(F.n_dof, (const T*)b, (const T*)F.dinv, (T*)cur, (T)om);
         TO_CUDA(cudaGetLastError());
     }
     for (int it = 1; it < nu1; ++it) {
@@ -724,7 +801,7 @@ static int vcycle_t(to_problem* P, int l, const void* b, void* x, void* t, cudaS
     const bool fuse = l + 1 < L - 1;
     void* cfirst = ((nu1 - 1 + nu2) % 2 == 0) ? C.x : C.t;
     k_restrict<T><<<grid3(C.nx + 1, C.ny + 1, C.nz + 1), block3(), 0, s>>>(
-        C.nx, C.ny, C.nz, (const T*)oth, F.mask, C.mask, (T*)C.b, (const T*)C.d, fuse ? (T*)cfirst : nullptr, (T)om);
+        C.nx, C.ny, C.nz, (const T*)oth, F.mask, C.mask, (T*)C.b, (const T*)C.dinv, fuse ? (T*)cfirst : nullptr, (T)om);
     TO_CUDA(cudaGetLastError());
     if (P->mg_tail == l + 1) {
         if ((rc = tail_t<T>(P, s))) return rc;   // levels l+1 .. L-1 in one CTA

@@ -34,7 +34,7 @@ struct OpArgs {
     const T* x;
     T* y;
     const T* b;       // f (RESID) or right-hand side (SMOOTH / BMINUS)
-    const T* d;       // diag(K^) (RESID with Jacobi z, SMOOTH)
+    const T* dinv;    // 1 / diag(K^) (RESID with Jacobi z, SMOOTH)
     T* z;             // RESID: z = r / d (optional)
     const T* E;
     const T* Ed;      // RESID: dE/drho~ for the fused sensitivity (optional)
@@ -110,24 +110,6 @@ __device__ __forceinline__ void face_forward4(const N4& a00, const N4& a10, cons
     F.z[3] = zd1 - zd0;
 }
 
-// ----------------------------------------------------------------------------- async copies
-__device__ __forceinline__ void cp_async_4(void* smem, const void* gmem, bool valid) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gmem), "r"(valid ? 4 : 0));
-}
-__device__ __forceinline__ void cp_async_8(void* smem, const void* gmem, bool valid) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(gmem), "r"(valid ? 8 : 0));
-}
-template <typename T>
-__device__ __forceinline__ void cp_async_t(T* smem, const T* gmem, bool valid) {
-    if (sizeof(T) == 8) cp_async_8(smem, gmem, valid);
-    else cp_async_4(smem, gmem, valid);
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-template <int N>
-__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
-
 // Shared-memory layout of the operator kernel (NB-deep ring of staged planes).
 template <typename T, int TX, int TY, int NB>
 struct OpSmem {
@@ -137,7 +119,7 @@ struct OpSmem {
     uint32_t mword[NB][PN];    // 4-byte word holding each node's mask byte
     T ebuf[NB][TY][TX];        // element moduli of the CTA's columns, per layer
     T eb[NB][TY][TX][3];       // epilogue right-hand side at the owned node
-    T ed[NB][TY][TX][3];       // epilogue diagonal at the owned node
+    T ed[NB][TY][TX][3];       // epilogue inverse diagonal at the owned node
     N4 ybuf[TY][TX];
     double red[32 * kRedQ];
 };
@@ -177,7 +159,7 @@ __device__ __forceinline__ void op_body(const OpArgs<T>& a, const HaarK<T>& kh, 
     const bool owner = tx < TX - 1 && ty < TY - 1 && ni < nxn && nj < nyn;
     const long long own_base = (long long)ni + (long long)nxn * nj;
     const long long elem_base = col_in ? (long long)ie + (long long)a.nx * je : 0;
-    const bool dz = NEED_D && a.d != nullptr && (MODE != OP_RESID || a.z != nullptr);
+    const bool dz = NEED_D && a.dinv != nullptr && (MODE != OP_RESID || a.z != nullptr);
     // tiles whose footprint holds no fixed node skip every mask operation
     const bool hm = a.tmask == nullptr || a.tmask[bx + ((a.nx + 1 + TX - 2) / (TX - 1)) * by] != 0;
 
@@ -196,7 +178,7 @@ __device__ __forceinline__ void op_body(const OpArgs<T>& a, const HaarK<T>& kh, 
     }
     const T* e_src = a.E + elem_base;
     const T* b_src = NEED_B ? a.b + 3 * own_base : nullptr;
-    const T* d_src = dz ? a.d + 3 * own_base : nullptr;
+    const T* d_src = dz ? a.dinv + 3 * own_base : nullptr;
 
     // all asynchronous copies that plane p (and element layer p-1) needs, into ring slot SP
     auto issue = [&](int p, auto SPc) {
@@ -228,7 +210,7 @@ __device__ __forceinline__ void op_body(const OpArgs<T>& a, const HaarK<T>& kh, 
                 for (int c = 0; c < 3; ++c) cp_async_t<T>(&sm.eb[SP][ty][tx][c], ov ? b_src + 3 * pn + c : a.b, ov);
             if (dz)
 #pragma unroll
-                for (int c = 0; c < 3; ++c) cp_async_t<T>(&sm.ed[SP][ty][tx][c], ov ? d_src + 3 * pn + c : a.d, ov);
+                for (int c = 0; c < 3; ++c) cp_async_t<T>(&sm.ed[SP][ty][tx][c], ov ? d_src + 3 * pn + c : a.dinv, ov);
         }
         cp_commit();
     };
@@ -403,7 +385,7 @@ __device__ __forceinline__ void op_body(const OpArgs<T>& a, const HaarK<T>& kh, 
                     yo[c] = sm.eb[SB][ty][tx][c] - Kx;
                 } else if (MODE == OP_SMOOTH) {
                     const T bv = sm.eb[SB][ty][tx][c];
-                    const T yv = xv + a.omega * (bv - Kx) / sm.ed[SB][ty][tx][c];
+                    const T yv = xv + a.omega * (bv - Kx) * sm.ed[SB][ty][tx][c];
                     yo[c] = yv;
                     acc0 = fma(bv, yv, acc0);
                 } else if (MODE == OP_RESID) {
@@ -411,7 +393,7 @@ __device__ __forceinline__ void op_body(const OpArgs<T>& a, const HaarK<T>& kh, 
                     const T rv2 = bv - Kx;
                     yo[c] = rv2;
                     if (a.z) {
-                        const T zv = rv2 / sm.ed[SB][ty][tx][c];
+                        const T zv = rv2 * sm.ed[SB][ty][tx][c];
                         a.z[3 * (own_base + (long long)k * nplane) + c] = zv;
                         acc0 = fma(rv2, zv, acc0);
                     }
@@ -520,7 +502,7 @@ static int launch_t(to_problem* P, int level, int mode, const void* x, void* y, 
     a.x = (const T*)x;
     a.y = (T*)y;
     a.b = (const T*)b;
-    a.d = (const T*)L.d;
+    a.dinv = (const T*)L.dinv;
     a.E = (const T*)L.E;
     a.mask = L.mask;
     a.tmask = L.tmask;
@@ -709,7 +691,7 @@ static OpArgs<T> batch_args(to_problem* P, int mode, int first, int kchunk) {
     a.E = (const T*)L.E;
     a.mask = L.mask;
     a.tmask = L.tmask;
-    a.d = (const T*)L.d;
+    a.dinv = (const T*)L.dinv;
     a.red = P->red;
     a.sc = P->sc;
     a.first_step = first;

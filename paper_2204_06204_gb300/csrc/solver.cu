@@ -26,10 +26,10 @@ static int grid_1d(long long n, int threads, int num_sms) {
     return (int)(b < 1 ? 1 : b);
 }
 
-// u += beta z; r -= beta q; (Jacobi) z = r / d and r^T z
+// u += beta z; r -= beta q; (Jacobi) z = r / d and r^T z (dinv = 1 / d)
 template <typename T, bool JACOBI>
 __global__ void __launch_bounds__(256) k_update_sd(long long n, T* __restrict__ u, T* __restrict__ r, T* __restrict__ z,
-                                                   const T* __restrict__ q, const T* __restrict__ d, double* red,
+                                                   const T* __restrict__ q, const T* __restrict__ dinv, double* red,
                                                    unsigned* counter, DevScalars* sc) {
     __shared__ double sh[32 * kRedQ];
     __shared__ T s_beta;
@@ -43,7 +43,7 @@ __global__ void __launch_bounds__(256) k_update_sd(long long n, T* __restrict__ 
         const T ri = r[i] - beta * q[i];
         r[i] = ri;
         if (JACOBI) {
-            const T zn = ri / d[i];
+            const T zn = ri * dinv[i];
             z[i] = zn;
             acc += ri * zn;
         }
@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(256) k_update_sd(long long n, T* __restrict__ 
 // pass); keeps the previous r^T z, and with the Jacobi M also z = r / d and the new r^T z
 template <typename T, bool JACOBI>
 __global__ void __launch_bounds__(256) k_cg_update(long long n, T* __restrict__ u, T* __restrict__ r, T* __restrict__ z,
-                                                   const T* __restrict__ p, const T* __restrict__ q, const T* __restrict__ d,
+                                                   const T* __restrict__ p, const T* __restrict__ q, const T* __restrict__ dinv,
                                                    double* red, unsigned* counter, DevScalars* sc) {
     __shared__ double sh[32 * kRedQ];
     __shared__ T s_alpha;
@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(256) k_cg_update(long long n, T* __restrict__ 
         const T ri = r[i] - alpha * q[i];
         r[i] = ri;
         if (JACOBI) {
-            const T zn = ri / d[i];
+            const T zn = ri * dinv[i];
             z[i] = zn;
             acc += ri * zn;
         }
@@ -164,10 +164,10 @@ static int update_t(to_problem* P, void* u, cudaStream_t s) {
     const int nb = grid_1d(P->n_dof, 256, P->num_sms);
     if (P->prm.precond == TO_PRECOND_JACOBI)
         k_update_sd<T, true><<<nb, 256, 0, s>>>(P->n_dof, (T*)u, (T*)P->r, (T*)P->z, (const T*)P->q,
-                                                (const T*)P->lv[0].d, P->red, P->counters + 4, P->sc);
+                                                (const T*)P->lv[0].dinv, P->red, P->counters + 4, P->sc);
     else
         k_update_sd<T, false><<<nb, 256, 0, s>>>(P->n_dof, (T*)u, (T*)P->r, (T*)P->z, (const T*)P->q,
-                                                 (const T*)P->lv[0].d, P->red, P->counters + 4, P->sc);
+                                                 (const T*)P->lv[0].dinv, P->red, P->counters + 4, P->sc);
     TO_CUDA(cudaGetLastError());
     return TO_OK;
 }
@@ -197,12 +197,12 @@ int launch_precond(to_problem* P, const void*, void*, cudaStream_t s) {
     return P->prec == TO_FP64 ? precond_t<double>(P, s) : precond_t<float>(P, s);
 }
 
-// out = in / d (the Jacobi M^-1 as a separate pass)
+// out = in / d (the Jacobi M^-1 as a separate pass; dinv = 1 / d)
 template <typename T>
-__global__ void __launch_bounds__(256) k_div_diag(long long n, const T* __restrict__ in, const T* __restrict__ d,
+__global__ void __launch_bounds__(256) k_mul_dinv(long long n, const T* __restrict__ in, const T* __restrict__ dinv,
                                                   T* __restrict__ out) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        out[i] = in[i] / d[i];
+        out[i] = in[i] * dinv[i];
 }
 
 // out = M^-1 in for any preconditioner (in and out distinct)
@@ -216,7 +216,7 @@ static int apply_M_t(to_problem* P, const void* in, void* out, cudaStream_t s) {
             TO_CUDA(cudaMemcpyAsync(out, in, P->n_dof * sizeof(T), cudaMemcpyDeviceToDevice, s));
             return TO_OK;
         default:
-            k_div_diag<T><<<nb, 256, 0, s>>>(P->n_dof, (const T*)in, (const T*)P->lv[0].d, (T*)out);
+            k_mul_dinv<T><<<nb, 256, 0, s>>>(P->n_dof, (const T*)in, (const T*)P->lv[0].dinv, (T*)out);
             TO_CUDA(cudaGetLastError());
             return TO_OK;
     }
@@ -240,11 +240,11 @@ int run_inner(to_problem* P, void* u, int nsteps, int primary, cudaStream_t s) {
         for (int it = 0; it < nsteps; ++it) {
             if ((rc = launch_operator(P, 0, OP_Q, P->tmp_v, P->q, nullptr, s, 0.0, it == 0))) return rc;
             if (P->prec == TO_FP64) {
-                if (jac) k_cg_update<double, true><<<nb, 256, 0, s>>>(P->n_dof, (double*)u, (double*)P->r, (double*)P->z, (const double*)P->tmp_v, (const double*)P->q, (const double*)P->lv[0].d, P->red, P->counters + 4, P->sc);
-                else k_cg_update<double, false><<<nb, 256, 0, s>>>(P->n_dof, (double*)u, (double*)P->r, (double*)P->z, (const double*)P->tmp_v, (const double*)P->q, (const double*)P->lv[0].d, P->red, P->counters + 4, P->sc);
+                if (jac) k_cg_update<double, true><<<nb, 256, 0, s>>>(P->n_dof, (double*)u, (double*)P->r, (double*)P->z, (const double*)P->tmp_v, (const double*)P->q, (const double*)P->lv[0].dinv, P->red, P->counters + 4, P->sc);
+                else k_cg_update<double, false><<<nb, 256, 0, s>>>(P->n_dof, (double*)u, (double*)P->r, (double*)P->z, (const double*)P->tmp_v, (const double*)P->q, (const double*)P->lv[0].dinv, P->red, P->counters + 4, P->sc);
             } else {
-                if (jac) k_cg_update<float, true><<<nb, 256, 0, s>>>(P->n_dof, (float*)u, (float*)P->r, (float*)P->z, (const float*)P->tmp_v, (const float*)P->q, (const float*)P->lv[0].d, P->red, P->counters + 4, P->sc);
-                else k_cg_update<float, false><<<nb, 256, 0, s>>>(P->n_dof, (float*)u, (float*)P->r, (float*)P->z, (const float*)P->tmp_v, (const float*)P->q, (const float*)P->lv[0].d, P->red, P->counters + 4, P->sc);
+                if (jac) k_cg_update<float, true><<<nb, 256, 0, s>>>(P->n_dof, (float*)u, (float*)P->r, (float*)P->z, (const float*)P->tmp_v, (const float*)P->q, (const float*)P->lv[0].dinv, P->red, P->counters + 4, P->sc);
+                else k_cg_update<float, false><<<nb, 256, 0, s>>>(P->n_dof, (float*)u, (float*)P->r, (float*)P->z, (const float*)P->tmp_v, (const float*)P->q, (const float*)P->lv[0].dinv, P->red, P->counters + 4, P->sc);
             }
             TO_CUDA(cudaGetLastError());
             if (it + 1 == nsteps) break;

@@ -79,6 +79,24 @@ def test_filter_forward_and_transpose(precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_filter_multi_tile_ragged(precision):
+    """Grids spanning several 32 x 8 tiles and z chunks with ragged edges (100 = 3 * 32 + 4,
+    50 = 6 * 8 + 2, 37 planes in chunks of 2), for both radii of the workloads."""
+    fb = _fb()
+    for dims, r in (((100, 50, 37), 1.5), ((70, 30, 21), 2.5)):
+        pb = W.cantilever(*dims, rmin=r)
+        prec = fb.TO_FP64 if precision == "fp64" else fb.TO_FP32_MIXED
+        with _problem(pb, prec) as P:
+            H, Hs = filt.filter_matrix(*dims, r)
+            x = W.random_rho(pb.n_elem, -1.0, 1.0)
+            tol = 1e-13 if prec == fb.TO_FP64 else 2e-6
+            for tr in (False, True):
+                y = P.filter(_t(x, P), transpose=tr).cpu().numpy()
+                yref = filt.filter_transpose(H, Hs, x) if tr else filt.filter_forward(H, Hs, x)
+                assert np.abs(y - yref).max() <= tol * max(np.abs(yref).max(), 1.0)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_sensitivity(precision):
     fb = _fb()
     pb = W.cantilever(12, 6, 5)
