@@ -124,8 +124,10 @@ typedef struct {
  *   tile_x, tile_y, tile_z   node planes per operator tile (tile_z): > 0 fixed; 0: picked
  *               per multigrid level by an autotuner at to_create (the sweep is timed for
  *               1 .. 32 planes and the cost model's choice); < 0 (the default): the cost
- *               model alone (waves of resident CTAs x planes walked).  tile_x / tile_y are
- *               reserved (the tile is 32 x 8 threads)
+ *               model alone (waves of resident CTAs x planes walked).  In a batch
+ *               (to_batch_create) the first problem's tile_z > 0 fixes the batched
+ *               launches' planes per tile; otherwise the batch autotunes it.  tile_x /
+ *               tile_y are reserved (the tile is 32 x 8 threads)
  *   no_graph    0: to_step replays one captured CUDA graph per outer iteration;
  *               1: to_step launches the kernels one by one
  *   krylov_dim  D of Eq. (LSP), 0 <= D <= 30 (the paper uses 20); it costs D + 1
@@ -225,11 +227,14 @@ int to_set_state(to_problem* P, const void* rho_dev, const void* u_dev, int64_t 
  * advances it: Algorithms 1 / 3 with its own lambda, beta, alpha and state).
  * to_batch_create groups existing problems (not copied, not owned: destroy the
  * batch before its problems).  They must share precision, device, element
- * size h, E0 / Emin / p / nu and n_inner, and use TO_PRECOND_JACOBI with
- * TO_INNER_SD; grids, loads, fixtures, volume fractions and filter radii may
- * differ.  to_batch_step runs n_outer outer iterations of every problem with
- * one kernel launch per phase for the whole batch (captured once as a CUDA
- * graph); stats_out (may be NULL) receives n problems x n_outer records,
+ * size h, E0 / Emin / p / nu and n_inner, and use TO_INNER_SD with the same
+ * preconditioner: TO_PRECOND_JACOBI, or TO_PRECOND_MG with the same nu_pre,
+ * nu_post and omega, every grid halving at least twice (each problem's coarse
+ * levels below 1024 elements run as one CTA, all problems' in one launch;
+ * TO_ERR_ARG otherwise); grids, loads, fixtures, volume fractions, filter
+ * radii and multigrid depths may differ.  to_batch_step runs n_outer outer
+ * iterations of every problem with one kernel launch per phase (per multigrid
+ * step and level) for the whole batch (captured once as a CUDA graph); stats_out (may be NULL) receives n problems x n_outer records,
  * problem-major, and then the call synchronises.  n_outer must not exceed any
  * problem's stats ring (256 after to_create; a longer to_step grows it). */
 int to_batch_create(to_problem* const* problems, int32_t n, to_batch** out);

@@ -12,7 +12,7 @@ namespace to {
 int project_coop_blocks(int prec, int num_sms, int* out);
 int launch_rowsum(to_problem* P, cudaStream_t s);
 int run_inner(to_problem* P, void* u, int nsteps, int primary, cudaStream_t s);
-int refresh_preconditioner(to_problem* P, cudaStream_t s);
+int refresh_preconditioner(to_problem* P, cudaStream_t s, bool join = true);
 int launch_filter_prescaled_T(to_problem* P, const void* x, void* y, cudaStream_t s);
 
 namespace {

@@ -8,15 +8,19 @@
 // clusters).  Phases, per outer iteration:
 //   design   rho -> rho~ -> E, E'/Hs            k_b_design
 //   diag     Jacobi diagonal                     k_b_diag
+//   (multigrid: coarse moduli and diagonals, dense coarsest operators and their
+//    inverses, one launch per step and level; see the batched multigrid in mg.cu)
 //   resid    r = f - K u, z = r/d, sensitivity   k_operator_batch<OP_RESID>
-//   n_inner x (Q apply, update)                  k_operator_batch<OP_Q>, k_b_update
+//   (multigrid: z = V-cycle(r), r^T z in its last sweep)
+//   n_inner x (Q apply, update[, V-cycle])       k_operator_batch<OP_Q>, k_b_update
 //   filterT  g = C^T g~, ||g||_inf, alpha_k      k_b_filter_T
 //   project  one thread-block cluster per problem (distributed shared memory
 //            for the pass totals: no grid-wide barrier between problems)
 //   record   per-problem stats                    k_b_record
-// Requirements: every problem uses the Jacobi preconditioner and steepest
-// descent with the same n_inner, the same precision, device, element size and
-// material moduli (the element matrix constants are common to the launch).
+// Requirements: every problem uses steepest descent with the same n_inner and
+// the same preconditioner (Jacobi, or multigrid with the same smoothing
+// parameters), the same precision, device, element size and material moduli
+// (the element matrix constants are common to the launch).
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -112,8 +116,8 @@ __global__ void __launch_bounds__(256) k_b_diag(const BProb<T>* __restrict__ tab
     }
 }
 
-// u += beta z, r -= beta q, z = r / d, and r^T z per problem
-template <typename T>
+// u += beta z, r -= beta q and (Jacobi) z = r / d with r^T z, per problem
+template <typename T, bool JACOBI>
 __global__ void __launch_bounds__(256) k_b_update(const BProb<T>* __restrict__ tab) {
     __shared__ double sh[32 * kRedQ];
     const BProb<T>& P = tab[blockIdx.y];
@@ -126,10 +130,13 @@ __global__ void __launch_bounds__(256) k_b_update(const BProb<T>* __restrict__ t
         P.u[i] += beta * P.z[i];
         const T ri = P.r[i] - beta * P.q[i];
         P.r[i] = ri;
-        const T zn = ri * P.dinv[i];
-        P.z[i] = zn;
-        acc += ri * zn;
+        if (JACOBI) {
+            const T zn = ri * P.dinv[i];
+            P.z[i] = zn;
+            acc += ri * zn;
+        }
     }
+    if (!JACOBI) return;
     T v[1] = {acc};
     const int kind[1] = {0};
     double tot[1];
@@ -285,6 +292,7 @@ struct to_batch {
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     cudaGraphExec_t gexec = nullptr;
     int graph_state = 0;
+    to::BatchMG* mg = nullptr;            // batched multigrid tables (multigrid batches)
 };
 
 using namespace to;
@@ -359,13 +367,17 @@ int iteration_t(to_batch* B, cudaStream_t s) {
     k_b_design<T><<<g2, 256, 0, s>>>(tab, simp_params<T>(P0->mat));
     k_b_diag<T><<<g2, 256, 0, s>>>(tab);
     TO_CUDA(cudaGetLastError());
-    int rc = batch_operator_launch(B->prec, OP_RESID, B->tab_resid, B->kh, B->max_tiles, B->n, s);
-    if (rc) return rc;
+    int rc;
+    if (B->mg && (rc = batch_mg_refresh(B->mg, s))) return rc;
+    if ((rc = batch_operator_launch(B->prec, OP_RESID, B->tab_resid, B->kh, B->max_tiles, B->n, s))) return rc;
+    if (B->mg && (rc = batch_mg_vcycle(B->mg, s))) return rc;
     for (int it = 0; it < B->n_inner; ++it) {
         rc = batch_operator_launch(B->prec, OP_Q, it == 0 ? B->tab_q_first : B->tab_q, B->kh, B->max_tiles, B->n, s);
         if (rc) return rc;
-        k_b_update<T><<<g2, 256, 0, s>>>(tab);
+        if (B->mg) k_b_update<T, false><<<g2, 256, 0, s>>>(tab);
+        else k_b_update<T, true><<<g2, 256, 0, s>>>(tab);
         TO_CUDA(cudaGetLastError());
+        if (B->mg && it + 1 < B->n_inner && (rc = batch_mg_vcycle(B->mg, s))) return rc;
     }
     k_b_filter_T<T><<<g2, 256, 0, s>>>(tab);
     if ((rc = launch_cluster_project<T>(tab, B->n, kClusterCTAs, 256, B->proj_cache, B->proj_smem, s))) return rc;
@@ -385,6 +397,7 @@ void destroy_batch(to_batch* B) {
     for (void* p : ps)
         if (p) cudaFree(p);
     free(B->kh);
+    batch_mg_free(B->mg);
     delete B;
 }
 
@@ -400,12 +413,17 @@ extern "C" int to_batch_create(to_problem* const* problems, int32_t n, to_batch*
     for (int i = 0; i < n; ++i) {
         const to_problem* P = problems[i];
         if (!P) return fail(TO_ERR_ARG, "null problem");
-        if (P->prec != P0->prec || P->device != P0->device || P->prm.precond != TO_PRECOND_JACOBI ||
-            P->prm.inner_mode != TO_INNER_SD || P->prm.n_inner != P0->prm.n_inner || P->g.h != P0->g.h ||
-            P->mat.E0 != P0->mat.E0 || P->mat.Emin != P0->mat.Emin || P->mat.p != P0->mat.p || P->mat.nu != P0->mat.nu)
+        const bool pre_ok = P->prm.precond == P0->prm.precond &&
+                            (P0->prm.precond == TO_PRECOND_JACOBI ||
+                             (P0->prm.precond == TO_PRECOND_MG && P->prm.mg_nu_pre == P0->prm.mg_nu_pre &&
+                              P->prm.mg_nu_post == P0->prm.mg_nu_post && P->prm.mg_omega == P0->prm.mg_omega));
+        if (P->prec != P0->prec || P->device != P0->device || !pre_ok || P->prm.inner_mode != TO_INNER_SD ||
+            P->prm.n_inner != P0->prm.n_inner || P->g.h != P0->g.h || P->mat.E0 != P0->mat.E0 ||
+            P->mat.Emin != P0->mat.Emin || P->mat.p != P0->mat.p || P->mat.nu != P0->mat.nu)
             return fail(TO_ERR_ARG,
                         "batched problems must share precision, device, element size, material moduli and n_inner, "
-                        "and use the Jacobi preconditioner with steepest descent");
+                        "and use steepest descent with the same preconditioner (Jacobi, or multigrid with the same "
+                        "smoothing parameters)");
     }
     int prev = -1;
     cudaGetDevice(&prev);
@@ -423,8 +441,10 @@ extern "C" int to_batch_create(to_problem* const* problems, int32_t n, to_batch*
         rc = fail(TO_ERR_CUDA, "batch stream / event creation failed");
     // tile shapes: time the batched operator for each candidate depth, keep the fastest
     if (!rc) rc = op_tables_build(B->probs.data(), n, &B->tab_resid, &B->tab_q_first, &B->tab_q, &B->kh, &B->max_tiles, 8);
-    if (!rc) rc = batch_autotune_kchunk(B->probs.data(), n, B->kh, B->stream, &B->kchunk, &B->tune_us);
+    if (!rc && P0->tile_z > 0) B->kchunk = P0->tile_z;   // a fixed tile depth: no autotuning
+    else if (!rc) rc = batch_autotune_kchunk(B->probs.data(), n, B->kh, B->stream, &B->kchunk, &B->tune_us);
     if (!rc) rc = op_tables_build(B->probs.data(), n, &B->tab_resid, &B->tab_q_first, &B->tab_q, &B->kh, &B->max_tiles, B->kchunk);
+    if (!rc && P0->prm.precond == TO_PRECOND_MG) rc = batch_mg_build(B->probs.data(), n, B->kchunk, &B->mg);
     if (prev >= 0) cudaSetDevice(prev);
     if (rc) {
         destroy_batch(B);

@@ -4,6 +4,7 @@
 #include <cmath>
 
 #include "device.cuh"
+#include "transfer.cuh"
 
 namespace to {
 
@@ -177,26 +178,10 @@ __global__ void k_filter_rowsum(int nx, int ny, int nz, T* Hs, const int4* st, c
     }
 }
 
-// 1 / diag(K^): diag(K^) is kdiag times the sum of the moduli of the (up to 8) elements
-// around a node, 1 on fixed DOFs; one divide per DOF here, multiplications where it is used
 template <typename T>
 __global__ void k_diag(int nx, int ny, int nz, const T* E, const uint8_t* mask, T* dinv, double kdiag) {
     const Idx3 t = idx3(nx + 1, ny + 1, nz + 1);
-    if (t.ok) {
-        const int i = t.i, j = t.j, k = t.k;
-        const long long n = i + (long long)(nx + 1) * (j + (long long)(ny + 1) * k);
-        T s = T(0);
-        for (int dk = -1; dk <= 0; ++dk)
-            for (int dj = -1; dj <= 0; ++dj)
-                for (int di = -1; di <= 0; ++di) {
-                    const int ei = i + di, ej = j + dj, ek = k + dk;
-                    if (ei < 0 || ei >= nx || ej < 0 || ej >= ny || ek < 0 || ek >= nz) continue;
-                    s += E[ei + (long long)nx * (ej + (long long)ny * ek)];
-                }
-        const uint8_t mk = mask[n];
-        const T v = T(1) / ((T)kdiag * s);
-        for (int c = 0; c < 3; ++c) dinv[3 * n + c] = ((mk >> c) & 1) ? T(1) : v;
-    }
+    if (t.ok) diag_node<T>(nx, ny, nz, t.i, t.j, t.k, E, mask, dinv, kdiag);
 }
 
 static int grid_for(long long n, int threads, int num_sms) {

@@ -211,10 +211,20 @@ int launch_richardson(to_problem* P, cudaStream_t s);
 
 // multigrid
 int mg_build(to_problem* P);
-int mg_refresh(to_problem* P, cudaStream_t s);   // coarse moduli, diagonals, coarse factor
+// coarse moduli, diagonals, the coarsest inverse (on a forked branch of s; join: s waits for it
+// at once, else the first coarse solve on s does)
+int mg_refresh(to_problem* P, cudaStream_t s, bool join = true);
 int mg_vcycle(to_problem* P, const void* r, void* z, cudaStream_t s);
 
 int outer_iteration(to_problem* P, cudaStream_t s);
 int inner_steps(to_problem* P, int nsteps, int from_resid, cudaStream_t s);
+
+// batched multigrid (mg.cu): the V-cycle and the per-iteration refresh of many problems
+struct BatchMG;
+int batch_mg_build(to_problem* const* probs, int n, int kchunk, BatchMG** out);
+int batch_mg_refresh(const BatchMG* M, cudaStream_t s);
+int batch_mg_vcycle(const BatchMG* M, cudaStream_t s);
+int batch_mg_launches(const BatchMG* M, int* refresh, int* vcycle);
+void batch_mg_free(BatchMG* M);
 
 }  // namespace to

@@ -34,20 +34,24 @@ static int grid1(long long n, int num_sms) {
     return (int)(b < 1 ? 1 : b);
 }
 
+// coarse modulus = mean of the 8 fine children (coarse element (I, J, K))
+template <typename T>
+__device__ __forceinline__ void coarsen_elem(int cx, int cy, int I, int J, int K, const T* __restrict__ Ef,
+                                             T* __restrict__ Ec) {
+    const int fx = 2 * cx, fy = 2 * cy;
+    const long long e = I + (long long)cx * (J + (long long)cy * K);
+    T s = T(0);
+    for (int c = 0; c < 2; ++c)
+        for (int b = 0; b < 2; ++b)
+            for (int a = 0; a < 2; ++a)
+                s += Ef[(2 * I + a) + (long long)fx * ((2 * J + b) + (long long)fy * (2 * K + c))];
+    Ec[e] = T(0.125) * s;
+}
+
 template <typename T>
 __global__ void k_coarsen_E(int cx, int cy, int cz, const T* __restrict__ Ef, T* __restrict__ Ec) {
-    const int fx = 2 * cx, fy = 2 * cy;
     const Idx3 t = idx3(cx, cy, cz);
-    if (t.ok) {
-        const int I = t.i, J = t.j, K = t.k;
-        const long long e = I + (long long)cx * (J + (long long)cy * K);
-        T s = T(0);
-        for (int c = 0; c < 2; ++c)
-            for (int b = 0; b < 2; ++b)
-                for (int a = 0; a < 2; ++a)
-                    s += Ef[(2 * I + a) + (long long)fx * ((2 * J + b) + (long long)fy * (2 * K + c))];
-        Ec[e] = T(0.125) * s;
-    }
+    if (t.ok) coarsen_elem<T>(cx, cy, t.i, t.j, t.k, Ef, Ec);
 }
 
 // b_c = m_c P^T (m_f t), optionally with the coarse level's first sweep
@@ -76,11 +80,10 @@ __global__ void k_jacobi_first(long long n, const T* __restrict__ b, const T* __
 
 // dense coarsest operator (fixed rows / columns = identity)
 template <typename T>
-__global__ void k_dense_assemble(int nx, int ny, int nz, const T* __restrict__ E, const uint8_t* __restrict__ mask,
-                                 const double* __restrict__ ke, double hscale, T* __restrict__ A, int n) {
+__device__ __forceinline__ T dense_entry(int nx, int ny, int nz, const T* __restrict__ E, const uint8_t* __restrict__ mask,
+                                         const double* __restrict__ ke, double hscale, int n, long long idx) {
     const int nxn = nx + 1, nyn = ny + 1;
-    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < (long long)n * n;
-         idx += (long long)gridDim.x * blockDim.x) {
+    {
         const int a = (int)(idx / n), b = (int)(idx % n);
         const int na = a / 3, ca = a % 3, nb = b / 3, cb = b % 3;
         const int ia = na % nxn, ja = (na / nxn) % nyn, kka = na / (nxn * nyn);
@@ -104,8 +107,16 @@ __global__ void k_dense_assemble(int nx, int ny, int nz, const T* __restrict__ E
                         v += (double)E[ei + nx * (ej + ny * ek)] * hscale * ke[(3 * la + ca) * 24 + 3 * lb + cb];
                     }
         }
-        A[idx] = (T)v;
+        return (T)v;
     }
+}
+
+template <typename T>
+__global__ void k_dense_assemble(int nx, int ny, int nz, const T* __restrict__ E, const uint8_t* __restrict__ mask,
+                                 const double* __restrict__ ke, double hscale, T* __restrict__ A, int n) {
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < (long long)n * n;
+         idx += (long long)gridDim.x * blockDim.x)
+        A[idx] = dense_entry<T>(nx, ny, nz, E, mask, ke, hscale, n, idx);
 }
 
 // In-place inverse of the unit-diagonal-scaled SPD matrix by Gauss-Jordan
@@ -113,9 +124,8 @@ __global__ void k_dense_assemble(int nx, int ny, int nz, const T* __restrict__ E
 // (SMEM) or in the output buffer otherwise; writes S A S inverted and the
 // scaling s = diag(A)^-1/2.
 template <typename T, bool SMEM>
-__global__ void __launch_bounds__(1024) k_dense_invert(const T* __restrict__ A, T* __restrict__ Ainv, T* __restrict__ sc,
-                                                       int n, int* err) {
-    extern __shared__ unsigned char smem_raw[];
+__device__ __forceinline__ void dense_invert_body(const T* __restrict__ A, T* __restrict__ Ainv, T* __restrict__ sc,
+                                                  int n, int* err, unsigned char* smem_raw) {
     __shared__ T row[kMaxCoarseDof];
     __shared__ T col[kMaxCoarseDof];
     __shared__ T s[kMaxCoarseDof];
@@ -167,6 +177,13 @@ __global__ void __launch_bounds__(1024) k_dense_invert(const T* __restrict__ A, 
     for (int i = tid; i < n; i += nt) sc[i] = s[i];
 }
 
+template <typename T, bool SMEM>
+__global__ void __launch_bounds__(1024) k_dense_invert(const T* __restrict__ A, T* __restrict__ Ainv, T* __restrict__ sc,
+                                                       int n, int* err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    dense_invert_body<T, SMEM>(A, Ainv, sc, n, err, smem_raw);
+}
+
 // Register-blocked variant for n <= 160: thread (tx, ty) of a 32 x 32 block keeps
 // entries (ty + 32a, tx + 32b), a, b < 5, in registers; each elimination step
 // publishes the pivot row and column through double-buffered shared memory
@@ -174,8 +191,8 @@ __global__ void __launch_bounds__(1024) k_dense_invert(const T* __restrict__ A, 
 constexpr int kRegDof = 160;
 
 template <typename T>
-__global__ void __launch_bounds__(1024) k_dense_invert_reg(const T* __restrict__ A, T* __restrict__ Ainv,
-                                                           T* __restrict__ sc, int n, int* err) {
+__device__ __forceinline__ void dense_invert_reg_body(const T* __restrict__ A, T* __restrict__ Ainv,
+                                                      T* __restrict__ sc, int n, int* err) {
     __shared__ T rowb[2][kRegDof];
     __shared__ T colb[2][kRegDof];
     __shared__ T s[kRegDof];
@@ -270,6 +287,12 @@ __global__ void __launch_bounds__(1024) k_dense_invert_reg(const T* __restrict__
             if (i < n && j < n) Ainv[(long long)i * n + j] = R[a][b];
         }
     for (int i = tid; i < n; i += 1024) sc[i] = s[i];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_dense_invert_reg(const T* __restrict__ A, T* __restrict__ Ainv,
+                                                           T* __restrict__ sc, int n, int* err) {
+    dense_invert_reg_body<T>(A, Ainv, sc, n, err);
 }
 
 // x = S Ainv S b   (one CTA per row block)
@@ -431,8 +454,7 @@ __device__ __forceinline__ void tail_operator(const TailLevel<T>& Lv, const Haar
 }
 
 template <typename T>
-__global__ void __launch_bounds__(tail_threads<T>()) k_mg_tail(const TailArgs<T> a, const HaarK<T> kh) {
-    extern __shared__ __align__(16) unsigned char tsm[];
+__device__ __forceinline__ void tail_body(const TailArgs<T>& a, const HaarK<T>& kh, unsigned char* tsm) {
     T* contrib = reinterpret_cast<T*>(tsm + a.ocontrib);
     TailLevel<T> lv[kTailMaxLevels];
     T* cur[kTailMaxLevels];
@@ -555,6 +577,12 @@ __global__ void __launch_bounds__(tail_threads<T>()) k_mg_tail(const TailArgs<T>
     const TailGlobal<T>& G = a.lv[0];
     const int nn = (G.nx + 1) * (G.ny + 1) * (G.nz + 1);
     for (int q = threadIdx.x; q < 3 * nn; q += blockDim.x) G.x[q] = tl[0].x[q];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(tail_threads<T>()) k_mg_tail(const TailArgs<T> a, const HaarK<T> kh) {
+    extern __shared__ __align__(16) unsigned char tsm[];
+    tail_body<T>(a, kh, tsm);
 }
 
 // ----------------------------------------------------------------------------- host side
@@ -688,13 +716,13 @@ int mg_build(to_problem* P) {
         if (e != cudaSuccess) return fail(TO_ERR_CUDA, std::string("shared memory opt-in: ") + cudaGetErrorString(e));
     }
     // the coarse tail: from the first level (>= 1, above the coarsest) with at most
-    // kTailMaxElems elements, when its levels fit in shared memory
+    // kTailMaxElems elements whose levels fit in shared memory
     P->mg_tail = 0;
     for (int l = 1; l + 1 < L && L - l <= kTailMaxLevels; ++l) {
         if (P->lv[l].n_elem > kTailMaxElems) continue;
         if ((unsigned long long)P->lv[l].n_node * (unsigned long long)P->lv[l].n_node >= (1ull << 32)) continue;   // FastDiv range
         const size_t tsm = P->prec == TO_FP64 ? tail_layout<double>(P, l, nullptr) : tail_layout<float>(P, l, nullptr);
-        if (tsm > kTailSmem) break;
+        if (tsm > kTailSmem) continue;   // FP64 at ~1024 elements: start one level coarser
         cudaError_t e = P->prec == TO_FP64
                             ? cudaFuncSetAttribute(k_mg_tail<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm)
                             : cudaFuncSetAttribute(k_mg_tail<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm);
@@ -706,7 +734,7 @@ int mg_build(to_problem* P) {
 }
 
 template <typename T>
-static int refresh_t(to_problem* P, cudaStream_t s) {
+static int refresh_t(to_problem* P, cudaStream_t s, bool join) {
     const int L = (int)P->lv.size();
     for (int l = 1; l < L; ++l) {
         const Level& C = P->lv[l];
@@ -735,27 +763,24 @@ static int refresh_t(to_problem* P, cudaStream_t s) {
         k_dense_invert<T, false><<<1, dim3(32, 32), 0, s>>>((const T*)P->coarse_A, inv, inv + (size_t)n * n, n, &P->sc->err);
     TO_CUDA(cudaGetLastError());
     TO_CUDA(cudaEventRecord(P->ev_join, s));
-    (void)main_s;
+    // outside the outer iteration nothing else joins the branch: without this a later
+    // refresh could rewrite coarse_A / coarse_L while this inverse still runs
+    if (join) TO_CUDA(cudaStreamWaitEvent(main_s, P->ev_join, 0));
     return TO_OK;
 }
 
-int mg_refresh(to_problem* P, cudaStream_t s) {
-    return P->prec == TO_FP64 ? refresh_t<double>(P, s) : refresh_t<float>(P, s);
+int mg_refresh(to_problem* P, cudaStream_t s, bool join) {
+    return P->prec == TO_FP64 ? refresh_t<double>(P, s, join) : refresh_t<float>(P, s, join);
 }
 
 // levels mg_tail .. L-1 in one launch (after the coarsest inverse is ready)
 template <typename T>
+static int tail_args(to_problem* P, int l0, TailArgs<T>* a);
+
+template <typename T>
 static int tail_t(to_problem* P, cudaStream_t s) {
-    const int L = (int)P->lv.size(), l0 = P->mg_tail;
-    TailArgs<T> a{};
-    a.nlev = L - l0;
-    a.nu1 = P->prm.mg_nu_pre;
-    a.nu2 = P->prm.mg_nu_post;
-    a.omega = (T)P->prm.mg_omega;
-    a.inv = (const T*)P->coarse_L;
-    a.n_c = P->n_coarse;
-    a.inv_smem = (size_t)(a.n_c + 1) * a.n_c <= (size_t)24 * P->lv[l0].n_elem;
-    const size_t tsm = tail_layout<T>(P, l0, &a);
+    TailArgs<T> a;
+    const size_t tsm = (size_t)tail_args<T>(P, P->mg_tail, &a);
     HaarK<T> kh;
     for (int q = 0; q < kHaarNnz; ++q) kh.v[q] = (T)P->haar[q];
     TO_CUDA(cudaStreamWaitEvent(s, P->ev_join, 0));   // the inverse of this design is ready
@@ -832,6 +857,448 @@ int mg_launches(const to_problem* P) {
     if (L == 1) return 1;
     const int host_levels = P->mg_tail > 0 ? P->mg_tail : L - 1;
     return 1 + host_levels * ((nu1 - 1) + 1 + 1 + 1 + nu2) + 1;   // + the dense solve or the tail kernel
+}
+
+// ----------------------------------------------------------------------------- batched multigrid
+// The V-cycle and the per-iteration refresh of many problems, one launch per
+// step: every batched kernel reads a table of per-problem arguments (blockIdx.y,
+// or blockIdx.x for the one-CTA kernels) and grid-strides over that problem's
+// nodes or elements.  The launch sequence replays the single-problem V-cycle
+// (the same buffers, sweep order and reductions): levels above each problem's
+// coarse tail one launch per step and level (problems whose tail starts higher
+// sit those launches out), then every problem's tail in one launch, one CTA each.
+
+int op_table_level(to_problem* const* probs, int n, int level, int mode, const void* const* x, void* const* y,
+                   const void* const* b, double omega, int first, int kchunk, void** dev, int* max_tiles);
+void* level_haar(const to_problem* P, int level);
+int batch_operator_launch(int prec, int mode, const void* tab, const void* kh, int max_tiles, int n, cudaStream_t s);
+
+template <typename T>
+struct BmJac {          // x = omega b / d
+    long long n;
+    const T* b;
+    const T* dinv;
+    T* x;
+    T omega;
+};
+template <typename T>
+struct BmRestrict {     // b_c = m_c P^T (m_f t) and the coarse first sweep
+    int cx, cy, cz;
+    const T* tf;
+    const uint8_t* mf;
+    const uint8_t* mc;
+    T* bc;
+    const T* dinvc;
+    T* xc;
+    T omega;
+};
+template <typename T>
+struct BmProlong {      // x_f += m_f P (m_c x_c)
+    int cx, cy, cz;
+    const T* xc;
+    const uint8_t* mc;
+    const uint8_t* mf;
+    T* xf;
+};
+template <typename T>
+struct BmLevel {        // a coarse level's moduli and inverse diagonal
+    int nx, ny, nz;
+    const T* Ef;
+    T* E;
+    const uint8_t* mask;
+    T* dinv;
+    double kdiag;
+};
+template <typename T>
+struct BmDense {        // the coarsest level's dense operator and its inverse
+    int nx, ny, nz, n;
+    const T* E;
+    const uint8_t* mask;
+    const double* ke;
+    double hscale;
+    T* A;
+    T* inv;             // n x n, then the n scale factors
+    int* err;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_bm_jacobi_first(const BmJac<T>* __restrict__ tab) {
+    const BmJac<T>& a = tab[blockIdx.y];
+    for (long long i = blockIdx.x * 256LL + threadIdx.x; i < a.n; i += (long long)gridDim.x * 256)
+        a.x[i] = a.omega * a.b[i] * a.dinv[i];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_bm_restrict(const BmRestrict<T>* __restrict__ tab) {
+    const BmRestrict<T>& a = tab[blockIdx.y];
+    const long long X = a.cx + 1, Y = a.cy + 1, nn = X * Y * (a.cz + 1);
+    for (long long q = blockIdx.x * 256LL + threadIdx.x; q < nn; q += (long long)gridDim.x * 256)
+        restrict_node<T, long long, true>(a.cx, a.cy, a.cz, (int)(q % X), (int)((q / X) % Y), (int)(q / (X * Y)), a.tf,
+                                          a.mf, a.mc, a.bc, a.dinvc, a.xc, a.omega);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_bm_prolong(const BmProlong<T>* __restrict__ tab) {
+    const BmProlong<T>& a = tab[blockIdx.y];
+    const long long X = 2 * a.cx + 1, Y = 2 * a.cy + 1, nn = X * Y * (2 * a.cz + 1);
+    for (long long q = blockIdx.x * 256LL + threadIdx.x; q < nn; q += (long long)gridDim.x * 256)
+        prolong_node<T>(a.cx, a.cy, a.cz, (int)(q % X), (int)((q / X) % Y), (int)(q / (X * Y)), a.xc, a.mc, a.mf, a.xf);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_bm_coarsen(const BmLevel<T>* __restrict__ tab) {
+    const BmLevel<T>& a = tab[blockIdx.y];
+    const long long X = a.nx, Y = a.ny, ne = X * Y * a.nz;
+    for (long long q = blockIdx.x * 256LL + threadIdx.x; q < ne; q += (long long)gridDim.x * 256)
+        coarsen_elem<T>(a.nx, a.ny, (int)(q % X), (int)((q / X) % Y), (int)(q / (X * Y)), a.Ef, a.E);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_bm_diag(const BmLevel<T>* __restrict__ tab) {
+    const BmLevel<T>& a = tab[blockIdx.y];
+    const long long X = a.nx + 1, Y = a.ny + 1, nn = X * Y * (a.nz + 1);
+    for (long long q = blockIdx.x * 256LL + threadIdx.x; q < nn; q += (long long)gridDim.x * 256)
+        diag_node<T>(a.nx, a.ny, a.nz, (int)(q % X), (int)((q / X) % Y), (int)(q / (X * Y)), a.E, a.mask, a.dinv, a.kdiag);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_bm_assemble(const BmDense<T>* __restrict__ tab) {
+    const BmDense<T>& a = tab[blockIdx.y];
+    const long long nn = (long long)a.n * a.n;
+    for (long long q = blockIdx.x * 256LL + threadIdx.x; q < nn; q += (long long)gridDim.x * 256)
+        a.A[q] = dense_entry<T>(a.nx, a.ny, a.nz, a.E, a.mask, a.ke, a.hscale, a.n, q);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_bm_invert_reg(const BmDense<T>* __restrict__ tab) {
+    const BmDense<T>& a = tab[blockIdx.x];
+    dense_invert_reg_body<T>(a.A, a.inv, a.inv + (size_t)a.n * a.n, a.n, a.err);
+}
+
+template <typename T, bool SMEM>
+__global__ void __launch_bounds__(1024) k_bm_invert(const BmDense<T>* __restrict__ tab) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const BmDense<T>& a = tab[blockIdx.x];
+    dense_invert_body<T, SMEM>(a.A, a.inv, a.inv + (size_t)a.n * a.n, a.n, a.err, smem_raw);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(tail_threads<T>()) k_mg_tail_batch(const TailArgs<T>* __restrict__ tab, const HaarK<T> kh) {
+    extern __shared__ __align__(16) unsigned char tsm[];
+    tail_body<T>(tab[blockIdx.x], kh, tsm);
+}
+
+enum BmKind { BM_JAC, BM_OPER, BM_RESTRICT, BM_PROLONG, BM_TAIL, BM_COARSEN, BM_DIAG, BM_ASSEMBLE, BM_INVERT_REG,
+              BM_INVERT_SMEM, BM_INVERT_GLOBAL };
+
+struct BmOp {
+    int kind = 0, mode = 0, n = 0, grid_x = 1, max_tiles = 0;
+    void* tab = nullptr;        // device table
+    const void* kh = nullptr;   // host element constants (operator and tail launches)
+    size_t smem = 0;
+};
+
+struct BatchMG {
+    int prec = TO_FP32_MIXED, n = 0;
+    std::vector<BmOp> refresh, vcycle;
+    std::vector<void*> dev, host;
+};
+
+static int grid_x_for(long long items, int num_sms, int n) {
+    // enough CTAs for the largest problem, about 8 per SM over the whole batch
+    long long g = (items + 255) / 256;
+    const long long cap = std::max<long long>(1, (8LL * num_sms + n - 1) / n);
+    return (int)std::max<long long>(1, std::min(g, cap));
+}
+
+template <typename S>
+static int upload_table(BatchMG* M, const std::vector<S>& h, void** out) {
+    void* d = nullptr;
+    if (cudaMalloc(&d, sizeof(S) * h.size()) != cudaSuccess) return fail(TO_ERR_CUDA, "batched multigrid table allocation");
+    M->dev.push_back(d);
+    if (cudaMemcpy(d, h.data(), sizeof(S) * h.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(TO_ERR_CUDA, "batched multigrid table upload");
+    *out = d;
+    return TO_OK;
+}
+
+template <typename T>
+static int tail_args(to_problem* P, int l0, TailArgs<T>* a) {
+    const int L = (int)P->lv.size();
+    *a = TailArgs<T>{};
+    a->nlev = L - l0;
+    a->nu1 = P->prm.mg_nu_pre;
+    a->nu2 = P->prm.mg_nu_post;
+    a->omega = (T)P->prm.mg_omega;
+    a->inv = (const T*)P->coarse_L;
+    a->n_c = P->n_coarse;
+    a->inv_smem = (size_t)(a->n_c + 1) * a->n_c <= (size_t)24 * P->lv[l0].n_elem;
+    return (int)tail_layout<T>(P, l0, a);
+}
+
+template <typename T>
+static int batch_mg_build_t(to_problem* const* probs, int n, int kchunk, BatchMG* M) {
+    const int nu1 = probs[0]->prm.mg_nu_pre, nu2 = probs[0]->prm.mg_nu_post;
+    const double om = probs[0]->prm.mg_omega;
+    const int num_sms = probs[0]->num_sms;
+    const bool even = (nu1 - 1 + nu2) % 2 == 0;
+    // each problem's tail: its one-CTA coarse tail, or (where none fits) the dense coarsest solve alone
+    std::vector<int> tail(n);
+    int maxH = 0, maxL = 0;
+    for (int i = 0; i < n; ++i) {
+        const int L = (int)probs[i]->lv.size();
+        tail[i] = probs[i]->mg_tail > 0 ? probs[i]->mg_tail : L - 1;
+        maxH = std::max(maxH, tail[i]);
+        maxL = std::max(maxL, L);
+    }
+    // V-cycle vectors of problem p on level l: (b, x, t)
+    auto vb = [&](int p, int l) -> void* { return l == 0 ? probs[p]->r : probs[p]->lv[l].b; };
+    auto vx = [&](int p, int l) -> void* { return l == 0 ? probs[p]->z : probs[p]->lv[l].x; };
+    auto vt = [&](int p, int l) -> void* { return probs[p]->lv[l].t; };
+    auto cur0 = [&](int p, int l) { return even ? vx(p, l) : vt(p, l); };
+    auto oth0 = [&](int p, int l) { return even ? vt(p, l) : vx(p, l); };
+    auto members = [&](int l) {   // problems with a host-side level l
+        std::vector<int> m;
+        for (int i = 0; i < n; ++i)
+            if (tail[i] > l) m.push_back(i);
+        return m;
+    };
+    auto oper = [&](int l, int mode, const std::vector<int>& m, bool cur_is_0, int first) -> int {
+        std::vector<to_problem*> ps;
+        std::vector<const void*> xs, bs;
+        std::vector<void*> ys;
+        for (int p : m) {
+            ps.push_back(probs[p]);
+            xs.push_back(cur_is_0 ? cur0(p, l) : oth0(p, l));
+            ys.push_back(cur_is_0 ? oth0(p, l) : cur0(p, l));
+            bs.push_back(vb(p, l));
+        }
+        BmOp op;
+        op.kind = BM_OPER;
+        op.mode = mode;
+        op.n = (int)m.size();
+        int rc = op_table_level(ps.data(), op.n, l, mode, xs.data(), ys.data(), bs.data(), om, first, kchunk, &op.tab,
+                                &op.max_tiles);
+        if (op.tab) M->dev.push_back(op.tab);
+        if (rc) return rc;
+        void* kh = level_haar(probs[m[0]], l);
+        if (!kh) return fail(TO_ERR_CUDA, "host allocation");
+        M->host.push_back(kh);
+        op.kh = kh;
+        M->vcycle.push_back(op);
+        return TO_OK;
+    };
+    int rc;
+    // ---- down
+    std::vector<bool> cur_is_0(maxH, true);   // after the pre-sweeps: the current iterate is cur0 (else oth0)
+    for (int l = 0; l < maxH; ++l) {
+        const std::vector<int> m = members(l);
+        if (l == 0) {
+            std::vector<BmJac<T>> h;
+            long long mx = 0;
+            for (int p : m) {
+                const Level& F = probs[p]->lv[0];
+                h.push_back(BmJac<T>{F.n_dof, (const T*)vb(p, 0), (const T*)F.dinv, (T*)cur0(p, 0), (T)om});
+                mx = std::max<long long>(mx, F.n_dof);
+            }
+            BmOp op;
+            op.kind = BM_JAC;
+            op.n = (int)m.size();
+            op.grid_x = grid_x_for(mx, num_sms, op.n);
+            if ((rc = upload_table(M, h, &op.tab))) return rc;
+            M->vcycle.push_back(op);
+        }
+        bool c0 = true;
+        for (int it = 1; it < nu1; ++it) {
+            if ((rc = oper(l, OP_SMOOTH, m, c0, 0))) return rc;
+            c0 = !c0;
+        }
+        if ((rc = oper(l, OP_BMINUS, m, c0, 0))) return rc;   // b - K x into the other buffer
+        cur_is_0[l] = c0;
+        std::vector<BmRestrict<T>> h;
+        long long mx = 0;
+        for (int p : m) {
+            const Level& F = probs[p]->lv[l];
+            const Level& C = probs[p]->lv[l + 1];
+            // above the coarsest level the restriction also takes the coarse level's first sweep
+            const bool fuse = l + 1 < (int)probs[p]->lv.size() - 1;
+            h.push_back(BmRestrict<T>{C.nx, C.ny, C.nz, (const T*)(c0 ? oth0(p, l) : cur0(p, l)), F.mask, C.mask, (T*)C.b,
+                                      (const T*)C.dinv, fuse ? (T*)(even ? C.x : C.t) : (T*)nullptr, (T)om});
+            mx = std::max<long long>(mx, C.n_node);
+        }
+        BmOp op;
+        op.kind = BM_RESTRICT;
+        op.n = (int)m.size();
+        op.grid_x = grid_x_for(mx, num_sms, op.n);
+        if ((rc = upload_table(M, h, &op.tab))) return rc;
+        M->vcycle.push_back(op);
+    }
+    // ---- the tails, one CTA per problem
+    {
+        std::vector<TailArgs<T>> h(n);
+        size_t smem = 0;
+        for (int p = 0; p < n; ++p) smem = std::max<size_t>(smem, (size_t)tail_args<T>(probs[p], tail[p], &h[p]));
+        if (smem > 227 * 1024) return fail(TO_ERR_ARG, "batched multigrid: a coarse tail exceeds shared memory");
+        BmOp op;
+        op.kind = BM_TAIL;
+        op.n = n;
+        op.smem = smem;
+        if ((rc = upload_table(M, h, &op.tab))) return rc;
+        HaarK<T>* kh = (HaarK<T>*)malloc(sizeof(HaarK<T>));
+        if (!kh) return fail(TO_ERR_CUDA, "host allocation");
+        M->host.push_back(kh);
+        for (int q = 0; q < kHaarNnz; ++q) kh->v[q] = (T)probs[0]->haar[q];
+        op.kh = kh;
+        TO_CUDA(cudaFuncSetAttribute(k_mg_tail_batch<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        M->vcycle.push_back(op);
+    }
+    // ---- up
+    for (int l = maxH - 1; l >= 0; --l) {
+        const std::vector<int> m = members(l);
+        std::vector<BmProlong<T>> h;
+        long long mx = 0;
+        for (int p : m) {
+            const Level& F = probs[p]->lv[l];
+            const Level& C = probs[p]->lv[l + 1];
+            h.push_back(BmProlong<T>{C.nx, C.ny, C.nz, (const T*)C.x, C.mask, F.mask,
+                                     (T*)(cur_is_0[l] ? cur0(p, l) : oth0(p, l))});
+            mx = std::max<long long>(mx, F.n_node);
+        }
+        BmOp op;
+        op.kind = BM_PROLONG;
+        op.n = (int)m.size();
+        op.grid_x = grid_x_for(mx, num_sms, op.n);
+        if ((rc = upload_table(M, h, &op.tab))) return rc;
+        M->vcycle.push_back(op);
+        bool c0 = cur_is_0[l];
+        for (int it = 0; it < nu2; ++it) {
+            if ((rc = oper(l, OP_SMOOTH, m, c0, (l == 0 && it == nu2 - 1) ? 2 : 0))) return rc;
+            c0 = !c0;
+        }
+        // the last sweep lands in x (the buffer parity chosen at the first sweep): cur0 = x exactly when even
+        if (c0 != even) return fail(TO_ERR_STATE, "batched V-cycle buffer parity");
+    }
+    // ---- refresh: coarse moduli and diagonals, the dense coarsest operators and their inverses
+    for (int l = 1; l < maxL; ++l) {
+        std::vector<BmLevel<T>> h;
+        long long mxe = 0, mxn = 0;
+        for (int p = 0; p < n; ++p) {
+            if ((int)probs[p]->lv.size() <= l) continue;
+            const Level& F = probs[p]->lv[l - 1];
+            const Level& C = probs[p]->lv[l];
+            h.push_back(BmLevel<T>{C.nx, C.ny, C.nz, (const T*)F.E, (T*)C.E, C.mask, (T*)C.dinv, C.kdiag});
+            mxe = std::max<long long>(mxe, C.n_elem);
+            mxn = std::max<long long>(mxn, C.n_node);
+        }
+        BmOp op;
+        op.kind = BM_COARSEN;
+        op.n = (int)h.size();
+        op.grid_x = grid_x_for(mxe, num_sms, op.n);
+        if ((rc = upload_table(M, h, &op.tab))) return rc;
+        M->refresh.push_back(op);
+        op.kind = BM_DIAG;
+        op.grid_x = grid_x_for(mxn, num_sms, op.n);
+        M->refresh.push_back(op);
+    }
+    {
+        std::vector<BmDense<T>> h;
+        long long mx = 0;
+        int nmax = 0;
+        for (int p = 0; p < n; ++p) {
+            to_problem* P = probs[p];
+            const Level& C = P->lv.back();
+            h.push_back(BmDense<T>{C.nx, C.ny, C.nz, P->n_coarse, (const T*)C.E, C.mask, P->ke_dev, C.h,
+                                   (T*)P->coarse_A, (T*)P->coarse_L, &P->sc->err});
+            mx = std::max<long long>(mx, (long long)P->n_coarse * P->n_coarse);
+            nmax = std::max(nmax, P->n_coarse);
+        }
+        BmOp op;
+        op.kind = BM_ASSEMBLE;
+        op.n = n;
+        op.grid_x = grid_x_for(mx, num_sms, n);
+        if ((rc = upload_table(M, h, &op.tab))) return rc;
+        M->refresh.push_back(op);
+        const size_t sm = (size_t)nmax * nmax * sizeof(T);
+        if (nmax <= kRegDof) {
+            op.kind = BM_INVERT_REG;
+        } else if (sm <= smem_cap<T>()) {
+            op.kind = BM_INVERT_SMEM;
+            op.smem = sm;
+            TO_CUDA(cudaFuncSetAttribute(k_bm_invert<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        } else {
+            op.kind = BM_INVERT_GLOBAL;
+        }
+        M->refresh.push_back(op);
+    }
+    return TO_OK;
+}
+
+template <typename T>
+static int batch_mg_run(const BatchMG* M, const std::vector<BmOp>& ops, cudaStream_t s) {
+    for (const BmOp& op : ops) {
+        const dim3 g2(op.grid_x, op.n);
+        switch (op.kind) {
+            case BM_JAC: k_bm_jacobi_first<T><<<g2, 256, 0, s>>>((const BmJac<T>*)op.tab); break;
+            case BM_OPER: {
+                const int rc = batch_operator_launch(M->prec, op.mode, op.tab, op.kh, op.max_tiles, op.n, s);
+                if (rc) return rc;
+                break;
+            }
+            case BM_RESTRICT: k_bm_restrict<T><<<g2, 256, 0, s>>>((const BmRestrict<T>*)op.tab); break;
+            case BM_PROLONG: k_bm_prolong<T><<<g2, 256, 0, s>>>((const BmProlong<T>*)op.tab); break;
+            case BM_TAIL:
+                k_mg_tail_batch<T><<<op.n, tail_threads<T>(), op.smem, s>>>((const TailArgs<T>*)op.tab, *(const HaarK<T>*)op.kh);
+                break;
+            case BM_COARSEN: k_bm_coarsen<T><<<g2, 256, 0, s>>>((const BmLevel<T>*)op.tab); break;
+            case BM_DIAG: k_bm_diag<T><<<g2, 256, 0, s>>>((const BmLevel<T>*)op.tab); break;
+            case BM_ASSEMBLE: k_bm_assemble<T><<<g2, 256, 0, s>>>((const BmDense<T>*)op.tab); break;
+            case BM_INVERT_REG: k_bm_invert_reg<T><<<op.n, dim3(32, 32), 0, s>>>((const BmDense<T>*)op.tab); break;
+            case BM_INVERT_SMEM: k_bm_invert<T, true><<<op.n, dim3(32, 32), op.smem, s>>>((const BmDense<T>*)op.tab); break;
+            default: k_bm_invert<T, false><<<op.n, dim3(32, 32), 0, s>>>((const BmDense<T>*)op.tab); break;
+        }
+        TO_CUDA(cudaGetLastError());
+    }
+    return TO_OK;
+}
+
+void batch_mg_free(BatchMG* M) {
+    if (!M) return;
+    for (void* d : M->dev) cudaFree(d);
+    for (void* h : M->host) free(h);
+    delete M;
+}
+
+// tables of the batched V-cycle and refresh; every problem has a multigrid hierarchy
+// of at least two levels and the same smoothing parameters
+int batch_mg_build(to_problem* const* probs, int n, int kchunk, BatchMG** out) {
+    *out = nullptr;
+    for (int i = 0; i < n; ++i)
+        if (probs[i]->lv.size() < 2)
+            return fail(TO_ERR_ARG, "batched multigrid needs every grid to halve at least once");
+    BatchMG* M = new BatchMG();
+    M->prec = probs[0]->prec;
+    M->n = n;
+    const int rc = M->prec == TO_FP64 ? batch_mg_build_t<double>(probs, n, kchunk, M) : batch_mg_build_t<float>(probs, n, kchunk, M);
+    if (rc) {
+        batch_mg_free(M);
+        return rc;
+    }
+    *out = M;
+    return TO_OK;
+}
+
+int batch_mg_refresh(const BatchMG* M, cudaStream_t s) {
+    return M->prec == TO_FP64 ? batch_mg_run<double>(M, M->refresh, s) : batch_mg_run<float>(M, M->refresh, s);
+}
+
+int batch_mg_vcycle(const BatchMG* M, cudaStream_t s) {
+    return M->prec == TO_FP64 ? batch_mg_run<double>(M, M->vcycle, s) : batch_mg_run<float>(M, M->vcycle, s);
+}
+
+int batch_mg_launches(const BatchMG* M, int* refresh, int* vcycle) {
+    *refresh = (int)M->refresh.size();
+    *vcycle = (int)M->vcycle.size();
+    return TO_OK;
 }
 
 }  // namespace to

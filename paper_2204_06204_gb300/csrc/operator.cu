@@ -700,7 +700,7 @@ static OpArgs<T> batch_args(to_problem* P, int mode, int first, int kchunk) {
         a.x = (const T*)P->u;
         a.y = (T*)P->r;
         a.b = (const T*)P->f;
-        a.z = (T*)P->z;
+        a.z = P->prm.precond == TO_PRECOND_JACOBI ? (T*)P->z : nullptr;   // multigrid: z comes from the V-cycle
         a.Ed = (const T*)P->Ed;
         a.gt = (T*)P->gt;
         a.counter = P->counters + 0;
@@ -760,21 +760,84 @@ int op_tables_build(to_problem* const* probs, int n, void** resid, void** q_firs
     *max_tiles = mt;
     // shared-memory opt-in of the batched kernels
     const size_t smem = prec == TO_FP64 ? sizeof(OpSmem<double, 32, 8, kRing>) : sizeof(OpSmem<float, 32, 8, kRing>);
-    const void* fns[3];
+    const void* fns[5];
     if (prec == TO_FP64) {
         fns[0] = (const void*)k_operator_batch<double, 32, 8, OP_RESID>;
         fns[1] = (const void*)k_operator_batch<double, 32, 8, OP_Q>;
         fns[2] = (const void*)k_operator_batch<double, 32, 8, OP_APPLY>;
+        fns[3] = (const void*)k_operator_batch<double, 32, 8, OP_SMOOTH>;
+        fns[4] = (const void*)k_operator_batch<double, 32, 8, OP_BMINUS>;
     } else {
         fns[0] = (const void*)k_operator_batch<float, 32, 8, OP_RESID>;
         fns[1] = (const void*)k_operator_batch<float, 32, 8, OP_Q>;
         fns[2] = (const void*)k_operator_batch<float, 32, 8, OP_APPLY>;
+        fns[3] = (const void*)k_operator_batch<float, 32, 8, OP_SMOOTH>;
+        fns[4] = (const void*)k_operator_batch<float, 32, 8, OP_BMINUS>;
     }
     for (const void* f : fns) TO_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     return TO_OK;
 }
 
 int batch_operator_launch(int prec, int mode, const void* tab, const void* kh, int max_tiles, int n, cudaStream_t s);
+
+// One batched multigrid sweep's table: problem i applies `mode` (OP_SMOOTH or OP_BMINUS)
+// on its level `level` from x[i] into y[i] with right-hand side b[i]; `first` = 2 on the
+// fine level's last sweep (it also reduces b^T y, the r^T z of the lower-level step).
+template <typename T>
+static int op_table_level_t(to_problem* const* probs, int n, int level, int mode, const void* const* x, void* const* y,
+                            const void* const* b, double omega, int first, int kchunk, void** dev, int* max_tiles) {
+    std::vector<OpArgs<T>> h(n);
+    int mt = 0;
+    for (int i = 0; i < n; ++i) {
+        to_problem* P = probs[i];
+        const Level& L = P->lv[level];
+        OpArgs<T>& a = h[i];
+        a = OpArgs<T>{};
+        a.nx = L.nx;
+        a.ny = L.ny;
+        a.nz = L.nz;
+        a.kchunk = L.nz + 1 < kchunk ? L.nz + 1 : kchunk;
+        a.x = (const T*)x[i];
+        a.y = (T*)y[i];
+        a.b = (const T*)b[i];
+        a.dinv = (const T*)L.dinv;
+        a.E = (const T*)L.E;
+        a.mask = L.mask;
+        a.tmask = L.tmask;
+        a.omega = (T)omega;
+        a.red = P->red;
+        a.sc = P->sc;
+        a.first_step = first;
+        a.counter = mode == OP_SMOOTH ? P->counters + 6 : nullptr;
+        const int gx = (a.nx + 1 + 30) / 31, gy = (a.ny + 1 + 6) / 7, gz = (a.nz + 1 + a.kchunk - 1) / a.kchunk;
+        if ((long long)gx * gy * gz > kMaxRedBlocks) return fail(TO_ERR_ARG, "batched problem too large for the reduction slots");
+        mt = mt > gx * gy * gz ? mt : gx * gy * gz;
+    }
+    if (cudaMalloc(dev, sizeof(OpArgs<T>) * (size_t)n) != cudaSuccess) return fail(TO_ERR_CUDA, "table allocation");
+    if (cudaMemcpy(*dev, h.data(), sizeof(OpArgs<T>) * (size_t)n, cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(TO_ERR_CUDA, "table upload");
+    *max_tiles = mt;
+    return TO_OK;
+}
+
+int op_table_level(to_problem* const* probs, int n, int level, int mode, const void* const* x, void* const* y,
+                   const void* const* b, double omega, int first, int kchunk, void** dev, int* max_tiles) {
+    return probs[0]->prec == TO_FP64
+               ? op_table_level_t<double>(probs, n, level, mode, x, y, b, omega, first, kchunk, dev, max_tiles)
+               : op_table_level_t<float>(probs, n, level, mode, x, y, b, omega, first, kchunk, dev, max_tiles);
+}
+
+// host copy of a level's element constants (K_e scales with the element size: h_level / h_0)
+void* level_haar(const to_problem* P, int level) {
+    if (P->prec == TO_FP64) {
+        HaarK<double>* kh = (HaarK<double>*)malloc(sizeof(HaarK<double>));
+        if (kh) fill_haar<double>(P, P->lv[level].h / P->g.h, *kh);
+        return kh;
+    }
+    HaarK<float>* kh = (HaarK<float>*)malloc(sizeof(HaarK<float>));
+    if (kh) fill_haar<float>(P, P->lv[level].h / P->g.h, *kh);
+    return kh;
+}
 
 // Tile autotuner of the batched operator: time the batch's K u into scratch (no scalar
 // side effects) for each candidate number of node planes per tile and return the fastest.
@@ -819,27 +882,25 @@ int batch_autotune_kchunk(to_problem* const* probs, int n, const void* kh, cudaS
     return TO_OK;
 }
 
-int batch_operator_launch(int prec, int mode, const void* tab, const void* kh, int max_tiles, int n, cudaStream_t s) {
-    const dim3 grid(max_tiles, n), block(32, 8);
-    if (prec == TO_FP64) {
-        const size_t smem = sizeof(OpSmem<double, 32, 8, kRing>);
-        const HaarK<double>& k = *(const HaarK<double>*)kh;
-        if (mode == OP_RESID)
-            k_operator_batch<double, 32, 8, OP_RESID><<<grid, block, smem, s>>>((const OpArgs<double>*)tab, k);
-        else if (mode == OP_Q)
-            k_operator_batch<double, 32, 8, OP_Q><<<grid, block, smem, s>>>((const OpArgs<double>*)tab, k);
-        else
-            k_operator_batch<double, 32, 8, OP_APPLY><<<grid, block, smem, s>>>((const OpArgs<double>*)tab, k);
-    } else {
-        const size_t smem = sizeof(OpSmem<float, 32, 8, kRing>);
-        const HaarK<float>& k = *(const HaarK<float>*)kh;
-        if (mode == OP_RESID)
-            k_operator_batch<float, 32, 8, OP_RESID><<<grid, block, smem, s>>>((const OpArgs<float>*)tab, k);
-        else if (mode == OP_Q)
-            k_operator_batch<float, 32, 8, OP_Q><<<grid, block, smem, s>>>((const OpArgs<float>*)tab, k);
-        else
-            k_operator_batch<float, 32, 8, OP_APPLY><<<grid, block, smem, s>>>((const OpArgs<float>*)tab, k);
+template <typename T>
+static void batch_launch_t(int mode, const void* tab, const void* kh, dim3 grid, cudaStream_t s) {
+    const size_t smem = sizeof(OpSmem<T, 32, 8, kRing>);
+    const HaarK<T>& k = *(const HaarK<T>*)kh;
+    const OpArgs<T>* t = (const OpArgs<T>*)tab;
+    const dim3 block(32, 8);
+    switch (mode) {
+        case OP_RESID: k_operator_batch<T, 32, 8, OP_RESID><<<grid, block, smem, s>>>(t, k); break;
+        case OP_Q: k_operator_batch<T, 32, 8, OP_Q><<<grid, block, smem, s>>>(t, k); break;
+        case OP_SMOOTH: k_operator_batch<T, 32, 8, OP_SMOOTH><<<grid, block, smem, s>>>(t, k); break;
+        case OP_BMINUS: k_operator_batch<T, 32, 8, OP_BMINUS><<<grid, block, smem, s>>>(t, k); break;
+        default: k_operator_batch<T, 32, 8, OP_APPLY><<<grid, block, smem, s>>>(t, k); break;
     }
+}
+
+int batch_operator_launch(int prec, int mode, const void* tab, const void* kh, int max_tiles, int n, cudaStream_t s) {
+    const dim3 grid(max_tiles, n);
+    if (prec == TO_FP64) batch_launch_t<double>(mode, tab, kh, grid, s);
+    else batch_launch_t<float>(mode, tab, kh, grid, s);
     TO_CUDA(cudaGetLastError());
     return TO_OK;
 }

@@ -301,18 +301,21 @@ int run_inner(to_problem* P, void* u, int nsteps, int primary, cudaStream_t s) {
     return TO_OK;
 }
 
-int refresh_preconditioner(to_problem* P, cudaStream_t s) {
+int refresh_preconditioner(to_problem* P, cudaStream_t s, bool join) {
     int rc = launch_diag(P, 0, s);
     if (rc) return rc;
-    if (P->prm.precond == TO_PRECOND_MG) return mg_refresh(P, s);
+    if (P->prm.precond == TO_PRECOND_MG) return mg_refresh(P, s, join);
     return TO_OK;
 }
 
 int outer_iteration(to_problem* P, cudaStream_t s) {
     int rc;
     if ((rc = launch_moduli(P, s))) return rc;
-    if ((rc = refresh_preconditioner(P, s))) return rc;
+    // the coarsest inverse overlaps the residual and the fine-level smoothing: its
+    // branch is joined by the first coarse solve, and in any case before the iteration ends
+    if ((rc = refresh_preconditioner(P, s, false))) return rc;
     if ((rc = run_inner(P, P->u, P->prm.n_inner, 1, s))) return rc;
+    if (P->prm.precond == TO_PRECOND_MG) TO_CUDA(cudaStreamWaitEvent(s, P->ev_join, 0));
     if ((rc = launch_sens_filter_T(P, s))) return rc;
     if ((rc = launch_project(P, nullptr, P->rho, P->grad, P->rho, 1, s))) return rc;
     return launch_record(P, s);

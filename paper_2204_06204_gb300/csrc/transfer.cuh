@@ -1,6 +1,7 @@
-// Per-node bodies of the multigrid grid transfers (trilinear prolongation P and
-// its transpose, fixed DOFs masked on both sides), shared by the per-level
-// kernels and the cluster kernel that runs the coarse levels in one launch.
+// Per-node bodies of the multigrid level operations: the grid transfers
+// (trilinear prolongation P and its transpose, fixed DOFs masked on both sides)
+// and the inverse Jacobi diagonal, shared by the per-level kernels, the coarse
+// tail and the batched kernels.
 #pragma once
 
 #include "internal.cuh"
@@ -76,6 +77,26 @@ __device__ __forceinline__ void prolong_node(int cx, int cy, int cz, int i, int 
     }
     for (int c = 0; c < 3; ++c)
         if (!((m >> c) & 1)) xf[3 * n + c] += acc[c];
+}
+
+// 1 / diag(K^) at node (i, j, k): diag(K^) is kdiag times the sum of the moduli of
+// the (up to 8) elements around the node, 1 on fixed DOFs; one divide per DOF here,
+// multiplications where it is used
+template <typename T>
+__device__ __forceinline__ void diag_node(int nx, int ny, int nz, int i, int j, int k, const T* __restrict__ E,
+                                          const uint8_t* __restrict__ mask, T* __restrict__ dinv, double kdiag) {
+    const long long n = i + (long long)(nx + 1) * (j + (long long)(ny + 1) * k);
+    T s = T(0);
+    for (int dk = -1; dk <= 0; ++dk)
+        for (int dj = -1; dj <= 0; ++dj)
+            for (int di = -1; di <= 0; ++di) {
+                const int ei = i + di, ej = j + dj, ek = k + dk;
+                if (ei < 0 || ei >= nx || ej < 0 || ej >= ny || ek < 0 || ek >= nz) continue;
+                s += E[ei + (long long)nx * (ej + (long long)ny * ek)];
+            }
+    const uint8_t mk = mask[n];
+    const T v = T(1) / ((T)kdiag * s);
+    for (int c = 0; c < 3; ++c) dinv[3 * n + c] = ((mk >> c) & 1) ? T(1) : v;
 }
 
 }  // namespace to

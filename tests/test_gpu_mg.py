@@ -89,3 +89,21 @@ def test_mg_rejects_grid_without_coarse_levels():
     with pytest.raises(fb.ToError) as e:
         fb.Problem.from_workload(pb, prm)
     assert e.value.code == 1
+
+
+def test_mg_repeatable_with_large_coarsest_inverse():
+    """Two problem instances stepped the same way give bitwise identical designs.  The
+    coarsest inverse (here 300 DOFs: the in-place Gauss-Jordan in global memory) runs on a
+    forked stream branch; every refresh outside the outer iteration joins it at once, so a
+    later iteration cannot reassemble the coarse operator under a running inverse."""
+    fb = _fb()
+    pb = W.batch_cantilevers(6)[1]   # 32 x 24 x 32: coarsest 4 x 3 x 4
+    prm = fb.to_default_params(precision=fb.TO_FP64, precond=fb.TO_PRECOND_MG, n_inner=2)
+    out = []
+    for _ in range(3):
+        with fb.Problem.from_workload(pb, prm) as P:
+            st = P.step(4)
+            out.append((P.get_state()[0].cpu().numpy(), [s["J"] for s in st]))
+    for rho, J in out[1:]:
+        assert np.array_equal(rho, out[0][0])
+        assert J == out[0][1]
