@@ -325,32 +325,49 @@ def main():
         Pd.close()
         del rho_d, gd
 
-    # --- batched: 64 independent cantilevers of seeded uneven sizes, one launch per phase + a graph
+    # --- batched: 64 independent cantilevers of seeded uneven sizes, one launch per phase + a graph;
+    # the Jacobi x5 batch and the multigrid x2 batch (V-cycle steps batched per level, the coarse
+    # tails of all problems in one launch), each with the mean ||K u_k - f|| after 24 iterations
     batch = None
     if not args.no_batch:
         pbs = W.batch_cantilevers(64)
-        prm_b = fb.to_default_params(precision=fb.TO_FP32_MIXED, n_inner=5)
-        probs = [fb.Problem.from_workload(pb_, prm_b, device=local) for pb_ in pbs]
-        with fb.Batch(probs) as Bt:
-            tile_kc, tile_us = Bt.tile()
-            Bt.step(3, want_stats=False)
-            torch.cuda.synchronize()
-            kb = 20
-            a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a_.record(stream)
-            Bt.step(kb, want_stats=False)
-            b_.record(stream)
-            torch.cuda.synchronize()
-            tb = a_.elapsed_time(b_) / 1000.0
         ndof_b = sum(pb_.n_dof for pb_ in pbs)
+        kb = 20
+
+        def run_batch(prm_b):
+            probs = [fb.Problem.from_workload(pb_, prm_b, device=local) for pb_ in pbs]
+            with fb.Batch(probs) as Bt:
+                tile_kc, tile_us = Bt.tile()
+                Bt.step(3, want_stats=False)
+                torch.cuda.synchronize()
+                a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a_.record(stream)
+                Bt.step(kb, want_stats=False)
+                b_.record(stream)
+                torch.cuda.synchronize()
+                tb = a_.elapsed_time(b_) / 1000.0
+                st = Bt.step(1, want_stats=True)
+            res = float(np.mean([s_[-1]["res2"] for s_ in st]))
+            for P_ in probs:
+                P_.close()
+            return tb, tile_kc, tile_us, res
+
+        tb, tile_kc, tile_us, res_j = run_batch(fb.to_default_params(precision=fb.TO_FP32_MIXED, n_inner=5))
         batch = {"workload": "64 seeded cantilevers 16x16x16 .. 64x32x32, FP32-mixed, Jacobi steepest descent x5",
                  "problems": 64, "total_dofs": ndof_b, "batched_iterations": kb,
                  "ms_per_batched_iteration": tb * 1e3 / kb,
                  "outer_iters_per_s_aggregate": 64 * kb / tb,
                  "apply_gdofs_effective": ndof_b * 6 * kb / tb / 1e9,
-                 "autotuned_tile_planes": tile_kc, "autotuned_batched_apply_us": tile_us}
-        for P_ in probs:
-            P_.close()
+                 "autotuned_tile_planes": tile_kc, "autotuned_batched_apply_us": tile_us,
+                 "mean_residual_norm_at_24": res_j}
+        tbm, tile_kc, tile_us, res_m = run_batch(fb.to_default_params(precision=fb.TO_FP32_MIXED,
+                                                                     precond=fb.TO_PRECOND_MG, n_inner=2))
+        batch["multigrid"] = {"workload": "the same 64 cantilevers, FP32-mixed, multigrid-preconditioned steepest "
+                                          "descent x2 (batched V-cycles)",
+                              "ms_per_batched_iteration": tbm * 1e3 / kb,
+                              "outer_iters_per_s_aggregate": 64 * kb / tbm,
+                              "autotuned_tile_planes": tile_kc,
+                              "mean_residual_norm_at_24": res_m}
 
     # --- plain FP64
     res64 = None
