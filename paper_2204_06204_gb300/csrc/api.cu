@@ -114,7 +114,7 @@ extern "C" void to_destroy(to_problem* P) {
     if (!P) return;
     DeviceGuard dg(P->device);
     void** bufs[] = {&P->rho, &P->rhot, &P->Ed, &P->Hs, &P->gt, &P->grad, &P->tmp_e, &P->stencil_w,
-                     &P->u, &P->f, &P->r, &P->z, &P->q, &P->tmp_v, &P->coarse_A, &P->coarse_L, &P->iters};
+                     &P->u, &P->f, &P->r, &P->z, &P->q, &P->tmp_v, &P->coarse_A, &P->coarse_L, &P->iters, &P->gj_work, &P->gj_tab};
     for (void** b : bufs) dfree(*b);
     void* st = P->stencil;
     dfree(st);

@@ -131,6 +131,8 @@ struct to_problem {
     void* coarse_A = nullptr;      // dense coarsest operator (T), n_c x n_c
     void* coarse_L = nullptr;      // scaled inverse (T), n_c x n_c, then the n_c scale factors
     int n_coarse = 0;
+    void* gj_work = nullptr;       // blocked coarsest inversion (n_coarse > 160): work matrix, block column, pivot
+    void* gj_tab = nullptr;        // its one-entry argument table
     int mg_tail = 0;               // first level of the one-CTA coarse tail (0: none)
 
     // Krylov preconditioner (Eq. LSP): basis of D + 2 columns (leading dimension kry_ld),

@@ -25,8 +25,6 @@ namespace to {
 
 constexpr int kMaxCoarseDof = 1024;  // dense coarsest solve; in shared memory while n^2 entries fit
 // dynamic shared memory left for the matrix next to the static row / column / scale arrays
-template <typename T>
-constexpr size_t smem_cap() { return 232448 - 3 * kMaxCoarseDof * sizeof(T) - 1024; }
 
 static int grid1(long long n, int num_sms) {
     long long b = (n + 255) / 256;
@@ -117,71 +115,6 @@ __global__ void k_dense_assemble(int nx, int ny, int nz, const T* __restrict__ E
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < (long long)n * n;
          idx += (long long)gridDim.x * blockDim.x)
         A[idx] = dense_entry<T>(nx, ny, nz, E, mask, ke, hscale, n, idx);
-}
-
-// In-place inverse of the unit-diagonal-scaled SPD matrix by Gauss-Jordan
-// elimination (no pivoting needed for SPD), in shared memory when it fits
-// (SMEM) or in the output buffer otherwise; writes S A S inverted and the
-// scaling s = diag(A)^-1/2.
-template <typename T, bool SMEM>
-__device__ __forceinline__ void dense_invert_body(const T* __restrict__ A, T* __restrict__ Ainv, T* __restrict__ sc,
-                                                  int n, int* err, unsigned char* smem_raw) {
-    __shared__ T row[kMaxCoarseDof];
-    __shared__ T col[kMaxCoarseDof];
-    __shared__ T s[kMaxCoarseDof];
-    __shared__ int bad;
-    T* M = SMEM ? reinterpret_cast<T*>(smem_raw) : Ainv;
-    const int tid = threadIdx.x + 32 * threadIdx.y, nt = blockDim.x * blockDim.y;
-    if (tid == 0) bad = 0;
-    __syncthreads();
-    for (int i = tid; i < n; i += nt) {
-        const T d = A[(long long)i * n + i];
-        s[i] = d > T(0) ? T(1) / tsqrt(d) : T(0);
-        if (!(d > T(0))) bad = 1;
-    }
-    __syncthreads();
-    if (bad) {
-        if (tid == 0) set_err(err, TO_ERR_SINGULAR);
-        return;
-    }
-    const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 32 threads: column / row strides
-    for (int i = ty; i < n; i += 32)
-        for (int j = tx; j < n; j += 32) M[i * n + j] = s[i] * A[(long long)i * n + j] * s[j];
-    __syncthreads();
-    for (int k = 0; k < n; ++k) {
-        const T piv = M[k * n + k];
-        if (!(piv > T(0))) {
-            if (tid == 0) set_err(err, TO_ERR_SINGULAR);
-            return;
-        }
-        const T ip = T(1) / piv;
-        for (int j = tid; j < n; j += nt) {
-            row[j] = (j == k ? T(1) : M[k * n + j]) * ip;
-            col[j] = M[j * n + k];
-        }
-        __syncthreads();
-        for (int i = ty; i < n; i += 32) {
-            const T ci = col[i];
-            for (int j = tx; j < n; j += 32) {
-                if (i == k)
-                    M[i * n + j] = row[j];
-                else
-                    M[i * n + j] = (j == k ? T(0) : M[i * n + j]) - ci * row[j];
-            }
-        }
-        __syncthreads();
-    }
-    if (SMEM)
-        for (int i = ty; i < n; i += 32)
-            for (int j = tx; j < n; j += 32) Ainv[i * n + j] = M[i * n + j];
-    for (int i = tid; i < n; i += nt) sc[i] = s[i];
-}
-
-template <typename T, bool SMEM>
-__global__ void __launch_bounds__(1024) k_dense_invert(const T* __restrict__ A, T* __restrict__ Ainv, T* __restrict__ sc,
-                                                       int n, int* err) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    dense_invert_body<T, SMEM>(A, Ainv, sc, n, err, smem_raw);
 }
 
 // Register-blocked variant for n <= 160: thread (tx, ty) of a 32 x 32 block keeps
@@ -293,6 +226,151 @@ template <typename T>
 __global__ void __launch_bounds__(1024) k_dense_invert_reg(const T* __restrict__ A, T* __restrict__ Ainv,
                                                            T* __restrict__ sc, int n, int* err) {
     dense_invert_reg_body<T>(A, Ainv, sc, n, err);
+}
+
+// Blocked Gauss-Jordan inversion for the larger coarsest operators (n > 160): the
+// scaled matrix S A S (s = diag(A)^-1/2), padded with the identity to N = 32 nb, in
+// a global work matrix W; per 32-block k, the same in-place elimination as the
+// scalar form, by blocks:
+//   W_kk <- W_kk^-1 = P;  W_kj <- P W_kj (j != k);
+//   W_ij <- W_ij - W_ik W_kj (i, j != k, W_ik before this step);  W_ik <- -W_ik P (i != k).
+// One launch for the pivot block, one for the block row (which also saves the old
+// block column), one for every other block: many CTAs per step instead of one CTA
+// sweeping the whole matrix n times.  Tables hold one entry per problem.
+constexpr int kGjB = 32;
+
+template <typename T>
+struct GjArgs {
+    int n, nb;      // order, 32-blocks (N = 32 nb)
+    const T* A;     // n x n operator
+    T* W;           // N x N work matrix
+    T* C;           // N x 32: the block column of W before the current step
+    T* P;           // 32 x 32: the current pivot block's inverse
+    T* inv;         // n x n inverse of S A S, then the n scale factors s
+    int* err;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_gj_init(const GjArgs<T>* __restrict__ tab) {
+    const GjArgs<T>& a = tab[blockIdx.y];
+    const int n = a.n, N = a.nb * kGjB;
+    const long long NN = (long long)N * N;
+    for (long long q = blockIdx.x * 256LL + threadIdx.x; q < NN; q += (long long)gridDim.x * 256) {
+        const int i = (int)(q / N), j = (int)(q % N);
+        T v = i == j ? T(1) : T(0);
+        if (i < n && j < n) {
+            const T di = a.A[(long long)i * n + i], dj = a.A[(long long)j * n + j];
+            const T si = di > T(0) ? T(1) / tsqrt(di) : T(0), sj = dj > T(0) ? T(1) / tsqrt(dj) : T(0);
+            v = si * a.A[(long long)i * n + j] * sj;
+            if (j == 0) {
+                a.inv[(long long)n * n + i] = si;
+                if (!(di > T(0))) set_err(a.err, TO_ERR_SINGULAR);
+            }
+        }
+        a.W[q] = v;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_gj_pivot(const GjArgs<T>* __restrict__ tab, int k) {
+    const GjArgs<T>& a = tab[blockIdx.x];
+    if (k >= a.nb) return;
+    __shared__ T M[kGjB][kGjB + 1];
+    __shared__ T row[kGjB], col[kGjB];
+    const int tx = threadIdx.x, ty = threadIdx.y, N = a.nb * kGjB;
+    T* Wkk = a.W + (size_t)(k * kGjB) * N + k * kGjB;
+    M[ty][tx] = Wkk[(size_t)ty * N + tx];
+    __syncthreads();
+    for (int p = 0; p < kGjB; ++p) {
+        const T piv = M[p][p];
+        if (!(piv > T(0)) && tx == 0 && ty == 0) set_err(a.err, TO_ERR_SINGULAR);
+        const T ip = piv > T(0) ? T(1) / piv : T(0);
+        if (ty == 0) row[tx] = (tx == p ? T(1) : M[p][tx]) * ip;
+        if (ty == 1) col[tx] = M[tx][p];
+        __syncthreads();
+        M[ty][tx] = ty == p ? row[tx] : (tx == p ? T(0) : M[ty][tx]) - col[ty] * row[tx];
+        __syncthreads();
+    }
+    const T v = M[ty][tx];
+    Wkk[(size_t)ty * N + tx] = v;
+    a.P[ty * kGjB + tx] = v;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_gj_row(const GjArgs<T>* __restrict__ tab, int k) {
+    const GjArgs<T>& a = tab[blockIdx.y];
+    const int r = blockIdx.x;
+    if (k >= a.nb || r >= a.nb || r == k) return;
+    __shared__ T Ps[kGjB][kGjB + 1], Rs[kGjB][kGjB + 1];
+    const int tx = threadIdx.x, ty = threadIdx.y, N = a.nb * kGjB;
+    T* Wkr = a.W + (size_t)(k * kGjB) * N + r * kGjB;
+    Ps[ty][tx] = a.P[ty * kGjB + tx];
+    Rs[ty][tx] = Wkr[(size_t)ty * N + tx];
+    a.C[(size_t)(r * kGjB + ty) * kGjB + tx] = a.W[(size_t)(r * kGjB + ty) * N + k * kGjB + tx];   // block (r, k)
+    __syncthreads();
+    T acc = T(0);
+#pragma unroll 8
+    for (int t = 0; t < kGjB; ++t) acc = fma(Ps[ty][t], Rs[t][tx], acc);
+    Wkr[(size_t)ty * N + tx] = acc;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_gj_update(const GjArgs<T>* __restrict__ tab, int k, int nbmax) {
+    const GjArgs<T>& a = tab[blockIdx.y];
+    const int i = blockIdx.x / nbmax, j = blockIdx.x % nbmax;
+    if (k >= a.nb || i >= a.nb || j >= a.nb || i == k) return;
+    __shared__ T Cs[kGjB][kGjB + 1], Bs[kGjB][kGjB + 1];
+    const int tx = threadIdx.x, ty = threadIdx.y, N = a.nb * kGjB;
+    Cs[ty][tx] = a.C[(size_t)(i * kGjB + ty) * kGjB + tx];
+    Bs[ty][tx] = j == k ? a.P[ty * kGjB + tx] : a.W[(size_t)(k * kGjB + ty) * N + j * kGjB + tx];
+    __syncthreads();
+    T acc = T(0);
+#pragma unroll 8
+    for (int t = 0; t < kGjB; ++t) acc = fma(Cs[ty][t], Bs[t][tx], acc);
+    T* w = a.W + (size_t)(i * kGjB + ty) * N + j * kGjB + tx;
+    *w = j == k ? -acc : *w - acc;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_gj_final(const GjArgs<T>* __restrict__ tab) {
+    const GjArgs<T>& a = tab[blockIdx.y];
+    const int n = a.n, N = a.nb * kGjB;
+    const long long nn = (long long)n * n;
+    for (long long q = blockIdx.x * 256LL + threadIdx.x; q < nn; q += (long long)gridDim.x * 256)
+        a.inv[q] = a.W[(size_t)(q / n) * N + q % n];
+}
+
+// the blocked inversion of nprob problems' coarsest operators (largest nbmax blocks)
+template <typename T>
+static int gj_launch(const void* tab, int nprob, int nbmax, int num_sms, cudaStream_t s) {
+    const GjArgs<T>* t = (const GjArgs<T>*)tab;
+    const long long NN = (long long)nbmax * kGjB * nbmax * kGjB;
+    const int gx = (int)std::max<long long>(1, std::min<long long>((NN + 255) / 256, (8LL * num_sms + nprob - 1) / nprob));
+    k_gj_init<T><<<dim3(gx, nprob), 256, 0, s>>>(t);
+    for (int k = 0; k < nbmax; ++k) {
+        k_gj_pivot<T><<<nprob, dim3(kGjB, kGjB), 0, s>>>(t, k);
+        k_gj_row<T><<<dim3(nbmax, nprob), dim3(kGjB, kGjB), 0, s>>>(t, k);
+        k_gj_update<T><<<dim3(nbmax * nbmax, nprob), dim3(kGjB, kGjB), 0, s>>>(t, k, nbmax);
+    }
+    k_gj_final<T><<<dim3(gx, nprob), 256, 0, s>>>(t);
+    TO_CUDA(cudaGetLastError());
+    return TO_OK;
+}
+
+// one problem's blocked-inversion table entry (work buffers from gj_work)
+template <typename T>
+static GjArgs<T> gj_args(const to_problem* P) {
+    GjArgs<T> g;
+    g.n = P->n_coarse;
+    g.nb = (P->n_coarse + kGjB - 1) / kGjB;
+    const size_t N = (size_t)g.nb * kGjB;
+    g.A = (const T*)P->coarse_A;
+    g.W = (T*)P->gj_work;
+    g.C = g.W + N * N;
+    g.P = g.C + N * kGjB;
+    g.inv = (T*)P->coarse_L;
+    g.err = &P->sc->err;
+    return g;
 }
 
 // x = S Ainv S b   (one CTA per row block)
@@ -708,12 +786,20 @@ int mg_build(to_problem* P) {
     P->ke_dev = (double*)ked;
     // level-0 V-cycle scratch
     if (cudaMalloc(&P->lv[0].t, P->n_dof * es) != cudaSuccess) return fail(TO_ERR_CUDA, "scratch allocation");
-    const size_t smem = (size_t)n * n * es;
-    if (smem <= (P->prec == TO_FP64 ? smem_cap<double>() : smem_cap<float>())) {
-        cudaError_t e = P->prec == TO_FP64
-                            ? cudaFuncSetAttribute(k_dense_invert<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-                            : cudaFuncSetAttribute(k_dense_invert<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return fail(TO_ERR_CUDA, std::string("shared memory opt-in: ") + cudaGetErrorString(e));
+    if (n > kRegDof) {   // the blocked inversion's work matrix, block column and pivot block, and its table
+        const size_t N = (size_t)((n + kGjB - 1) / kGjB) * kGjB;
+        if (cudaMalloc(&P->gj_work, (N * N + N * kGjB + (size_t)kGjB * kGjB) * es) != cudaSuccess ||
+            cudaMalloc(&P->gj_tab, P->prec == TO_FP64 ? sizeof(GjArgs<double>) : sizeof(GjArgs<float>)) != cudaSuccess)
+            return fail(TO_ERR_CUDA, "coarse inversion scratch allocation");
+        cudaError_t e;
+        if (P->prec == TO_FP64) {
+            const GjArgs<double> g = gj_args<double>(P);
+            e = cudaMemcpy(P->gj_tab, &g, sizeof(g), cudaMemcpyHostToDevice);
+        } else {
+            const GjArgs<float> g = gj_args<float>(P);
+            e = cudaMemcpy(P->gj_tab, &g, sizeof(g), cudaMemcpyHostToDevice);
+        }
+        if (e != cudaSuccess) return fail(TO_ERR_CUDA, "coarse inversion table upload");
     }
     // the coarse tail: from the first level (>= 1, above the coarsest) with at most
     // kTailMaxElems elements whose levels fit in shared memory
@@ -748,20 +834,18 @@ static int refresh_t(to_problem* P, cudaStream_t s, bool join) {
     k_dense_assemble<T><<<grid1((long long)n * n, P->num_sms), 256, 0, s>>>(
         Cst.nx, Cst.ny, Cst.nz, (const T*)Cst.E, Cst.mask, P->ke_dev, Cst.h, (T*)P->coarse_A, n);
     TO_CUDA(cudaGetLastError());
-    const size_t smem = (size_t)n * n * sizeof(T);
     T* inv = (T*)P->coarse_L;
     // the inverse runs on a branch; the first coarse solve joins it (it is needed only there)
     TO_CUDA(cudaEventRecord(P->ev_fork, s));
     TO_CUDA(cudaStreamWaitEvent(P->side, P->ev_fork, 0));
     cudaStream_t main_s = s;
     s = P->side;
-    if (n <= kRegDof)
+    if (n <= kRegDof) {
         k_dense_invert_reg<T><<<1, dim3(32, 32), 0, s>>>((const T*)P->coarse_A, inv, inv + (size_t)n * n, n, &P->sc->err);
-    else if (smem <= smem_cap<T>())
-        k_dense_invert<T, true><<<1, dim3(32, 32), smem, s>>>((const T*)P->coarse_A, inv, inv + (size_t)n * n, n, &P->sc->err);
-    else
-        k_dense_invert<T, false><<<1, dim3(32, 32), 0, s>>>((const T*)P->coarse_A, inv, inv + (size_t)n * n, n, &P->sc->err);
-    TO_CUDA(cudaGetLastError());
+        TO_CUDA(cudaGetLastError());
+    } else if (int rc = gj_launch<T>(P->gj_tab, 1, (n + kGjB - 1) / kGjB, P->num_sms, s)) {
+        return rc;
+    }
     TO_CUDA(cudaEventRecord(P->ev_join, s));
     // outside the outer iteration nothing else joins the branch: without this a later
     // refresh could rewrite coarse_A / coarse_L while this inverse still runs
@@ -975,13 +1059,6 @@ __global__ void __launch_bounds__(1024) k_bm_invert_reg(const BmDense<T>* __rest
     dense_invert_reg_body<T>(a.A, a.inv, a.inv + (size_t)a.n * a.n, a.n, a.err);
 }
 
-template <typename T, bool SMEM>
-__global__ void __launch_bounds__(1024) k_bm_invert(const BmDense<T>* __restrict__ tab) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const BmDense<T>& a = tab[blockIdx.x];
-    dense_invert_body<T, SMEM>(a.A, a.inv, a.inv + (size_t)a.n * a.n, a.n, a.err, smem_raw);
-}
-
 template <typename T>
 __global__ void __launch_bounds__(tail_threads<T>()) k_mg_tail_batch(const TailArgs<T>* __restrict__ tab, const HaarK<T> kh) {
     extern __shared__ __align__(16) unsigned char tsm[];
@@ -989,7 +1066,7 @@ __global__ void __launch_bounds__(tail_threads<T>()) k_mg_tail_batch(const TailA
 }
 
 enum BmKind { BM_JAC, BM_OPER, BM_RESTRICT, BM_PROLONG, BM_TAIL, BM_COARSEN, BM_DIAG, BM_ASSEMBLE, BM_INVERT_REG,
-              BM_INVERT_SMEM, BM_INVERT_GLOBAL };
+              BM_INVERT_GJ };
 
 struct BmOp {
     int kind = 0, mode = 0, n = 0, grid_x = 1, max_tiles = 0;
@@ -999,7 +1076,7 @@ struct BmOp {
 };
 
 struct BatchMG {
-    int prec = TO_FP32_MIXED, n = 0;
+    int prec = TO_FP32_MIXED, n = 0, num_sms = 1;
     std::vector<BmOp> refresh, vcycle;
     std::vector<void*> dev, host;
 };
@@ -1218,17 +1295,35 @@ static int batch_mg_build_t(to_problem* const* probs, int n, int kchunk, BatchMG
         op.grid_x = grid_x_for(mx, num_sms, n);
         if ((rc = upload_table(M, h, &op.tab))) return rc;
         M->refresh.push_back(op);
-        const size_t sm = (size_t)nmax * nmax * sizeof(T);
-        if (nmax <= kRegDof) {
-            op.kind = BM_INVERT_REG;
-        } else if (sm <= smem_cap<T>()) {
-            op.kind = BM_INVERT_SMEM;
-            op.smem = sm;
-            TO_CUDA(cudaFuncSetAttribute(k_bm_invert<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        } else {
-            op.kind = BM_INVERT_GLOBAL;
+        // the inverses: register-blocked for n <= 160, blocked Gauss-Jordan over many CTAs above
+        std::vector<BmDense<T>> hr;
+        std::vector<GjArgs<T>> hg;
+        int nbmax = 0;
+        for (int p = 0; p < n; ++p) {
+            if (probs[p]->n_coarse <= kRegDof) {
+                hr.push_back(h[p]);
+            } else {
+                hg.push_back(gj_args<T>(probs[p]));
+                nbmax = std::max(nbmax, hg.back().nb);
+            }
         }
-        M->refresh.push_back(op);
+        (void)nmax;
+        if (!hr.empty()) {
+            BmOp r;
+            r.kind = BM_INVERT_REG;
+            r.n = (int)hr.size();
+            if ((rc = upload_table(M, hr, &r.tab))) return rc;
+            M->refresh.push_back(r);
+        }
+        if (!hg.empty()) {
+            BmOp g;
+            g.kind = BM_INVERT_GJ;
+            g.n = (int)hg.size();
+            g.max_tiles = nbmax;
+            if ((rc = upload_table(M, hg, &g.tab))) return rc;
+            M->refresh.push_back(g);
+        }
+        return TO_OK;
     }
     return TO_OK;
 }
@@ -1253,8 +1348,11 @@ static int batch_mg_run(const BatchMG* M, const std::vector<BmOp>& ops, cudaStre
             case BM_DIAG: k_bm_diag<T><<<g2, 256, 0, s>>>((const BmLevel<T>*)op.tab); break;
             case BM_ASSEMBLE: k_bm_assemble<T><<<g2, 256, 0, s>>>((const BmDense<T>*)op.tab); break;
             case BM_INVERT_REG: k_bm_invert_reg<T><<<op.n, dim3(32, 32), 0, s>>>((const BmDense<T>*)op.tab); break;
-            case BM_INVERT_SMEM: k_bm_invert<T, true><<<op.n, dim3(32, 32), op.smem, s>>>((const BmDense<T>*)op.tab); break;
-            default: k_bm_invert<T, false><<<op.n, dim3(32, 32), 0, s>>>((const BmDense<T>*)op.tab); break;
+            default: {
+                const int rc = gj_launch<T>(op.tab, op.n, op.max_tiles, M->num_sms, s);
+                if (rc) return rc;
+                break;
+            }
         }
         TO_CUDA(cudaGetLastError());
     }
@@ -1278,6 +1376,7 @@ int batch_mg_build(to_problem* const* probs, int n, int kchunk, BatchMG** out) {
     BatchMG* M = new BatchMG();
     M->prec = probs[0]->prec;
     M->n = n;
+    M->num_sms = probs[0]->num_sms;
     const int rc = M->prec == TO_FP64 ? batch_mg_build_t<double>(probs, n, kchunk, M) : batch_mg_build_t<float>(probs, n, kchunk, M);
     if (rc) {
         batch_mg_free(M);
