@@ -52,21 +52,22 @@ __global__ void k_coarsen_E(int cx, int cy, int cz, const T* __restrict__ Ef, T*
     if (t.ok) coarsen_elem<T>(cx, cy, t.i, t.j, t.k, Ef, Ec);
 }
 
-// b_c = m_c P^T (m_f t), optionally with the coarse level's first sweep
-template <typename T>
+// b_c = m_c P^T (m_f t), optionally with the coarse level's first sweep (IX: 32-bit indices
+// while the fine level has fewer than 2^31 DOFs)
+template <typename T, typename IX>
 __global__ void k_restrict(int cx, int cy, int cz, const T* __restrict__ tf, const uint8_t* __restrict__ mf,
                            const uint8_t* __restrict__ mc, T* __restrict__ bc, const T* __restrict__ dinvc,
                            T* __restrict__ xc, T omega) {
     const Idx3 t = idx3(cx + 1, cy + 1, cz + 1);
-    if (t.ok) restrict_node<T, long long, true>(cx, cy, cz, t.i, t.j, t.k, tf, mf, mc, bc, dinvc, xc, omega);
+    if (t.ok) restrict_node<T, IX, true>(cx, cy, cz, t.i, t.j, t.k, tf, mf, mc, bc, dinvc, xc, omega);
 }
 
 // x_f += m_f P (m_c x_c)
-template <typename T>
+template <typename T, typename IX>
 __global__ void k_prolong_add(int cx, int cy, int cz, const T* __restrict__ xc, const uint8_t* __restrict__ mc,
                               const uint8_t* __restrict__ mf, T* __restrict__ xf) {
     const Idx3 t = idx3(2 * cx + 1, 2 * cy + 1, 2 * cz + 1);
-    if (t.ok) prolong_node<T>(cx, cy, cz, t.i, t.j, t.k, xc, mc, mf, xf);
+    if (t.ok) prolong_node<T, IX>(cx, cy, cz, t.i, t.j, t.k, xc, mc, mf, xf);
 }
 
 // x = omega D^-1 b  (first Jacobi sweep from x = 0; dinv = D^-1)
@@ -909,15 +910,24 @@ static int vcycle_t(to_problem* P, int l, const void* b, void* x, void* t, cudaS
     // above the coarsest level the restriction also takes the coarse level's first sweep
     const bool fuse = l + 1 < L - 1;
     void* cfirst = ((nu1 - 1 + nu2) % 2 == 0) ? C.x : C.t;
-    k_restrict<T><<<grid3(C.nx + 1, C.ny + 1, C.nz + 1), block3(), 0, s>>>(
-        C.nx, C.ny, C.nz, (const T*)oth, F.mask, C.mask, (T*)C.b, (const T*)C.dinv, fuse ? (T*)cfirst : nullptr, (T)om);
+    const dim3 gr = grid3(C.nx + 1, C.ny + 1, C.nz + 1);
+    if (F.n_dof < (1LL << 31))
+        k_restrict<T, int><<<gr, block3(), 0, s>>>(C.nx, C.ny, C.nz, (const T*)oth, F.mask, C.mask, (T*)C.b,
+                                                   (const T*)C.dinv, fuse ? (T*)cfirst : nullptr, (T)om);
+    else
+        k_restrict<T, long long><<<gr, block3(), 0, s>>>(C.nx, C.ny, C.nz, (const T*)oth, F.mask, C.mask, (T*)C.b,
+                                                         (const T*)C.dinv, fuse ? (T*)cfirst : nullptr, (T)om);
     TO_CUDA(cudaGetLastError());
     if (P->mg_tail == l + 1) {
         if ((rc = tail_t<T>(P, s))) return rc;   // levels l+1 .. L-1 in one CTA
     } else if ((rc = vcycle_t<T>(P, l + 1, C.b, C.x, C.t, s, fuse))) {
         return rc;
     }
-    k_prolong_add<T><<<grid3(F.nx + 1, F.ny + 1, F.nz + 1), block3(), 0, s>>>(C.nx, C.ny, C.nz, (const T*)C.x, C.mask, F.mask, (T*)cur);
+    const dim3 gp = grid3(F.nx + 1, F.ny + 1, F.nz + 1);
+    if (F.n_dof < (1LL << 31))
+        k_prolong_add<T, int><<<gp, block3(), 0, s>>>(C.nx, C.ny, C.nz, (const T*)C.x, C.mask, F.mask, (T*)cur);
+    else
+        k_prolong_add<T, long long><<<gp, block3(), 0, s>>>(C.nx, C.ny, C.nz, (const T*)C.x, C.mask, F.mask, (T*)cur);
     TO_CUDA(cudaGetLastError());
     for (int it = 0; it < nu2; ++it) {
         // on the fine level the last sweep also reduces b^T x (= r^T z of the lower-level step)
