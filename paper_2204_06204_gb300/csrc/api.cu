@@ -340,7 +340,8 @@ extern "C" int to_set_design(to_problem* P, const void* rho_dev, void* stream) {
     TO_CUDA(cudaMemcpyAsync(P->rho, rho_dev, P->n_elem * P->esz, cudaMemcpyDeviceToDevice, s));
     int rc = launch_moduli(P, s);
     if (rc) return rc;
-    return refresh_preconditioner(P, s);
+    P->precond_stale = 1;   // refreshed by the next to_inner_solve (to_step refreshes every iteration)
+    return TO_OK;
 }
 
 extern "C" int to_apply_K(to_problem* P, const void* u_dev, void* y_dev, void* stream) {
@@ -353,6 +354,10 @@ extern "C" int to_apply_K(to_problem* P, const void* u_dev, void* y_dev, void* s
 extern "C" int to_inner_solve(to_problem* P, void* u_dev, int32_t nsteps, double* res_out, void* stream) {
     TO_ENTER(P);
     if (!u_dev || nsteps < 0) return fail(TO_ERR_ARG, "bad arguments");
+    if (P->precond_stale) {
+        if (int rc0 = refresh_preconditioner(P, s)) return rc0;
+        P->precond_stale = 0;
+    }
     void* gt = P->gt;
     P->gt = nullptr;
     int rc = run_inner(P, u_dev, nsteps, 0, s);
@@ -464,6 +469,7 @@ extern "C" int to_step(to_problem* P, int32_t n_outer, to_stats* stats_out, void
             if (rc) return rc;
         }
     }
+    P->precond_stale = 0;   // the last iteration refreshed it for its own moduli
     TO_CUDA(cudaEventRecord(P->ev_out, P->gstream));
     TO_CUDA(cudaStreamWaitEvent(s, P->ev_out, 0));
     if (stats_out) {
@@ -503,7 +509,8 @@ extern "C" int to_set_state(to_problem* P, const void* rho_dev, const void* u_de
     TO_CUDA(cudaGetLastError());
     int rc = launch_moduli(P, s);
     if (rc) return rc;
-    return refresh_preconditioner(P, s);
+    P->precond_stale = 1;   // refreshed by the next to_inner_solve (to_step refreshes every iteration)
+    return TO_OK;
 }
 
 __global__ void k_clear_err(to::DevScalars* sc) { sc->err = 0; }

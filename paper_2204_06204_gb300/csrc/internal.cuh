@@ -134,6 +134,7 @@ struct to_problem {
     void* gj_work = nullptr;       // blocked coarsest inversion (n_coarse > 160): work matrix, block column, pivot
     void* gj_tab = nullptr;        // its one-entry argument table
     int mg_tail = 0;               // first level of the one-CTA coarse tail (0: none)
+    int precond_stale = 0;         // the design changed outside to_step: refresh before the next lower-level solve
 
     // Krylov preconditioner (Eq. LSP): basis of D + 2 columns (leading dimension kry_ld),
     // device coefficients, per-block partials of its streaming passes
