@@ -297,39 +297,66 @@ __global__ void __launch_bounds__(1024) k_gj_pivot(const GjArgs<T>* __restrict__
     a.P[ty * kGjB + tx] = v;
 }
 
+// block tiles below: 32 x 8 threads, thread (tx, ty) owns rows ty + 8 m (m < 4) of column tx
+constexpr int kGjRows = kGjB / 8;
+
 template <typename T>
-__global__ void __launch_bounds__(1024) k_gj_row(const GjArgs<T>* __restrict__ tab, int k) {
+__global__ void __launch_bounds__(256) k_gj_row(const GjArgs<T>* __restrict__ tab, int k) {
     const GjArgs<T>& a = tab[blockIdx.y];
     const int r = blockIdx.x;
     if (k >= a.nb || r >= a.nb || r == k) return;
     __shared__ T Ps[kGjB][kGjB + 1], Rs[kGjB][kGjB + 1];
     const int tx = threadIdx.x, ty = threadIdx.y, N = a.nb * kGjB;
     T* Wkr = a.W + (size_t)(k * kGjB) * N + r * kGjB;
-    Ps[ty][tx] = a.P[ty * kGjB + tx];
-    Rs[ty][tx] = Wkr[(size_t)ty * N + tx];
-    a.C[(size_t)(r * kGjB + ty) * kGjB + tx] = a.W[(size_t)(r * kGjB + ty) * N + k * kGjB + tx];   // block (r, k)
+#pragma unroll
+    for (int m = 0; m < kGjRows; ++m) {
+        const int y = ty + 8 * m;
+        Ps[y][tx] = a.P[y * kGjB + tx];
+        Rs[y][tx] = Wkr[(size_t)y * N + tx];
+        a.C[(size_t)(r * kGjB + y) * kGjB + tx] = a.W[(size_t)(r * kGjB + y) * N + k * kGjB + tx];   // block (r, k)
+    }
     __syncthreads();
-    T acc = T(0);
+    T acc[kGjRows];
+#pragma unroll
+    for (int m = 0; m < kGjRows; ++m) acc[m] = T(0);
 #pragma unroll 8
-    for (int t = 0; t < kGjB; ++t) acc = fma(Ps[ty][t], Rs[t][tx], acc);
-    Wkr[(size_t)ty * N + tx] = acc;
+    for (int t = 0; t < kGjB; ++t) {
+        const T b = Rs[t][tx];
+#pragma unroll
+        for (int m = 0; m < kGjRows; ++m) acc[m] = fma(Ps[ty + 8 * m][t], b, acc[m]);
+    }
+#pragma unroll
+    for (int m = 0; m < kGjRows; ++m) Wkr[(size_t)(ty + 8 * m) * N + tx] = acc[m];
 }
 
 template <typename T>
-__global__ void __launch_bounds__(1024) k_gj_update(const GjArgs<T>* __restrict__ tab, int k, int nbmax) {
+__global__ void __launch_bounds__(256) k_gj_update(const GjArgs<T>* __restrict__ tab, int k, int nbmax) {
     const GjArgs<T>& a = tab[blockIdx.y];
     const int i = blockIdx.x / nbmax, j = blockIdx.x % nbmax;
     if (k >= a.nb || i >= a.nb || j >= a.nb || i == k) return;
     __shared__ T Cs[kGjB][kGjB + 1], Bs[kGjB][kGjB + 1];
     const int tx = threadIdx.x, ty = threadIdx.y, N = a.nb * kGjB;
-    Cs[ty][tx] = a.C[(size_t)(i * kGjB + ty) * kGjB + tx];
-    Bs[ty][tx] = j == k ? a.P[ty * kGjB + tx] : a.W[(size_t)(k * kGjB + ty) * N + j * kGjB + tx];
+#pragma unroll
+    for (int m = 0; m < kGjRows; ++m) {
+        const int y = ty + 8 * m;
+        Cs[y][tx] = a.C[(size_t)(i * kGjB + y) * kGjB + tx];
+        Bs[y][tx] = j == k ? a.P[y * kGjB + tx] : a.W[(size_t)(k * kGjB + y) * N + j * kGjB + tx];
+    }
     __syncthreads();
-    T acc = T(0);
+    T acc[kGjRows];
+#pragma unroll
+    for (int m = 0; m < kGjRows; ++m) acc[m] = T(0);
 #pragma unroll 8
-    for (int t = 0; t < kGjB; ++t) acc = fma(Cs[ty][t], Bs[t][tx], acc);
-    T* w = a.W + (size_t)(i * kGjB + ty) * N + j * kGjB + tx;
-    *w = j == k ? -acc : *w - acc;
+    for (int t = 0; t < kGjB; ++t) {
+        const T b = Bs[t][tx];
+#pragma unroll
+        for (int m = 0; m < kGjRows; ++m) acc[m] = fma(Cs[ty + 8 * m][t], b, acc[m]);
+    }
+#pragma unroll
+    for (int m = 0; m < kGjRows; ++m) {
+        T* w = a.W + (size_t)(i * kGjB + ty + 8 * m) * N + j * kGjB + tx;
+        *w = j == k ? -acc[m] : *w - acc[m];
+    }
 }
 
 template <typename T>
@@ -350,8 +377,8 @@ static int gj_launch(const void* tab, int nprob, int nbmax, int num_sms, cudaStr
     k_gj_init<T><<<dim3(gx, nprob), 256, 0, s>>>(t);
     for (int k = 0; k < nbmax; ++k) {
         k_gj_pivot<T><<<nprob, dim3(kGjB, kGjB), 0, s>>>(t, k);
-        k_gj_row<T><<<dim3(nbmax, nprob), dim3(kGjB, kGjB), 0, s>>>(t, k);
-        k_gj_update<T><<<dim3(nbmax * nbmax, nprob), dim3(kGjB, kGjB), 0, s>>>(t, k, nbmax);
+        k_gj_row<T><<<dim3(nbmax, nprob), dim3(kGjB, 8), 0, s>>>(t, k);
+        k_gj_update<T><<<dim3(nbmax * nbmax, nprob), dim3(kGjB, 8), 0, s>>>(t, k, nbmax);
     }
     k_gj_final<T><<<dim3(gx, nprob), 256, 0, s>>>(t);
     TO_CUDA(cudaGetLastError());
