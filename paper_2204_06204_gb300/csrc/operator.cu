@@ -565,10 +565,11 @@ int operator_init(to_problem* P) {
 }
 
 // Tile autotuner of a problem's operator: for every multigrid level (or the fine grid
-// alone), time the damped-Jacobi sweep (the most frequent operator launch) for the
-// cost model's choice and 1, 2, 4, ..., 32 node planes per tile, and keep the fastest for
-// all of that level's operator launches.  Inputs and outputs are the level's scratch
-// vectors: timing only, no state the method reads is changed.
+// alone), time the damped-Jacobi sweep (the most frequent operator launch) for every
+// distinct split of the level's node planes into chunks (the cost model's choice
+// first), twice, and keep the fastest for all of that level's operator launches.
+// Inputs and outputs are the level's scratch vectors: timing only, no state the
+// method reads is changed.
 int operator_autotune(to_problem* P, cudaStream_t s) {
     cudaEvent_t e0, e1;
     TO_CUDA(cudaEventCreate(&e0));
@@ -583,33 +584,36 @@ int operator_autotune(to_problem* P, cudaStream_t s) {
         void* y = l == 0 ? P->tmp_v : Lv.t;
         const void* b = l == 0 ? P->r : Lv.b;
         if (!x || !y || !b) continue;
+        const int planes = Lv.nz + 1;
         const int gx = (Lv.nx + 1 + 30) / 31, gy = (Lv.ny + 1 + 6) / 7;
-        const int model = choose_kchunk((long long)gx * gy, Lv.nz + 1, (long long)P->op_occ[OP_SMOOTH] * P->num_sms);
-        int cand[8] = {model, 1, 2, 4, 8, 16, 32, 0};
+        const int model = choose_kchunk((long long)gx * gy, planes, (long long)P->op_occ[OP_SMOOTH] * P->num_sms);
+        std::vector<int> cand{model};
+        for (int kc = 1; kc <= planes && kc <= 64; ++kc) {
+            const int gz = (planes + kc - 1) / kc;
+            if (kc > 1 && (planes + kc - 2) / (kc - 1) == gz) continue;   // same split as a shorter chunk
+            if (kc != model && (long long)gx * gy * gz <= kMaxRedBlocks) cand.push_back(kc);
+        }
         int best = model;
         float best_t = -1.f;
-        for (int c = 0; c < 7 && !rc; ++c) {
-            const int kc = cand[c];
-            if (kc > Lv.nz + 1 || (c > 0 && kc == model)) continue;
-            const long long ctas = (long long)gx * gy * ((Lv.nz + 1 + kc - 1) / kc);
-            if (ctas > kMaxRedBlocks) continue;
-            Lv.kchunk = kc;
-            for (int r = 0; r < 2 && !rc; ++r) rc = launch_operator(P, l, OP_SMOOTH, x, y, b, s, 0.5, 0);
-            cudaEventRecord(e0, s);
-            for (int r = 0; r < 5 && !rc; ++r) rc = launch_operator(P, l, OP_SMOOTH, x, y, b, s, 0.5, 0);
-            cudaEventRecord(e1, s);
-            if (rc) break;
-            if (cudaEventSynchronize(e1) != cudaSuccess) {
-                rc = fail(TO_ERR_CUDA, "autotune timing");
-                break;
+        for (int round = 0; round < 2 && !rc; ++round)
+            for (size_t c = 0; c < cand.size() && !rc; ++c) {
+                Lv.kchunk = cand[c];
+                for (int r = 0; r < 2 && !rc; ++r) rc = launch_operator(P, l, OP_SMOOTH, x, y, b, s, 0.5, 0);
+                cudaEventRecord(e0, s);
+                for (int r = 0; r < 5 && !rc; ++r) rc = launch_operator(P, l, OP_SMOOTH, x, y, b, s, 0.5, 0);
+                cudaEventRecord(e1, s);
+                if (rc) break;
+                if (cudaEventSynchronize(e1) != cudaSuccess) {
+                    rc = fail(TO_ERR_CUDA, "autotune timing");
+                    break;
+                }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (best_t < 0.f || ms < best_t) {
+                    best_t = ms;
+                    best = cand[c];
+                }
             }
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (best_t < 0.f || ms < best_t) {
-                best_t = ms;
-                best = kc;
-            }
-        }
         Lv.kchunk = best;
     }
     cudaEventDestroy(e0);
