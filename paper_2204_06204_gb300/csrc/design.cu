@@ -213,7 +213,13 @@ static int filter_launch(to_problem* P, const T* x, T* y, cudaStream_t s, T* Eou
     const size_t fs = filter_smem<T>(P->n_stencil, R, kchunk, DIV);
     if (fs > 227 * 1024) return fail(TO_ERR_ARG, "filter tile exceeds shared memory (radius too large for this grid)");
     auto kern = k_filter<T, TRANSPOSE, STATS, PRESCALED, MODULI>;
-    if (fs > 48 * 1024) TO_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fs));
+    // the opt-in is per kernel and shared by every problem (and by graphs captured
+    // earlier): it only ever grows
+    static size_t opted = 48 * 1024;
+    if (fs > opted) {
+        TO_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fs));
+        opted = fs;
+    }
     const dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)chunks);
     kern<<<grid, block3(), fs, s>>>(nx, ny, nz, kchunk, x, y, (const T*)P->Hs, P->stencil, (const T*)P->stencil_w,
                                     P->n_stencil, R, STATS ? P->red : nullptr, STATS ? P->counters + 2 : nullptr, P->sc,

@@ -838,8 +838,9 @@ int mg_build(to_problem* P) {
         const size_t tsm = P->prec == TO_FP64 ? tail_layout<double>(P, l, nullptr) : tail_layout<float>(P, l, nullptr);
         if (tsm > kTailSmem) continue;   // FP64 at ~1024 elements: start one level coarser
         cudaError_t e = P->prec == TO_FP64
-                            ? cudaFuncSetAttribute(k_mg_tail<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm)
-                            : cudaFuncSetAttribute(k_mg_tail<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm);
+                            ? cudaFuncSetAttribute(k_mg_tail<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmem)
+                            : cudaFuncSetAttribute(k_mg_tail<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmem);
+        // (the attribute is per kernel, shared by every problem: the cap, not this problem's size)
         if (e != cudaSuccess) return fail(TO_ERR_CUDA, std::string("shared memory opt-in: ") + cudaGetErrorString(e));
         P->mg_tail = l;
         break;
@@ -1252,7 +1253,7 @@ static int batch_mg_build_t(to_problem* const* probs, int n, int kchunk, BatchMG
         std::vector<TailArgs<T>> h(n);
         size_t smem = 0;
         for (int p = 0; p < n; ++p) smem = std::max<size_t>(smem, (size_t)tail_args<T>(probs[p], tail[p], &h[p]));
-        if (smem > 227 * 1024) return fail(TO_ERR_ARG, "batched multigrid: a coarse tail exceeds shared memory");
+        if (smem > kTailSmem) return fail(TO_ERR_ARG, "batched multigrid: a coarse tail exceeds shared memory");
         BmOp op;
         op.kind = BM_TAIL;
         op.n = n;
@@ -1263,7 +1264,8 @@ static int batch_mg_build_t(to_problem* const* probs, int n, int kchunk, BatchMG
         M->host.push_back(kh);
         for (int q = 0; q < kHaarNnz; ++q) kh->v[q] = (T)probs[0]->haar[q];
         op.kh = kh;
-        TO_CUDA(cudaFuncSetAttribute(k_mg_tail_batch<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        // per kernel, shared by every batch: the cap, not this batch's size
+        TO_CUDA(cudaFuncSetAttribute(k_mg_tail_batch<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmem));
         M->vcycle.push_back(op);
     }
     // ---- up

@@ -107,3 +107,20 @@ def test_mg_repeatable_with_large_coarsest_inverse():
     for rho, J in out[1:]:
         assert np.array_equal(rho, out[0][0])
         assert J == out[0][1]
+
+
+def test_mg_problems_with_different_tail_sizes_coexist():
+    """The tail kernel's shared-memory opt-in is per kernel: creating a problem with a
+    small coarse tail after one with a large tail must not break the first one."""
+    fb = _fb()
+    prm = fb.to_default_params(precision=fb.TO_FP32_MIXED, precond=fb.TO_PRECOND_MG, n_inner=2)
+    big = fb.Problem.from_workload(W.cantilever(32, 16, 16), prm)     # tail from 16 x 8 x 8 (1024 elements)
+    small = fb.Problem.from_workload(W.cantilever(16, 8, 8), prm)     # tail from 8 x 4 x 4 (128 elements)
+    try:
+        st_small = small.step(2)
+        st_big = big.step(3)
+        assert all(np.isfinite(s["J"]) for s in st_big + st_small)
+        assert st_big[-1]["J"] > 0.0
+    finally:
+        big.close()
+        small.close()
