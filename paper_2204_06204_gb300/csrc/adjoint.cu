@@ -171,6 +171,7 @@ static int forward_t(to_problem* P, const void* rho, int Tn, double beta, cudaSt
     int rc = launch_moduli(P, s);
     if (rc) return rc;
     if ((rc = launch_diag(P, 0, s))) return rc;
+    P->precond_stale = 1;   // a new design: the next to_inner_solve refreshes the preconditioner
     TO_CUDA(cudaMemsetAsync(iterate<T>(P, 0), 0, bytes, s));
     void* gt = P->gt;
     P->gt = nullptr;   // no fused sensitivity in these residuals
