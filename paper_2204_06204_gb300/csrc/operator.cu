@@ -50,20 +50,6 @@ struct OpArgs {
                       // RESID: this is the residual at u_k (record norms and J)
 };
 
-// top-face coefficients (ss, sd, ds, dd per component) from four nodes
-template <typename T>
-__device__ __forceinline__ void face_forward(const T* p00, const T* p10, const T* p01, const T* p11, T F[12]) {
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const T sx0 = p10[c] + p00[c], dx0 = p10[c] - p00[c];
-        const T sx1 = p11[c] + p01[c], dx1 = p11[c] - p01[c];
-        F[0 + c] = sx1 + sx0;
-        F[3 + c] = dx1 + dx0;
-        F[6 + c] = sx1 - sx0;
-        F[9 + c] = dx1 - dx0;
-    }
-}
-
 // ----------------------------------------------------------------------------- pairs
 // (x, y) components travel as a pair: packed FP32x2 arithmetic for float,
 // two scalar operations for double.
