@@ -6,14 +6,14 @@
 // (it is an ordinary to_problem); the batched kernels read a device table of
 // per-problem arguments indexed by blockIdx.y (blockIdx.x for the projection's
 // clusters).  Phases, per outer iteration:
-//   design   rho -> rho~ -> E, E'/Hs            k_b_design
+//   design   rho -> rho~ -> E, E'/Hs            k_filter_batch (moduli)
 //   diag     Jacobi diagonal                     k_b_diag
 //   (multigrid: coarse moduli and diagonals, dense coarsest operators and their
 //    inverses, one launch per step and level; see the batched multigrid in mg.cu)
 //   resid    r = f - K u, z = r/d, sensitivity   k_operator_batch<OP_RESID>
 //   (multigrid: z = V-cycle(r), r^T z in its last sweep)
 //   n_inner x (Q apply, update[, V-cycle])       k_operator_batch<OP_Q>, k_b_update
-//   filterT  g = C^T g~, ||g||_inf, alpha_k      k_b_filter_T
+//   filterT  g = C^T g~, ||g||_inf, alpha_k      k_filter_batch (transpose, statistics)
 //   project  one thread-block cluster per problem (distributed shared memory
 //            for the pass totals: no grid-wide barrier between problems)
 //   record   per-problem stats                    k_b_record
@@ -36,22 +36,18 @@ template <typename T>
 SimpT<T> simp_params(const to_material& m);
 
 int batch_operator_launch(int prec, int mode, const void* tab, const void* kh, int max_tiles, int n, cudaStream_t s);
+int filter_table_build(to_problem* const* probs, int n, int mode, void** dev, int* max_tiles, size_t* smem);
+int filter_batch_launch(int prec, int mode, const void* tab, int max_tiles, int n, size_t smem, cudaStream_t s);
 int batch_autotune_kchunk(to_problem* const* probs, int n, const void* kh, cudaStream_t s, int* best_out, float* us_out);
 int op_tables_build(to_problem* const* probs, int n, void** resid, void** q_first, void** q, void** kh_host,
                     int* max_tiles, int kchunk);
 
 template <typename T>
 struct BProb {
-    int nx, ny, nz, ns, R;
+    int nx, ny, nz;
     long long n_elem, n_dof;
     const T* rho;
-    T* rhot;
-    const T* Hs;
     T* E;
-    T* Ed;
-    const int4* st;
-    const T* stw;
-    const T* gt;
     T* grad;
     const uint8_t* mask;
     T* dinv;   // 1 / diag(K^)
@@ -66,34 +62,9 @@ struct BProb {
     DevScalars* sc;
     to_stats* dstats;
     int dstats_cap;
-    double vbar, lo, hi, alpha0_param, alpha_scale, m_exp;
+    double vbar, lo, hi;
     int mean_proj;
 };
-
-// rho~ = C(rho), E = Emin + rho~^p (E0 - Emin), E'/Hs  (grid-stride over each problem's elements)
-template <typename T>
-__global__ void __launch_bounds__(256) k_b_design(const BProb<T>* __restrict__ tab, const SimpT<T> simp) {
-    const BProb<T>& P = tab[blockIdx.y];
-    const int nx = P.nx, ny = P.ny, nz = P.nz;
-    for (long long e = blockIdx.x * 256LL + threadIdx.x; e < P.n_elem; e += (long long)gridDim.x * 256) {
-        const int i = (int)(e % nx), j = (int)((e / nx) % ny), k = (int)(e / ((long long)nx * ny));
-        T acc = T(0);
-        for (int s = 0; s < P.ns; ++s) {
-            const int4 o = P.st[s];
-            const int ii = i + o.x, jj = j + o.y, kk = k + o.z;
-            if (ii < 0 || ii >= nx || jj < 0 || jj >= ny || kk < 0 || kk >= nz) continue;
-            acc += P.stw[s] * P.rho[ii + (long long)nx * (jj + (long long)ny * kk)];
-        }
-        const T hs = P.Hs[e];
-        const T rt = acc / hs;
-        P.rhot[e] = rt;
-        if (!tfinite(rt)) set_err(&P.sc->err, TO_ERR_NONFINITE);
-        T Ee, Ed;
-        simp_moduli(simp, rt, Ee, Ed);
-        P.E[e] = Ee;
-        P.Ed[e] = Ed / hs;
-    }
-}
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_b_diag(const BProb<T>* __restrict__ tab) {
@@ -143,42 +114,6 @@ __global__ void __launch_bounds__(256) k_b_update(const BProb<T>* __restrict__ t
     block_reduce<T, 1>(v, kind, reinterpret_cast<T*>(sh));
     if (finish_reduction<T, 1>(v, kind, P.red, P.counters + 4, tot, sh, blockIdx.x, gridDim.x) && threadIdx.x == 0)
         P.sc->rz = tot[0];
-}
-
-// g = C^T (g~ / Hs) (prescaled), ||g||_inf, 1^T g, and the step size alpha_k per problem
-template <typename T>
-__global__ void __launch_bounds__(256) k_b_filter_T(const BProb<T>* __restrict__ tab) {
-    __shared__ double sh[32 * kRedQ];
-    const BProb<T>& P = tab[blockIdx.y];
-    const int nx = P.nx, ny = P.ny, nz = P.nz;
-    T amax = T(0), sum = T(0);
-    for (long long e = blockIdx.x * 256LL + threadIdx.x; e < P.n_elem; e += (long long)gridDim.x * 256) {
-        const int i = (int)(e % nx), j = (int)((e / nx) % ny), k = (int)(e / ((long long)nx * ny));
-        T acc = T(0);
-        for (int s = 0; s < P.ns; ++s) {
-            const int4 o = P.st[s];
-            const int ii = i + o.x, jj = j + o.y, kk = k + o.z;
-            if (ii < 0 || ii >= nx || jj < 0 || jj >= ny || kk < 0 || kk >= nz) continue;
-            acc += P.stw[s] * P.gt[ii + (long long)nx * (jj + (long long)ny * kk)];
-        }
-        P.grad[e] = acc;
-        amax = tmax(amax, tabs(acc));
-        sum += acc;
-    }
-    T v[2] = {amax, sum};
-    const int kind[2] = {1, 0};
-    double tot[2];
-    block_reduce<T, 2>(v, kind, reinterpret_cast<T*>(sh));
-    if (finish_reduction<T, 2>(v, kind, P.red, P.counters + 2, tot, sh, blockIdx.x, gridDim.x) && threadIdx.x == 0) {
-        DevScalars* sc = P.sc;
-        sc->gmax = tot[0];
-        sc->gsum = tot[1];
-        if (!isfinite(tot[0]) || !isfinite(tot[1])) set_err(&sc->err, TO_ERR_NONFINITE);
-        double a0 = P.alpha0_param > 0.0 ? P.alpha0_param : sc->alpha0;
-        if (!(a0 > 0.0) && tot[0] > 0.0) a0 = P.alpha_scale / tot[0];
-        sc->alpha0 = a0 > 0.0 ? a0 : 0.0;
-        sc->alpha = a0 > 0.0 ? a0 * pow((double)sc->k, -P.m_exp) : 0.0;
-    }
 }
 
 // ----------------------------------------------------------------------------- projection, one cluster per problem
@@ -293,6 +228,9 @@ struct to_batch {
     cudaGraphExec_t gexec = nullptr;
     int graph_state = 0;
     to::BatchMG* mg = nullptr;            // batched multigrid tables (multigrid batches)
+    void* ftab[2] = {nullptr, nullptr};   // batched filter tables: design, gradient
+    int ftiles[2] = {0, 0};
+    size_t fsmem[2] = {0, 0};
 };
 
 using namespace to;
@@ -309,18 +247,10 @@ int build_tables_t(to_batch* B) {
         b.nx = P->g.nx;
         b.ny = P->g.ny;
         b.nz = P->g.nz;
-        b.ns = P->n_stencil;
-        b.R = (int)std::ceil(P->mat.rmin);
         b.n_elem = P->n_elem;
         b.n_dof = P->n_dof;
         b.rho = (const T*)P->rho;
-        b.rhot = (T*)P->rhot;
-        b.Hs = (const T*)P->Hs;
         b.E = (T*)P->lv[0].E;
-        b.Ed = (T*)P->Ed;
-        b.st = P->stencil;
-        b.stw = (const T*)P->stencil_w;
-        b.gt = (const T*)P->gt;
         b.grad = (T*)P->grad;
         b.mask = P->lv[0].mask;
         b.dinv = (T*)P->lv[0].dinv;
@@ -338,9 +268,6 @@ int build_tables_t(to_batch* B) {
         b.vbar = P->mat.volfrac * (double)P->n_elem;
         b.lo = P->mat.rho_min;
         b.hi = P->mat.rho_max;
-        b.alpha0_param = P->prm.alpha0;
-        b.alpha_scale = P->prm.alpha_scale;
-        b.m_exp = P->prm.m;
         b.mean_proj = P->prm.mean_proj;
         max_elem = std::max<long long>(max_elem, (long long)P->n_elem);
         max_dof = std::max<long long>(max_dof, (long long)P->n_dof);
@@ -362,12 +289,11 @@ int build_tables_t(to_batch* B) {
 template <typename T>
 int iteration_t(to_batch* B, cudaStream_t s) {
     const BProb<T>* tab = (const BProb<T>*)B->btab;
-    const to_problem* P0 = B->probs[0];
     const dim3 g2(B->grid_x, B->n);
-    k_b_design<T><<<g2, 256, 0, s>>>(tab, simp_params<T>(P0->mat));
+    int rc;
+    if ((rc = filter_batch_launch(B->prec, 0, B->ftab[0], B->ftiles[0], B->n, B->fsmem[0], s))) return rc;
     k_b_diag<T><<<g2, 256, 0, s>>>(tab);
     TO_CUDA(cudaGetLastError());
-    int rc;
     if (B->mg && (rc = batch_mg_refresh(B->mg, s))) return rc;
     if ((rc = batch_operator_launch(B->prec, OP_RESID, B->tab_resid, B->kh, B->max_tiles, B->n, s))) return rc;
     if (B->mg && (rc = batch_mg_vcycle(B->mg, s))) return rc;
@@ -379,7 +305,7 @@ int iteration_t(to_batch* B, cudaStream_t s) {
         TO_CUDA(cudaGetLastError());
         if (B->mg && it + 1 < B->n_inner && (rc = batch_mg_vcycle(B->mg, s))) return rc;
     }
-    k_b_filter_T<T><<<g2, 256, 0, s>>>(tab);
+    if ((rc = filter_batch_launch(B->prec, 1, B->ftab[1], B->ftiles[1], B->n, B->fsmem[1], s))) return rc;
     if ((rc = launch_cluster_project<T>(tab, B->n, kClusterCTAs, 256, B->proj_cache, B->proj_smem, s))) return rc;
     k_b_record<T><<<(B->n + 63) / 64, 64, 0, s>>>(tab, B->n, 0);
     TO_CUDA(cudaGetLastError());
@@ -393,7 +319,7 @@ void destroy_batch(to_batch* B) {
     if (B->ev_in) cudaEventDestroy(B->ev_in);
     if (B->ev_out) cudaEventDestroy(B->ev_out);
     if (B->stream) cudaStreamDestroy(B->stream);
-    void* ps[] = {B->btab, B->tab_resid, B->tab_q_first, B->tab_q};
+    void* ps[] = {B->btab, B->tab_resid, B->tab_q_first, B->tab_q, B->ftab[0], B->ftab[1]};
     for (void* p : ps)
         if (p) cudaFree(p);
     free(B->kh);
@@ -445,6 +371,7 @@ extern "C" int to_batch_create(to_problem* const* problems, int32_t n, to_batch*
     else if (!rc) rc = batch_autotune_kchunk(B->probs.data(), n, B->kh, B->stream, &B->kchunk, &B->tune_us);
     if (!rc) rc = op_tables_build(B->probs.data(), n, &B->tab_resid, &B->tab_q_first, &B->tab_q, &B->kh, &B->max_tiles, B->kchunk);
     if (!rc && P0->prm.precond == TO_PRECOND_MG) rc = batch_mg_build(B->probs.data(), n, B->kchunk, &B->mg);
+    for (int m = 0; m < 2 && !rc; ++m) rc = filter_table_build(B->probs.data(), n, m, &B->ftab[m], &B->ftiles[m], &B->fsmem[m]);
     if (prev >= 0) cudaSetDevice(prev);
     if (rc) {
         destroy_batch(B);

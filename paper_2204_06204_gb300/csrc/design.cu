@@ -37,22 +37,44 @@ __host__ __device__ inline int filter_box_planes(int kchunk, int R) {
     return (kchunk + kFilterPlanes - 1) / kFilterPlanes * kFilterPlanes + 2 * R;
 }
 
-template <typename T, bool TRANSPOSE, bool STATS, bool PRESCALED, bool MODULI = false>
-__global__ void __launch_bounds__(256) k_filter(int nx, int ny, int nz, int kchunk, const T* __restrict__ x,
-                                                T* __restrict__ y, const T* __restrict__ Hs,
-                                                const int4* __restrict__ st, const T* __restrict__ w, int ns, int R,
-                                                double* red, unsigned* counter, DevScalars* sc, double alpha0_param,
-                                                double alpha_scale, double m_exp, T* Eout, T* Edout, SimpT<T> simp) {
+// one filter pass of one problem
+template <typename T>
+struct FilterArgs {
+    int nx, ny, nz, kchunk;
+    const T* x;
+    T* y;
+    const T* Hs;
+    const int4* st;      // the stencil (dx, dy, dz, -) in ascending dz
+    const T* w;          // its weights
+    int ns, R;           // taps, extent
+    double* red;         // STATS: reduction slots and counter
+    unsigned* counter;
+    DevScalars* sc;
+    double alpha0_param, alpha_scale, m_exp;
+    T* Eout;             // MODULI: E and E' / Hs
+    T* Edout;
+    SimpT<T> simp;
+};
+
+// the CTA tile (bx, by, bz) of one problem; bid / nblocks place it among the problem's
+// tiles for the STATS reduction
+template <typename T, bool TRANSPOSE, bool STATS, bool PRESCALED, bool MODULI>
+__device__ __forceinline__ void filter_body(const FilterArgs<T>& a, int bx, int by, int bz, unsigned bid, unsigned nblocks,
+                                            unsigned char* fsm) {
     constexpr bool DIV = TRANSPOSE && !PRESCALED;   // the staged value is x / Hs
     __shared__ double sh[32 * kRedQ];
-    extern __shared__ __align__(16) unsigned char fsm[];
+    const int nx = a.nx, ny = a.ny, nz = a.nz, kchunk = a.kchunk, ns = a.ns, R = a.R;
+    const T* __restrict__ x = a.x;
+    const T* __restrict__ Hs = a.Hs;
+    const int4* __restrict__ st = a.st;
+    const T* __restrict__ w = a.w;
     const int TW = 32 + 2 * R, TH = 8 + 2 * R, PS = TW * TH, NS = filter_box_planes(kchunk, R);
     FTap<T>* s_tap = reinterpret_cast<FTap<T>*>(fsm);
     T* box = reinterpret_cast<T*>(fsm + (size_t)ns * sizeof(FTap<T>));   // NS planes of the input
     T* hbox = box + (size_t)NS * PS;                                     // NS planes of Hs (DIV only)
     const int tid = threadIdx.x + 32 * threadIdx.y;
-    const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 8;
-    const int k0 = blockIdx.z * kchunk, k1 = min(k0 + kchunk, nz);
+    const int i0 = bx * 32, j0 = by * 8;
+    const int k0 = bz * kchunk, k1 = min(k0 + kchunk, nz);
     const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
     const bool ij_ok = i < nx && j < ny;
     const long long plane = (long long)nx * ny;
@@ -110,13 +132,13 @@ __global__ void __launch_bounds__(256) k_filter(int nx, int ny, int nz, int kchu
             const long long e = i + (long long)nx * (j + (long long)ny * k);
             const T hs_e = hsv[c];
             const T out = TRANSPOSE ? acc[c] : acc[c] / hs_e;
-            y[e] = out;
+            a.y[e] = out;
             if (MODULI) {   // E and E' / Hs (the sensitivity's prescaled factor)
                 T Ee, Ed;
-                simp_moduli(simp, out, Ee, Ed);
-                Eout[e] = Ee;
-                Edout[e] = Ed / hs_e;
-                if (!tfinite(out)) set_err(&sc->err, TO_ERR_NONFINITE);
+                simp_moduli(a.simp, out, Ee, Ed);
+                a.Eout[e] = Ee;
+                a.Edout[e] = Ed / hs_e;
+                if (!tfinite(out)) set_err(&a.sc->err, TO_ERR_NONFINITE);
             }
             if (STATS) {
                 amax = tmax(amax, tabs(out));
@@ -129,17 +151,37 @@ __global__ void __launch_bounds__(256) k_filter(int nx, int ny, int nz, int kchu
         const int kind[2] = {1, 0};
         double tot[2];
         block_reduce<T, 2>(v, kind, reinterpret_cast<T*>(sh));
-        if (finish_reduction<T, 2>(v, kind, red, counter, tot, sh, linear_block(), grid_blocks()) && tid == 0) {
+        if (finish_reduction<T, 2>(v, kind, a.red, a.counter, tot, sh, bid, nblocks) && tid == 0) {
+            DevScalars* sc = a.sc;
             sc->gmax = tot[0];
             sc->gsum = tot[1];
             if (!isfinite(tot[0]) || !isfinite(tot[1])) set_err(&sc->err, TO_ERR_NONFINITE);
             // high-level step alpha_k = alpha0 k^-m; alpha0 fixed at the first k with g != 0
-            double a0 = alpha0_param > 0.0 ? alpha0_param : sc->alpha0;
-            if (!(a0 > 0.0) && tot[0] > 0.0) a0 = alpha_scale / tot[0];
+            double a0 = a.alpha0_param > 0.0 ? a.alpha0_param : sc->alpha0;
+            if (!(a0 > 0.0) && tot[0] > 0.0) a0 = a.alpha_scale / tot[0];
             sc->alpha0 = a0 > 0.0 ? a0 : 0.0;
-            sc->alpha = a0 > 0.0 ? a0 * pow((double)sc->k, -m_exp) : 0.0;
+            sc->alpha = a0 > 0.0 ? a0 * pow((double)sc->k, -a.m_exp) : 0.0;
         }
     }
+}
+
+template <typename T, bool TRANSPOSE, bool STATS, bool PRESCALED, bool MODULI = false>
+__global__ void __launch_bounds__(256) k_filter(const FilterArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char fsm[];
+    filter_body<T, TRANSPOSE, STATS, PRESCALED, MODULI>(a, blockIdx.x, blockIdx.y, blockIdx.z, linear_block(),
+                                                         grid_blocks(), fsm);
+}
+
+// Many problems in one launch: blockIdx.y selects the problem, blockIdx.x its tile
+template <typename T, bool TRANSPOSE, bool STATS, bool PRESCALED, bool MODULI>
+__global__ void __launch_bounds__(256) k_filter_batch(const FilterArgs<T>* __restrict__ tab) {
+    extern __shared__ __align__(16) unsigned char fsm[];
+    const FilterArgs<T>& a = tab[blockIdx.y];
+    const int gx = (a.nx + 31) / 32, gy = (a.ny + 7) / 8, gz = (a.nz + a.kchunk - 1) / a.kchunk;
+    const int t = blockIdx.x;
+    if (t >= gx * gy * gz) return;
+    filter_body<T, TRANSPOSE, STATS, PRESCALED, MODULI>(a, t % gx, (t / gx) % gy, t / (gx * gy), (unsigned)t,
+                                                         (unsigned)(gx * gy * gz), fsm);
 }
 
 // dynamic shared memory of k_filter: the taps, the input box (and the Hs box)
@@ -192,6 +234,32 @@ static int grid_for(long long n, int threads, int num_sms) {
     return (int)b;
 }
 
+template <typename T>
+static FilterArgs<T> filter_args(const to_problem* P, const T* x, T* y, int kchunk, bool stats, T* Eout, T* Edout) {
+    FilterArgs<T> a;
+    a.nx = P->g.nx;
+    a.ny = P->g.ny;
+    a.nz = P->g.nz;
+    a.kchunk = kchunk;
+    a.x = x;
+    a.y = y;
+    a.Hs = (const T*)P->Hs;
+    a.st = P->stencil;
+    a.w = (const T*)P->stencil_w;
+    a.ns = P->n_stencil;
+    a.R = P->filter_ext;
+    a.red = stats ? P->red : nullptr;
+    a.counter = stats ? P->counters + 2 : nullptr;
+    a.sc = P->sc;
+    a.alpha0_param = P->prm.alpha0;
+    a.alpha_scale = P->prm.alpha_scale;
+    a.m_exp = P->prm.m;
+    a.Eout = Eout;
+    a.Edout = Edout;
+    a.simp = simp_params<T>(P->mat);
+    return a;
+}
+
 // the filter's launch shape: 32 x 8 element columns, each CTA a chunk of z planes
 // (about four CTAs per SM), and its shared memory
 template <typename T, bool TRANSPOSE, bool STATS, bool PRESCALED, bool MODULI>
@@ -221,9 +289,63 @@ static int filter_launch(to_problem* P, const T* x, T* y, cudaStream_t s, T* Eou
         opted = fs;
     }
     const dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)chunks);
-    kern<<<grid, block3(), fs, s>>>(nx, ny, nz, kchunk, x, y, (const T*)P->Hs, P->stencil, (const T*)P->stencil_w,
-                                    P->n_stencil, R, STATS ? P->red : nullptr, STATS ? P->counters + 2 : nullptr, P->sc,
-                                    P->prm.alpha0, P->prm.alpha_scale, P->prm.m, Eout, Edout, simp_params<T>(P->mat));
+    kern<<<grid, block3(), fs, s>>>(filter_args<T>(P, x, y, kchunk, STATS, Eout, Edout));
+    TO_CUDA(cudaGetLastError());
+    return TO_OK;
+}
+
+// Batched filters: one table entry per problem and one launch for all of them (the
+// design pass rho -> rho~, E, E'/Hs, and the gradient pass C^T g~ with the step-size
+// statistics).  Each problem walks chunks of up to 8 planes; the launch's shared
+// memory is the largest problem's box.
+template <typename T>
+static int filter_table_t(to_problem* const* probs, int n, int mode, void** dev, int* max_tiles, size_t* smem) {
+    std::vector<FilterArgs<T>> h(n);
+    int mt = 0;
+    size_t fs = 0;
+    for (int i = 0; i < n; ++i) {
+        to_problem* P = probs[i];
+        const int kchunk = std::min(P->g.nz, 8);
+        if (mode == 0)
+            h[i] = filter_args<T>(P, (const T*)P->rho, (T*)P->rhot, kchunk, false, (T*)P->lv[0].E, (T*)P->Ed);
+        else
+            h[i] = filter_args<T>(P, (const T*)P->gt, (T*)P->grad, kchunk, true, nullptr, nullptr);
+        const int tiles = ((P->g.nx + 31) / 32) * ((P->g.ny + 7) / 8) * ((P->g.nz + kchunk - 1) / kchunk);
+        if (tiles > kMaxRedBlocks) return fail(TO_ERR_ARG, "batched filter grid exceeds the reduction scratch");
+        mt = std::max(mt, tiles);
+        fs = std::max(fs, filter_smem<T>(P->n_stencil, P->filter_ext, kchunk, false));
+    }
+    if (fs > 227 * 1024) return fail(TO_ERR_ARG, "batched filter tile exceeds shared memory");
+    if (cudaMalloc(dev, sizeof(FilterArgs<T>) * (size_t)n) != cudaSuccess) return fail(TO_ERR_CUDA, "table allocation");
+    if (cudaMemcpy(*dev, h.data(), sizeof(FilterArgs<T>) * (size_t)n, cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(TO_ERR_CUDA, "table upload");
+    if (fs > 48 * 1024) {
+        if (mode == 0)
+            TO_CUDA(cudaFuncSetAttribute(k_filter_batch<T, false, false, false, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        else
+            TO_CUDA(cudaFuncSetAttribute(k_filter_batch<T, true, true, true, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    }
+    *max_tiles = mt;
+    *smem = fs;
+    return TO_OK;
+}
+
+int filter_table_build(to_problem* const* probs, int n, int mode, void** dev, int* max_tiles, size_t* smem) {
+    return probs[0]->prec == TO_FP64 ? filter_table_t<double>(probs, n, mode, dev, max_tiles, smem)
+                                     : filter_table_t<float>(probs, n, mode, dev, max_tiles, smem);
+}
+
+int filter_batch_launch(int prec, int mode, const void* tab, int max_tiles, int n, size_t smem, cudaStream_t s) {
+    const dim3 grid(max_tiles, n);
+    if (prec == TO_FP64) {
+        if (mode == 0) k_filter_batch<double, false, false, false, true><<<grid, block3(), smem, s>>>((const FilterArgs<double>*)tab);
+        else k_filter_batch<double, true, true, true, false><<<grid, block3(), smem, s>>>((const FilterArgs<double>*)tab);
+    } else {
+        if (mode == 0) k_filter_batch<float, false, false, false, true><<<grid, block3(), smem, s>>>((const FilterArgs<float>*)tab);
+        else k_filter_batch<float, true, true, true, false><<<grid, block3(), smem, s>>>((const FilterArgs<float>*)tab);
+    }
     TO_CUDA(cudaGetLastError());
     return TO_OK;
 }
