@@ -123,7 +123,8 @@ typedef struct {
  *               mg_omega damped-Jacobi weight
  *   tile_x, tile_y, tile_z   node planes per operator tile (tile_z): > 0 fixed; 0: picked
  *               per multigrid level by an autotuner at to_create (the sweep is timed for
- *               1 .. 32 planes and the cost model's choice); < 0 (the default): the cost
+ *               every distinct split of the level's planes into chunks of up to 64 and
+ *               the cost model's choice); < 0 (the default): the cost
  *               model alone (waves of resident CTAs x planes walked).  In a batch
  *               (to_batch_create) the first problem's tile_z > 0 fixes the batched
  *               launches' planes per tile; otherwise the batch autotunes it.  tile_x /
@@ -182,7 +183,9 @@ int to_sizes(const to_problem* P, int64_t* n_elem, int64_t* n_dof);
 
 /* Set the design rho (n_elem entries) and recompute rho~ = C(rho), E and dE/drho~
  * (Sec. III power law through the filter of Remark 3.1).  The operator of
- * to_apply_K, to_inner_solve and to_sensitivity uses this design. */
+ * to_apply_K, to_inner_solve and to_sensitivity uses this design; the next
+ * to_inner_solve first refreshes the preconditioner for it (to_step refreshes
+ * it every outer iteration). */
 int to_set_design(to_problem* P, const void* rho_dev, void* stream);
 
 /* y = K^(rho~) u, the matrix-free hex8 operator of Sec. III (K = sum_e E_e K_e with
