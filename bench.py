@@ -86,6 +86,23 @@ def apply_only(args):
     return 0
 
 
+# ----------------------------------------------------------------------------- ranks
+def max_over_ranks(value, dist, device):
+    """The largest of a per-rank scalar, on every rank (the job's time is its slowest
+    rank's); the value itself without a process group."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, seconds, world):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return world * units_per_rank / seconds
+
+
 # ----------------------------------------------------------------------------- clocks
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
@@ -501,12 +518,10 @@ def main():
         Pm.close()
         del um, ym
 
-    # max over ranks
-    if dist:
-        tt = torch.tensor([t32], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t32 = float(tt.item())
-        ips32 = args.steps / t32
+    # max over ranks (the timed region and the end-to-end loop)
+    t32 = max_over_ranks(t32, dist, dev)
+    t_e2e = max_over_ranks(t_e2e, dist, dev)
+    ips32 = args.steps / t32
 
     if rank != 0:
         dist.destroy_process_group()
@@ -521,7 +536,7 @@ def main():
     launches_per_step = _launches_per_step(use_mg, n_inner)
     line = {
         "metric": "outer TO iters/s (FP32-mixed) with K(rho)u GDOF/s, 1 GB300",
-        "value": ips32 * world,
+        "value": job_rate(args.steps, t32, world),
         "unit": "outer_iters/s",
         "n_gpus": world,
         "steps": args.steps,
@@ -551,9 +566,9 @@ def main():
                      "unit": "GB/s", "frac": ach / hbm, "traffic": APPLY_TRAFFIC_128,
                      "algorithmic_bytes": apply_bytes(s_el),
                      "peak_source": "MEASURED_PEAKS.json hbm_gbs" if pk else "fallback 6800"},
-        "e2e": {"value": ke / t_e2e, "unit": "outer_iters/s", "h2d_bytes_per_step": pb.n_elem * 4,
+        "e2e": {"value": job_rate(ke, t_e2e, world), "unit": "outer_iters/s", "h2d_bytes_per_step": pb.n_elem * 4,
                 "d2h_bytes_per_step": pb.n_elem * 4 + 96},
-        "gpu_launches": launches_per_step * args.steps,
+        "gpu_launches": launches_per_step * args.steps * world,
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
     }
