@@ -457,17 +457,49 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 ? (MODE == OP_RESID ?
     op_body<T, TX, TY, MODE>(a, a.kh, blockIdx.x, blockIdx.y, blockIdx.z, linear_block(), grid_blocks());
 }
 
-// Many problems in one launch: blockIdx.y selects the problem (its arguments come
-// from a device table), blockIdx.x enumerates that problem's tiles; the element
+// Many problems in one launch: each CTA takes one (problem, tile) pair of a compact
+// map built on the host (no CTA of a small problem idles in a grid sized for the
+// largest one); the problem's arguments come from a device table, and the element
 // matrix constants are common to the batch.
 template <typename T, int TX, int TY, int MODE>
-__global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 ? (MODE == OP_RESID ? 2 : 3) : 1)) k_operator_batch(const OpArgs<T>* __restrict__ tab, const HaarK<T> kh) {
-    const OpArgs<T> a = tab[blockIdx.y];
+__global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 ? (MODE == OP_RESID ? 2 : 3) : 1))
+    k_operator_batch(const OpArgs<T>* __restrict__ tab, const int2* __restrict__ map, const HaarK<T> kh) {
+    const int2 m = map[blockIdx.x];
+    const OpArgs<T> a = tab[m.x];
     const int gx = (a.nx + 1 + TX - 2) / (TX - 1), gy = (a.ny + 1 + TY - 2) / (TY - 1);
     const int gz = (a.nz + 1 + a.kchunk - 1) / a.kchunk;
-    const int t = blockIdx.x;
-    if (t >= gx * gy * gz) return;
+    const int t = m.y;
     op_body<T, TX, TY, MODE>(a, kh, t % gx, (t / gx) % gy, t / (gx * gy), (unsigned)t, (unsigned)(gx * gy * gz));
+}
+
+// the table of a batched launch: the problems' arguments, then the (problem, tile) map,
+// round-robin over the problems tile by tile; *total = the map's length (the grid)
+template <typename T>
+static int upload_op_table(const std::vector<OpArgs<T>>& h, void** dev, int* total) {
+    const int n = (int)h.size();
+    std::vector<int> tiles(n);
+    int mt = 0;
+    for (int p = 0; p < n; ++p) {
+        const OpArgs<T>& a = h[p];
+        const int gx = (a.nx + 1 + 30) / 31, gy = (a.ny + 1 + 6) / 7, gz = (a.nz + 1 + a.kchunk - 1) / a.kchunk;
+        if ((long long)gx * gy * gz > kMaxRedBlocks) return fail(TO_ERR_ARG, "batched problem too large for the reduction slots");
+        tiles[p] = gx * gy * gz;
+        mt = mt > tiles[p] ? mt : tiles[p];
+    }
+    std::vector<int2> map;
+    for (int t = 0; t < mt; ++t)
+        for (int p = 0; p < n; ++p)
+            if (t < tiles[p]) map.push_back(make_int2(p, t));
+    static_assert(sizeof(OpArgs<T>) % alignof(int2) == 0, "map alignment");
+    const size_t ab = sizeof(OpArgs<T>) * (size_t)n, mb = sizeof(int2) * map.size();
+    if (*dev) cudaFree(*dev);
+    *dev = nullptr;
+    if (cudaMalloc(dev, ab + mb) != cudaSuccess) return fail(TO_ERR_CUDA, "table allocation");
+    if (cudaMemcpy(*dev, h.data(), ab, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(static_cast<char*>(*dev) + ab, map.data(), mb, cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(TO_ERR_CUDA, "table upload");
+    *total = (int)map.size();
+    return TO_OK;
 }
 
 int choose_kchunk(long long columns, int planes, long long slots);
@@ -708,18 +740,8 @@ static OpArgs<T> batch_args(to_problem* P, int mode, int first, int kchunk) {
 template <typename T>
 static int op_table_t(to_problem* const* probs, int n, int mode, int first, void** dev, int* max_tiles, int kchunk) {
     std::vector<OpArgs<T>> h(n);
-    int mt = 0;
-    for (int i = 0; i < n; ++i) {
-        h[i] = batch_args<T>(probs[i], mode, first, kchunk);
-        const int gx = (h[i].nx + 1 + 30) / 31, gy = (h[i].ny + 1 + 6) / 7, gz = (h[i].nz + 1 + h[i].kchunk - 1) / h[i].kchunk;
-        if ((long long)gx * gy * gz > kMaxRedBlocks) return fail(TO_ERR_ARG, "batched problem too large for the reduction slots");
-        mt = mt > gx * gy * gz ? mt : gx * gy * gz;
-    }
-    if (!*dev && cudaMalloc(dev, sizeof(OpArgs<T>) * (size_t)n) != cudaSuccess) return fail(TO_ERR_CUDA, "table allocation");
-    if (cudaMemcpy(*dev, h.data(), sizeof(OpArgs<T>) * (size_t)n, cudaMemcpyHostToDevice) != cudaSuccess)
-        return fail(TO_ERR_CUDA, "table upload");
-    *max_tiles = mt;
-    return TO_OK;
+    for (int i = 0; i < n; ++i) h[i] = batch_args<T>(probs[i], mode, first, kchunk);
+    return upload_op_table<T>(h, dev, max_tiles);
 }
 
 // device tables of operator arguments for a list of problems (node planes per tile:
@@ -777,7 +799,6 @@ template <typename T>
 static int op_table_level_t(to_problem* const* probs, int n, int level, int mode, const void* const* x, void* const* y,
                             const void* const* b, double omega, int first, int kchunk, void** dev, int* max_tiles) {
     std::vector<OpArgs<T>> h(n);
-    int mt = 0;
     for (int i = 0; i < n; ++i) {
         to_problem* P = probs[i];
         const Level& L = P->lv[level];
@@ -799,15 +820,8 @@ static int op_table_level_t(to_problem* const* probs, int n, int level, int mode
         a.sc = P->sc;
         a.first_step = first;
         a.counter = mode == OP_SMOOTH ? P->counters + 6 : nullptr;
-        const int gx = (a.nx + 1 + 30) / 31, gy = (a.ny + 1 + 6) / 7, gz = (a.nz + 1 + a.kchunk - 1) / a.kchunk;
-        if ((long long)gx * gy * gz > kMaxRedBlocks) return fail(TO_ERR_ARG, "batched problem too large for the reduction slots");
-        mt = mt > gx * gy * gz ? mt : gx * gy * gz;
     }
-    if (cudaMalloc(dev, sizeof(OpArgs<T>) * (size_t)n) != cudaSuccess) return fail(TO_ERR_CUDA, "table allocation");
-    if (cudaMemcpy(*dev, h.data(), sizeof(OpArgs<T>) * (size_t)n, cudaMemcpyHostToDevice) != cudaSuccess)
-        return fail(TO_ERR_CUDA, "table upload");
-    *max_tiles = mt;
-    return TO_OK;
+    return upload_op_table<T>(h, dev, max_tiles);
 }
 
 int op_table_level(to_problem* const* probs, int n, int level, int mode, const void* const* x, void* const* y,
@@ -873,24 +887,26 @@ int batch_autotune_kchunk(to_problem* const* probs, int n, const void* kh, cudaS
 }
 
 template <typename T>
-static void batch_launch_t(int mode, const void* tab, const void* kh, dim3 grid, cudaStream_t s) {
+static void batch_launch_t(int mode, const void* tab, int n, const void* kh, dim3 grid, cudaStream_t s) {
     const size_t smem = sizeof(OpSmem<T, 32, 8, kRing>);
     const HaarK<T>& k = *(const HaarK<T>*)kh;
     const OpArgs<T>* t = (const OpArgs<T>*)tab;
+    const int2* m = reinterpret_cast<const int2*>(t + n);
     const dim3 block(32, 8);
     switch (mode) {
-        case OP_RESID: k_operator_batch<T, 32, 8, OP_RESID><<<grid, block, smem, s>>>(t, k); break;
-        case OP_Q: k_operator_batch<T, 32, 8, OP_Q><<<grid, block, smem, s>>>(t, k); break;
-        case OP_SMOOTH: k_operator_batch<T, 32, 8, OP_SMOOTH><<<grid, block, smem, s>>>(t, k); break;
-        case OP_BMINUS: k_operator_batch<T, 32, 8, OP_BMINUS><<<grid, block, smem, s>>>(t, k); break;
-        default: k_operator_batch<T, 32, 8, OP_APPLY><<<grid, block, smem, s>>>(t, k); break;
+        case OP_RESID: k_operator_batch<T, 32, 8, OP_RESID><<<grid, block, smem, s>>>(t, m, k); break;
+        case OP_Q: k_operator_batch<T, 32, 8, OP_Q><<<grid, block, smem, s>>>(t, m, k); break;
+        case OP_SMOOTH: k_operator_batch<T, 32, 8, OP_SMOOTH><<<grid, block, smem, s>>>(t, m, k); break;
+        case OP_BMINUS: k_operator_batch<T, 32, 8, OP_BMINUS><<<grid, block, smem, s>>>(t, m, k); break;
+        default: k_operator_batch<T, 32, 8, OP_APPLY><<<grid, block, smem, s>>>(t, m, k); break;
     }
 }
 
-int batch_operator_launch(int prec, int mode, const void* tab, const void* kh, int max_tiles, int n, cudaStream_t s) {
-    const dim3 grid(max_tiles, n);
-    if (prec == TO_FP64) batch_launch_t<double>(mode, tab, kh, grid, s);
-    else batch_launch_t<float>(mode, tab, kh, grid, s);
+// `tiles`: the length of the table's (problem, tile) map
+int batch_operator_launch(int prec, int mode, const void* tab, const void* kh, int tiles, int n, cudaStream_t s) {
+    const dim3 grid(tiles);
+    if (prec == TO_FP64) batch_launch_t<double>(mode, tab, n, kh, grid, s);
+    else batch_launch_t<float>(mode, tab, n, kh, grid, s);
     TO_CUDA(cudaGetLastError());
     return TO_OK;
 }
