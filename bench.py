@@ -599,8 +599,9 @@ def _mg_levels(nx, ny, nz):
 def _launches_per_step(mg, n_inner, dims=(128, 64, 64), nu1=2, nu2=2):
     """Kernel launches of one outer iteration (one to_step(1) call), as issued by the library."""
     # stats-slot reset (once per to_step call), filter + moduli, diag, residual with the fused
-    # sensitivity, (Q + update) per step, filter^T with the step-size statistics, projection, record
-    base = 1 + 1 + 1 + 1 + 2 * n_inner + 1 + 1 + 1
+    # sensitivity, (Q + update) per step, filter^T with the step-size statistics, the projection
+    # (first pass, multiplier search, final pass), record
+    base = 1 + 1 + 1 + 1 + 2 * n_inner + 1 + 3 + 1
     if not mg:
         return base
     L = _mg_levels(*dims)
