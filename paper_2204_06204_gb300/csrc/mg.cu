@@ -12,8 +12,10 @@
 // Coarsest solve: the dense operator is assembled on the device, scaled to a
 // unit diagonal (S A S, S = diag(A)^-1/2, so that the 1e9 stiffness contrast of
 // void regions does not reach the factorisation) and inverted by Gauss-Jordan
-// elimination by one CTA (in shared memory while the matrix fits); each V-cycle
-// then applies S A^-1 S.
+// elimination: by one CTA with the entries in registers up to 160 DOFs, above
+// that by 32-blocks over many CTAs; each V-cycle then applies S A^-1 S.  The
+// levels below about a thousand elements run as one CTA (the coarse tail), and
+// the last part of the file batches all of it over many problems.
 #include <algorithm>
 #include <cmath>
 
