@@ -1,5 +1,6 @@
-// Device helpers shared by the kernels: deterministic block / grid reductions
-// and a bounded grid barrier.
+// Device helpers shared by the kernels: deterministic block / grid reductions,
+// float-pair sums, a bounded grid barrier, the projection's search step, the
+// 3-D lattice launch shape and the asynchronous-copy wrappers.
 #pragma once
 
 #include "internal.cuh"
