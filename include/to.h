@@ -135,7 +135,13 @@ typedef struct {
  *               operator applications and (D + 2) vectors of n_dof per application
  *   proj_sort   0: the projection's multiplier by the safeguarded Newton search;
  *               1: by the paper's parallel form of Algorithm 4 (a radix sort of the
- *               2E breakpoints and scans, Sec. IV-D); the same rho */
+ *               2E breakpoints and scans, Sec. IV-D); the same rho
+ *   adj_stride  iterates of to_compliance_truncated kept for its reverse sweep:
+ *               0 or 1: all of u_0 .. u_T ((T + 1) n_dof entries);  s > 1: every s-th
+ *               (u_0, u_s, u_2s, ...) plus one segment of s + 1, the reverse sweep
+ *               recomputing each segment from its kept iterate (one more forward
+ *               pass; (ceil(T / s) + s + 1) n_dof entries);  -1: s = ceil(sqrt(T)).
+ *               The gradient is bitwise the same in every mode. */
 typedef struct {
     int32_t precision, precond, inner_mode, n_inner;
     double beta, alpha0, alpha_scale, m;
@@ -143,6 +149,7 @@ typedef struct {
     double mg_omega;
     int32_t tile_x, tile_y, tile_z, no_graph;
     int32_t krylov_dim, proj_sort;
+    int32_t adj_stride, reserved_;
 } to_params;
 
 /* Per-outer-iteration record (host copy). */
@@ -192,6 +199,30 @@ int to_set_design(to_problem* P, const void* rho_dev, void* stream);
  * fixtures eliminated).  u, y: n_dof entries, node-major xyz-interleaved;
  * u and y must not overlap. */
 int to_apply_K(to_problem* P, const void* u_dev, void* y_dev, void* stream);
+
+/* The residual at u and what the first step of an outer iteration takes from it
+ * (Algorithms 1 / 3: line 2 evaluates the sensitivity at u_k; line 1's descent
+ * step starts from r = f - K u_k), all in one pass of the operator:
+ *   r_dev   (n_dof, required)  r = f - K^(rho~) u
+ *   z_dev   (n_dof, may be NULL) z = r / diag(K^), the Jacobi-preconditioned residual
+ *           ("damped Jacobi", Sec. IV-A)
+ *   gt_dev  (n_elem, may be NULL) -E'_e u_e^T k_e u_e / Hs_e: the element sensitivity
+ *           with respect to rho~ (Sec. III, exact-gradient formula at u, J = f^T u)
+ *           divided by the filter row sum Hs_e = sum_i max(0, rmin - |c_e - c_i|), the
+ *           form the filter transpose consumes (to_sensitivity returns the chained
+ *           dJ/drho)
+ *   scalars_out (host, 4 doubles, may be NULL; synchronises) r^T z (0 without z),
+ *           ||r||_2, ||r||_inf, f^T u, reduced in double.
+ * u must not overlap r or z.  The Jacobi diagonal of the current design is
+ * refreshed first if the design changed since the last lower-level solve. */
+int to_residual(to_problem* P, const void* u_dev, void* r_dev, void* z_dev, void* gt_dev,
+                double* scalars_out, void* stream);
+
+/* One damped-Jacobi sweep y = x + omega diag(K^)^-1 (b - K^ x) on the fine grid: the
+ * smoother of the multigrid preconditioner M (the paper names multigrid as prior
+ * art for M, Sec. IV-A; "damped Jacobi" is its Jacobi step).  x, b, y: n_dof
+ * entries; y must not overlap x or b. */
+int to_smooth(to_problem* P, const void* x_dev, const void* b_dev, void* y_dev, double omega, void* stream);
 
 /* nsteps lower-level steps on K^(rho~) u = f from the given u (in place), with the
  * problem's preconditioner and inner_mode (Algorithm 1 / 3, line 1).  If res_out
@@ -254,11 +285,12 @@ int to_batch_tile(const to_batch* batch, int32_t* kchunk_out, double* us_out);
 /* Differentiable compliance through a truncated lower-level solve.
  * J(rho) = f^T u_T where u_0 = 0 and u_{j+1} = u_j + beta D^-1 (f - K^(rho~) u_j),
  * D = diag K^ (the literal constant-beta step of Algorithms 1 / 3 with the Jacobi M),
- * j < T_steps.  Sets the problem's design to rho (as to_set_design), keeps
- * u_0 .. u_T for the reverse sweep (the problem allocates (T_steps + 1) n_dof
- * entries on the first call with this T) and, if J_out is not NULL, returns J
- * (synchronises).  Requires precond = TO_PRECOND_JACOBI (TO_ERR_STATE otherwise).
- * As T grows the gradient tends to the exact sensitivity of Sec. III. */
+ * j < T_steps.  Sets the problem's design to rho (as to_set_design), keeps the
+ * iterates that to_params.adj_stride asks for (all of u_0 .. u_T by default; the
+ * problem grows its iterate buffer when a call needs more) and, if J_out is not
+ * NULL, returns J (synchronises).  Requires precond = TO_PRECOND_JACOBI
+ * (TO_ERR_STATE otherwise).  As T grows the gradient tends to the exact
+ * sensitivity of Sec. III. */
 int to_compliance_truncated(to_problem* P, const void* rho_dev, int32_t T_steps, double beta,
                             double* J_out, void* stream);
 
@@ -266,9 +298,18 @@ int to_compliance_truncated(to_problem* P, const void* rho_dev, int32_t T_steps,
  * over the kept iterates (adjoint lambda_T = f, lambda_j = lambda_{j+1} - K^ s_j,
  * s_j = beta D^-1 lambda_{j+1}) with the element terms
  * -E'_e [ s_e^T k_e u_j,e + sum_{d in e} k_dd s_d z_j,d ] (z_j = D^-1 r_j, the
- * dependence of D on rho included), chained through the filter transpose.
- * g: n_elem entries.  TO_ERR_STATE if no forward call preceded. */
+ * dependence of D on rho included), chained through the filter transpose;
+ * iterates not kept are recomputed segment by segment.  g: n_elem entries.
+ * TO_ERR_STATE if no forward call preceded, or if the design changed since it
+ * (to_set_design, to_set_state, to_step, a batch step). */
 int to_compliance_truncated_grad(to_problem* P, double scale, void* g_dev, void* stream);
+
+/* Identifier of the iterates the last to_compliance_truncated call kept: > 0 and
+ * different for every forward call; 0 when none are kept or the design changed
+ * since (then to_compliance_truncated_grad returns TO_ERR_STATE).  A caller that
+ * interleaves several forward calls on one problem compares it with the value
+ * read after its own forward to know whether its iterates are still there. */
+int to_compliance_truncated_id(const to_problem* P, int64_t* id_out);
 
 /* Allocation-free projection.  The paper has no counterpart: this entry point
  * exists for callers that may not allocate device memory, for instance code
@@ -284,6 +325,10 @@ int to_compliance_truncated_grad(to_problem* P, double scale, void* g_dev, void*
  *   n               1 <= n <= 2,097,152; larger n returns TO_ERR_ARG (also when the
  *                   device cannot keep every per-block chunk in shared memory).
  *   lambda_out      host, may be NULL; when set the call synchronises `stream`.
+ * Device-side errors (a non-finite w, a grid barrier that gave up) are kept in the
+ * array until a call with lambda_out != NULL reads them: that call returns the
+ * error, whether this call or an earlier one made without lambda_out raised it,
+ * and clears it.  A caller that never passes lambda_out never sees them.
  * The first call on a device looks up the array's device address and the
  * kernel's co-residency limit for that device (with it current); make that first
  * call before any stream capture.  Every call shares the one array and resets the
@@ -291,6 +336,18 @@ int to_compliance_truncated_grad(to_problem* P, double scale, void* g_dev, void*
  * streams or threads) race: serialise them. */
 int to_project_noalloc(const void* w_dev, void* rho_dev, int64_t n, int32_t precision, double vbar,
                        double lo, double hi, double* lambda_out, void* stream);
+
+/* Failure-detection self-test of the grid barrier that the projection's
+ * cooperative kernel uses between its passes (no counterpart in the paper).  It
+ * launches up to 8 co-resident blocks that meet at that barrier with an
+ * iteration limit of spin_limit polls (1 <= spin_limit <= 2^24; 2^24 is the
+ * limit the library itself uses, about a second).  absent_block = -1: every
+ * block arrives and the call returns TO_OK.  absent_block = b >= 0: block b skips
+ * the barrier, the others wait for it until the limit runs out and then return,
+ * and the call returns TO_ERR_TIMEOUT.  Either way the call synchronises, clears
+ * the barrier words and the problem's device error flag, and leaves the context
+ * usable: no kernel waits without a bound. */
+int to_barrier_selftest(to_problem* P, int32_t absent_block, int64_t spin_limit, void* stream);
 
 /* Synchronise the stream and report (and clear) the device error flag. */
 int to_check(to_problem* P, void* stream);

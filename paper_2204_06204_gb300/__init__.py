@@ -19,9 +19,10 @@ from ._abi import (TO_FP32_MIXED, TO_FP64, TO_INNER_PCG, TO_INNER_PFBTO, TO_INNE
                    TO_PRECOND_MG, TO_PRECOND_NONE, ToError, to_stats)
 
 __all__ = ["to_default_params", "to_create", "to_destroy", "to_sizes", "to_set_design", "to_apply_K",
+           "to_residual", "to_smooth",
            "to_inner_solve", "to_sensitivity", "to_filter", "to_project", "to_step", "to_get_state",
-           "to_set_state", "to_check", "to_last_error", "to_project_noalloc", "to_compliance_truncated",
-           "to_compliance_truncated_grad", "to_batch_create", "to_batch_destroy", "to_batch_step", "to_batch_tile", "Batch",
+           "to_set_state", "to_check", "to_barrier_selftest", "to_last_error", "to_project_noalloc", "to_compliance_truncated",
+           "to_compliance_truncated_grad", "to_compliance_truncated_id", "to_batch_create", "to_batch_destroy", "to_batch_step", "to_batch_tile", "Batch",
            "Problem", "ToError",
            "TO_FP64", "TO_FP32_MIXED", "TO_PRECOND_JACOBI", "TO_PRECOND_MG", "TO_PRECOND_NONE", "TO_PRECOND_KRYLOV",
            "TO_INNER_SD", "TO_INNER_RICHARDSON", "TO_INNER_PFBTO", "TO_INNER_PCG"]
@@ -139,6 +140,16 @@ class Problem:
         to_apply_K(self, u, y)
         return y
 
+    def residual(self, u, r=None, z=None, gt=None, want_scalars=True):
+        r = self.dof() if r is None else r
+        sc = to_residual(self, u, r, z, gt, want_scalars)
+        return r, sc
+
+    def smooth(self, x, b, omega, y=None):
+        y = self.dof() if y is None else y
+        to_smooth(self, x, b, y, omega)
+        return y
+
     def inner_solve(self, u, nsteps, want_res=False):
         return to_inner_solve(self, u, nsteps, want_res)
 
@@ -187,6 +198,19 @@ def to_set_design(P, rho):
 def to_apply_K(P, u, y):
     _abi.check(_lib().to_apply_K(_h(P), _ptr(u, _dt(P), P.n_dof, "u"), _ptr(y, _dt(P), P.n_dof, "y"),
                                  _stream(P.device)))
+
+
+def to_residual(P, u, r, z=None, gt=None, want_scalars=True):
+    sc = (C.c_double * 4)()
+    _abi.check(_lib().to_residual(_h(P), _ptr(u, _dt(P), P.n_dof, "u"), _ptr(r, _dt(P), P.n_dof, "r"),
+                                  _ptr(z, _dt(P), P.n_dof, "z"), _ptr(gt, _dt(P), P.n_elem, "gt"),
+                                  sc if want_scalars else None, _stream(P.device)))
+    return dict(rz=sc[0], res2=sc[1], res_inf=sc[2], fu=sc[3]) if want_scalars else None
+
+
+def to_smooth(P, x, b, y, omega):
+    _abi.check(_lib().to_smooth(_h(P), _ptr(x, _dt(P), P.n_dof, "x"), _ptr(b, _dt(P), P.n_dof, "b"),
+                                _ptr(y, _dt(P), P.n_dof, "y"), float(omega), _stream(P.device)))
 
 
 def to_inner_solve(P, u, nsteps, want_res=False):
@@ -238,6 +262,10 @@ def to_check(P):
     _abi.check(_lib().to_check(_h(P), _stream(P.device)))
 
 
+def to_barrier_selftest(P, absent_block, spin_limit):
+    _abi.check(_lib().to_barrier_selftest(_h(P), int(absent_block), int(spin_limit), _stream(P.device)))
+
+
 def to_compliance_truncated(P, rho, T, beta, want_J=True):
     J = C.c_double()
     _abi.check(_lib().to_compliance_truncated(_h(P), _ptr(rho, _dt(P), P.n_elem, "rho"), int(T), float(beta),
@@ -248,6 +276,12 @@ def to_compliance_truncated(P, rho, T, beta, want_J=True):
 def to_compliance_truncated_grad(P, scale, g):
     _abi.check(_lib().to_compliance_truncated_grad(_h(P), float(scale), _ptr(g, _dt(P), P.n_elem, "g"),
                                                    _stream(P.device)))
+
+
+def to_compliance_truncated_id(P):
+    i = C.c_int64()
+    _abi.check(_lib().to_compliance_truncated_id(_h(P), C.byref(i)))
+    return i.value
 
 
 def to_batch_create(problems):

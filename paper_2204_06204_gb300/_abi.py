@@ -38,7 +38,8 @@ class to_params(C.Structure):
                 ("mean_proj", C.c_int32), ("mg_levels", C.c_int32), ("mg_nu_pre", C.c_int32), ("mg_nu_post", C.c_int32),
                 ("mg_omega", C.c_double),
                 ("tile_x", C.c_int32), ("tile_y", C.c_int32), ("tile_z", C.c_int32), ("no_graph", C.c_int32),
-                ("krylov_dim", C.c_int32), ("proj_sort", C.c_int32)]
+                ("krylov_dim", C.c_int32), ("proj_sort", C.c_int32), ("adj_stride", C.c_int32),
+                ("reserved_", C.c_int32)]
 
 
 class to_stats(C.Structure):
@@ -61,6 +62,8 @@ SIGNATURES = {
     "to_sizes": (C.c_int, [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "to_set_design": (C.c_int, [P, P, P]),
     "to_apply_K": (C.c_int, [P, P, P, P]),
+    "to_residual": (C.c_int, [P, P, P, P, P, C.POINTER(C.c_double), P]),
+    "to_smooth": (C.c_int, [P, P, P, P, C.c_double, P]),
     "to_inner_solve": (C.c_int, [P, P, C.c_int32, C.POINTER(C.c_double), P]),
     "to_sensitivity": (C.c_int, [P, P, P, P]),
     "to_filter": (C.c_int, [P, P, P, C.c_int32, P]),
@@ -69,12 +72,14 @@ SIGNATURES = {
     "to_get_state": (C.c_int, [P, P, P, C.POINTER(C.c_int64), C.POINTER(C.c_double), P]),
     "to_set_state": (C.c_int, [P, P, P, C.c_int64, C.c_double, P]),
     "to_check": (C.c_int, [P, P]),
+    "to_barrier_selftest": (C.c_int, [P, C.c_int32, C.c_int64, P]),
     "to_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(C.c_void_p)]),
     "to_batch_destroy": (None, [P]),
     "to_batch_step": (C.c_int, [P, C.c_int32, C.POINTER(to_stats), P]),
     "to_batch_tile": (C.c_int, [P, C.POINTER(C.c_int32), C.POINTER(C.c_double)]),
     "to_compliance_truncated": (C.c_int, [P, P, C.c_int32, C.c_double, C.POINTER(C.c_double), P]),
     "to_compliance_truncated_grad": (C.c_int, [P, C.c_double, P, P]),
+    "to_compliance_truncated_id": (C.c_int, [P, C.POINTER(C.c_int64)]),
     "to_project_noalloc": (C.c_int, [P, P, C.c_int64, C.c_int32, C.c_double, C.c_double, C.c_double,
                                      C.POINTER(C.c_double), P]),
     "to_last_error": (C.c_char_p, []),

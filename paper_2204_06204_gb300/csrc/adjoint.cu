@@ -13,6 +13,7 @@
 // (u_j, s and z_j vanish on fixed DOFs; the element terms are evaluated in the
 // sum/difference basis, where x^T y = (T x)^T (T y) / 8.)  As T grows, u_T tends
 // to K^-1 f and the gradient to the exact sensitivity of Sec. III.
+#include <algorithm>
 #include <cstring>
 
 #include "device.cuh"
@@ -151,54 +152,111 @@ static int grid_n(long long n, int num_sms) {
     return (int)(b < 1 ? 1 : b);
 }
 
+// Iterate storage.  Stride s = 1: slot j holds u_j (j = 0 .. T).  Stride s > 1:
+// slots 0 .. nck-1 hold the kept iterates u_0, u_s, u_2s, ... (nck = ceil(T / s)),
+// slots nck .. nck+s hold one segment u_ms .. u_ms+s being walked.
 template <typename T>
-static T* iterate(to_problem* P, int j) {
+static T* slot(to_problem* P, int j) {
     return (T*)P->iters + (size_t)j * (size_t)P->n_dof;
+}
+
+static int stride_for(const to_problem* P, int Tn) {
+    int s = P->prm.adj_stride;
+    if (s == -1) {
+        s = 1;
+        while ((long long)s * s < Tn) ++s;   // ceil(sqrt(T))
+    }
+    if (s < 1) s = 1;
+    if (s > Tn && Tn > 0) s = Tn;
+    return s;
+}
+
+static int n_slots(int Tn, int s) {
+    if (s <= 1) return Tn + 1;
+    const int nck = (Tn + s - 1) / s;
+    return nck + s + 1;
+}
+
+// u_out = u_in + beta D^-1 (f - K^ u_in): the residual with the fused Jacobi epilogue
+// (z = r / d into P->z), then the update
+template <typename T>
+static int fwd_step(to_problem* P, const T* u_in, T* u_out, double beta, cudaStream_t s) {
+    int rc = launch_operator(P, 0, OP_RESID, u_in, P->r, P->f, s, 0.0, 0);
+    if (rc) return rc;
+    const int nb = grid_n(P->n_dof, P->num_sms);
+    k_axpy_out<T><<<nb, 256, 0, s>>>(P->n_dof, u_in, (const T*)P->z, (T)beta, u_out);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(TO_ERR_CUDA, std::string("axpy: ") + cudaGetErrorString(e));
+    return TO_OK;
+}
+
+// walk segment m (stride s > 1) from its kept iterate: segment slots 0 .. len hold
+// u_ms .. u_ms+len afterwards
+template <typename T>
+static int walk_segment(to_problem* P, int m, int len, int nck, double beta, cudaStream_t s) {
+    const size_t bytes = (size_t)P->n_dof * sizeof(T);
+    TO_CUDA(cudaMemcpyAsync(slot<T>(P, nck), slot<T>(P, m), bytes, cudaMemcpyDeviceToDevice, s));
+    for (int i = 0; i < len; ++i)
+        if (int rc = fwd_step<T>(P, slot<T>(P, nck + i), slot<T>(P, nck + i + 1), beta, s)) return rc;
+    return TO_OK;
 }
 
 template <typename T>
 static int forward_t(to_problem* P, const void* rho, int Tn, double beta, cudaStream_t s) {
     const size_t bytes = (size_t)P->n_dof * sizeof(T);
-    if (Tn + 1 > P->iters_cap) {
+    const int st = stride_for(P, Tn);
+    const int need = n_slots(Tn, st);
+    P->fwd_id = 0;
+    if (need > P->iters_cap) {
         TO_CUDA(cudaStreamSynchronize(s));
         if (P->iters) cudaFree(P->iters);
         P->iters = nullptr;
         P->iters_cap = 0;
-        TO_CUDA(cudaMalloc(&P->iters, bytes * (size_t)(Tn + 1)));
-        P->iters_cap = Tn + 1;
+        TO_CUDA(cudaMalloc(&P->iters, bytes * (size_t)need));
+        P->iters_cap = need;
     }
     TO_CUDA(cudaMemcpyAsync(P->rho, rho, P->n_elem * sizeof(T), cudaMemcpyDeviceToDevice, s));
     int rc = launch_moduli(P, s);
     if (rc) return rc;
     if ((rc = launch_diag(P, 0, s))) return rc;
     P->precond_stale = 1;   // a new design: the next to_inner_solve refreshes the preconditioner
-    TO_CUDA(cudaMemsetAsync(iterate<T>(P, 0), 0, bytes, s));
+    TO_CUDA(cudaMemsetAsync(slot<T>(P, 0), 0, bytes, s));
     void* gt = P->gt;
     P->gt = nullptr;   // no fused sensitivity in these residuals
-    const int nb = grid_n(P->n_dof, P->num_sms);
-    for (int j = 0; j < Tn; ++j) {
-        // r_j = f - K^ u_j and z_j = r_j / D (fused Jacobi epilogue), then u_{j+1} = u_j + beta z_j
-        rc = launch_operator(P, 0, OP_RESID, iterate<T>(P, j), P->r, P->f, s, 0.0, 0);
-        if (rc) break;
-        k_axpy_out<T><<<nb, 256, 0, s>>>(P->n_dof, iterate<T>(P, j), (const T*)P->z, (T)beta, iterate<T>(P, j + 1));
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) {
-            rc = fail(TO_ERR_CUDA, std::string("axpy: ") + cudaGetErrorString(e));
-            break;
+    const T* uT = nullptr;
+    if (st == 1) {
+        for (int j = 0; j < Tn && !rc; ++j) rc = fwd_step<T>(P, slot<T>(P, j), slot<T>(P, j + 1), beta, s);
+        uT = slot<T>(P, Tn);
+    } else {
+        // keep u_ms at slot m; the segment's last iterate seeds the next kept one
+        const int nck = (Tn + st - 1) / st;
+        for (int m = 0; m < nck && !rc; ++m) {
+            const int len = std::min(st, Tn - m * st);
+            rc = walk_segment<T>(P, m, len, nck, beta, s);
+            if (!rc && m + 1 < nck)
+                if (cudaMemcpyAsync(slot<T>(P, m + 1), slot<T>(P, nck + len), bytes, cudaMemcpyDeviceToDevice, s) !=
+                    cudaSuccess)
+                    rc = fail(TO_ERR_CUDA, "kept iterate copy");
+            if (!rc && m + 1 == nck) uT = slot<T>(P, nck + len);
         }
+        if (Tn == 0) uT = slot<T>(P, 0);
     }
     P->gt = gt;
     if (rc) return rc;
-    k_dot_J<T><<<nb, 256, 0, s>>>(P->n_dof, (const T*)P->f, iterate<T>(P, Tn), P->red, P->counters + 7, P->sc);
+    const int nb = grid_n(P->n_dof, P->num_sms);
+    k_dot_J<T><<<nb, 256, 0, s>>>(P->n_dof, (const T*)P->f, uT, P->red, P->counters + 7, P->sc);
     TO_CUDA(cudaGetLastError());
     P->iters_T = Tn;
     P->iters_beta = beta;
+    P->iters_stride = st;
+    P->fwd_id = ++P->fwd_count;
     return TO_OK;
 }
 
 template <typename T>
 static int backward_t(to_problem* P, double scale, void* g, cudaStream_t s) {
     const int Tn = P->iters_T;
+    const int st = P->iters_stride;
     const double beta = P->iters_beta;
     const int nb = grid_n(P->n_dof, P->num_sms);
     T* lam = (T*)P->tmp_v;
@@ -209,18 +267,39 @@ static int backward_t(to_problem* P, double scale, void* g, cudaStream_t s) {
     for (int n = 0; n < kHaarNnz; ++n) kh.v[n] = (T)P->haar[n];
     const dim3 eg = grid3(P->g.nx, P->g.ny, P->g.nz);
     if (Tn == 0) TO_CUDA(cudaMemsetAsync(P->gt, 0, P->n_elem * sizeof(T), s));
-    for (int j = Tn - 1; j >= 0; --j) {
+    // one reverse step j with u_j, u_{j+1}; lambda holds lambda_{j+1} on entry, lambda_j on exit
+    auto rstep = [&](int j, const T* uj, const T* uj1) -> int {
         k_adj_s<T><<<nb, 256, 0, s>>>(P->n_dof, lam, (const T*)P->lv[0].dinv, (T)beta, sv);
         TO_CUDA(cudaGetLastError());
-        k_adjoint_elem<T><<<eg, block3(), 0, s>>>(P->g.nx, P->g.ny, P->g.nz, sv, iterate<T>(P, j), iterate<T>(P, j + 1),
-                                                  P->lv[0].mask, (const T*)P->Ed, (T*)P->gt, kh, (T)P->kdiag,
-                                                  (T)(1.0 / beta), (T)scale, j < Tn - 1);
+        k_adjoint_elem<T><<<eg, block3(), 0, s>>>(P->g.nx, P->g.ny, P->g.nz, sv, uj, uj1, P->lv[0].mask,
+                                                  (const T*)P->Ed, (T*)P->gt, kh, (T)P->kdiag, (T)(1.0 / beta),
+                                                  (T)scale, j < Tn - 1);
         TO_CUDA(cudaGetLastError());
         if (j > 0) {
             int rc = launch_operator(P, 0, OP_APPLY, sv, q, nullptr, s);
             if (rc) return rc;
             k_sub_inplace<T><<<nb, 256, 0, s>>>(P->n_dof, lam, q);
             TO_CUDA(cudaGetLastError());
+        }
+        return TO_OK;
+    };
+    if (st == 1) {
+        for (int j = Tn - 1; j >= 0; --j)
+            if (int rc = rstep(j, slot<T>(P, j), slot<T>(P, j + 1))) return rc;
+    } else {
+        // segments last to first: recompute the segment's iterates (the residual scratch r and
+        // z are free here: lambda lives in tmp_v, s is rewritten at each reverse step), then
+        // run its reverse steps
+        const int nck = (Tn + st - 1) / st;
+        void* gt = P->gt;
+        for (int m = nck - 1; m >= 0; --m) {
+            const int len = std::min(st, Tn - m * st);
+            P->gt = nullptr;
+            int rc = walk_segment<T>(P, m, len, nck, beta, s);
+            P->gt = gt;
+            if (rc) return rc;
+            for (int i = len - 1; i >= 0; --i)
+                if ((rc = rstep(m * st + i, slot<T>(P, nck + i), slot<T>(P, nck + i + 1)))) return rc;
         }
     }
     return launch_filter_prescaled_T(P, P->gt, g, s);
@@ -259,7 +338,9 @@ extern "C" int to_compliance_truncated(to_problem* P, const void* rho_dev, int32
 extern "C" int to_compliance_truncated_grad(to_problem* P, double scale, void* g_dev, void* stream) {
     if (!P) return fail(TO_ERR_ARG, "null problem");
     if (!g_dev) return fail(TO_ERR_ARG, "null gradient");
-    if (P->iters_T < 0) return fail(TO_ERR_STATE, "call to_compliance_truncated first");
+    if (P->iters_T < 0 || P->fwd_id == 0)
+        return fail(TO_ERR_STATE, P->iters_T < 0 ? "call to_compliance_truncated first"
+                                                 : "the design changed since the last to_compliance_truncated");
     int prev = -1;
     cudaGetDevice(&prev);
     if (cudaSetDevice(P->device) != cudaSuccess) return fail(TO_ERR_CUDA, "cudaSetDevice failed");
@@ -267,4 +348,10 @@ extern "C" int to_compliance_truncated_grad(to_problem* P, double scale, void* g
     int rc = P->prec == TO_FP64 ? backward_t<double>(P, scale, g_dev, s) : backward_t<float>(P, scale, g_dev, s);
     if (prev >= 0) cudaSetDevice(prev);
     return rc;
+}
+
+extern "C" int to_compliance_truncated_id(const to_problem* P, int64_t* id_out) {
+    if (!P || !id_out) return fail(TO_ERR_ARG, "null argument");
+    *id_out = P->fwd_id;
+    return TO_OK;
 }

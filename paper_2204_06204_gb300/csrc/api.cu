@@ -98,6 +98,7 @@ static int validate(const to_grid* g, const to_material* m, const to_loads* L, c
     if (p->precond < 0 || p->precond > 3) return fail(TO_ERR_ARG, "bad preconditioner");
     if (p->precond == TO_PRECOND_KRYLOV && (p->krylov_dim < 0 || p->krylov_dim > 30))
         return fail(TO_ERR_ARG, "krylov_dim must lie in [0, 30]");
+    if (p->adj_stride < -1) return fail(TO_ERR_ARG, "adj_stride must be >= -1");
     if (p->inner_mode < TO_INNER_SD || p->inner_mode > TO_INNER_PCG) return fail(TO_ERR_ARG, "bad inner mode");
     if (p->n_inner < 0) return fail(TO_ERR_ARG, "n_inner must be >= 0");
     if (!(p->m >= 0.0)) return fail(TO_ERR_ARG, "alpha exponent m must be >= 0");
@@ -338,6 +339,7 @@ extern "C" int to_set_design(to_problem* P, const void* rho_dev, void* stream) {
     TO_ENTER(P);
     if (!rho_dev) return fail(TO_ERR_ARG, "rho is null");
     TO_CUDA(cudaMemcpyAsync(P->rho, rho_dev, P->n_elem * P->esz, cudaMemcpyDeviceToDevice, s));
+    P->fwd_id = 0;   // iterates kept by a truncated forward belong to the old design
     int rc = launch_moduli(P, s);
     if (rc) return rc;
     P->precond_stale = 1;   // refreshed by the next to_inner_solve (to_step refreshes every iteration)
@@ -349,6 +351,43 @@ extern "C" int to_apply_K(to_problem* P, const void* u_dev, void* y_dev, void* s
     if (!u_dev || !y_dev) return fail(TO_ERR_ARG, "null vector");
     if (u_dev == y_dev) return fail(TO_ERR_ARG, "u and y must not overlap");
     return launch_operator(P, 0, OP_APPLY, u_dev, y_dev, nullptr, s);
+}
+
+extern "C" int to_residual(to_problem* P, const void* u_dev, void* r_dev, void* z_dev, void* gt_dev,
+                           double* scalars_out, void* stream) {
+    TO_ENTER(P);
+    if (!u_dev || !r_dev) return fail(TO_ERR_ARG, "null vector");
+    if (u_dev == r_dev || u_dev == z_dev || (z_dev && z_dev == r_dev)) return fail(TO_ERR_ARG, "vectors must not overlap");
+    if (P->precond_stale) {   // 1 / diag(K^) of the current design
+        if (int rc0 = refresh_preconditioner(P, s)) return rc0;
+        P->precond_stale = 0;
+    }
+    const OpOut out{z_dev, gt_dev};
+    int rc = launch_operator(P, 0, OP_RESID, u_dev, r_dev, P->f, s, 0.0, 1, &out);
+    if (rc) return rc;
+    if (scalars_out) {
+        DevScalars h;
+        TO_CUDA(cudaMemcpyAsync(&h, P->sc, sizeof h, cudaMemcpyDeviceToHost, s));
+        TO_CUDA(cudaStreamSynchronize(s));
+        scalars_out[0] = z_dev ? h.rz : 0.0;
+        scalars_out[1] = h.res2;
+        scalars_out[2] = h.res_inf;
+        scalars_out[3] = h.J;
+        if (h.err) return fail(h.err, "device-side error in the residual");
+    }
+    return TO_OK;
+}
+
+extern "C" int to_smooth(to_problem* P, const void* x_dev, const void* b_dev, void* y_dev, double omega, void* stream) {
+    TO_ENTER(P);
+    if (!x_dev || !b_dev || !y_dev) return fail(TO_ERR_ARG, "null vector");
+    if (y_dev == x_dev || y_dev == b_dev) return fail(TO_ERR_ARG, "y must not overlap x or b");
+    if (!std::isfinite(omega)) return fail(TO_ERR_ARG, "omega must be finite");
+    if (P->precond_stale) {
+        if (int rc0 = refresh_preconditioner(P, s)) return rc0;
+        P->precond_stale = 0;
+    }
+    return launch_operator(P, 0, OP_SMOOTH, x_dev, y_dev, b_dev, s, omega, 0);
 }
 
 extern "C" int to_inner_solve(to_problem* P, void* u_dev, int32_t nsteps, double* res_out, void* stream) {
@@ -438,6 +477,7 @@ extern "C" int to_step(to_problem* P, int32_t n_outer, to_stats* stats_out, void
     TO_ENTER(P);
     if (n_outer < 0) return fail(TO_ERR_ARG, "n_outer must be >= 0");
     if (n_outer == 0) return TO_OK;
+    P->fwd_id = 0;   // the outer iterations change the design
     if (n_outer > P->dstats_cap) {
         TO_CUDA(cudaStreamSynchronize(s));
         TO_CUDA(cudaStreamSynchronize(P->gstream));
@@ -503,6 +543,7 @@ __global__ void k_set_counters(to::DevScalars* sc, long long k, double alpha0, i
 extern "C" int to_set_state(to_problem* P, const void* rho_dev, const void* u_dev, int64_t k, double alpha0, void* stream) {
     TO_ENTER(P);
     if (k < 1) return fail(TO_ERR_ARG, "k must be >= 1");
+    P->fwd_id = 0;
     if (rho_dev) TO_CUDA(cudaMemcpyAsync(P->rho, rho_dev, P->n_elem * P->esz, cudaMemcpyDeviceToDevice, s));
     if (u_dev) TO_CUDA(cudaMemcpyAsync(P->u, u_dev, P->n_dof * P->esz, cudaMemcpyDeviceToDevice, s));
     k_set_counters<<<1, 1, 0, s>>>(P->sc, (long long)k, alpha0, 1, 1);
@@ -511,6 +552,17 @@ extern "C" int to_set_state(to_problem* P, const void* rho_dev, const void* u_de
     if (rc) return rc;
     P->precond_stale = 1;   // refreshed by the next to_inner_solve (to_step refreshes every iteration)
     return TO_OK;
+}
+
+namespace to {
+int barrier_selftest(to_problem* P, int absent, long long spin_limit, cudaStream_t s);
+}
+
+extern "C" int to_barrier_selftest(to_problem* P, int32_t absent_block, int64_t spin_limit, void* stream) {
+    TO_ENTER(P);
+    if (spin_limit < 1 || spin_limit > (int64_t)kBarrierSpins) return fail(TO_ERR_ARG, "spin_limit out of range");
+    if (absent_block < -1) return fail(TO_ERR_ARG, "absent_block must be >= -1");
+    return barrier_selftest(P, absent_block, spin_limit, s);
 }
 
 __global__ void k_clear_err(to::DevScalars* sc) { sc->err = 0; }

@@ -401,6 +401,7 @@ extern "C" int to_batch_step(to_batch* B, int32_t n_outer, to_stats* stats_out, 
     if (!B) return fail(TO_ERR_ARG, "null batch");
     if (n_outer < 0) return fail(TO_ERR_ARG, "n_outer must be >= 0");
     if (n_outer == 0) return TO_OK;
+    for (to_problem* P : B->probs) P->fwd_id = 0;   // the outer iterations change every design
     for (to_problem* P : B->probs)
         if (n_outer > P->dstats_cap)
             return fail(TO_ERR_ARG, "n_outer exceeds a problem's stats ring (run to_step once with that many iterations "

@@ -51,6 +51,7 @@ struct FilterArgs {
     unsigned* counter;
     DevScalars* sc;
     double alpha0_param, alpha_scale, m_exp;
+    int mean_proj;       // STATS: ||g||_inf of the mean-projected g - 1 1^T g / E (Sec. IV-B)
     T* Eout;             // MODULI: E and E' / Hs
     T* Edout;
     SimpT<T> simp;
@@ -107,7 +108,7 @@ __device__ __forceinline__ void filter_body(const FilterArgs<T>& a, int bx, int 
         }
     __syncthreads();
 
-    T amax = T(0), sum = T(0);   // per-thread partials in the element precision
+    T vmax = T(-INFINITY), vmin = T(INFINITY), sum = T(0);   // per-thread partials in the element precision
     const T* col = box + (size_t)R * PS + (threadIdx.y + R) * TW + threadIdx.x + R;   // (i, j, k0) in the box
     for (int kb = k0; kb < k1; kb += kFilterPlanes) {
         T acc[kFilterPlanes];
@@ -141,24 +142,28 @@ __device__ __forceinline__ void filter_body(const FilterArgs<T>& a, int bx, int 
                 if (!tfinite(out)) set_err(&a.sc->err, TO_ERR_NONFINITE);
             }
             if (STATS) {
-                amax = tmax(amax, tabs(out));
+                vmax = tmax(vmax, out);
+                vmin = tmin(vmin, out);
                 sum += out;
             }
         }
     }
     if (STATS) {
-        T v[2] = {amax, sum};
-        const int kind[2] = {1, 0};
-        double tot[2];
-        block_reduce<T, 2>(v, kind, reinterpret_cast<T*>(sh));
-        if (finish_reduction<T, 2>(v, kind, a.red, a.counter, tot, sh, bid, nblocks) && tid == 0) {
+        T v[3] = {vmax, -vmin, sum};
+        const int kind[3] = {1, 1, 0};
+        double tot[3];
+        block_reduce<T, 3>(v, kind, reinterpret_cast<T*>(sh));
+        if (finish_reduction<T, 3>(v, kind, a.red, a.counter, tot, sh, bid, nblocks) && tid == 0) {
             DevScalars* sc = a.sc;
-            sc->gmax = tot[0];
-            sc->gsum = tot[1];
-            if (!isfinite(tot[0]) || !isfinite(tot[1])) set_err(&sc->err, TO_ERR_NONFINITE);
+            // ||g||_inf of the step direction: g itself, or g - mean(g) with the mean projection
+            const double shift = a.mean_proj ? tot[2] / ((double)nx * ny * nz) : 0.0;
+            const double gmax = fmax(tot[0] - shift, tot[1] + shift);
+            sc->gmax = gmax;
+            sc->gsum = tot[2];
+            if (!isfinite(gmax) || !isfinite(tot[2])) set_err(&sc->err, TO_ERR_NONFINITE);
             // high-level step alpha_k = alpha0 k^-m; alpha0 fixed at the first k with g != 0
             double a0 = a.alpha0_param > 0.0 ? a.alpha0_param : sc->alpha0;
-            if (!(a0 > 0.0) && tot[0] > 0.0) a0 = a.alpha_scale / tot[0];
+            if (!(a0 > 0.0) && gmax > 0.0) a0 = a.alpha_scale / gmax;
             sc->alpha0 = a0 > 0.0 ? a0 : 0.0;
             sc->alpha = a0 > 0.0 ? a0 * pow((double)sc->k, -a.m_exp) : 0.0;
         }
@@ -254,6 +259,7 @@ static FilterArgs<T> filter_args(const to_problem* P, const T* x, T* y, int kchu
     a.alpha0_param = P->prm.alpha0;
     a.alpha_scale = P->prm.alpha_scale;
     a.m_exp = P->prm.m;
+    a.mean_proj = P->prm.mean_proj;
     a.Eout = Eout;
     a.Edout = Edout;
     a.simp = simp_params<T>(P->mat);

@@ -246,9 +246,11 @@ __device__ __forceinline__ bool finish_reduction(const V (&v)[NQ], const int (&k
 }
 
 // Grid-wide barrier for a cooperative (co-resident) launch.  bar[0] counts
-// arrivals, bar[1] is the generation.  Spins a bounded number of times; on
-// timeout records TO_ERR_TIMEOUT in *err and returns false.
-__device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err) {
+// arrivals, bar[1] is the generation.  Spins at most spin_limit times (about
+// 1 s with the default); on timeout records TO_ERR_TIMEOUT in *err and returns
+// false.
+constexpr unsigned long long kBarrierSpins = 1ull << 24;
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err, unsigned long long spin_limit = kBarrierSpins) {
     __shared__ int s_ok;
     const unsigned nblocks = gridDim.x * gridDim.y * gridDim.z;
     __syncthreads();
@@ -265,7 +267,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err) {
         } else {
             unsigned long long spins = 0;
             while (*vgen == gen) {
-                if (++spins > (1ull << 24)) {
+                if (++spins > spin_limit) {
                     atomicCAS(err, 0, (int)TO_ERR_TIMEOUT);
                     s_ok = 0;
                     break;

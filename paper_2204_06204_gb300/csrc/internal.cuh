@@ -160,6 +160,9 @@ struct to_problem {
     int iters_cap = 0;
     int iters_T = -1;
     double iters_beta = 0.0;
+    int iters_stride = 1;          // every iters_stride-th iterate kept (1: all)
+    int64_t fwd_id = 0;            // id of the kept iterates; 0: none, or the design changed since
+    int64_t fwd_count = 0;
 
     // can one 16-CTA cluster run the projection's search passes
     int cluster16 = 0;
@@ -191,9 +194,15 @@ int launch_moduli(to_problem* P, cudaStream_t s);  // rho -> rho~, E, E'
 int launch_diag(to_problem* P, int level, cudaStream_t s);
 
 enum OpMode { OP_APPLY = 0, OP_RESID = 1, OP_Q = 2, OP_SMOOTH = 3, OP_BMINUS = 4 };
+// OP_RESID outputs named by the caller instead of the problem's buffers (nullptr skips one)
+struct OpOut {
+    void* z;    // r / d
+    void* gt;   // -E'_e u_e^T k_e u_e / Hs_e
+};
 // y = K^ x (+ mode epilogue) on multigrid level `level` (0 = fine grid).
 int launch_operator(to_problem* P, int level, int mode, const void* x, void* y,
-                    const void* b, cudaStream_t s, double omega = 0.0, int first = 0);
+                    const void* b, cudaStream_t s, double omega = 0.0, int first = 0,
+                    const OpOut* out = nullptr);
 
 int launch_project(to_problem* P, const void* w, const void* rho_in, const void* g,
                    void* rho_out, int fused, cudaStream_t s);

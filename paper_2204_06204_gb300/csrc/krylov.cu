@@ -25,9 +25,6 @@
 
 namespace to {
 
-int launch_operator(to_problem* P, int level, int mode, const void* x, void* y, const void* b, cudaStream_t s,
-                    double omega, int first);
-
 constexpr int kKryThreads = 512;
 constexpr int kKryMax = 30;   // largest Krylov dimension D
 

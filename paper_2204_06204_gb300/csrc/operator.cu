@@ -511,7 +511,7 @@ static void fill_haar(const to_problem* P, double scale_h, HaarK<T>& kh) {
 
 template <typename T, int TX, int TY>
 static int launch_t(to_problem* P, int level, int mode, const void* x, void* y, const void* b,
-                    cudaStream_t s, double omega, int first) {
+                    cudaStream_t s, double omega, int first, const OpOut* out) {
     const Level& L = P->lv[level];
     OpArgs<T> a{};
     a.nx = L.nx;
@@ -534,6 +534,10 @@ static int launch_t(to_problem* P, int level, int mode, const void* x, void* y, 
         a.z = (P->prm.precond == TO_PRECOND_JACOBI && level == 0) ? (T*)P->z : nullptr;
         a.Ed = (const T*)P->Ed;
         a.gt = (T*)P->gt;
+        if (out) {   // caller-supplied outputs (to_residual): z = r / d and g~ / Hs, either optional
+            a.z = (T*)out->z;
+            a.gt = (T*)out->gt;
+        }
     } else if (mode == OP_Q) {
         a.counter = P->counters + 1;
     } else if (mode == OP_SMOOTH) {
@@ -692,9 +696,9 @@ int build_tile_mask(Level& L, const uint8_t* mask_host) {
 }
 
 int launch_operator(to_problem* P, int level, int mode, const void* x, void* y, const void* b,
-                    cudaStream_t s, double omega, int first) {
-    if (P->prec == TO_FP64) return launch_t<double, 32, 8>(P, level, mode, x, y, b, s, omega, first);
-    return launch_t<float, 32, 8>(P, level, mode, x, y, b, s, omega, first);
+                    cudaStream_t s, double omega, int first, const OpOut* out) {
+    if (P->prec == TO_FP64) return launch_t<double, 32, 8>(P, level, mode, x, y, b, s, omega, first, out);
+    return launch_t<float, 32, 8>(P, level, mode, x, y, b, s, omega, first, out);
 }
 
 }  // namespace to

@@ -462,6 +462,35 @@ static int project_t(to_problem* P, const void* w, const void* rho_in, const voi
     return TO_OK;
 }
 
+// Self-test of the bounded grid barrier: every block but `absent` waits at the
+// barrier with the given spin limit; with a block absent nobody releases it, so
+// the waiting blocks give up, record TO_ERR_TIMEOUT and return.
+__global__ void __launch_bounds__(256) k_barrier_selftest(unsigned* bar, int* err, int absent,
+                                                          unsigned long long spin_limit) {
+    if ((int)blockIdx.x == absent) return;
+    grid_barrier(bar, err, spin_limit);
+}
+
+int barrier_selftest(to_problem* P, int absent, long long spin_limit, cudaStream_t s) {
+    const int nb = P->coop_blocks > 1 ? (P->coop_blocks < 8 ? P->coop_blocks : 8) : 1;
+    if (absent >= nb) return fail(TO_ERR_ARG, "absent block index beyond the launch");
+    unsigned* bar = P->counters + 8;
+    int* err = &P->sc->err;
+    unsigned long long lim = (unsigned long long)spin_limit;
+    void* args[] = {(void*)&bar, (void*)&err, (void*)&absent, (void*)&lim};
+    TO_CUDA(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s));
+    TO_CUDA(cudaLaunchCooperativeKernel((const void*)k_barrier_selftest, dim3((unsigned)nb), dim3(256), args, 0, s));
+    DevScalars h;
+    TO_CUDA(cudaMemcpyAsync(&h, P->sc, sizeof h, cudaMemcpyDeviceToHost, s));
+    TO_CUDA(cudaStreamSynchronize(s));
+    // the barrier words of an abandoned barrier are not reusable: clear them and the flag
+    TO_CUDA(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s));
+    TO_CUDA(cudaMemsetAsync(reinterpret_cast<char*>(P->sc) + offsetof(DevScalars, err), 0, sizeof(int), s));
+    TO_CUDA(cudaStreamSynchronize(s));
+    if (h.err) return fail(h.err, "grid barrier self-test: a block did not arrive and the waiting blocks gave up");
+    return TO_OK;
+}
+
 // can one 16-CTA cluster of the search kernel be placed on this device?
 int project_cluster_setup(to_problem* P) {
     cudaError_t e;
@@ -580,8 +609,12 @@ template <typename T>
 int project_noalloc_t(NoAllocDevice& D, const void* w, void* rho, long long n, double vbar, double lo, double hi,
                       double* lambda_out, cudaStream_t s) {
     NoAllocScratch* S = D.ptr;
-    // the last call's contents stay in the array: reset what must start at zero
-    TO_CUDA(cudaMemsetAsync(S, 0, offsetof(NoAllocScratch, part), s));
+    // the last call's contents stay in the array: reset what must start at zero,
+    // except the error word, which is sticky until a synchronising call reports it
+    const size_t e0 = offsetof(NoAllocScratch, sc) + offsetof(DevScalars, err);
+    const size_t e1 = e0 + sizeof(int);
+    TO_CUDA(cudaMemsetAsync(S, 0, e0, s));
+    TO_CUDA(cudaMemsetAsync(reinterpret_cast<char*>(S) + e1, 0, offsetof(NoAllocScratch, part) - e1, s));
     ProjArgs<T> a{};
     a.n = n;
     a.w_in = (const T*)w;
@@ -611,7 +644,13 @@ int project_noalloc_t(NoAllocDevice& D, const void* w, void* rho, long long n, d
         TO_CUDA(cudaMemcpyAsync(&h, &S->sc, sizeof h, cudaMemcpyDeviceToHost, s));
         TO_CUDA(cudaStreamSynchronize(s));
         *lambda_out = h.lambda;
-        if (h.err) return fail(h.err, "device-side error in the allocation-free projection");
+        if (h.err) {
+            // report once: clear the sticky word so that the next call starts clean
+            TO_CUDA(cudaMemsetAsync(reinterpret_cast<char*>(S) + e0, 0, sizeof(int), s));
+            TO_CUDA(cudaStreamSynchronize(s));
+            return fail(h.err, "device-side error in the allocation-free projection (this call or an earlier "
+                               "call made without lambda_out)");
+        }
     }
     return TO_OK;
 }

@@ -1,0 +1,246 @@
+"""Parity of the benchmarked multigrid path at the shapes it is launched with.
+
+* 64x32x32 cantilever and MBB half model, two multigrid-preconditioned steps per
+  outer iteration: several fine-level tiles per dimension, z-chunked operator
+  launches, and multigrid levels 0 and 1 as separate launches before the one-CTA
+  coarse tail.  FP64 against the oracle's outer loop live (5 iterations, 1e-8);
+  FP32-mixed over 30 iterations against the oracle's stored trajectory
+  (``tests/golden/*_mg2_30.json``, written by ``make_mg2_trajectory.py``, which
+  calls only ``oracle/``): exact final compliance within 1e-3, mean per-element
+  |drho| within 1e-2 on the stored sample.
+* 128x64x64 (the benchmark workload) in the benchmark's launch configuration:
+  the fused residual epilogue (r = f - K u, z = r / d, the element sensitivity
+  and the reductions) and the damped-Jacobi epilogue, checked at sampled nodes
+  and elements that the oracle computes one at a time, including whole lines of
+  nodes across every tile boundary in x, y and z; and the 200-iteration
+  FP32-mixed run against the oracle's stored 200-iteration trajectory.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import fem, filt, outer
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _fb():
+    import __graft_entry__ as g
+    g.build()
+    import paper_2204_06204_gb300 as fb
+    return fb
+
+
+def _t(x, P):
+    return torch.tensor(np.asarray(x), dtype=P.dtype, device=P.device)
+
+
+def _workload(which, dims):
+    return W.cantilever(*dims) if which == "cantilever" else W.mbb_half(*dims)
+
+
+def _exact_compliance_gpu(fb, pb, rho):
+    """f^T K(rho)^-1 f for a design, by 200 multigrid-preconditioned CG iterations in FP64."""
+    prm = fb.to_default_params(precision=fb.TO_FP64, precond=fb.TO_PRECOND_MG, inner_mode=fb.TO_INNER_PCG,
+                               n_inner=1)
+    with fb.Problem.from_workload(pb, prm) as Pe:
+        Pe.set_design(torch.as_tensor(rho, dtype=torch.float64, device=Pe.device))
+        u = Pe.dof()
+        u.zero_()
+        res = Pe.inner_solve(u, 200, want_res=True)
+        f = np.zeros(pb.n_dof)
+        np.add.at(f, pb.load_dof, pb.load_val)
+        f[pb.fixed_dof] = 0.0
+        J = float(np.dot(f, u.cpu().numpy()))
+    assert res <= 1e-9 * np.linalg.norm(f)
+    return J
+
+
+@pytest.mark.parametrize("which", ["cantilever", "mbb"])
+def test_mg2_outer_loop_fp64_64x32x32(which):
+    fb = _fb()
+    pb = _workload(which, (64, 32, 32))
+    n = 5
+    prm = fb.to_default_params(precision=fb.TO_FP64, precond=fb.TO_PRECOND_MG, n_inner=2)
+    with fb.Problem.from_workload(pb, prm) as P:
+        st = P.step(n)
+        rho, u, k, a0 = P.get_state()
+    rho_o, u_o, hist, a0_o = outer.run(pb, n, precond="mg", n_inner=2)
+    assert k == n + 1
+    assert np.abs(rho.cpu().numpy() - rho_o).max() <= 1e-8
+    assert np.abs(u.cpu().numpy() - u_o).max() <= 1e-8 * np.abs(u_o).max()
+    J = np.array([s["J"] for s in st])
+    Jo = np.array([h["J"] for h in hist])
+    assert np.abs(J - Jo).max() <= 1e-8 * np.abs(Jo).max()
+    for key, okey in (("beta_first", None), ("lambda", "lam"), ("volume", "volume"), ("res2", "res2")):
+        g = np.array([s[key] for s in st[1:]])
+        o = np.array([h["betas"][0] for h in hist[1:]]) if okey is None else np.array([h[okey] for h in hist[1:]])
+        assert np.abs(g - o).max() <= 1e-8 * max(np.abs(o).max(), 1e-30), key
+
+
+def _golden(name):
+    path = os.path.join(GOLDEN, name)
+    if not os.path.exists(path):
+        pytest.fail(f"missing oracle fixture {name}: run tests/golden/make_mg2_trajectory.py")
+    return json.load(open(path))
+
+
+def _check_against_golden(fb, pb, rec, n):
+    prm = fb.to_default_params(precision=fb.TO_FP32_MIXED, precond=fb.TO_PRECOND_MG, n_inner=2)
+    with fb.Problem.from_workload(pb, prm) as P:
+        st = P.step(n)
+        rho = P.get_state()[0].double().cpu().numpy()
+    assert len(rec["J"]) == n
+    # tracked compliance f^T u_k at the last iteration, and the exact compliance of the final design
+    assert abs(st[-1]["J"] - rec["J"][-1]) <= 1e-3 * abs(rec["J"][-1])
+    J_gpu = _exact_compliance_gpu(fb, pb, rho)
+    assert abs(J_gpu - rec["J_exact_final"]) <= 1e-3 * abs(rec["J_exact_final"])
+    idx = np.asarray(rec["rho_sample_index"], dtype=np.int64)
+    assert np.mean(np.abs(rho[idx] - np.asarray(rec["rho_sample"]))) <= 1e-2
+    assert abs(st[-1]["volume"] - rec["volume"][-1]) <= 1e-3 * rec["volume"][-1]
+    return J_gpu
+
+
+@pytest.mark.parametrize("which", ["cantilever", "mbb"])
+def test_mg2_outer_loop_fp32_64x32x32_vs_oracle_trajectory(which):
+    fb = _fb()
+    rec = _golden(f"{which}_64x32x32_mg2_30.json")
+    _check_against_golden(fb, _workload(which, (64, 32, 32)), rec, 30)
+
+
+def test_mg2_fp32_128x64x64_200_iterations_vs_oracle():
+    """The benchmark workload end to end: 200 FP32-mixed outer iterations against the
+    oracle's FP64 run of the same 200 iterations."""
+    fb = _fb()
+    rec = _golden("cantilever_128x64x64_mg2_200.json")
+    _check_against_golden(fb, W.cantilever_128x64x64(), rec, 200)
+
+
+# ----------------------------------------------------------------------------- sampled nodes at 128x64x64
+def _sample_nodes(pb):
+    nx, ny, nz = pb.nx, pb.ny, pb.nz
+    node = lambda i, j, k: i + (nx + 1) * (j + (ny + 1) * k)
+    s = set(int(n) for n in W.rng(11).integers(0, pb.n_node, 300))
+    s |= {node(i, 33, 17) for i in range(nx + 1)}          # every x tile boundary
+    s |= {node(64, j, 40) for j in range(ny + 1)}          # every y tile boundary
+    s |= {node(100, 7, k) for k in range(nz + 1)}          # every z chunk boundary
+    s |= {node(0, j, 5) for j in range(0, ny + 1, 8)}      # clamped face
+    s |= {node(i, j, k) for i in (0, nx) for j in (0, ny) for k in (0, nz)}
+    s |= {node(nx, 0, k) for k in range(0, nz + 1, 4)}     # loaded edge
+    return sorted(s)
+
+
+class _NodeOracle:
+    """K^ x, diag(K^) and element energies at single nodes / elements (FP64, one at a time)."""
+
+    def __init__(self, pb, Ee):
+        self.pb, self.Ee = pb, Ee
+        self.ke = fem.ke_hex8(pb.nu, pb.h)
+        self.m = fem.free_mask(pb.n_dof, pb.fixed_dof)
+
+    def elem_nodes(self, ei, ej, ek):
+        nx, ny = self.pb.nx, self.pb.ny
+        return [(ei + a) + (nx + 1) * ((ej + b) + (ny + 1) * (ek + c)) for a, b, c in fem.LOCAL_NODES]
+
+    def at_node(self, n, x):
+        """((K^ x)_n, (|K| |m x|)_n bound, diag(K^)_n), 3 components each."""
+        pb = self.pb
+        nx, ny, nz = pb.nx, pb.ny, pb.nz
+        i, j, k = n % (nx + 1), (n // (nx + 1)) % (ny + 1), n // ((nx + 1) * (ny + 1))
+        acc, absacc, diag = np.zeros(3), np.zeros(3), np.zeros(3)
+        for dk in (-1, 0):
+            for dj in (-1, 0):
+                for di in (-1, 0):
+                    ei, ej, ek = i + di, j + dj, k + dk
+                    if not (0 <= ei < nx and 0 <= ej < ny and 0 <= ek < nz):
+                        continue
+                    e = ei + nx * (ej + ny * ek)
+                    l = [tuple(o) for o in fem.LOCAL_NODES].index((-di, -dj, -dk))
+                    gn = self.elem_nodes(ei, ej, ek)
+                    xe = np.array([self.m[3 * q + c] * x[3 * q + c] for q in gn for c in range(3)])
+                    acc += self.Ee[e] * (self.ke[3 * l:3 * l + 3] @ xe)
+                    absacc += self.Ee[e] * (np.abs(self.ke[3 * l:3 * l + 3]) @ np.abs(xe))
+                    diag += self.Ee[e] * np.diag(self.ke)[3 * l:3 * l + 3]
+        Kx = np.empty(3)
+        for c in range(3):
+            d = 3 * n + c
+            Kx[c] = acc[c] * self.m[d] + (1 - self.m[d]) * x[d]
+            diag[c] = diag[c] * self.m[d] + (1 - self.m[d])
+        return Kx, absacc, diag
+
+    def energy(self, e, x):
+        nx, ny = self.pb.nx, self.pb.ny
+        ei, ej, ek = e % nx, (e // nx) % ny, e // (nx * ny)
+        gn = self.elem_nodes(ei, ej, ek)
+        xe = np.array([self.m[3 * q + c] * x[3 * q + c] for q in gn for c in range(3)])
+        return float(xe @ self.ke @ xe), float(np.abs(xe) @ np.abs(self.ke) @ np.abs(xe))
+
+
+def _full_size_problem(fb):
+    """The benchmark's problem and parameters (multigrid x2, FP32-mixed) with a random design."""
+    pb = W.cantilever_128x64x64()
+    rho = W.random_rho(pb.n_elem, 0.0, 1.0, seed=W.SEED + 5)
+    prm = fb.to_default_params(precision=fb.TO_FP32_MIXED, precond=fb.TO_PRECOND_MG, n_inner=2)
+    P = fb.Problem.from_workload(pb, prm)
+    P.set_design(_t(rho, P))
+    H, Hs = filt.filter_matrix(pb.nx, pb.ny, pb.nz, pb.rmin)
+    rt = filt.filter_forward(H, Hs, rho)
+    Ee = fem.young(rt, pb.E0, pb.Emin, pb.p)
+    Ed = fem.young_deriv(rt, pb.E0, pb.Emin, pb.p)
+    return pb, P, Ee, Ed, Hs
+
+
+def test_residual_epilogue_full_size_sampled():
+    fb = _fb()
+    pb, P, Ee, Ed, Hs = _full_size_problem(fb)
+    with P:
+        u = W.random_u(pb.n_dof, seed=W.SEED + 6)
+        r, z, gt = P.dof(), P.dof(), P.elem()
+        _, sc = P.residual(_t(u, P), r, z, gt)
+        r = r.double().cpu().numpy()
+        z = z.double().cpu().numpy()
+        gt = gt.double().cpu().numpy()
+    O = _NodeOracle(pb, Ee)
+    f = fem.load_vector(pb.n_dof, pb.load_dof, pb.load_val, pb.fixed_dof)
+    for n in _sample_nodes(pb):
+        Ku, bound, d = O.at_node(n, u)
+        for c in range(3):
+            q = 3 * n + c
+            tol = 1e-5 * max(bound[c], abs(u[q]), 1e-30)
+            assert abs(r[q] - (f[q] - Ku[c])) <= tol, (n, c)
+            assert abs(z[q] - (f[q] - Ku[c]) / d[c]) <= 2 * tol / d[c] + 1e-6 * abs(z[q]), (n, c)
+    # the element sensitivity at u (before the filter transpose), divided by the filter row sum
+    for e in sorted(set(int(x) for x in W.random_elements(pb.n_elem, 400, seed=W.SEED + 8)) | {0, pb.n_elem - 1}):
+        en, ben = O.energy(e, u)
+        ref = -Ed[e] * en / Hs[e]
+        assert abs(gt[e] - ref) <= 1e-4 * Ed[e] * ben / Hs[e] + 1e-30, e
+    # the fused reductions agree with the vectors they reduce (double sums on the host)
+    assert abs(sc["res2"] - np.linalg.norm(r)) <= 1e-5 * np.linalg.norm(r)
+    assert abs(sc["res_inf"] - np.abs(r).max()) <= 1e-6 * np.abs(r).max()
+    assert abs(sc["rz"] - float(r @ z)) <= 1e-5 * float(np.abs(r * z).sum())
+    fu = float(f @ u)
+    assert abs(sc["fu"] - fu) <= 1e-5 * float(np.abs(f * u).sum())
+
+
+def test_smoothing_epilogue_full_size_sampled():
+    fb = _fb()
+    pb, P, Ee, Ed, Hs = _full_size_problem(fb)
+    omega = 0.5
+    with P:
+        x = W.random_u(pb.n_dof, seed=W.SEED + 9)
+        b = W.random_u(pb.n_dof, seed=W.SEED + 10)
+        y = P.smooth(_t(x, P), _t(b, P), omega).double().cpu().numpy()
+    O = _NodeOracle(pb, Ee)
+    for n in _sample_nodes(pb):
+        Kx, bound, d = O.at_node(n, x)
+        for c in range(3):
+            q = 3 * n + c
+            ref = x[q] + omega * (b[q] - Kx[c]) / d[c]
+            tol = 1e-5 * (abs(x[q]) + omega * (abs(b[q]) + bound[c]) / d[c]) + 1e-30
+            assert abs(y[q] - ref) <= tol, (n, c)

@@ -45,3 +45,65 @@ def test_resume_is_bitwise_identical():
     rho_1, u_1, _, a01 = outer.run(pb, 3, setup=S)
     rho_b, u_b, _, _ = outer.run(pb, 5, setup=S, rho=rho_1, u=u_1, k0=4, alpha0=a01)
     assert np.array_equal(rho_a, rho_b) and np.array_equal(u_a, u_b)
+
+
+# ----------------------------------------------------------------------------- mean projection (Sec. IV-B)
+def _grad_at(S, pb, rho, u):
+    """dJ/drho at (rho, u): the element sensitivity chained through the filter transpose."""
+    from oracle import filt
+    _, _, Ed = S.moduli(rho)
+    return filt.filter_transpose(S.H, S.Hs, S.sens_rho_tilde(Ed, u))
+
+
+def test_mean_projected_step_is_the_paper_projector():
+    """One outer step with the mean projection equals w = rho - alpha (I - 1 1^T / E) g written
+    with the projector as an explicit E x E matrix (Sec. IV-B), then projected onto X."""
+    from oracle import project
+    pb = W.cantilever(4, 2, 2)
+    S = outer.Setup(pb)
+    a0 = 0.05
+    rho2, u2, h1, _ = outer.run(pb, 1, setup=S, alpha0=a0, mean_proj=True)      # k = 1: g = 0
+    rho3, u3, h2, _ = outer.run(pb, 1, setup=S, rho=rho2, u=u2, k0=2, alpha0=a0, mean_proj=True)
+    E = pb.n_elem
+    Pm = np.eye(E) - np.ones((E, E)) / E
+    g = _grad_at(S, pb, rho2, u2)
+    alpha = a0 * 2.0 ** -0.75
+    w = rho2 - alpha * (Pm @ g)
+    ref, lam = project.project_alg4(w, S.vbar, pb.rho_min, pb.rho_max)
+    assert np.abs(rho3 - ref).max() <= 1e-14
+    assert abs(h2[0]["gmax"] - np.abs(Pm @ g).max()) <= 1e-14 * np.abs(g).max()
+    assert abs(float(np.ones(E) @ (Pm @ g))) <= 1e-12 * np.abs(g).sum()   # 1^T P g = 0
+
+
+def test_mean_projection_keeps_volume_when_no_bound_is_active():
+    """With the volume and box bounds inactive the mean-projected step moves along
+    1^perp: the volume stays at its start value exactly (up to rounding), while the
+    plain gradient step changes it."""
+    pb = W.cantilever(8, 4, 4, volfrac=0.9, rho_init=0.3)
+    S = outer.Setup(pb)
+    a0 = 1e-3
+    rho_m, _, hm, _ = outer.run(pb, 6, setup=S, alpha0=a0, mean_proj=True)
+    rho_p, _, hp, _ = outer.run(pb, 6, setup=S, alpha0=a0, mean_proj=False)
+    assert rho_m.min() > pb.rho_min and rho_m.max() < pb.rho_max         # box inactive
+    assert all(h["lam"] == 0.0 for h in hm)                               # volume bound inactive
+    assert abs(rho_m.sum() - 0.3 * pb.n_elem) <= 1e-12 * pb.n_elem
+    assert rho_p.sum() > 0.3 * pb.n_elem + 1e-3                           # compliance gradient < 0 adds volume
+
+
+def test_mean_projection_only_shifts_the_multiplier_when_the_volume_bound_binds():
+    """Proj_X(rho - alpha g) = Proj_X(rho - alpha (g - c 1)) when the volume bound is active
+    and no box bound binds (the KKT multiplier absorbs c): same rho, lambda + alpha c."""
+    from oracle import project
+    pb = W.cantilever(4, 2, 2)
+    S = outer.Setup(pb)
+    r = W.rng(5)
+    rho = r.uniform(0.25, 0.35, pb.n_elem)
+    rho *= S.vbar / rho.sum()
+    u = W.random_u(pb.n_dof) * 0.1
+    g = _grad_at(S, pb, rho, u)
+    alpha = 1e-3 / np.abs(g).max()
+    a, la = project.project_alg4(rho - alpha * g, S.vbar, pb.rho_min, pb.rho_max)
+    b, lb = project.project_alg4(rho - alpha * (g - g.mean()), S.vbar, pb.rho_min, pb.rho_max)
+    assert la > 0.0
+    assert np.abs(a - b).max() <= 1e-14
+    assert abs((lb - la) - alpha * g.mean()) <= 1e-12 * abs(alpha * g.mean())
