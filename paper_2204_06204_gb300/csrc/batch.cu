@@ -141,6 +141,7 @@ __global__ void __launch_bounds__(1024) k_b_project(const BProb<T>* __restrict__
     io.fused = 1;
     io.mean_proj = P.mean_proj;
     io.writer = rank == 0;
+    io.wdirect = 0;
     ClusterComm comm{slots};
     T* rho = const_cast<T*>(P.rho);
     projection_body<T, CACHE>(comm, io, nullptr, P.rho, P.grad, reinterpret_cast<T*>(smem_raw), P.wbuf, rho, P.sc);

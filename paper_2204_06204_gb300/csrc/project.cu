@@ -35,6 +35,7 @@ struct ProjArgs {
     T* rho_out;
     double vbar, lo, hi;
     int fused, mean_proj;
+    int wdirect;         // plain mode without a cache: read w from w_in, store nothing (wbuf == w_in)
     long long chunk;     // elements per block (contiguous)
     double* part;        // 2 * nblocks * kProjSlot words
     unsigned* bar;       // barrier words
@@ -87,6 +88,7 @@ __global__ void __launch_bounds__(256) k_project(const ProjArgs<T> a) {
     io.fused = a.fused;
     io.mean_proj = a.mean_proj;
     io.writer = blockIdx.x == 0;
+    io.wdirect = a.wdirect;
     projection_body<T, CACHE>(comm, io, a.w_in, a.rho_in, a.g, reinterpret_cast<T*>(smem_raw), a.wbuf, a.rho_out,
                               a.sc);
 }
@@ -635,10 +637,16 @@ int project_noalloc_t(NoAllocDevice& D, const void* w, void* rho, long long n, d
     a.chunk = (n + nb - 1) / nb;
     nb = (n + a.chunk - 1) / a.chunk;
     const size_t smem = (size_t)a.chunk * sizeof(T);
-    if (smem > kProjSmem)
-        return fail(TO_ERR_ARG, "n too large for the allocation-free projection on this device");
     void* args[] = {(void*)&a};
-    TO_CUDA(cudaLaunchCooperativeKernel((const void*)k_project<T, true>, dim3((unsigned)nb), dim3(256), args, smem, s));
+    if (smem <= kProjSmem) {   // each block keeps its chunk of w in shared memory
+        TO_CUDA(cudaLaunchCooperativeKernel((const void*)k_project<T, true>, dim3((unsigned)nb), dim3(256), args, smem,
+                                            s));
+    } else {                   // the search passes re-read w from the input (nothing is stored)
+        a.wbuf = const_cast<T*>(a.w_in);
+        a.wdirect = 1;
+        TO_CUDA(cudaLaunchCooperativeKernel((const void*)k_project<T, false>, dim3((unsigned)nb), dim3(256), args, 0,
+                                            s));
+    }
     if (lambda_out) {
         DevScalars h;
         TO_CUDA(cudaMemcpyAsync(&h, &S->sc, sizeof h, cudaMemcpyDeviceToHost, s));

@@ -135,6 +135,7 @@ struct ProjIO {
     long long n, b0, b1;      // all elements; this block's range [b0, b1)
     double vbar, lo, hi;
     int fused, mean_proj, writer;   // writer: the block that stores the scalars
+    int wdirect;                    // uncached plain mode: wbuf is the input w itself (read, never stored)
 };
 
 // Comm: exchange(const ProjPart& mine (thread 0), int parity, ProjPart& tot (thread 0)) -> false on a timeout;
@@ -192,7 +193,7 @@ __device__ __forceinline__ void projection_body(Comm& comm, const ProjIO& io, co
                 if (e < b1) {
                     const T w = io.fused ? rv[q] - alpha_t * (gv[q] - gmean_t) : rv[q];
                     if (CACHE) wloc[e - b0] = w;
-                    else wbuf[e] = w;
+                    else if (!io.wdirect) wbuf[e] = w;
                     if (w >= tu0) ++cnt[0];
                     else if (w <= tl0) ++cnt[1];
                     else { ++cnt[2]; sum[0].add(w); }

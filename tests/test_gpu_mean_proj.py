@@ -45,7 +45,8 @@ def test_mean_projected_outer_loop_matches_oracle(case, precision):
         assert np.abs(rho - rho_o).max() <= 1e-10
         for s, h in zip(st, hist):
             assert abs(s["gmax"] - h["gmax"]) <= 1e-10 * max(h["gmax"], 1e-30)
-            assert abs(s["lambda"] - h["lam"]) <= 1e-10 * max(abs(h["lam"]), 1e-12)
+            # lambda shifts w (values of order one): compare it on that scale
+            assert abs(s["lambda"] - h["lam"]) <= 1e-10 * max(abs(h["lam"]), 1.0)
             assert abs(s["volume"] - h["volume"]) <= 1e-10 * h["volume"]
     else:
         assert abs(a0 - a0_o) <= 1e-4 * a0_o
