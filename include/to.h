@@ -141,7 +141,14 @@ typedef struct {
  *               (u_0, u_s, u_2s, ...) plus one segment of s + 1, the reverse sweep
  *               recomputing each segment from its kept iterate (one more forward
  *               pass; (ceil(T / s) + s + 1) n_dof entries);  -1: s = ceil(sqrt(T)).
- *               The gradient is bitwise the same in every mode. */
+ *               The gradient is bitwise the same in every mode.
+ *   op_kernel   0 (default): the operator K^ x runs the general kernel (cp.async
+ *               staging, 31 x 7 node tiles, one element column per thread);
+ *               1: FP32 problems run the TMA-staged kernel (64 x 8 node tiles, element
+ *               pairs in packed FP32x2, persistent CTAs) wherever its vectors are
+ *               16-byte aligned, its copy coordinates fit 32 bits and the grid spans
+ *               its copy boxes, else the general kernel.  FP64 problems and batches
+ *               always use the general kernel.  Both give the same K^ x up to rounding */
 typedef struct {
     int32_t precision, precond, inner_mode, n_inner;
     double beta, alpha0, alpha_scale, m;
@@ -149,7 +156,7 @@ typedef struct {
     double mg_omega;
     int32_t tile_x, tile_y, tile_z, no_graph;
     int32_t krylov_dim, proj_sort;
-    int32_t adj_stride, reserved_;
+    int32_t adj_stride, op_kernel;
 } to_params;
 
 /* Per-outer-iteration record (host copy). */

@@ -155,9 +155,16 @@ static int grid_n(long long n, int num_sms) {
 // Iterate storage.  Stride s = 1: slot j holds u_j (j = 0 .. T).  Stride s > 1:
 // slots 0 .. nck-1 hold the kept iterates u_0, u_s, u_2s, ... (nck = ceil(T / s)),
 // slots nck .. nck+s hold one segment u_ms .. u_ms+s being walked.
+// slots are n_dof entries rounded up to 256 bytes apart, so that every slot is aligned
+// like the problem's other vectors (and takes the same operator kernel)
+template <typename T>
+static size_t slot_ld(const to_problem* P) {
+    const size_t per = 256 / sizeof(T);
+    return ((size_t)P->n_dof + per - 1) / per * per;
+}
 template <typename T>
 static T* slot(to_problem* P, int j) {
-    return (T*)P->iters + (size_t)j * (size_t)P->n_dof;
+    return (T*)P->iters + (size_t)j * slot_ld<T>(P);
 }
 
 static int stride_for(const to_problem* P, int Tn) {
@@ -212,7 +219,7 @@ static int forward_t(to_problem* P, const void* rho, int Tn, double beta, cudaSt
         if (P->iters) cudaFree(P->iters);
         P->iters = nullptr;
         P->iters_cap = 0;
-        TO_CUDA(cudaMalloc(&P->iters, bytes * (size_t)need));
+        TO_CUDA(cudaMalloc(&P->iters, slot_ld<T>(P) * sizeof(T) * (size_t)need));
         P->iters_cap = need;
     }
     TO_CUDA(cudaMemcpyAsync(P->rho, rho, P->n_elem * sizeof(T), cudaMemcpyDeviceToDevice, s));

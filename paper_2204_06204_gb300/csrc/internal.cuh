@@ -82,6 +82,7 @@ struct Level {
     void* dinv = nullptr;     // 1 / diag(K^) (T): the Jacobi scaling, applied by multiplication
     uint8_t* mask = nullptr;  // per node: bit c set = DOF c fixed
     uint8_t* tmask = nullptr; // per operator tile column: any fixed node in its footprint
+    uint8_t* tmask64 = nullptr; // the same for the 64 x kTmaTileY tiles of the TMA operator
     void* x = nullptr;        // V-cycle vectors (T)
     void* b = nullptr;
     void* t = nullptr;
@@ -180,6 +181,8 @@ struct to_problem {
     // launch configuration of the operator kernel; resident CTAs per SM of each mode
     int tile_x = 32, tile_y = 8, tile_z = 8;
     int op_occ[5] = {0, 0, 0, 0, 0};
+    int tma_occ[5] = {0, 0, 0, 0, 0};  // the FP32 TMA operator: resident CTAs per SM of each mode
+    int tma_ready = 0;                 // its shared-memory opt-ins are set
     int num_sms = 0;
     int coop_blocks = 0;           // co-resident blocks for the projection kernel
 };
@@ -213,6 +216,13 @@ int launch_energy(to_problem* P, const void* u, cudaStream_t s);
 int launch_record(to_problem* P, cudaStream_t s);
 int operator_init(to_problem* P);
 int build_tile_mask(Level& L, const uint8_t* mask_host);
+// the FP32 operator with TMA staging (optma.cu): node rows per tile, set-up, applicability
+constexpr int kTmaTileY = 8;
+int operator_tma_init(to_problem* P);
+bool operator_tma_applicable(const to_problem* P, int level, const void* x, const void* y, const void* b);
+int launch_operator_tma(to_problem* P, int level, int mode, const void* x, void* y, const void* b, cudaStream_t s,
+                        double omega, int first, const OpOut* out);
+int build_tile_mask64(Level& L, const uint8_t* mask_host);
 int project_cluster_setup(to_problem* P);
 int krylov_build(to_problem* P);
 int operator_autotune(to_problem* P, cudaStream_t s);

@@ -583,7 +583,9 @@ static int init_t(to_problem* P) {
 
 // shared-memory opt-in and residency of the operator kernels (on the problem's device, before any capture)
 int operator_init(to_problem* P) {
-    return P->prec == TO_FP64 ? init_t<double, 32, 8>(P) : init_t<float, 32, 8>(P);
+    if (P->prec == TO_FP64) return init_t<double, 32, 8>(P);
+    int rc = init_t<float, 32, 8>(P);
+    return rc ? rc : operator_tma_init(P);
 }
 
 // Tile autotuner of a problem's operator: for every multigrid level (or the fine grid
@@ -692,11 +694,12 @@ int build_tile_mask(Level& L, const uint8_t* mask_host) {
     TO_CUDA(cudaMalloc(&d, t.size()));
     TO_CUDA(cudaMemcpy(d, t.data(), t.size(), cudaMemcpyHostToDevice));
     L.tmask = (uint8_t*)d;
-    return TO_OK;
+    return build_tile_mask64(L, mask_host);
 }
 
 int launch_operator(to_problem* P, int level, int mode, const void* x, void* y, const void* b,
                     cudaStream_t s, double omega, int first, const OpOut* out) {
+    if (operator_tma_applicable(P, level, x, y, b)) return launch_operator_tma(P, level, mode, x, y, b, s, omega, first, out);
     if (P->prec == TO_FP64) return launch_t<double, 32, 8>(P, level, mode, x, y, b, s, omega, first, out);
     return launch_t<float, 32, 8>(P, level, mode, x, y, b, s, omega, first, out);
 }

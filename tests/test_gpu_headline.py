@@ -91,8 +91,8 @@ def _golden(name):
     return json.load(open(path))
 
 
-def _check_against_golden(fb, pb, rec, n):
-    prm = fb.to_default_params(precision=fb.TO_FP32_MIXED, precond=fb.TO_PRECOND_MG, n_inner=2)
+def _check_against_golden(fb, pb, rec, n, op_kernel=0):
+    prm = fb.to_default_params(precision=fb.TO_FP32_MIXED, precond=fb.TO_PRECOND_MG, n_inner=2, op_kernel=op_kernel)
     with fb.Problem.from_workload(pb, prm) as P:
         st = P.step(n)
         rho = P.get_state()[0].double().cpu().numpy()
@@ -107,11 +107,14 @@ def _check_against_golden(fb, pb, rec, n):
     return J_gpu
 
 
+@pytest.mark.parametrize("op_kernel", [0, 1])
 @pytest.mark.parametrize("which", ["cantilever", "mbb"])
-def test_mg2_outer_loop_fp32_64x32x32_vs_oracle_trajectory(which):
+def test_mg2_outer_loop_fp32_64x32x32_vs_oracle_trajectory(which, op_kernel):
+    """op_kernel 1: every FP32 operator launch of the run (all modes, levels 0 and 1) on the
+    TMA-staged kernel."""
     fb = _fb()
     rec = _golden(f"{which}_64x32x32_mg2_30.json")
-    _check_against_golden(fb, _workload(which, (64, 32, 32)), rec, 30)
+    _check_against_golden(fb, _workload(which, (64, 32, 32)), rec, 30, op_kernel)
 
 
 def test_mg2_fp32_128x64x64_200_iterations_vs_oracle():
@@ -182,11 +185,11 @@ class _NodeOracle:
         return float(xe @ self.ke @ xe), float(np.abs(xe) @ np.abs(self.ke) @ np.abs(xe))
 
 
-def _full_size_problem(fb):
+def _full_size_problem(fb, op_kernel=0):
     """The benchmark's problem and parameters (multigrid x2, FP32-mixed) with a random design."""
     pb = W.cantilever_128x64x64()
     rho = W.random_rho(pb.n_elem, 0.0, 1.0, seed=W.SEED + 5)
-    prm = fb.to_default_params(precision=fb.TO_FP32_MIXED, precond=fb.TO_PRECOND_MG, n_inner=2)
+    prm = fb.to_default_params(precision=fb.TO_FP32_MIXED, precond=fb.TO_PRECOND_MG, n_inner=2, op_kernel=op_kernel)
     P = fb.Problem.from_workload(pb, prm)
     P.set_design(_t(rho, P))
     H, Hs = filt.filter_matrix(pb.nx, pb.ny, pb.nz, pb.rmin)
@@ -196,9 +199,10 @@ def _full_size_problem(fb):
     return pb, P, Ee, Ed, Hs
 
 
-def test_residual_epilogue_full_size_sampled():
+@pytest.mark.parametrize("op_kernel", [0, 1])
+def test_residual_epilogue_full_size_sampled(op_kernel):
     fb = _fb()
-    pb, P, Ee, Ed, Hs = _full_size_problem(fb)
+    pb, P, Ee, Ed, Hs = _full_size_problem(fb, op_kernel)
     with P:
         u = W.random_u(pb.n_dof, seed=W.SEED + 6)
         r, z, gt = P.dof(), P.dof(), P.elem()
@@ -228,9 +232,10 @@ def test_residual_epilogue_full_size_sampled():
     assert abs(sc["fu"] - fu) <= 1e-5 * float(np.abs(f * u).sum())
 
 
-def test_smoothing_epilogue_full_size_sampled():
+@pytest.mark.parametrize("op_kernel", [0, 1])
+def test_smoothing_epilogue_full_size_sampled(op_kernel):
     fb = _fb()
-    pb, P, Ee, Ed, Hs = _full_size_problem(fb)
+    pb, P, Ee, Ed, Hs = _full_size_problem(fb, op_kernel)
     omega = 0.5
     with P:
         x = W.random_u(pb.n_dof, seed=W.SEED + 9)

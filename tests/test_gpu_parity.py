@@ -35,16 +35,19 @@ def _t(x, P):
 
 
 GRIDS = [(1, 1, 1), (3, 2, 5), (17, 9, 5), (32, 16, 16), (40, 20, 9)]
+# grids for the TMA-staged kernel (op_kernel 1): one and several 64-column tiles, ragged x
+# and y, tiles whose column element lies outside the grid, tiles of 8 node rows and fewer
+TMA_GRIDS = [(17, 9, 5), (32, 16, 16), (40, 20, 9), (64, 8, 8), (65, 9, 3), (100, 23, 6), (130, 10, 4)]
 
 
-@pytest.mark.parametrize("dims", GRIDS)
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_apply_K_matches_assembled_operator(dims, precision):
+@pytest.mark.parametrize("dims,precision,op_kernel",
+                         [(d, p, 0) for d in GRIDS for p in ("fp64", "fp32")] + [(d, "fp32", 1) for d in TMA_GRIDS])
+def test_apply_K_matches_assembled_operator(dims, precision, op_kernel):
     fb = _fb()
     pb = W.cantilever(*dims)
     pb.rho0 = W.random_rho(pb.n_elem, 0.0, 1.0)
     prec = fb.TO_FP64 if precision == "fp64" else fb.TO_FP32_MIXED
-    with _problem(pb, prec) as P:
+    with _problem(pb, prec, op_kernel=op_kernel) as P:
         P.set_design(_t(pb.rho0, P))
         S = outer.Setup(pb)
         _, Ee_ref, _ = S.moduli(pb.rho0)
@@ -187,11 +190,12 @@ def test_outer_loop_fp64_matches_oracle_cantilever_32x16x16():
         assert abs(s["res_inf"] - h["res_inf"]) <= 1e-8 * max(h["res_inf"], 1e-30)
 
 
-def test_outer_loop_fp32_mixed_matches_oracle_compliance():
+@pytest.mark.parametrize("op_kernel", [0, 1])
+def test_outer_loop_fp32_mixed_matches_oracle_compliance(op_kernel):
     fb = _fb()
     pb = W.cantilever_32x16x16()
     n = 50
-    with _problem(pb, fb.TO_FP32_MIXED, n_inner=5) as P:
+    with _problem(pb, fb.TO_FP32_MIXED, n_inner=5, op_kernel=op_kernel) as P:
         P.step(n)
         rho, u, k, a0 = P.get_state()
     rho_o, u_o, hist, a0_o = outer.run(pb, n, precond="jacobi", n_inner=5)
