@@ -306,6 +306,7 @@ int iteration_t(to_batch* B, cudaStream_t s) {
         TO_CUDA(cudaGetLastError());
         if (B->mg && it + 1 < B->n_inner && (rc = batch_mg_vcycle(B->mg, s))) return rc;
     }
+    if (B->mg && (rc = batch_mg_join(B->mg, s))) return rc;   // the refresh branch, if no tail joined it
     if ((rc = filter_batch_launch(B->prec, 1, B->ftab[1], B->ftiles[1], B->n, B->fsmem[1], s))) return rc;
     if ((rc = launch_cluster_project<T>(tab, B->n, kClusterCTAs, 256, B->proj_cache, B->proj_smem, s))) return rc;
     k_b_record<T><<<(B->n + 63) / 64, 64, 0, s>>>(tab, B->n, 0);

@@ -246,6 +246,7 @@ struct BatchMG;
 int batch_mg_build(to_problem* const* probs, int n, int kchunk, BatchMG** out);
 int batch_mg_refresh(const BatchMG* M, cudaStream_t s);
 int batch_mg_vcycle(const BatchMG* M, cudaStream_t s);
+int batch_mg_join(const BatchMG* M, cudaStream_t s);
 int batch_mg_launches(const BatchMG* M, int* refresh, int* vcycle);
 void batch_mg_free(BatchMG* M);
 

@@ -370,6 +370,118 @@ __global__ void __launch_bounds__(256) k_gj_final(const GjArgs<T>* __restrict__ 
         a.inv[q] = a.W[(size_t)(q / n) * N + q % n];
 }
 
+// The same block steps for a batch, over compact tile maps: the problems are ordered
+// by block count (largest first) so that step k's pivots are the first m_k of them,
+// and each step's block-row and rank-32-update tiles are listed as (problem, tile)
+// pairs, so that no CTA is launched for a problem that has no block left.
+template <typename T>
+__global__ void __launch_bounds__(256) k_gj_row_map(const GjArgs<T>* __restrict__ tab, const int2* __restrict__ map,
+                                                    int k) {
+    const int2 m = map[blockIdx.x];
+    const GjArgs<T>& a = tab[m.x];
+    const int r = m.y;
+    __shared__ T Ps[kGjB][kGjB + 1], Rs[kGjB][kGjB + 1];
+    const int tx = threadIdx.x, ty = threadIdx.y, N = a.nb * kGjB;
+    T* Wkr = a.W + (size_t)(k * kGjB) * N + r * kGjB;
+#pragma unroll
+    for (int mm = 0; mm < kGjRows; ++mm) {
+        const int y = ty + 8 * mm;
+        Ps[y][tx] = a.P[y * kGjB + tx];
+        Rs[y][tx] = Wkr[(size_t)y * N + tx];
+        a.C[(size_t)(r * kGjB + y) * kGjB + tx] = a.W[(size_t)(r * kGjB + y) * N + k * kGjB + tx];   // block (r, k)
+    }
+    __syncthreads();
+    T acc[kGjRows];
+#pragma unroll
+    for (int mm = 0; mm < kGjRows; ++mm) acc[mm] = T(0);
+#pragma unroll 8
+    for (int t = 0; t < kGjB; ++t) {
+        const T b = Rs[t][tx];
+#pragma unroll
+        for (int mm = 0; mm < kGjRows; ++mm) acc[mm] = fma(Ps[ty + 8 * mm][t], b, acc[mm]);
+    }
+#pragma unroll
+    for (int mm = 0; mm < kGjRows; ++mm) Wkr[(size_t)(ty + 8 * mm) * N + tx] = acc[mm];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_gj_update_map(const GjArgs<T>* __restrict__ tab, const int2* __restrict__ map,
+                                                       int k) {
+    const int2 m = map[blockIdx.x];
+    const GjArgs<T>& a = tab[m.x];
+    const int i = m.y >> 16, j = m.y & 0xffff;
+    __shared__ T Cs[kGjB][kGjB + 1], Bs[kGjB][kGjB + 1];
+    const int tx = threadIdx.x, ty = threadIdx.y, N = a.nb * kGjB;
+#pragma unroll
+    for (int mm = 0; mm < kGjRows; ++mm) {
+        const int y = ty + 8 * mm;
+        Cs[y][tx] = a.C[(size_t)(i * kGjB + y) * kGjB + tx];
+        Bs[y][tx] = j == k ? a.P[y * kGjB + tx] : a.W[(size_t)(k * kGjB + y) * N + j * kGjB + tx];
+    }
+    __syncthreads();
+    T acc[kGjRows];
+#pragma unroll
+    for (int mm = 0; mm < kGjRows; ++mm) acc[mm] = T(0);
+#pragma unroll 8
+    for (int t = 0; t < kGjB; ++t) {
+        const T b = Bs[t][tx];
+#pragma unroll
+        for (int mm = 0; mm < kGjRows; ++mm) acc[mm] = fma(Cs[ty + 8 * mm][t], b, acc[mm]);
+    }
+#pragma unroll
+    for (int mm = 0; mm < kGjRows; ++mm) {
+        T* w = a.W + (size_t)(i * kGjB + ty + 8 * mm) * N + j * kGjB + tx;
+        *w = j == k ? -acc[mm] : *w - acc[mm];
+    }
+}
+
+// per block step k: pivots over the first piv[k] problems, rows map[row_off[k] ..] (row_n[k]
+// entries), updates map[upd_off[k] ..] (upd_n[k] entries)
+struct GjMaps {
+    const int2* map = nullptr;
+    std::vector<int> piv, row_off, row_n, upd_off, upd_n;
+};
+
+// tile maps for problems sorted by block count (descending); returns the host map
+static std::vector<int2> gj_build_maps(const std::vector<int>& nbs, GjMaps& g) {
+    std::vector<int2> h;
+    const int nbmax = nbs.empty() ? 0 : nbs[0];
+    for (int k = 0; k < nbmax; ++k) {
+        int m = 0;
+        while (m < (int)nbs.size() && nbs[m] > k) ++m;
+        g.piv.push_back(m);
+        g.row_off.push_back((int)h.size());
+        for (int p = 0; p < m; ++p)
+            for (int r = 0; r < nbs[p]; ++r)
+                if (r != k) h.push_back(make_int2(p, r));
+        g.row_n.push_back((int)h.size() - g.row_off.back());
+        g.upd_off.push_back((int)h.size());
+        for (int p = 0; p < m; ++p)
+            for (int i = 0; i < nbs[p]; ++i)
+                if (i != k)
+                    for (int j = 0; j < nbs[p]; ++j) h.push_back(make_int2(p, (i << 16) | j));
+        g.upd_n.push_back((int)h.size() - g.upd_off.back());
+    }
+    return h;
+}
+
+template <typename T>
+static int gj_launch_maps(const void* tab, int nprob, const GjMaps& g, int num_sms, cudaStream_t s) {
+    const GjArgs<T>* t = (const GjArgs<T>*)tab;
+    const int nbmax = (int)g.piv.size();
+    const long long NN = (long long)nbmax * kGjB * nbmax * kGjB;
+    const int gx = (int)std::max<long long>(1, std::min<long long>((NN + 255) / 256, (8LL * num_sms + nprob - 1) / nprob));
+    k_gj_init<T><<<dim3(gx, nprob), 256, 0, s>>>(t);
+    for (int k = 0; k < nbmax; ++k) {
+        k_gj_pivot<T><<<g.piv[k], dim3(kGjB, kGjB), 0, s>>>(t, k);
+        if (g.row_n[k] > 0) k_gj_row_map<T><<<g.row_n[k], dim3(kGjB, 8), 0, s>>>(t, g.map + g.row_off[k], k);
+        if (g.upd_n[k] > 0) k_gj_update_map<T><<<g.upd_n[k], dim3(kGjB, 8), 0, s>>>(t, g.map + g.upd_off[k], k);
+    }
+    k_gj_final<T><<<dim3(gx, nprob), 256, 0, s>>>(t);
+    TO_CUDA(cudaGetLastError());
+    return TO_OK;
+}
+
 // the blocked inversion of nprob problems' coarsest operators (largest nbmax blocks)
 template <typename T>
 static int gj_launch(const void* tab, int nprob, int nbmax, int num_sms, cudaStream_t s) {
@@ -1113,12 +1225,18 @@ struct BmOp {
     void* tab = nullptr;        // device table
     const void* kh = nullptr;   // host element constants (operator and tail launches)
     size_t smem = 0;
+    GjMaps gj;                  // BM_INVERT_GJ: the compact tile maps of its block steps
 };
 
 struct BatchMG {
     int prec = TO_FP32_MIXED, n = 0, num_sms = 1;
     std::vector<BmOp> refresh, vcycle;
     std::vector<void*> dev, host;
+    // the coarsest operators' assembly and inversion run on a forked branch that the first
+    // coarse tail joins, overlapping the fine-level work before it
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    mutable bool join_pending = false;
 };
 
 static int grid_x_for(long long items, int num_sms, int n) {
@@ -1361,6 +1479,14 @@ static int batch_mg_build_t(to_problem* const* probs, int n, int kchunk, BatchMG
             g.kind = BM_INVERT_GJ;
             g.n = (int)hg.size();
             g.max_tiles = nbmax;
+            // largest first, so that every block step's pivots are a prefix of the table
+            std::stable_sort(hg.begin(), hg.end(), [](const GjArgs<T>& x, const GjArgs<T>& y) { return x.nb > y.nb; });
+            std::vector<int> nbs;
+            for (const GjArgs<T>& x : hg) nbs.push_back(x.nb);
+            const std::vector<int2> hm = gj_build_maps(nbs, g.gj);
+            void* dm = nullptr;
+            if ((rc = upload_table(M, hm, &dm))) return rc;
+            g.gj.map = (const int2*)dm;
             if ((rc = upload_table(M, hg, &g.tab))) return rc;
             M->refresh.push_back(g);
         }
@@ -1370,9 +1496,20 @@ static int batch_mg_build_t(to_problem* const* probs, int n, int kchunk, BatchMG
 }
 
 template <typename T>
-static int batch_mg_run(const BatchMG* M, const std::vector<BmOp>& ops, cudaStream_t s) {
+static int batch_mg_run(const BatchMG* M, const std::vector<BmOp>& ops, cudaStream_t s_main, bool fork = false) {
+    cudaStream_t s = s_main;
     for (const BmOp& op : ops) {
         const dim3 g2(op.grid_x, op.n);
+        const bool dense = op.kind == BM_ASSEMBLE || op.kind == BM_INVERT_REG || op.kind == BM_INVERT_GJ;
+        if (fork && dense && s == s_main) {   // the rest of the refresh on the side branch
+            TO_CUDA(cudaEventRecord(M->ev_fork, s_main));
+            TO_CUDA(cudaStreamWaitEvent(M->side, M->ev_fork, 0));
+            s = M->side;
+        }
+        if (op.kind == BM_TAIL && M->join_pending) {   // the coarse solves need the inverses
+            TO_CUDA(cudaStreamWaitEvent(s, M->ev_join, 0));
+            M->join_pending = false;
+        }
         switch (op.kind) {
             case BM_JAC: k_bm_jacobi_first<T><<<g2, 256, 0, s>>>((const BmJac<T>*)op.tab); break;
             case BM_OPER: {
@@ -1390,20 +1527,28 @@ static int batch_mg_run(const BatchMG* M, const std::vector<BmOp>& ops, cudaStre
             case BM_ASSEMBLE: k_bm_assemble<T><<<g2, 256, 0, s>>>((const BmDense<T>*)op.tab); break;
             case BM_INVERT_REG: k_bm_invert_reg<T><<<op.n, dim3(32, 32), 0, s>>>((const BmDense<T>*)op.tab); break;
             default: {
-                const int rc = gj_launch<T>(op.tab, op.n, op.max_tiles, M->num_sms, s);
+                const int rc = gj_launch_maps<T>(op.tab, op.n, op.gj, M->num_sms, s);
                 if (rc) return rc;
                 break;
             }
         }
         TO_CUDA(cudaGetLastError());
     }
+    if (s != s_main) {
+        TO_CUDA(cudaEventRecord(M->ev_join, s));
+        M->join_pending = true;
+    }
     return TO_OK;
 }
 
 void batch_mg_free(BatchMG* M) {
     if (!M) return;
+    if (M->side) cudaStreamSynchronize(M->side);
     for (void* d : M->dev) cudaFree(d);
     for (void* h : M->host) free(h);
+    if (M->ev_fork) cudaEventDestroy(M->ev_fork);
+    if (M->ev_join) cudaEventDestroy(M->ev_join);
+    if (M->side) cudaStreamDestroy(M->side);
     delete M;
 }
 
@@ -1418,6 +1563,12 @@ int batch_mg_build(to_problem* const* probs, int n, int kchunk, BatchMG** out) {
     M->prec = probs[0]->prec;
     M->n = n;
     M->num_sms = probs[0]->num_sms;
+    if (cudaStreamCreateWithFlags(&M->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&M->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&M->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        batch_mg_free(M);
+        return fail(TO_ERR_CUDA, "batched multigrid stream / events");
+    }
     const int rc = M->prec == TO_FP64 ? batch_mg_build_t<double>(probs, n, kchunk, M) : batch_mg_build_t<float>(probs, n, kchunk, M);
     if (rc) {
         batch_mg_free(M);
@@ -1428,7 +1579,16 @@ int batch_mg_build(to_problem* const* probs, int n, int kchunk, BatchMG** out) {
 }
 
 int batch_mg_refresh(const BatchMG* M, cudaStream_t s) {
-    return M->prec == TO_FP64 ? batch_mg_run<double>(M, M->refresh, s) : batch_mg_run<float>(M, M->refresh, s);
+    return M->prec == TO_FP64 ? batch_mg_run<double>(M, M->refresh, s, true) : batch_mg_run<float>(M, M->refresh, s, true);
+}
+
+// make s wait for a refresh branch that no coarse tail has joined yet
+int batch_mg_join(const BatchMG* M, cudaStream_t s) {
+    if (M->join_pending) {
+        TO_CUDA(cudaStreamWaitEvent(s, M->ev_join, 0));
+        M->join_pending = false;
+    }
+    return TO_OK;
 }
 
 int batch_mg_vcycle(const BatchMG* M, cudaStream_t s) {
