@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--fp64", action="store_true", help="with --apply-only: the plain FP64 operator")
     ap.add_argument("--op-kernel", type=int, default=0, choices=[0, 1],
                     help="operator kernel: 0 the general kernel (default), 1 the TMA-staged FP32 kernel")
+    ap.add_argument("--mg-legs", type=int, default=0, choices=[0, 1],
+                    help="multigrid levels below the fine grid: 0 one launch per step, 1 two cooperative launches per V-cycle")
     ap.add_argument("--oracle-worker", nargs=3, metavar=("WARM", "ITERS", "BUDGET_S"), help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -318,7 +320,8 @@ def main():
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     def make(precision):
-        prm = fb.to_default_params(precision=precision, precond=precond, n_inner=n_inner)
+        prm = fb.to_default_params(precision=precision, precond=precond, n_inner=n_inner, op_kernel=args.op_kernel,
+                                   mg_legs=args.mg_legs)
         return fb.Problem.from_workload(pb, prm, device=local)
 
     def time_steps(P, K, W_):

@@ -148,7 +148,13 @@ typedef struct {
  *               pairs in packed FP32x2, persistent CTAs) wherever its vectors are
  *               16-byte aligned, its copy coordinates fit 32 bits and the grid spans
  *               its copy boxes, else the general kernel.  FP64 problems and batches
- *               always use the general kernel.  Both give the same K^ x up to rounding */
+ *               always use the general kernel.  Both give the same K^ x up to rounding
+ *   mg_legs     0 (default): the multigrid levels between the fine grid and the one-CTA
+ *               coarse tail run one launch per step; 1: as two cooperative launches per
+ *               V-cycle (the down leg's smoothing, residuals and restrictions, the up leg's
+ *               prolongations and smoothing), separated inside by bounded grid barriers
+ *               (general operator kernel only).  The same steps, buffers and order: bitwise
+ *               the same results */
 typedef struct {
     int32_t precision, precond, inner_mode, n_inner;
     double beta, alpha0, alpha_scale, m;
@@ -157,6 +163,7 @@ typedef struct {
     int32_t tile_x, tile_y, tile_z, no_graph;
     int32_t krylov_dim, proj_sort;
     int32_t adj_stride, op_kernel;
+    int32_t mg_legs, reserved_;
 } to_params;
 
 /* Per-outer-iteration record (host copy). */

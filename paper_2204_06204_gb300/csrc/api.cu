@@ -77,6 +77,7 @@ extern "C" void to_default_params(to_params* o) {
     o->mg_nu_post = 2;
     o->mg_omega = 0.5;
     o->krylov_dim = 20;
+    o->mg_legs = 0;
     o->tile_z = -1;   // the cost model: measured per level, the autotuner's isolated timings lost in the graph
 }
 
@@ -116,7 +117,8 @@ extern "C" void to_destroy(to_problem* P) {
     if (!P) return;
     DeviceGuard dg(P->device);
     void** bufs[] = {&P->rho, &P->rhot, &P->Ed, &P->Hs, &P->gt, &P->grad, &P->tmp_e, &P->stencil_w,
-                     &P->u, &P->f, &P->r, &P->z, &P->q, &P->tmp_v, &P->coarse_A, &P->coarse_L, &P->iters, &P->gj_work, &P->gj_tab};
+                     &P->u, &P->f, &P->r, &P->z, &P->q, &P->tmp_v, &P->coarse_A, &P->coarse_L, &P->iters, &P->gj_work, &P->gj_tab,
+                     &P->legs_prog};
     for (void** b : bufs) dfree(*b);
     void* st = P->stencil;
     dfree(st);
@@ -314,7 +316,7 @@ extern "C" int to_create(const to_grid* g, const to_material* m, const to_loads*
         return bail(rc);
     }
     if ((rc = launch_moduli(P, s)) || (rc = refresh_preconditioner(P, s)) ||
-        (prm->tile_z == 0 && (rc = operator_autotune(P, s)))) {
+        (prm->tile_z == 0 && (rc = operator_autotune(P, s))) || (rc = mg_legs_build(P))) {
         cudaStreamDestroy(s);
         return bail(rc);
     }

@@ -135,6 +135,9 @@ struct to_problem {
     void* gj_work = nullptr;       // blocked coarsest inversion (n_coarse > 160): work matrix, block column, pivot
     void* gj_tab = nullptr;        // its one-entry argument table
     int mg_tail = 0;               // first level of the one-CTA coarse tail (0: none)
+    void* legs_prog = nullptr;     // the V-cycle's persistent legs over levels 1 .. tail - 1 (device steps)
+    int legs_n[2] = {0, 0};        // steps of the down and up legs
+    int legs_grid = 0;             // co-resident CTAs of their cooperative launches (0: not used)
     int precond_stale = 0;         // the design changed outside to_step: refresh before the next lower-level solve
 
     // Krylov preconditioner (Eq. LSP): basis of D + 2 columns (leading dimension kry_ld),
@@ -237,6 +240,8 @@ int mg_build(to_problem* P);
 // at once, else the first coarse solve on s does)
 int mg_refresh(to_problem* P, cudaStream_t s, bool join = true);
 int mg_vcycle(to_problem* P, const void* r, void* z, cudaStream_t s);
+int mg_legs_build(to_problem* P);
+int mg_legs_launch(to_problem* P, int leg, void* fine, cudaStream_t s);
 
 int outer_iteration(to_problem* P, cudaStream_t s);
 int inner_steps(to_problem* P, int nsteps, int from_resid, cudaStream_t s);

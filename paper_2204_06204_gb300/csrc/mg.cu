@@ -1048,6 +1048,19 @@ static int vcycle_t(to_problem* P, int l, const void* b, void* x, void* t, cudaS
     }
     // residual into oth, restrict to the coarse right-hand side
     if ((rc = launch_operator(P, l, OP_BMINUS, cur, oth, b, s))) return rc;
+    if (l == 0 && P->legs_grid > 0) {
+        // levels 1 .. tail - 1 as two cooperative launches around the coarse tail
+        if ((rc = mg_legs_launch(P, 0, oth, s))) return rc;
+        if ((rc = tail_t<T>(P, s))) return rc;
+        if ((rc = mg_legs_launch(P, 1, cur, s))) return rc;
+        for (int it = 0; it < nu2; ++it) {
+            const int flag = it == nu2 - 1 ? 2 : 0;   // r^T z of the lower-level step
+            if ((rc = launch_operator(P, l, OP_SMOOTH, cur, oth, b, s, om, flag))) return rc;
+            std::swap(cur, oth);
+        }
+        if (cur != x) return fail(TO_ERR_STATE, "V-cycle buffer parity");
+        return TO_OK;
+    }
     const Level& C = P->lv[l + 1];
     // above the coarsest level the restriction also takes the coarse level's first sweep
     const bool fuse = l + 1 < L - 1;

@@ -25,6 +25,7 @@
 
 #include "device.cuh"
 #include "haar.cuh"
+#include "transfer.cuh"
 
 namespace to {
 
@@ -563,6 +564,240 @@ static int launch_t(to_problem* P, int level, int mode, const void* x, void* y, 
         default: return fail(TO_ERR_ARG, "bad operator mode");
     }
     TO_CUDA(cudaGetLastError());
+    return TO_OK;
+}
+
+// ----------------------------------------------------------------------------- persistent multigrid legs
+// The multigrid levels between the fine grid and the one-CTA coarse tail, run as one
+// cooperative launch per leg of the V-cycle instead of one launch per step: the down
+// leg (the restriction from the fine level, then on every level its pre-smoothing
+// sweeps, b - K x and the restriction to the next level) and the up leg (on every level
+// the prolongation from the level below and the post-smoothing sweeps, then the
+// prolongation to the fine level).  Steps are the same bodies, buffers and order as the
+// launch-per-step V-cycle (so the results are bitwise the same); a bounded grid barrier
+// separates them.  The fine level's residual (down) and correction target (up) are the
+// only pointers that vary between calls: they are kernel arguments.
+enum LegKind { LEG_OPER = 0, LEG_RESTRICT = 1, LEG_PROLONG = 2 };
+
+template <typename T>
+struct LegStep {
+    int kind, mode;                 // LEG_*; OP_SMOOTH / OP_BMINUS for LEG_OPER
+    int gx, gy, gz;                 // operator tiles
+    OpArgs<T> op;
+    int cx, cy, cz;                 // transfers: the coarse grid
+    const T* src;                   // restriction: fine residual (nullptr: the launch's fine pointer);
+                                    // prolongation: coarse correction
+    const uint8_t* mf;
+    const uint8_t* mc;
+    T* dst;                         // restriction: coarse right-hand side; prolongation: fine target
+                                    // (nullptr: the launch's fine pointer)
+    const T* dc;                    // restriction: coarse 1 / d
+    T* xc;                          // restriction: the coarse first sweep (nullptr: none)
+    T omega;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_mg_legs(const LegStep<T>* __restrict__ steps, int nsteps, const T* fine_src,
+                                                 T* fine_dst, unsigned* bar, int* err) {
+    const int tid = threadIdx.x + 32 * threadIdx.y;
+    __shared__ OpArgs<T> s_op;   // the current operator step's arguments, read by every thread
+    for (int q = 0; q < nsteps; ++q) {
+        const LegStep<T>& st = steps[q];
+        if (st.kind == LEG_OPER) {
+            {   // word by word: no local copy of the step
+                const unsigned* src = reinterpret_cast<const unsigned*>(&st.op);
+                unsigned* dst = reinterpret_cast<unsigned*>(&s_op);
+                for (int w = tid; w < (int)(sizeof(OpArgs<T>) / 4); w += 256) dst[w] = src[w];
+            }
+            __syncthreads();
+            const int nt = st.gx * st.gy * st.gz;
+            for (int t = blockIdx.x; t < nt; t += gridDim.x) {
+                const int bx = t % st.gx, by = (t / st.gx) % st.gy, bz = t / (st.gx * st.gy);
+                if (st.mode == OP_SMOOTH) op_body<T, 32, 8, OP_SMOOTH>(s_op, s_op.kh, bx, by, bz, (unsigned)t, (unsigned)nt);
+                else op_body<T, 32, 8, OP_BMINUS>(s_op, s_op.kh, bx, by, bz, (unsigned)t, (unsigned)nt);
+                __syncthreads();   // the next tile reuses the shared-memory ring
+            }
+        } else if (st.kind == LEG_RESTRICT) {
+            const T* tf = st.src ? st.src : fine_src;
+            const int nxc = st.cx + 1, nyc = st.cy + 1;
+            const long long n = (long long)nxc * nyc * (st.cz + 1);
+            for (long long i = blockIdx.x * 256LL + tid; i < n; i += (long long)gridDim.x * 256) {
+                const int I = (int)(i % nxc), J = (int)((i / nxc) % nyc), K = (int)(i / ((long long)nxc * nyc));
+                restrict_node<T, int, true>(st.cx, st.cy, st.cz, I, J, K, tf, st.mf, st.mc, st.dst, st.dc, st.xc, st.omega);
+            }
+        } else {
+            T* xf = st.dst ? st.dst : fine_dst;
+            const int nxf = 2 * st.cx + 1, nyf = 2 * st.cy + 1;
+            const long long n = (long long)nxf * nyf * (2 * st.cz + 1);
+            for (long long i = blockIdx.x * 256LL + tid; i < n; i += (long long)gridDim.x * 256) {
+                const int x = (int)(i % nxf), y = (int)((i / nxf) % nyf), z = (int)(i / ((long long)nxf * nyf));
+                prolong_node<T, int>(st.cx, st.cy, st.cz, x, y, z, st.src, st.mc, st.mf, xf);
+            }
+        }
+        if (q + 1 < nsteps && !grid_barrier(bar, err)) return;
+    }
+}
+
+// the operator arguments and tile grid of one launch on level `level` (as launch_t)
+template <typename T>
+static int level_op_args(to_problem* P, int level, int mode, const void* x, void* y, const void* b, double omega,
+                         OpArgs<T>& a, int& gx, int& gy, int& gz) {
+    constexpr int TX = 32, TY = 8;
+    const Level& L = P->lv[level];
+    a = OpArgs<T>{};
+    a.nx = L.nx;
+    a.ny = L.ny;
+    a.nz = L.nz;
+    a.x = (const T*)x;
+    a.y = (T*)y;
+    a.b = (const T*)b;
+    a.dinv = (const T*)L.dinv;
+    a.E = (const T*)L.E;
+    a.mask = L.mask;
+    a.tmask = L.tmask;
+    fill_haar<T>(P, L.h / P->g.h, a.kh);
+    a.omega = (T)omega;
+    a.red = P->red;
+    a.sc = P->sc;
+    a.first_step = 0;
+    a.counter = P->counters + 6;
+    gx = (L.nx + 1 + TX - 2) / (TX - 1);
+    gy = (L.ny + 1 + TY - 2) / (TY - 1);
+    int kchunk = P->tile_z > 0 ? P->tile_z : L.kchunk;
+    if (kchunk <= 0) kchunk = choose_kchunk((long long)gx * gy, L.nz + 1, (long long)P->op_occ[mode] * P->num_sms);
+    if (kchunk > L.nz + 1) kchunk = L.nz + 1;
+    a.kchunk = kchunk;
+    gz = (L.nz + 1 + kchunk - 1) / kchunk;
+    return TO_OK;
+}
+
+// the two leg programs of the V-cycle's levels 1 .. tail - 1, in the order and with the
+// buffers of the launch-per-step V-cycle (first sweeps fused into the restrictions)
+template <typename T>
+static int legs_build_t(to_problem* P) {
+    const int L = (int)P->lv.size();
+    const int tail = P->mg_tail;
+    const int nu1 = P->prm.mg_nu_pre, nu2 = P->prm.mg_nu_post;
+    const double om = P->prm.mg_omega;
+    const bool odd = (nu1 - 1 + nu2) % 2 != 0;   // the first sweep's target: t if odd, else x
+    std::vector<LegStep<T>> down, up;
+    std::vector<void*> cur(L, nullptr), oth(L, nullptr);
+    auto restrict_step = [&](int l, const void* src) {   // level l -> l + 1
+        const Level& F = P->lv[l];
+        const Level& C = P->lv[l + 1];
+        LegStep<T> st{};
+        st.kind = LEG_RESTRICT;
+        st.cx = C.nx;
+        st.cy = C.ny;
+        st.cz = C.nz;
+        st.src = (const T*)src;
+        st.mf = F.mask;
+        st.mc = C.mask;
+        st.dst = (T*)C.b;
+        st.dc = (const T*)C.dinv;
+        st.xc = (l + 1 < L - 1) ? (T*)(odd ? C.t : C.x) : nullptr;
+        st.omega = (T)om;
+        down.push_back(st);
+    };
+    auto oper_step = [&](std::vector<LegStep<T>>& prog, int l, int mode, void* x, void* y) {
+        LegStep<T> st{};
+        st.kind = LEG_OPER;
+        st.mode = mode;
+        int rc = level_op_args<T>(P, l, mode, x, y, P->lv[l].b, om, st.op, st.gx, st.gy, st.gz);
+        prog.push_back(st);
+        return rc;
+    };
+    restrict_step(0, nullptr);
+    for (int l = 1; l < tail; ++l) {
+        const Level& F = P->lv[l];
+        cur[l] = odd ? F.t : F.x;
+        oth[l] = cur[l] == F.t ? F.x : F.t;
+        for (int it = 1; it < nu1; ++it) {
+            if (int rc = oper_step(down, l, OP_SMOOTH, cur[l], oth[l])) return rc;
+            std::swap(cur[l], oth[l]);
+        }
+        if (int rc = oper_step(down, l, OP_BMINUS, cur[l], oth[l])) return rc;
+        restrict_step(l, oth[l]);
+    }
+    for (int l = tail - 1; l >= 1; --l) {
+        const Level& F = P->lv[l];
+        const Level& C = P->lv[l + 1];
+        LegStep<T> pr{};
+        pr.kind = LEG_PROLONG;
+        pr.cx = C.nx;
+        pr.cy = C.ny;
+        pr.cz = C.nz;
+        pr.src = (const T*)C.x;
+        pr.mc = C.mask;
+        pr.mf = F.mask;
+        pr.dst = (T*)cur[l];
+        up.push_back(pr);
+        for (int it = 0; it < nu2; ++it) {
+            if (int rc = oper_step(up, l, OP_SMOOTH, cur[l], oth[l])) return rc;
+            std::swap(cur[l], oth[l]);
+        }
+        if (cur[l] != F.x) return fail(TO_ERR_STATE, "multigrid legs: buffer parity");
+    }
+    {
+        const Level& C = P->lv[1];
+        LegStep<T> pr{};
+        pr.kind = LEG_PROLONG;
+        pr.cx = C.nx;
+        pr.cy = C.ny;
+        pr.cz = C.nz;
+        pr.src = (const T*)C.x;
+        pr.mc = C.mask;
+        pr.mf = P->lv[0].mask;
+        pr.dst = nullptr;
+        up.push_back(pr);
+    }
+    int maxt = 1;
+    for (const auto* prog : {&down, &up})
+        for (const LegStep<T>& st : *prog)
+            if (st.kind == LEG_OPER) maxt = std::max(maxt, st.gx * st.gy * st.gz);
+    const size_t bytes = sizeof(LegStep<T>) * (down.size() + up.size());
+    void* d = nullptr;
+    TO_CUDA(cudaMalloc(&d, bytes));
+    TO_CUDA(cudaMemcpy(d, down.data(), sizeof(LegStep<T>) * down.size(), cudaMemcpyHostToDevice));
+    TO_CUDA(cudaMemcpy(static_cast<char*>(d) + sizeof(LegStep<T>) * down.size(), up.data(),
+                       sizeof(LegStep<T>) * up.size(), cudaMemcpyHostToDevice));
+    P->legs_prog = d;
+    P->legs_n[0] = (int)down.size();
+    P->legs_n[1] = (int)up.size();
+    // co-resident CTAs: the operator's residency (it bounds the shared memory) on every SM
+    const size_t smem = sizeof(OpSmem<T, 32, 8, kRing>);
+    TO_CUDA(cudaFuncSetAttribute(k_mg_legs<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int occ = 0;
+    TO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_mg_legs<T>, 256, smem));
+    if (occ < 1) return TO_OK;   // no cooperative residency: the launch-per-step V-cycle stays
+    P->legs_grid = std::min(maxt, occ * P->num_sms);
+    return TO_OK;
+}
+
+int mg_legs_build(to_problem* P) {
+    P->legs_grid = 0;
+    if (P->prm.precond != TO_PRECOND_MG || P->prm.mg_legs == 0 || P->prm.op_kernel == 1 || P->mg_tail < 2) return TO_OK;
+    return P->prec == TO_FP64 ? legs_build_t<double>(P) : legs_build_t<float>(P);
+}
+
+// one leg: 0 down (fine residual `fine` restricted), 1 up (the correction added into `fine`)
+int mg_legs_launch(to_problem* P, int leg, void* fine, cudaStream_t s) {
+    const size_t stride = P->prec == TO_FP64 ? sizeof(LegStep<double>) : sizeof(LegStep<float>);
+    const void* steps = static_cast<const char*>(P->legs_prog) + (leg ? stride * P->legs_n[0] : 0);
+    int n = P->legs_n[leg];
+    unsigned* bar = P->counters + 20;
+    int* err = &P->sc->err;
+    const void* fsrc = leg ? nullptr : fine;
+    void* fdst = leg ? fine : nullptr;
+    void* args[] = {(void*)&steps, (void*)&n, (void*)&fsrc, (void*)&fdst, (void*)&bar, (void*)&err};
+    const dim3 block(32, 8);
+    if (P->prec == TO_FP64) {
+        TO_CUDA(cudaLaunchCooperativeKernel((const void*)k_mg_legs<double>, dim3(P->legs_grid), block, args,
+                                            sizeof(OpSmem<double, 32, 8, kRing>), s));
+    } else {
+        TO_CUDA(cudaLaunchCooperativeKernel((const void*)k_mg_legs<float>, dim3(P->legs_grid), block, args,
+                                            sizeof(OpSmem<float, 32, 8, kRing>), s));
+    }
     return TO_OK;
 }
 

@@ -124,3 +124,22 @@ def test_mg_problems_with_different_tail_sizes_coexist():
     finally:
         big.close()
         small.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("which,dims", [("cantilever", (128, 64, 64)), ("cantilever", (64, 32, 32)), ("mbb", (64, 32, 48))])
+def test_persistent_legs_are_bitwise_the_launch_per_step_v_cycle(which, dims, precision):
+    """The cooperative down / up legs over levels 1 .. tail - 1 run the same steps on the same
+    buffers in the same order as one launch per step: the outer iterations agree bit for bit."""
+    fb = _fb()
+    pb = W.cantilever(*dims) if which == "cantilever" else W.mbb_half(*dims)
+    prec = fb.TO_FP64 if precision == "fp64" else fb.TO_FP32_MIXED
+    out = {}
+    for legs in (0, 1):
+        prm = fb.to_default_params(precision=prec, precond=fb.TO_PRECOND_MG, n_inner=2, mg_legs=legs)
+        with fb.Problem.from_workload(pb, prm) as P:
+            st = P.step(4)
+            rho, u, k, a0 = P.get_state()
+            out[legs] = (rho.cpu(), u.cpu(), [s["J"] for s in st], [s["beta_first"] for s in st])
+    assert torch.equal(out[0][0], out[1][0]) and torch.equal(out[0][1], out[1][1])
+    assert out[0][2] == out[1][2] and out[0][3] == out[1][3]
