@@ -45,3 +45,26 @@ def filter_forward(H, Hs, x: np.ndarray) -> np.ndarray:
 
 def filter_transpose(H, Hs, g: np.ndarray) -> np.ndarray:
     return H.T @ (g / Hs)
+
+
+def filter_forward_at(nx: int, ny: int, nz: int, rmin: float, x: np.ndarray, elements) -> np.ndarray:
+    """rho~_e = sum_i H_ei x_i / Hs_e at the listed elements only, by the same cone
+    and in-domain rule as ``filter_matrix`` written as a plain loop over each
+    element's neighbours (for grids whose full H does not fit in memory)."""
+    R = int(np.ceil(rmin)) + 1
+    out = np.empty(len(elements))
+    for q, e in enumerate(elements):
+        e = int(e)
+        i, j, k = e % nx, (e // nx) % ny, e // (nx * ny)
+        num = den = 0.0
+        for dk in range(-R, R + 1):
+            for dj in range(-R, R + 1):
+                for di in range(-R, R + 1):
+                    w = rmin - np.sqrt(di * di + dj * dj + dk * dk)
+                    ii, jj, kk = i + di, j + dj, k + dk
+                    if w <= 0 or not (0 <= ii < nx and 0 <= jj < ny and 0 <= kk < nz):
+                        continue
+                    num += w * x[ii + nx * (jj + ny * kk)]
+                    den += w
+        out[q] = num / den
+    return out

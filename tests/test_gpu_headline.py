@@ -249,3 +249,47 @@ def test_smoothing_epilogue_full_size_sampled(op_kernel):
             ref = x[q] + omega * (b[q] - Kx[c]) / d[c]
             tol = 1e-5 * (abs(x[q]) + omega * (abs(b[q]) + bound[c]) / d[c]) + 1e-30
             assert abs(y[q] - ref) <= tol, (n, c)
+
+
+class _Mask:
+    """Free-DOF indicator from the fixed-DOF list, without an n_dof array."""
+
+    def __init__(self, fixed):
+        self.fixed = set(int(d) for d in fixed)
+
+    def __getitem__(self, d):
+        return 0.0 if int(d) in self.fixed else 1.0
+
+
+def test_apply_K_mbb_512x256x256_sampled_nodes():
+    """The large single-problem workload (MBB half model 512x256x256, r = 2.5) in the
+    configuration the benchmark times (FP32-mixed, multigrid x2): y = K u at sampled nodes,
+    the moduli of their elements filtered one element at a time by the oracle."""
+    fb = _fb()
+    pb = W.mbb_512x256x256()
+    rho = W.random_rho(pb.n_elem, 0.0, 1.0, seed=W.SEED + 12)
+    prm = fb.to_default_params(precision=fb.TO_FP32_MIXED, precond=fb.TO_PRECOND_MG, n_inner=2)
+    u = W.random_u(pb.n_dof, seed=W.SEED + 13)
+    nodes = _sample_nodes(pb)
+    with fb.Problem.from_workload(pb, prm) as P:
+        P.set_design(_t(rho, P))
+        ut = _t(u, P)
+        y = P.apply_K(ut)
+        idx = torch.as_tensor(np.array([3 * n + c for n in nodes for c in range(3)]), device=P.device)
+        ys = y[idx].double().cpu().numpy().reshape(-1, 3)
+        del ut, y
+    nx, ny, nz = pb.nx, pb.ny, pb.nz
+    els = sorted({(i + di) + nx * ((j + dj) + ny * (k + dk))
+                  for n in nodes for i, j, k in [(n % (nx + 1), (n // (nx + 1)) % (ny + 1), n // ((nx + 1) * (ny + 1)))]
+                  for dk in (-1, 0) for dj in (-1, 0) for di in (-1, 0)
+                  if 0 <= i + di < nx and 0 <= j + dj < ny and 0 <= k + dk < nz})
+    rt = filt.filter_forward_at(nx, ny, nz, pb.rmin, rho, els)
+    Ee = dict(zip(els, fem.young(rt, pb.E0, pb.Emin, pb.p)))
+    O = _NodeOracle.__new__(_NodeOracle)
+    O.pb, O.Ee = pb, Ee
+    O.ke = fem.ke_hex8(pb.nu, pb.h)
+    O.m = _Mask(pb.fixed_dof)
+    for q, n in enumerate(nodes):
+        Kx, bound, _ = O.at_node(n, u)
+        for c in range(3):
+            assert abs(ys[q, c] - Kx[c]) <= 1e-5 * max(bound[c], abs(u[3 * n + c]), 1e-30), (n, c)

@@ -52,3 +52,15 @@ def test_sensitivity_matches_central_differences_of_exact_compliance():
         assert abs(g[e] - fd) <= 1e-6 * abs(fd) + 1e-12
     # compliance is non-increasing in every design variable
     assert np.all(g <= 0)
+
+
+def test_filter_at_sampled_elements_equals_the_full_filter():
+    """The per-element loop (used where the full H does not fit) gives the full filter's
+    values, for both workload radii, at interior, edge and corner elements."""
+    for dims, r in (((9, 7, 6), 1.5), ((11, 8, 7), 2.5)):
+        H, Hs = filt.filter_matrix(*dims, r)
+        x = W.random_rho(dims[0] * dims[1] * dims[2], 0.0, 1.0, seed=W.SEED + 40)
+        full = filt.filter_forward(H, Hs, x)
+        els = [0, 1, dims[0] - 1, dims[0] * dims[1] * dims[2] - 1] + list(W.random_elements(x.size, 20, seed=W.SEED + 41))
+        at = filt.filter_forward_at(*dims, r, x, els)
+        assert np.abs(at - full[els]).max() <= 1e-15
