@@ -59,7 +59,17 @@ template <> struct PairT<float> { using t = float2; };
 template <> struct PairT<double> { using t = double2; };
 
 __device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 psub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 psub(float2 a, float2 b) {   // one packed subtract (no -1 operand pair)
+    float2 r;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\t"
+        "mov.b64 rb, {%4, %5};\n\t"
+        "sub.rn.f32x2 rd, ra, rb;\n\t"
+        "mov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
 __device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ double2 padd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
@@ -144,15 +154,17 @@ __device__ __forceinline__ void op_body(const OpArgs<T>& a, const HaarK<T>& kh, 
     const bool col_in = ie >= 0 && ie < a.nx && je >= 0 && je < a.ny;
     const int ni = X0 + tx, nj = Y0 + ty;
     const bool owner = tx < TX - 1 && ty < TY - 1 && ni < nxn && nj < nyn;
-    const long long own_base = (long long)ni + (long long)nxn * nj;
-    const long long elem_base = col_in ? (long long)ie + (long long)a.nx * je : 0;
+    // in-plane offsets are 32-bit (the launch checks 3 (nx + 1)(ny + 1) < 2^31); plane
+    // bases are 64-bit and formed once per layer
+    const unsigned own_n = owner ? (unsigned)ni + (unsigned)nxn * (unsigned)nj : 0u;   // owned node in its plane
+    const unsigned own3 = 3u * own_n;
+    const unsigned ecol = col_in ? (unsigned)ie + (unsigned)a.nx * (unsigned)je : 0u;   // element column in its layer
     const bool dz = NEED_D && a.dinv != nullptr && (MODE != OP_RESID || a.z != nullptr);
     // tiles whose footprint holds no fixed node skip every mask operation
     const bool hm = a.tmask == nullptr || a.tmask[bx + ((a.nx + 1 + TX - 2) / (TX - 1)) * by] != 0;
 
     // per-thread staging pointers (advanced by whole planes)
-    const T* st_x[SR];
-    long long st_node[SR];
+    unsigned st_node[SR];   // staged node in its plane
     bool st_ok[SR];
 #pragma unroll
     for (int r = 0; r < SR; ++r) {
@@ -160,44 +172,41 @@ __device__ __forceinline__ void op_body(const OpArgs<T>& a, const HaarK<T>& kh, 
         const int px = sidx % (TX + 1), py = sidx / (TX + 1);
         const int gi = X0 - 1 + px, gj = Y0 - 1 + py;
         st_ok[r] = sidx < PN && gi >= 0 && gi < nxn && gj >= 0 && gj < nyn;
-        st_node[r] = st_ok[r] ? (long long)gi + (long long)nxn * gj : 0;
-        st_x[r] = a.x + 3 * st_node[r];
+        st_node[r] = st_ok[r] ? (unsigned)gi + (unsigned)nxn * (unsigned)gj : 0u;
     }
-    const T* e_src = a.E + elem_base;
-    const T* b_src = NEED_B ? a.b + 3 * own_base : nullptr;
-    const T* d_src = dz ? a.dinv + 3 * own_base : nullptr;
 
     // all asynchronous copies that plane p (and element layer p-1) needs, into ring slot SP
     auto issue = [&](int p, auto SPc) {
         constexpr int SP = decltype(SPc)::value;
         const bool pin = p >= 0 && p <= a.nz;
-        const long long pn = (long long)p * nplane;
+        const long long pn = pin ? (long long)p * nplane : 0;
+        const T* xp = a.x + 3 * pn;
 #pragma unroll
         for (int r = 0; r < SR; ++r) {
             const int sidx = tid + r * NT;
             if (sidx < PN) {
                 const bool v = st_ok[r] && pin;
-                const T* src = v ? st_x[r] + 3 * pn : a.x;
+                const T* src = xp + 3u * st_node[r];
                 T* dst = reinterpret_cast<T*>(&sm.plane[SP][sidx]);
                 cp_async_t<T>(dst + 0, src + 0, v);
                 cp_async_t<T>(dst + 1, src + 1, v);
                 cp_async_t<T>(dst + 2, src + 2, v);
                 if (hm)
                     cp_async_4(&sm.mword[SP][sidx],
-                               reinterpret_cast<const uint32_t*>(a.mask) + (v ? (st_node[r] + pn) >> 2 : 0), v);
+                               reinterpret_cast<const uint32_t*>(a.mask) + ((st_node[r] + pn) >> 2), v);
             }
         }
         const int L = p - 1;
         const bool ev = col_in && L >= 0 && L < a.nz;
-        cp_async_t<T>(&sm.ebuf[SP][ty][tx], ev ? e_src + (long long)L * eplane : a.E, ev);
+        cp_async_t<T>(&sm.ebuf[SP][ty][tx], a.E + (ev ? (long long)L * eplane : 0) + ecol, ev);
         if (NEED_B || dz) {
             const bool ov = owner && p >= kb && p < ke;
             if (NEED_B)
 #pragma unroll
-                for (int c = 0; c < 3; ++c) cp_async_t<T>(&sm.eb[SP][ty][tx][c], ov ? b_src + 3 * pn + c : a.b, ov);
+                for (int c = 0; c < 3; ++c) cp_async_t<T>(&sm.eb[SP][ty][tx][c], a.b + 3 * pn + own3 + c, ov);
             if (dz)
 #pragma unroll
-                for (int c = 0; c < 3; ++c) cp_async_t<T>(&sm.ed[SP][ty][tx][c], ov ? d_src + 3 * pn + c : a.dinv, ov);
+                for (int c = 0; c < 3; ++c) cp_async_t<T>(&sm.ed[SP][ty][tx][c], a.dinv + 3 * pn + own3 + c, ov);
         }
         cp_commit();
     };
@@ -209,8 +218,8 @@ __device__ __forceinline__ void op_body(const OpArgs<T>& a, const HaarK<T>& kh, 
         for (int r = 0; r < SR; ++r) {
             const int sidx = tid + r * NT;
             if (sidx < PN && st_ok[r]) {
-                const long long node = st_node[r] + pn;
-                const uint32_t m = (sm.mword[SP][sidx] >> (8 * (int)(node & 3))) & 0xffu;
+                const unsigned node = st_node[r] + (unsigned)pn;   // low bits only
+                const uint32_t m = (sm.mword[SP][sidx] >> (8 * (node & 3u))) & 0xffu;
                 if (m) {
                     T* dst = reinterpret_cast<T*>(&sm.plane[SP][sidx]);
                     if (m & 1) dst[0] = T(0);
@@ -261,8 +270,6 @@ __device__ __forceinline__ void op_body(const OpArgs<T>& a, const HaarK<T>& kh, 
         Gc.p[f] = P{T(0), T(0)};
         Gc.z[f] = T(0);
     }
-    T* y_own = a.y + 3 * own_base;
-    const T* x_own = a.x + 3 * own_base;
 
     // one element layer with compile-time ring slots: top plane k+1 in slot ST, bottom plane k in SB
     auto layer = [&](int k, auto STc) {
@@ -298,7 +305,7 @@ __device__ __forceinline__ void op_body(const OpArgs<T>& a, const HaarK<T>& kh, 
                     T en = T(0);
 #pragma unroll
                     for (int i = 3; i < 24; ++i) en = fma(uh[i], v[i], en);
-                    const long long e = elem_base + k * eplane;
+                    const long long e = (long long)k * eplane + ecol;
                     a.gt[e] = -a.Ed[e] * en;
                 }
             }
@@ -354,13 +361,14 @@ __device__ __forceinline__ void op_body(const OpArgs<T>& a, const HaarK<T>& kh, 
             const N4 xs = sm.plane[SB][oidx];
             const T xv3[3] = {xs.x, xs.y, xs.z};
             uint32_t mk = 0;
-            if (hm) mk = (sm.mword[SB][oidx] >> (8 * (int)((own_base + (long long)k * nplane) & 3))) & 0xffu;
-            T* yo = y_own + pofs;
+            if (hm) mk = (sm.mword[SB][oidx] >> (8 * ((own_n + (unsigned)((long long)k * nplane)) & 3u))) & 0xffu;
+            T* yo = a.y + pofs + own3;
+            const T* xo = a.x + pofs + own3;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 T Kx = Kx3[c], xv = xv3[c];
                 if ((mk >> c) & 1) {               // K^ is the identity on fixed DOFs
-                    xv = x_own[pofs + c];
+                    xv = xo[c];
                     Kx = xv;
                 }
                 if (MODE == OP_APPLY) {
@@ -381,7 +389,7 @@ __device__ __forceinline__ void op_body(const OpArgs<T>& a, const HaarK<T>& kh, 
                     yo[c] = rv2;
                     if (a.z) {
                         const T zv = rv2 * sm.ed[SB][ty][tx][c];
-                        a.z[3 * (own_base + (long long)k * nplane) + c] = zv;
+                        a.z[pofs + own3 + c] = zv;
                         acc0 = fma(rv2, zv, acc0);
                     }
                     acc1 = fma(rv2, rv2, acc1);
@@ -395,13 +403,25 @@ __device__ __forceinline__ void op_body(const OpArgs<T>& a, const HaarK<T>& kh, 
         __syncthreads();   // (B)
     };
 
-    for (int k = kb - 1; k < ke; ++k) {
+    // four layers per trip with every ring slot a compile-time constant (the carried
+    // faces change registers without copies); the layers before the first slot-0 top
+    // plane and the last ones dispatch on the slot one at a time
+    for (int k = kb - 1; k < ke;) {
+        if (((k + 1 + 4) & 3) == 0 && k + 4 <= ke) {
+            layer(k, I0{});
+            layer(k + 1, I1{});
+            layer(k + 2, I2{});
+            layer(k + 3, I3{});
+            k += 4;
+            continue;
+        }
         switch ((k + 1 + 4) & 3) {
             case 0: layer(k, I0{}); break;
             case 1: layer(k, I1{}); break;
             case 2: layer(k, I2{}); break;
             default: layer(k, I3{}); break;
         }
+        ++k;
     }
     cp_wait<0>();
     double* sh_red = sm.red;
@@ -473,6 +493,9 @@ __global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 ? (MODE == OP_RESID ?
     op_body<T, TX, TY, MODE>(a, kh, t % gx, (t / gx) % gy, t / (gx * gy), (unsigned)t, (unsigned)(gx * gy * gz));
 }
 
+// the kernel's in-plane offsets are 32-bit
+static bool plane_fits(int nx, int ny) { return 3LL * (nx + 1) * (ny + 1) < (1LL << 31); }
+
 // the table of a batched launch: the problems' arguments, then the (problem, tile) map,
 // round-robin over the problems tile by tile; *total = the map's length (the grid)
 template <typename T>
@@ -482,6 +505,7 @@ static int upload_op_table(const std::vector<OpArgs<T>>& h, void** dev, int* tot
     int mt = 0;
     for (int p = 0; p < n; ++p) {
         const OpArgs<T>& a = h[p];
+        if (!plane_fits(a.nx, a.ny)) return fail(TO_ERR_ARG, "grid plane too large for the operator kernel");
         const int gx = (a.nx + 1 + 30) / 31, gy = (a.ny + 1 + 6) / 7, gz = (a.nz + 1 + a.kchunk - 1) / a.kchunk;
         if ((long long)gx * gy * gz > kMaxRedBlocks) return fail(TO_ERR_ARG, "batched problem too large for the reduction slots");
         tiles[p] = gx * gy * gz;
@@ -514,6 +538,7 @@ template <typename T, int TX, int TY>
 static int launch_t(to_problem* P, int level, int mode, const void* x, void* y, const void* b,
                     cudaStream_t s, double omega, int first, const OpOut* out) {
     const Level& L = P->lv[level];
+    if (!plane_fits(L.nx, L.ny)) return fail(TO_ERR_ARG, "grid plane too large for the operator kernel");
     OpArgs<T> a{};
     a.nx = L.nx;
     a.ny = L.ny;
@@ -644,6 +669,7 @@ static int level_op_args(to_problem* P, int level, int mode, const void* x, void
                          OpArgs<T>& a, int& gx, int& gy, int& gz) {
     constexpr int TX = 32, TY = 8;
     const Level& L = P->lv[level];
+    if (!plane_fits(L.nx, L.ny)) return fail(TO_ERR_ARG, "grid plane too large for the operator kernel");
     a = OpArgs<T>{};
     a.nx = L.nx;
     a.ny = L.ny;

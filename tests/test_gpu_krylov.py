@@ -73,6 +73,39 @@ def test_cpfbto_outer_loop_matches_oracle_fp64():
     assert np.abs(rho - rho_o).mean() <= 1e-2
 
 
+def test_cpfbto_every_step_from_the_gpu_state_fp64():
+    """All 12 iterations of Algorithm CPFBTO checked tightly: before each GPU step the
+    oracle takes the same step from the GPU's own state (rho_k, u_k, k, alpha_0; alpha_0 is
+    fixed at the first nonzero gradient), so the trajectory's sensitivity (above) does not
+    enter.  rho_{k+1} depends on u_k only
+    (the gradient step and the projection): 1e-10.  u_{k+1} is the minimal-residual
+    vector of Eq. (LSP), compared like the single application (1e-7)."""
+    fb = _fb()
+    pb = W.cantilever(16, 8, 8)
+    S = outer.Setup(pb)
+    with fb.Problem.from_workload(pb, _params(fb, fb.TO_FP64, 20)) as P:
+        for it in range(12):
+            rho, u, k, a0 = P.get_state()
+            rho, u = rho.cpu().numpy(), u.cpu().numpy()
+            st = P.step(1, want_stats=True)[0]
+            st = st if isinstance(st, dict) else st.as_dict()
+            rho1, u1, k1, a1 = P.get_state()
+            rho1, u1 = rho1.cpu().numpy(), u1.cpu().numpy()
+            rho_o, u_o, hist, a0_o = outer.run(pb, 1, precond="krylov", n_inner=1, inner_mode="richardson",
+                                               beta=1.0, krylov_dim=20, setup=S, rho=rho, u=u, k0=k,
+                                               alpha0=a0 if a0 > 0.0 else None)
+            h = hist[0]
+            assert k1 == k + 1
+            if a0_o is None:   # u_1 = 0: no gradient yet, the step size is set at the first nonzero one
+                assert a1 == 0.0
+            else:
+                assert abs(a1 - a0_o) <= 1e-11 * a0_o
+            assert abs(st["J"] - h["J"]) <= 1e-11 * abs(h["J"])
+            assert np.abs(rho1 - rho_o).max() <= 1e-10
+            assert abs(st["lambda"] - h["lam"]) <= 1e-10 * max(abs(h["lam"]), 1.0)
+            assert np.linalg.norm(u1 - u_o) <= 1e-7 * np.linalg.norm(u_o)
+
+
 def test_cpfbto_tracking_error_contracts_fp32():
     """Eq. (contractXi) on the GPU: the residual at u_{k+1} (same design) is below the one at u_k."""
     fb = _fb()
