@@ -11,7 +11,7 @@
 namespace to {
 int project_coop_blocks(int prec, int num_sms, int* out);
 int launch_rowsum(to_problem* P, cudaStream_t s);
-int run_inner(to_problem* P, void* u, int nsteps, int primary, cudaStream_t s);
+int run_inner(to_problem* P, void* u, int nsteps, int primary, cudaStream_t s, int resid_done);
 int refresh_preconditioner(to_problem* P, cudaStream_t s, bool join = true);
 int launch_filter_prescaled_T(to_problem* P, const void* x, void* y, cudaStream_t s);
 
@@ -143,6 +143,10 @@ extern "C" void to_destroy(to_problem* P) {
     if (P->ev_fork) cudaEventDestroy(P->ev_fork);
     if (P->ev_join) cudaEventDestroy(P->ev_join);
     if (P->side) cudaStreamDestroy(P->side);
+    if (P->dside) cudaStreamSynchronize(P->dside);
+    if (P->ev_dfork) cudaEventDestroy(P->ev_dfork);
+    if (P->ev_djoin) cudaEventDestroy(P->ev_djoin);
+    if (P->dside) cudaStreamDestroy(P->dside);
     if (P->gstream) cudaStreamDestroy(P->gstream);
     void* p;
     p = P->ke_dev; dfree(p);
@@ -152,6 +156,7 @@ extern "C" void to_destroy(to_problem* P) {
     p = P->ps_buf; dfree(p);
     p = P->sc; dfree(p);
     p = P->red; dfree(p);
+    p = P->red_d; dfree(p);
     p = P->counters; dfree(p);
     p = P->dstats; dfree(p);
     delete P;
@@ -200,7 +205,10 @@ extern "C" int to_create(const to_grid* g, const to_material* m, const to_loads*
     if ((rc = operator_init(P))) return bail(rc);
     if (cudaStreamCreateWithFlags(&P->gstream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&P->ev_in, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&P->ev_out, cudaEventDisableTiming) != cudaSuccess)
+        cudaEventCreateWithFlags(&P->ev_out, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&P->dside, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&P->ev_dfork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&P->ev_djoin, cudaEventDisableTiming) != cudaSuccess)
         return bail(fail(TO_ERR_CUDA, "stream / event creation failed"));
 
     // filter stencil: offsets with w = rmin - |d| > 0 (identity when rmin <= 0)
@@ -254,6 +262,8 @@ extern "C" int to_create(const to_grid* g, const to_material* m, const to_loads*
     P->sc = (DevScalars*)p;
     if ((rc = dalloc(&p, sizeof(double) * (size_t)kMaxRedBlocks * (kRedQ + 2 * 12)))) return bail(rc);
     P->red = (double*)p;
+    if ((rc = dalloc(&p, sizeof(double) * (size_t)kMaxRedBlocks * (kRedQ + 2 * 12)))) return bail(rc);
+    P->red_d = (double*)p;
     if ((rc = dalloc(&p, sizeof(unsigned) * 64))) return bail(rc);
     P->counters = (unsigned*)p;
     if ((rc = dalloc(&p, sizeof(to_stats) * 256))) return bail(rc);
@@ -404,7 +414,7 @@ extern "C" int to_inner_solve(to_problem* P, void* u_dev, int32_t nsteps, double
     }
     void* gt = P->gt;
     P->gt = nullptr;
-    int rc = run_inner(P, u_dev, nsteps, 0, s);
+    int rc = run_inner(P, u_dev, nsteps, 0, s, 0);
     if (!rc && res_out) rc = launch_operator(P, 0, OP_RESID, u_dev, P->r, P->f, s, 0.0, 1);
     P->gt = gt;
     if (rc) return rc;

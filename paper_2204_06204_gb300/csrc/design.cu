@@ -253,7 +253,7 @@ static FilterArgs<T> filter_args(const to_problem* P, const T* x, T* y, int kchu
     a.w = (const T*)P->stencil_w;
     a.ns = P->n_stencil;
     a.R = P->filter_ext;
-    a.red = stats ? P->red : nullptr;
+    a.red = stats ? P->red_d : nullptr;
     a.counter = stats ? P->counters + 2 : nullptr;
     a.sc = P->sc;
     a.alpha0_param = P->prm.alpha0;

@@ -152,6 +152,8 @@ struct to_problem {
     // device scalars, reductions, stats
     to::DevScalars* sc = nullptr;
     double* red = nullptr;         // kMaxRedBlocks * kRedQ doubles
+    double* red_d = nullptr;       // the same for the design update (filter^T statistics, projection),
+                                   // which runs beside the lower-level steps
     // completion counters / barrier words (64): [0] residual, [1] z^T q, [2] filter^T statistics,
     // [4] update, [5] r^T z, [6] smoother r^T z, [7] f^T u, [8..9] grid barrier,
     // [10..11] projection first / final pass, [12] Krylov passes
@@ -180,6 +182,8 @@ struct to_problem {
     int graph_state = 0;           // 0: not captured yet, 1: ready, -1: capture unavailable
     cudaStream_t side = nullptr;   // branch for the coarsest inverse (overlaps the fine-level work)
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaStream_t dside = nullptr;  // branch for the design update (overlaps the lower-level steps)
+    cudaEvent_t ev_dfork = nullptr, ev_djoin = nullptr;
 
     // launch configuration of the operator kernel; resident CTAs per SM of each mode
     int tile_x = 32, tile_y = 8, tile_z = 8;

@@ -420,8 +420,8 @@ static int project_t(to_problem* P, const void* w, const void* rho_in, const voi
     a.hi = P->mat.rho_max;
     a.fused = fused;
     a.mean_proj = P->prm.mean_proj;
-    a.part = P->red + (size_t)kMaxRedBlocks * kRedQ;
-    a.red = P->red;
+    a.part = P->red_d + (size_t)kMaxRedBlocks * kRedQ;
+    a.red = P->red_d;
     a.counter = P->counters + 10;   // [10] first pass, [11] final pass
     a.sc = P->sc;
     // the streaming passes: 512 threads, four elements per thread and round, at most

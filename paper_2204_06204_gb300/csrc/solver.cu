@@ -222,14 +222,17 @@ static int apply_M_t(to_problem* P, const void* in, void* out, cudaStream_t s) {
     }
 }
 
-// Residual at u (with the fused sensitivity when `primary`), then nsteps steps.
-int run_inner(to_problem* P, void* u, int nsteps, int primary, cudaStream_t s) {
+// Residual at u (with the fused sensitivity when `primary`; already launched by the
+// caller when `resid_done`), then nsteps steps.
+int run_inner(to_problem* P, void* u, int nsteps, int primary, cudaStream_t s, int resid_done) {
     int rc;
     void* gt_save = P->gt;
-    if (!primary) P->gt = nullptr;
-    rc = launch_operator(P, 0, OP_RESID, u, P->r, P->f, s, 0.0, 1);
-    P->gt = gt_save;
-    if (rc) return rc;
+    if (!resid_done) {
+        if (!primary) P->gt = nullptr;
+        rc = launch_operator(P, 0, OP_RESID, u, P->r, P->f, s, 0.0, 1);
+        P->gt = gt_save;
+        if (rc) return rc;
+    }
     if (P->prm.inner_mode == TO_INNER_PCG) {
         // preconditioned conjugate gradients from u: p = z, then per iteration q = K p with
         // alpha = r^T z / p^T q, the update, z = M^-1 r, p = z + beta p
@@ -314,10 +317,20 @@ int outer_iteration(to_problem* P, cudaStream_t s) {
     // the coarsest inverse overlaps the residual and the fine-level smoothing: its
     // branch is joined by the first coarse solve, and in any case before the iteration ends
     if ((rc = refresh_preconditioner(P, s, false))) return rc;
-    if ((rc = run_inner(P, P->u, P->prm.n_inner, 1, s))) return rc;
+    // the residual at u_k with the sensitivity at u_k fused
+    if ((rc = launch_operator(P, 0, OP_RESID, P->u, P->r, P->f, s, 0.0, 1))) return rc;
+    // The design update (filter transpose, gradient step, projection) reads rho_k and the
+    // sensitivity at u_k only, and the lower-level steps read K(rho_k) only: the update
+    // runs on a branch beside the steps (its reductions have their own scratch and
+    // counters; the two write disjoint device scalars) and is joined before the record.
+    TO_CUDA(cudaEventRecord(P->ev_dfork, s));
+    TO_CUDA(cudaStreamWaitEvent(P->dside, P->ev_dfork, 0));
+    if ((rc = launch_sens_filter_T(P, P->dside))) return rc;
+    if ((rc = launch_project(P, nullptr, P->rho, P->grad, P->rho, 1, P->dside))) return rc;
+    TO_CUDA(cudaEventRecord(P->ev_djoin, P->dside));
+    if ((rc = run_inner(P, P->u, P->prm.n_inner, 1, s, 1))) return rc;
     if (P->prm.precond == TO_PRECOND_MG) TO_CUDA(cudaStreamWaitEvent(s, P->ev_join, 0));
-    if ((rc = launch_sens_filter_T(P, s))) return rc;
-    if ((rc = launch_project(P, nullptr, P->rho, P->grad, P->rho, 1, s))) return rc;
+    TO_CUDA(cudaStreamWaitEvent(s, P->ev_djoin, 0));
     return launch_record(P, s);
 }
 
