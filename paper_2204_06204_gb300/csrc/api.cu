@@ -12,7 +12,6 @@ namespace to {
 int project_coop_blocks(int prec, int num_sms, int* out);
 int launch_rowsum(to_problem* P, cudaStream_t s);
 int run_inner(to_problem* P, void* u, int nsteps, int primary, cudaStream_t s, int resid_done);
-int refresh_preconditioner(to_problem* P, cudaStream_t s, bool join = true);
 int launch_filter_prescaled_T(to_problem* P, const void* x, void* y, cudaStream_t s);
 
 namespace {
@@ -136,6 +135,9 @@ extern "C" void to_destroy(to_problem* P) {
         dfree(L.t);
     }
     if (P->gexec) cudaGraphExecDestroy(P->gexec);
+    for (int p = 0; p < 2; ++p)
+        for (int f = 0; f < 2; ++f)
+            if (P->gexec_pipe[p][f]) cudaGraphExecDestroy(P->gexec_pipe[p][f]);
     if (P->gstream) cudaStreamSynchronize(P->gstream);
     if (P->ev_in) cudaEventDestroy(P->ev_in);
     if (P->ev_out) cudaEventDestroy(P->ev_out);
@@ -157,6 +159,12 @@ extern "C" void to_destroy(to_problem* P) {
     p = P->sc; dfree(p);
     p = P->red; dfree(p);
     p = P->red_d; dfree(p);
+    p = P->alt_rhot; dfree(p);
+    p = P->alt_Ed; dfree(p);
+    for (void* q : P->alt_E) dfree(q);
+    for (void* q : P->alt_dinv) dfree(q);
+    p = P->alt_coarse_L; dfree(p);
+    p = P->alt_gj_tab; dfree(p);
     p = P->counters; dfree(p);
     p = P->dstats; dfree(p);
     delete P;
@@ -358,6 +366,7 @@ extern "C" int to_set_design(to_problem* P, const void* rho_dev, void* stream) {
     int rc = launch_moduli(P, s);
     if (rc) return rc;
     P->precond_stale = 1;   // refreshed by the next to_inner_solve (to_step refreshes every iteration)
+    P->pipe_ready = 0;
     return TO_OK;
 }
 
@@ -488,6 +497,36 @@ static int capture_outer(to_problem* P) {
     return TO_OK;
 }
 
+// The same for the pipelined iteration of the live set (one graph per set: the kernels'
+// pointers differ)
+static int capture_pipelined(to_problem* P, int fresh) {
+    const int p = P->set_parity;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(P->gstream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        P->pipe_state[p][fresh] = -1;
+        return TO_OK;
+    }
+    const int rc = outer_iteration_pipelined(P, P->gstream, fresh != 0);
+    const cudaError_t e = cudaStreamEndCapture(P->gstream, &g);
+    if (rc != TO_OK || e != cudaSuccess || !g) {
+        cudaGetLastError();
+        if (g) cudaGraphDestroy(g);
+        P->pipe_state[p][fresh] = -1;
+        return TO_OK;
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&P->gexec_pipe[p][fresh], g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+        cudaGetLastError();
+        P->gexec_pipe[p][fresh] = nullptr;
+        P->pipe_state[p][fresh] = -1;
+        return TO_OK;
+    }
+    P->pipe_state[p][fresh] = 1;
+    return TO_OK;
+}
+
 extern "C" int to_step(to_problem* P, int32_t n_outer, to_stats* stats_out, void* stream) {
     TO_ENTER(P);
     if (n_outer < 0) return fail(TO_ERR_ARG, "n_outer must be >= 0");
@@ -506,25 +545,61 @@ extern "C" int to_step(to_problem* P, int32_t n_outer, to_stats* stats_out, void
         if (P->gexec) cudaGraphExecDestroy(P->gexec);   // the captured record kernel holds the old ring
         P->gexec = nullptr;
         if (P->graph_state == 1) P->graph_state = 0;
+        for (int p = 0; p < 2; ++p)
+            for (int f = 0; f < 2; ++f) {
+                if (P->gexec_pipe[p][f]) cudaGraphExecDestroy(P->gexec_pipe[p][f]);
+                P->gexec_pipe[p][f] = nullptr;
+                if (P->pipe_state[p][f] == 1) P->pipe_state[p][f] = 0;
+            }
     }
     // run on the library stream, ordered after the caller's stream and before its next work
     TO_CUDA(cudaEventRecord(P->ev_in, s));
     TO_CUDA(cudaStreamWaitEvent(P->gstream, P->ev_in, 0));
     k_reset_rec<<<1, 1, 0, P->gstream>>>(P->sc);
     TO_CUDA(cudaGetLastError());
-    if (P->prm.no_graph == 0 && P->graph_state == 0) {
-        int rc = capture_outer(P);
-        if (rc) return rc;
+    // Pipelined iterations (each builds the next design's preconditioner beside its own
+    // lower-level steps) unless the persistent multigrid legs or a batch hold this
+    // problem's buffer pointers, or the second set could not be allocated.
+    bool pipe = P->prm.mg_legs == 0 && !P->in_batch && P->alt_alloc != 2;
+    if (pipe && pipe_alloc(P) != TO_OK) {
+        cudaGetLastError();
+        pipe = false;
     }
-    for (int i = 0; i < n_outer; ++i) {
-        if (P->graph_state == 1) {
-            TO_CUDA(cudaGraphLaunch(P->gexec, P->gstream));
-        } else {
-            int rc = outer_iteration(P, P->gstream);
+    if (pipe) {
+        // the first iteration computes the live set itself unless the last to_step left it
+        int fresh = P->pipe_ready ? 0 : 1;
+        P->pipe_ready = 0;
+        for (int i = 0; i < n_outer; ++i, fresh = 0) {
+            const int p = P->set_parity;
+            if (P->prm.no_graph == 0 && P->pipe_state[p][fresh] == 0) {
+                int rc = capture_pipelined(P, fresh);
+                if (rc) return rc;
+            }
+            if (P->pipe_state[p][fresh] == 1) {
+                TO_CUDA(cudaGraphLaunch(P->gexec_pipe[p][fresh], P->gstream));
+            } else {
+                int rc = outer_iteration_pipelined(P, P->gstream, fresh != 0);
+                if (rc) return rc;
+            }
+            pipe_swap(P);   // the set built for rho_{k+1} is live from here on
+        }
+        P->pipe_ready = 1;
+    } else {
+        if (P->prm.no_graph == 0 && P->graph_state == 0) {
+            int rc = capture_outer(P);
             if (rc) return rc;
         }
+        for (int i = 0; i < n_outer; ++i) {
+            if (P->graph_state == 1) {
+                TO_CUDA(cudaGraphLaunch(P->gexec, P->gstream));
+            } else {
+                int rc = outer_iteration(P, P->gstream);
+                if (rc) return rc;
+            }
+        }
+        P->pipe_ready = 0;   // the moduli lag rho by one iteration here
     }
-    P->precond_stale = 0;   // the last iteration refreshed it for its own moduli
+    P->precond_stale = 0;   // the last iteration refreshed it for its own moduli (pipelined: for rho)
     TO_CUDA(cudaEventRecord(P->ev_out, P->gstream));
     TO_CUDA(cudaStreamWaitEvent(s, P->ev_out, 0));
     if (stats_out) {
@@ -566,6 +641,7 @@ extern "C" int to_set_state(to_problem* P, const void* rho_dev, const void* u_de
     int rc = launch_moduli(P, s);
     if (rc) return rc;
     P->precond_stale = 1;   // refreshed by the next to_inner_solve (to_step refreshes every iteration)
+    P->pipe_ready = 0;
     return TO_OK;
 }
 

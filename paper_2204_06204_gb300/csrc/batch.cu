@@ -358,6 +358,7 @@ extern "C" int to_batch_create(to_problem* const* problems, int32_t n, to_batch*
     if (cudaSetDevice(P0->device) != cudaSuccess) return fail(TO_ERR_CUDA, "cudaSetDevice failed");
     to_batch* B = new to_batch();
     B->probs.assign(problems, problems + n);
+    for (to_problem* P : B->probs) P->in_batch += 1;   // the batch's tables hold their buffer pointers
     B->n = n;
     B->prec = P0->prec;
     B->n_inner = P0->prm.n_inner;
@@ -403,7 +404,10 @@ extern "C" int to_batch_step(to_batch* B, int32_t n_outer, to_stats* stats_out, 
     if (!B) return fail(TO_ERR_ARG, "null batch");
     if (n_outer < 0) return fail(TO_ERR_ARG, "n_outer must be >= 0");
     if (n_outer == 0) return TO_OK;
-    for (to_problem* P : B->probs) P->fwd_id = 0;   // the outer iterations change every design
+    for (to_problem* P : B->probs) {
+        P->fwd_id = 0;       // the outer iterations change every design
+        P->pipe_ready = 0;
+    }
     for (to_problem* P : B->probs)
         if (n_outer > P->dstats_cap)
             return fail(TO_ERR_ARG, "n_outer exceeds a problem's stats ring (run to_step once with that many iterations "

@@ -184,6 +184,22 @@ struct to_problem {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaStream_t dside = nullptr;  // branch for the design update (overlaps the lower-level steps)
     cudaEvent_t ev_dfork = nullptr, ev_djoin = nullptr;
+    // Pipelined outer iterations: the next iteration's design-dependent data (rho~, E', every
+    // level's moduli and 1 / d, the coarsest inverse with its inversion table) are built on
+    // the design branch into a second set of buffers, swapped with the live set after the
+    // iteration; set_parity says which physical set is live (one captured graph per set).
+    void* alt_rhot = nullptr;
+    void* alt_Ed = nullptr;
+    std::vector<void*> alt_E, alt_dinv;
+    void* alt_coarse_L = nullptr;
+    void* alt_gj_tab = nullptr;
+    int alt_alloc = 0;
+    int set_parity = 0;
+    cudaGraphExec_t gexec_pipe[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};   // [set][fresh]
+    int pipe_state[2][2] = {{0, 0}, {0, 0}};   // as graph_state, per set and variant
+    int pipe_ready = 0;            // the live set belongs to the current rho (a pipelined to_step left it)
+    int in_batch = 0;              // a batch's tables hold this problem's buffers: no swapping
+    int coarse_wait = 1;           // coarse solves wait for the forked inverse (ev_join)
 
     // launch configuration of the operator kernel; resident CTAs per SM of each mode
     int tile_x = 32, tile_y = 8, tile_z = 8;
@@ -242,12 +258,20 @@ int launch_richardson(to_problem* P, cudaStream_t s);
 int mg_build(to_problem* P);
 // coarse moduli, diagonals, the coarsest inverse (on a forked branch of s; join: s waits for it
 // at once, else the first coarse solve on s does)
-int mg_refresh(to_problem* P, cudaStream_t s, bool join = true);
+int mg_refresh(to_problem* P, cudaStream_t s, bool join = true, bool inline_inv = false);
+// the diagonal and (multigrid) the refresh above; inline_inv: the coarsest inverse on s itself
+int refresh_preconditioner(to_problem* P, cudaStream_t s, bool join = true, bool inline_inv = false);
+// the second set of design-dependent buffers (allocated once) and the swap of the two sets
+int pipe_alloc(to_problem* P);
+void pipe_swap(to_problem* P);
 int mg_vcycle(to_problem* P, const void* r, void* z, cudaStream_t s);
 int mg_legs_build(to_problem* P);
 int mg_legs_launch(to_problem* P, int leg, void* fine, cudaStream_t s);
 
 int outer_iteration(to_problem* P, cudaStream_t s);
+// one outer iteration that also builds the next design's set; the live set must match rho,
+// or `fresh`: the iteration first computes the live set itself
+int outer_iteration_pipelined(to_problem* P, cudaStream_t s, bool fresh);
 int inner_steps(to_problem* P, int nsteps, int from_resid, cudaStream_t s);
 
 // batched multigrid (mg.cu): the V-cycle and the per-iteration refresh of many problems

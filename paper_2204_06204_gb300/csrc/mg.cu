@@ -963,7 +963,7 @@ int mg_build(to_problem* P) {
 }
 
 template <typename T>
-static int refresh_t(to_problem* P, cudaStream_t s, bool join) {
+static int refresh_t(to_problem* P, cudaStream_t s, bool join, bool inline_inv) {
     const int L = (int)P->lv.size();
     for (int l = 1; l < L; ++l) {
         const Level& C = P->lv[l];
@@ -978,17 +978,21 @@ static int refresh_t(to_problem* P, cudaStream_t s, bool join) {
         Cst.nx, Cst.ny, Cst.nz, (const T*)Cst.E, Cst.mask, P->ke_dev, Cst.h, (T*)P->coarse_A, n);
     TO_CUDA(cudaGetLastError());
     T* inv = (T*)P->coarse_L;
-    // the inverse runs on a branch; the first coarse solve joins it (it is needed only there)
-    TO_CUDA(cudaEventRecord(P->ev_fork, s));
-    TO_CUDA(cudaStreamWaitEvent(P->side, P->ev_fork, 0));
+    // the inverse runs on a branch; the first coarse solve joins it (it is needed only
+    // there) -- unless s is itself a branch that the caller joins (inline_inv)
     cudaStream_t main_s = s;
-    s = P->side;
+    if (!inline_inv) {
+        TO_CUDA(cudaEventRecord(P->ev_fork, s));
+        TO_CUDA(cudaStreamWaitEvent(P->side, P->ev_fork, 0));
+        s = P->side;
+    }
     if (n <= kRegDof) {
         k_dense_invert_reg<T><<<1, dim3(32, 32), 0, s>>>((const T*)P->coarse_A, inv, inv + (size_t)n * n, n, &P->sc->err);
         TO_CUDA(cudaGetLastError());
     } else if (int rc = gj_launch<T>(P->gj_tab, 1, (n + kGjB - 1) / kGjB, P->num_sms, s)) {
         return rc;
     }
+    if (inline_inv) return TO_OK;
     TO_CUDA(cudaEventRecord(P->ev_join, s));
     // outside the outer iteration nothing else joins the branch: without this a later
     // refresh could rewrite coarse_A / coarse_L while this inverse still runs
@@ -996,8 +1000,56 @@ static int refresh_t(to_problem* P, cudaStream_t s, bool join) {
     return TO_OK;
 }
 
-int mg_refresh(to_problem* P, cudaStream_t s, bool join) {
-    return P->prec == TO_FP64 ? refresh_t<double>(P, s, join) : refresh_t<float>(P, s, join);
+int mg_refresh(to_problem* P, cudaStream_t s, bool join, bool inline_inv) {
+    return P->prec == TO_FP64 ? refresh_t<double>(P, s, join, inline_inv) : refresh_t<float>(P, s, join, inline_inv);
+}
+
+// The second set of design-dependent buffers: rho~, E', every level's moduli and 1 / d,
+// the coarsest inverse (with its own inversion table; the work matrix is shared, as only
+// one inversion runs at a time).  Allocated on the first pipelined outer iteration.
+int pipe_alloc(to_problem* P) {
+    if (P->alt_alloc) return TO_OK;
+    const size_t es = P->esz;
+    const int L = (int)P->lv.size();
+    P->alt_E.assign(L, nullptr);
+    P->alt_dinv.assign(L, nullptr);
+    bool ok = cudaMalloc(&P->alt_rhot, P->n_elem * es) == cudaSuccess && cudaMalloc(&P->alt_Ed, P->n_elem * es) == cudaSuccess;
+    for (int l = 0; l < L && ok; ++l)
+        ok = cudaMalloc(&P->alt_E[l], P->lv[l].n_elem * es) == cudaSuccess &&
+             cudaMalloc(&P->alt_dinv[l], P->lv[l].n_dof * es) == cudaSuccess;
+    const size_t n = (size_t)P->n_coarse;
+    if (ok && P->coarse_L) ok = cudaMalloc(&P->alt_coarse_L, (n * n + n) * es) == cudaSuccess;
+    if (ok && P->gj_tab) {
+        std::swap(P->coarse_L, P->alt_coarse_L);   // the table of the other set's inverse
+        if (P->prec == TO_FP64) {
+            const GjArgs<double> g = gj_args<double>(P);
+            ok = cudaMalloc(&P->alt_gj_tab, sizeof g) == cudaSuccess &&
+                 cudaMemcpy(P->alt_gj_tab, &g, sizeof g, cudaMemcpyHostToDevice) == cudaSuccess;
+        } else {
+            const GjArgs<float> g = gj_args<float>(P);
+            ok = cudaMalloc(&P->alt_gj_tab, sizeof g) == cudaSuccess &&
+                 cudaMemcpy(P->alt_gj_tab, &g, sizeof g, cudaMemcpyHostToDevice) == cudaSuccess;
+        }
+        std::swap(P->coarse_L, P->alt_coarse_L);
+    }
+    P->alt_alloc = 1;   // whatever was allocated is freed with the problem
+    if (!ok) {
+        P->alt_alloc = 2;   // unusable: the pipelined iteration stays off
+        return fail(TO_ERR_CUDA, "allocation of the second design set");
+    }
+    return TO_OK;
+}
+
+void pipe_swap(to_problem* P) {
+    std::swap(P->rhot, P->alt_rhot);
+    std::swap(P->Ed, P->alt_Ed);
+    for (size_t l = 0; l < P->lv.size(); ++l) {
+        std::swap(P->lv[l].E, P->alt_E[l]);
+        std::swap(P->lv[l].dinv, P->alt_dinv[l]);
+    }
+    std::swap(P->coarse_L, P->alt_coarse_L);
+    std::swap(P->gj_tab, P->alt_gj_tab);
+    P->set_parity ^= 1;
 }
 
 // levels mg_tail .. L-1 in one launch (after the coarsest inverse is ready)
@@ -1010,7 +1062,7 @@ static int tail_t(to_problem* P, cudaStream_t s) {
     const size_t tsm = (size_t)tail_args<T>(P, P->mg_tail, &a);
     HaarK<T> kh;
     for (int q = 0; q < kHaarNnz; ++q) kh.v[q] = (T)P->haar[q];
-    TO_CUDA(cudaStreamWaitEvent(s, P->ev_join, 0));   // the inverse of this design is ready
+    if (P->coarse_wait) TO_CUDA(cudaStreamWaitEvent(s, P->ev_join, 0));   // the inverse of this design is ready
     k_mg_tail<T><<<1, tail_threads<T>(), tsm, s>>>(a, kh);
     TO_CUDA(cudaGetLastError());
     return TO_OK;
@@ -1019,7 +1071,7 @@ static int tail_t(to_problem* P, cudaStream_t s) {
 template <typename T>
 static int coarse_solve_t(to_problem* P, const void* b, void* x, cudaStream_t s) {
     const int n = P->n_coarse;
-    TO_CUDA(cudaStreamWaitEvent(s, P->ev_join, 0));   // the inverse of this design is ready
+    if (P->coarse_wait) TO_CUDA(cudaStreamWaitEvent(s, P->ev_join, 0));   // the inverse of this design is ready
     const T* inv = (const T*)P->coarse_L;
     k_dense_solve<T><<<(n + 7) / 8, dim3(32, 8), 0, s>>>(inv, inv + (size_t)n * n, (const T*)b, (T*)x, n);
     TO_CUDA(cudaGetLastError());

@@ -304,10 +304,10 @@ int run_inner(to_problem* P, void* u, int nsteps, int primary, cudaStream_t s, i
     return TO_OK;
 }
 
-int refresh_preconditioner(to_problem* P, cudaStream_t s, bool join) {
+int refresh_preconditioner(to_problem* P, cudaStream_t s, bool join, bool inline_inv) {
     int rc = launch_diag(P, 0, s);
     if (rc) return rc;
-    if (P->prm.precond == TO_PRECOND_MG) return mg_refresh(P, s, join);
+    if (P->prm.precond == TO_PRECOND_MG) return mg_refresh(P, s, join, inline_inv);
     return TO_OK;
 }
 
@@ -330,6 +330,40 @@ int outer_iteration(to_problem* P, cudaStream_t s) {
     TO_CUDA(cudaEventRecord(P->ev_djoin, P->dside));
     if ((rc = run_inner(P, P->u, P->prm.n_inner, 1, s, 1))) return rc;
     if (P->prm.precond == TO_PRECOND_MG) TO_CUDA(cudaStreamWaitEvent(s, P->ev_join, 0));
+    TO_CUDA(cudaStreamWaitEvent(s, P->ev_djoin, 0));
+    return launch_record(P, s);
+}
+
+// The same iteration with the next design's preconditioner built beside it.  The live
+// set (moduli, diagonals, coarsest inverse) belongs to rho_k on entry, or (`fresh`) is
+// computed first as in outer_iteration, its inverse on the multigrid branch.  After the
+// residual at u_k the design branch forms rho_{k+1} (filter transpose, step,
+// projection), then its moduli, diagonals, coarse moduli and coarsest inverse, all
+// into the other set, while the lower-level steps run on the live set; the caller
+// swaps the sets afterwards.  Every kernel sees the same inputs as in
+// outer_iteration, so the iterates are the same.
+int outer_iteration_pipelined(to_problem* P, cudaStream_t s, bool fresh) {
+    int rc;
+    const bool mg = P->prm.precond == TO_PRECOND_MG;
+    if (fresh && ((rc = launch_moduli(P, s)) || (rc = refresh_preconditioner(P, s, false, false)))) return rc;
+    if ((rc = launch_operator(P, 0, OP_RESID, P->u, P->r, P->f, s, 0.0, 1))) return rc;
+    TO_CUDA(cudaEventRecord(P->ev_dfork, s));
+    TO_CUDA(cudaStreamWaitEvent(P->dside, P->ev_dfork, 0));
+    if ((rc = launch_sens_filter_T(P, P->dside))) return rc;
+    if ((rc = launch_project(P, nullptr, P->rho, P->grad, P->rho, 1, P->dside))) return rc;
+    // the live inverse (fresh: still on the multigrid branch) shares the assembled
+    // operator and the inversion scratch with the next one
+    if (fresh && mg) TO_CUDA(cudaStreamWaitEvent(P->dside, P->ev_join, 0));
+    pipe_swap(P);   // enqueue the next design's refresh into the other set
+    rc = launch_moduli(P, P->dside);
+    if (!rc) rc = refresh_preconditioner(P, P->dside, false, true);
+    pipe_swap(P);
+    if (rc) return rc;
+    TO_CUDA(cudaEventRecord(P->ev_djoin, P->dside));
+    P->coarse_wait = fresh ? 1 : 0;   // else the live inverse was completed before this iteration
+    rc = run_inner(P, P->u, P->prm.n_inner, 1, s, 1);
+    P->coarse_wait = 1;
+    if (rc) return rc;
     TO_CUDA(cudaStreamWaitEvent(s, P->ev_djoin, 0));
     return launch_record(P, s);
 }
