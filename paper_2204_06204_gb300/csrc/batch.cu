@@ -232,6 +232,22 @@ struct to_batch {
     void* ftab[2] = {nullptr, nullptr};   // batched filter tables: design, gradient
     int ftiles[2] = {0, 0};
     size_t fsmem[2] = {0, 0};
+    // Pipelined iterations (as to_step's): the tables over the members' second design sets;
+    // swapped with the live ones above (and every member's sets) after each iteration
+    struct Alt {
+        void* btab = nullptr;
+        void* tab_resid = nullptr;
+        void* tab_q_first = nullptr;
+        void* tab_q = nullptr;
+        void* ftab0 = nullptr;
+        to::BatchMG* mg = nullptr;
+    } alt;
+    int pipe = 0;                         // the second sets and their tables exist
+    int parity = 0;
+    cudaStream_t dside = nullptr;         // the design branch
+    cudaEvent_t ev_dfork = nullptr, ev_djoin = nullptr;
+    cudaGraphExec_t gexec_pipe[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};   // [parity][fresh]
+    int pipe_state[2][2] = {{0, 0}, {0, 0}};
 };
 
 using namespace to;
@@ -314,10 +330,121 @@ int iteration_t(to_batch* B, cudaStream_t s) {
     return TO_OK;
 }
 
+// The same iteration with the next designs' moduli, diagonals and (multigrid) coarse
+// refresh built on the design branch into the members' second sets (B->alt tables)
+// while the lower-level steps run on the live sets; `fresh`: the live sets are
+// computed first.  The kernels see the same inputs as in iteration_t.
+template <typename T>
+int iteration_pipelined_t(to_batch* B, cudaStream_t s, bool fresh) {
+    const BProb<T>* tab = (const BProb<T>*)B->btab;
+    const BProb<T>* tabn = (const BProb<T>*)B->alt.btab;
+    const dim3 g2(B->grid_x, B->n);
+    int rc;
+    if (fresh) {
+        if ((rc = filter_batch_launch(B->prec, 0, B->ftab[0], B->ftiles[0], B->n, B->fsmem[0], s))) return rc;
+        k_b_diag<T><<<g2, 256, 0, s>>>(tab);
+        TO_CUDA(cudaGetLastError());
+        if (B->mg && (rc = batch_mg_refresh(B->mg, s))) return rc;
+    }
+    if ((rc = batch_operator_launch(B->prec, OP_RESID, B->tab_resid, B->kh, B->max_tiles, B->n, s))) return rc;
+    cudaStream_t d = B->dside;
+    TO_CUDA(cudaEventRecord(B->ev_dfork, s));
+    TO_CUDA(cudaStreamWaitEvent(d, B->ev_dfork, 0));
+    if ((rc = filter_batch_launch(B->prec, 1, B->ftab[1], B->ftiles[1], B->n, B->fsmem[1], d))) return rc;
+    if ((rc = launch_cluster_project<T>(tab, B->n, kClusterCTAs, 256, B->proj_cache, B->proj_smem, d))) return rc;
+    // the live inverses (fresh: still on the multigrid branch) share the assembled
+    // operators and the inversion scratch with the next ones
+    if (fresh && B->mg && (rc = batch_mg_wait(B->mg, d))) return rc;
+    if ((rc = filter_batch_launch(B->prec, 0, B->alt.ftab0, B->ftiles[0], B->n, B->fsmem[0], d))) return rc;
+    k_b_diag<T><<<g2, 256, 0, d>>>(tabn);
+    TO_CUDA(cudaGetLastError());
+    if (B->alt.mg && (rc = batch_mg_refresh_inline(B->alt.mg, d))) return rc;
+    TO_CUDA(cudaEventRecord(B->ev_djoin, d));
+    if (B->mg && (rc = batch_mg_vcycle(B->mg, s))) return rc;
+    for (int it = 0; it < B->n_inner; ++it) {
+        rc = batch_operator_launch(B->prec, OP_Q, it == 0 ? B->tab_q_first : B->tab_q, B->kh, B->max_tiles, B->n, s);
+        if (rc) return rc;
+        if (B->mg) k_b_update<T, false><<<g2, 256, 0, s>>>(tab);
+        else k_b_update<T, true><<<g2, 256, 0, s>>>(tab);
+        TO_CUDA(cudaGetLastError());
+        if (B->mg && it + 1 < B->n_inner && (rc = batch_mg_vcycle(B->mg, s))) return rc;
+    }
+    if (B->mg && (rc = batch_mg_join(B->mg, s))) return rc;
+    TO_CUDA(cudaStreamWaitEvent(s, B->ev_djoin, 0));
+    k_b_record<T><<<(B->n + 63) / 64, 64, 0, s>>>(tab, B->n, 0);
+    TO_CUDA(cudaGetLastError());
+    return TO_OK;
+}
+
+// the live tables and every member's live set become the other ones
+void batch_swap(to_batch* B) {
+    std::swap(B->btab, B->alt.btab);
+    std::swap(B->tab_resid, B->alt.tab_resid);
+    std::swap(B->tab_q_first, B->alt.tab_q_first);
+    std::swap(B->tab_q, B->alt.tab_q);
+    std::swap(B->ftab[0], B->alt.ftab0);
+    std::swap(B->mg, B->alt.mg);
+    for (to_problem* P : B->probs) pipe_swap(P);
+    B->parity ^= 1;
+}
+
+// the members' second sets and the tables over them (built with the sets swapped in)
+int build_alt(to_batch* B) {
+    for (to_problem* P : B->probs)
+        if (P->alt_alloc == 2 || pipe_alloc(P) != TO_OK) {
+            cudaGetLastError();
+            return TO_OK;   // no pipelining for this batch
+        }
+    if (cudaStreamCreateWithFlags(&B->dside, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&B->ev_dfork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&B->ev_djoin, cudaEventDisableTiming) != cudaSuccess)
+        return fail(TO_ERR_CUDA, "batch stream / event creation failed");
+    const int n = B->n;
+    for (to_problem* P : B->probs) pipe_swap(P);
+    // build the second tables into the live fields, then exchange the two
+    std::swap(B->btab, B->alt.btab);
+    std::swap(B->tab_resid, B->alt.tab_resid);
+    std::swap(B->tab_q_first, B->alt.tab_q_first);
+    std::swap(B->tab_q, B->alt.tab_q);
+    std::swap(B->ftab[0], B->alt.ftab0);
+    std::swap(B->mg, B->alt.mg);
+    void* kh = nullptr;
+    int mt = 0, ft = 0;
+    size_t fs = 0;
+    int rc = B->prec == TO_FP64 ? build_tables_t<double>(B) : build_tables_t<float>(B);
+    if (!rc) rc = op_tables_build(B->probs.data(), n, &B->tab_resid, &B->tab_q_first, &B->tab_q, &kh, &mt, B->kchunk);
+    free(kh);
+    if (!rc && B->alt.mg) rc = batch_mg_build(B->probs.data(), n, B->kchunk, &B->mg);
+    if (!rc) rc = filter_table_build(B->probs.data(), n, 0, &B->ftab[0], &ft, &fs);
+    std::swap(B->btab, B->alt.btab);
+    std::swap(B->tab_resid, B->alt.tab_resid);
+    std::swap(B->tab_q_first, B->alt.tab_q_first);
+    std::swap(B->tab_q, B->alt.tab_q);
+    std::swap(B->ftab[0], B->alt.ftab0);
+    std::swap(B->mg, B->alt.mg);
+    for (to_problem* P : B->probs) pipe_swap(P);
+    if (rc) return rc;
+    B->pipe = 1;
+    return TO_OK;
+}
+
 void destroy_batch(to_batch* B) {
     if (!B) return;
     if (B->stream) cudaStreamSynchronize(B->stream);
+    if (B->dside) cudaStreamSynchronize(B->dside);
     if (B->gexec) cudaGraphExecDestroy(B->gexec);
+    for (int p = 0; p < 2; ++p)
+        for (int f = 0; f < 2; ++f)
+            if (B->gexec_pipe[p][f]) cudaGraphExecDestroy(B->gexec_pipe[p][f]);
+    if (B->ev_dfork) cudaEventDestroy(B->ev_dfork);
+    if (B->ev_djoin) cudaEventDestroy(B->ev_djoin);
+    if (B->dside) cudaStreamDestroy(B->dside);
+    {
+        void* ps[] = {B->alt.btab, B->alt.tab_resid, B->alt.tab_q_first, B->alt.tab_q, B->alt.ftab0};
+        for (void* p : ps)
+            if (p) cudaFree(p);
+        batch_mg_free(B->alt.mg);
+    }
     if (B->ev_in) cudaEventDestroy(B->ev_in);
     if (B->ev_out) cudaEventDestroy(B->ev_out);
     if (B->stream) cudaStreamDestroy(B->stream);
@@ -375,6 +502,7 @@ extern "C" int to_batch_create(to_problem* const* problems, int32_t n, to_batch*
     if (!rc) rc = op_tables_build(B->probs.data(), n, &B->tab_resid, &B->tab_q_first, &B->tab_q, &B->kh, &B->max_tiles, B->kchunk);
     if (!rc && P0->prm.precond == TO_PRECOND_MG) rc = batch_mg_build(B->probs.data(), n, B->kchunk, &B->mg);
     for (int m = 0; m < 2 && !rc; ++m) rc = filter_table_build(B->probs.data(), n, m, &B->ftab[m], &B->ftiles[m], &B->fsmem[m]);
+    if (!rc) rc = build_alt(B);
     if (prev >= 0) cudaSetDevice(prev);
     if (rc) {
         destroy_batch(B);
@@ -404,10 +532,7 @@ extern "C" int to_batch_step(to_batch* B, int32_t n_outer, to_stats* stats_out, 
     if (!B) return fail(TO_ERR_ARG, "null batch");
     if (n_outer < 0) return fail(TO_ERR_ARG, "n_outer must be >= 0");
     if (n_outer == 0) return TO_OK;
-    for (to_problem* P : B->probs) {
-        P->fwd_id = 0;       // the outer iterations change every design
-        P->pipe_ready = 0;
-    }
+    for (to_problem* P : B->probs) P->fwd_id = 0;   // the outer iterations change every design
     for (to_problem* P : B->probs)
         if (n_outer > P->dstats_cap)
             return fail(TO_ERR_ARG, "n_outer exceeds a problem's stats ring (run to_step once with that many iterations "
@@ -425,7 +550,37 @@ extern "C" int to_batch_step(to_batch* B, int32_t n_outer, to_stats* stats_out, 
         else
             k_b_record<float><<<(B->n + 63) / 64, 64, 0, B->stream>>>((const BProb<float>*)B->btab, B->n, 1);
         TO_CUDA(cudaGetLastError());
-        if (B->graph_state == 0) {
+        if (B->pipe) {
+            // the first iteration computes the live sets unless the last batched step left them
+            bool fresh = false;
+            for (to_problem* P : B->probs) fresh = fresh || !P->pipe_ready;
+            for (to_problem* P : B->probs) P->pipe_ready = 0;
+            for (int i = 0; i < n_outer; ++i, fresh = false) {
+                const int p = B->parity, f = fresh ? 1 : 0;
+                if (B->pipe_state[p][f] == 0) {
+                    cudaGraph_t g = nullptr;
+                    B->pipe_state[p][f] = -1;
+                    if (cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+                        const int r2 = B->prec == TO_FP64 ? iteration_pipelined_t<double>(B, B->stream, fresh)
+                                                          : iteration_pipelined_t<float>(B, B->stream, fresh);
+                        if (cudaStreamEndCapture(B->stream, &g) == cudaSuccess && g && r2 == TO_OK &&
+                            cudaGraphInstantiate(&B->gexec_pipe[p][f], g, 0) == cudaSuccess)
+                            B->pipe_state[p][f] = 1;
+                        if (g) cudaGraphDestroy(g);
+                    }
+                    cudaGetLastError();
+                }
+                if (B->pipe_state[p][f] == 1) {
+                    TO_CUDA(cudaGraphLaunch(B->gexec_pipe[p][f], B->stream));
+                } else {
+                    const int r2 = B->prec == TO_FP64 ? iteration_pipelined_t<double>(B, B->stream, fresh)
+                                                      : iteration_pipelined_t<float>(B, B->stream, fresh);
+                    if (r2) return r2;
+                }
+                batch_swap(B);   // the sets built for the next designs are live from here on
+            }
+            for (to_problem* P : B->probs) P->pipe_ready = 1;
+        } else if (B->graph_state == 0) {
             cudaGraph_t g = nullptr;
             B->graph_state = -1;
             if (cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
@@ -437,7 +592,7 @@ extern "C" int to_batch_step(to_batch* B, int32_t n_outer, to_stats* stats_out, 
             }
             cudaGetLastError();
         }
-        for (int i = 0; i < n_outer; ++i) {
+        for (int i = 0; i < n_outer && !B->pipe; ++i) {
             if (B->graph_state == 1) {
                 TO_CUDA(cudaGraphLaunch(B->gexec, B->stream));
             } else {
@@ -445,6 +600,8 @@ extern "C" int to_batch_step(to_batch* B, int32_t n_outer, to_stats* stats_out, 
                 if (r2) return r2;
             }
         }
+        if (!B->pipe)
+            for (to_problem* P : B->probs) P->pipe_ready = 0;   // the moduli lag rho by one iteration here
         TO_CUDA(cudaEventRecord(B->ev_out, B->stream));
         TO_CUDA(cudaStreamWaitEvent(s, B->ev_out, 0));
         if (stats_out) {

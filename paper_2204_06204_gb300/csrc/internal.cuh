@@ -280,6 +280,8 @@ int batch_mg_build(to_problem* const* probs, int n, int kchunk, BatchMG** out);
 int batch_mg_refresh(const BatchMG* M, cudaStream_t s);
 int batch_mg_vcycle(const BatchMG* M, cudaStream_t s);
 int batch_mg_join(const BatchMG* M, cudaStream_t s);
+int batch_mg_refresh_inline(const BatchMG* M, cudaStream_t s);
+int batch_mg_wait(const BatchMG* M, cudaStream_t s);
 int batch_mg_launches(const BatchMG* M, int* refresh, int* vcycle);
 void batch_mg_free(BatchMG* M);
 

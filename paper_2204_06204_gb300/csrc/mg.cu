@@ -1647,6 +1647,17 @@ int batch_mg_refresh(const BatchMG* M, cudaStream_t s) {
     return M->prec == TO_FP64 ? batch_mg_run<double>(M, M->refresh, s, true) : batch_mg_run<float>(M, M->refresh, s, true);
 }
 
+// the whole refresh on s (a branch that its caller joins)
+int batch_mg_refresh_inline(const BatchMG* M, cudaStream_t s) {
+    return M->prec == TO_FP64 ? batch_mg_run<double>(M, M->refresh, s, false) : batch_mg_run<float>(M, M->refresh, s, false);
+}
+
+// make s wait for a pending refresh branch, leaving it pending for the coarse tails
+int batch_mg_wait(const BatchMG* M, cudaStream_t s) {
+    if (M->join_pending) TO_CUDA(cudaStreamWaitEvent(s, M->ev_join, 0));
+    return TO_OK;
+}
+
 // make s wait for a refresh branch that no coarse tail has joined yet
 int batch_mg_join(const BatchMG* M, cudaStream_t s) {
     if (M->join_pending) {
