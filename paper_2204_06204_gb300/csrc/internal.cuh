@@ -199,7 +199,7 @@ struct to_problem {
     int pipe_state[2][2] = {{0, 0}, {0, 0}};   // as graph_state, per set and variant
     int pipe_ready = 0;            // the live set belongs to the current rho (a pipelined to_step left it)
     int in_batch = 0;              // a batch's tables hold this problem's buffers: no swapping
-    int coarse_wait = 1;           // coarse solves wait for the forked inverse (ev_join)
+    int coarse_wait = 0;           // a forked coarsest inverse may still run: coarse solves wait for ev_join
 
     // launch configuration of the operator kernel; resident CTAs per SM of each mode
     int tile_x = 32, tile_y = 8, tile_z = 8;

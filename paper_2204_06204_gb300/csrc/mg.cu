@@ -997,6 +997,7 @@ static int refresh_t(to_problem* P, cudaStream_t s, bool join, bool inline_inv) 
     // outside the outer iteration nothing else joins the branch: without this a later
     // refresh could rewrite coarse_A / coarse_L while this inverse still runs
     if (join) TO_CUDA(cudaStreamWaitEvent(main_s, P->ev_join, 0));
+    P->coarse_wait = join ? 0 : 1;   // the coarse solves on main_s join it
     return TO_OK;
 }
 

@@ -330,6 +330,7 @@ int outer_iteration(to_problem* P, cudaStream_t s) {
     TO_CUDA(cudaEventRecord(P->ev_djoin, P->dside));
     if ((rc = run_inner(P, P->u, P->prm.n_inner, 1, s, 1))) return rc;
     if (P->prm.precond == TO_PRECOND_MG) TO_CUDA(cudaStreamWaitEvent(s, P->ev_join, 0));
+    P->coarse_wait = 0;
     TO_CUDA(cudaStreamWaitEvent(s, P->ev_djoin, 0));
     return launch_record(P, s);
 }
@@ -362,7 +363,7 @@ int outer_iteration_pipelined(to_problem* P, cudaStream_t s, bool fresh) {
     TO_CUDA(cudaEventRecord(P->ev_djoin, P->dside));
     P->coarse_wait = fresh ? 1 : 0;   // else the live inverse was completed before this iteration
     rc = run_inner(P, P->u, P->prm.n_inner, 1, s, 1);
-    P->coarse_wait = 1;
+    P->coarse_wait = 0;               // joined below (fresh: through the design branch)
     if (rc) return rc;
     TO_CUDA(cudaStreamWaitEvent(s, P->ev_djoin, 0));
     return launch_record(P, s);

@@ -1,0 +1,115 @@
+"""The pipelined outer iteration (the next design's moduli, diagonals and coarsest
+inverse built on a branch beside the lower-level steps, into a second buffer set) is
+scheduling only: every call pattern of to_step gives the same iterates bit for bit,
+and after a step the live moduli are those of the current design.  Workloads: 32x16x16
+cantilever (multigrid: two launched levels and the coarse tail) and 16x8x8 (Jacobi)."""
+import numpy as np
+import pytest
+
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _fb():
+    import __graft_entry__ as g
+    g.build()
+    import paper_2204_06204_gb300 as fb
+    return fb
+
+
+CASES = {
+    "mg": (lambda: W.cantilever(32, 16, 16), "TO_PRECOND_MG", 2),
+    "jacobi": (lambda: W.cantilever(16, 8, 8), "TO_PRECOND_JACOBI", 5),
+}
+
+
+def _params(fb, case, precision):
+    _, pre, n_inner = CASES[case]
+    prec = fb.TO_FP64 if precision == "fp64" else fb.TO_FP32_MIXED
+    return fb.to_default_params(precision=prec, precond=getattr(fb, pre), n_inner=n_inner)
+
+
+def _run(fb, case, precision, pattern):
+    """pattern: list of ("step", n) / ("reset",) / ("probe",) applied in order."""
+    pb = CASES[case][0]()
+    stats = []
+    with fb.Problem.from_workload(pb, _params(fb, case, precision)) as P:
+        for op in pattern:
+            if op[0] == "step":
+                stats += P.step(op[1])
+            elif op[0] == "reset":   # the same state written back: the next step starts afresh
+                rho, u, k, a0 = P.get_state()
+                P.set_state(rho, u, k, a0)
+            else:                    # read-only calls between steps
+                rho, u, k, a0 = P.get_state()
+                P.apply_K(u)
+                P.inner_solve(u.clone(), 0, want_res=True)
+        rho, u, k, a0 = P.get_state()
+        return rho.cpu(), u.cpu(), k, a0, [(s["J"], s["beta_first"], s["lambda"], s["volume"]) for s in stats]
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_call_patterns_agree_bitwise(case, precision):
+    fb = _fb()
+    ref = _run(fb, case, precision, [("step", 6)])
+    for pattern in ([("step", 1)] * 6,
+                    [("step", 2), ("step", 1), ("step", 3)],
+                    [("step", 2), ("reset",), ("step", 1), ("probe",), ("step", 3)]):
+        got = _run(fb, case, precision, pattern)
+        assert torch.equal(ref[0], got[0]) and torch.equal(ref[1], got[1]), pattern
+        assert ref[2] == got[2] == 7 and ref[3] == got[3]
+        assert ref[4] == got[4], pattern
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_live_moduli_belong_to_the_current_design(precision):
+    """After to_step the operator is K(rho) of the design to_step left: the same K u as a
+    problem given that design directly."""
+    fb = _fb()
+    pb = CASES["mg"][0]()
+    prm = _params(fb, "mg", precision)
+    with fb.Problem.from_workload(pb, prm) as P:
+        P.step(3)
+        rho, u, k, a0 = P.get_state()
+        y1 = P.apply_K(u).cpu()
+    with fb.Problem.from_workload(pb, prm) as Q:
+        Q.set_design(rho)
+        y2 = Q.apply_K(u).cpu()
+    assert torch.equal(y1, y2)
+
+
+def test_batched_call_patterns_agree_bitwise():
+    """The pipelined batched iteration: one call of 4 iterations, four calls of one, and
+    a member's state rewritten between calls (the next call starts afresh) agree."""
+    fb = _fb()
+    pbs = [W.cantilever(16, 8, 8), W.cantilever(32, 16, 16), W.cantilever(16, 16, 16)]
+    prm = fb.to_default_params(precision=fb.TO_FP32_MIXED, precond=fb.TO_PRECOND_MG, n_inner=2, tile_z=8)
+
+    def run(pattern):
+        probs = [fb.Problem.from_workload(pb, prm) for pb in pbs]
+        try:
+            B = fb.Batch(probs)
+            try:
+                for op in pattern:
+                    if op[0] == "step":
+                        B.step(op[1], want_stats=False)
+                    else:
+                        torch.cuda.synchronize()
+                        rho, u, k, a0 = probs[1].get_state()
+                        probs[1].set_state(rho, u, k, a0)
+                torch.cuda.synchronize()
+                return [tuple(x.cpu() if torch.is_tensor(x) else x for x in P.get_state()) for P in probs]
+            finally:
+                B.close()
+        finally:
+            for P in probs:
+                P.close()
+
+    ref = run([("step", 4)])
+    for pattern in ([("step", 1)] * 4, [("step", 2), ("reset",), ("step", 2)]):
+        got = run(pattern)
+        for a, b in zip(ref, got):
+            assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1]) and a[2] == b[2] and a[3] == b[3]
