@@ -30,7 +30,7 @@ L2_FLUSH_BYTES = 512 << 20       # > 129 MB L2: written between timed steps
 # DRAM bytes (read + written) of one K(rho)u launch at 128x64x64, FP32, from one ncu capture of the current
 # operator kernel (dram__bytes_read.sum + dram__bytes_write.sum); below the algorithmic bytes because the
 # working set stays in L2.  Set to None whenever the operator kernel changes until it is measured again.
-APPLY_TRAFFIC_128 = 9238784
+APPLY_TRAFFIC_128 = 9249536
 
 
 def parse():
