@@ -262,7 +262,15 @@ int to_project(to_problem* P, const void* w_dev, void* rho_dev, double* lambda_o
 /* Run n_outer outer iterations (Algorithms 1 / 3 with the problem's M) on the
  * problem's own state (rho_k, u_k, k).  If stats_out is not NULL it receives
  * n_outer records and the call synchronises; the return value then also
- * reports device-side errors.  Without stats_out nothing is copied back. */
+ * reports device-side errors.  Without stats_out nothing is copied back.
+ * Each iteration builds the next design's moduli and preconditioner beside its
+ * own lower-level steps (in a second buffer set, allocated on the first call:
+ * one more copy of rho~, E', every level's moduli and 1 / d and the coarsest
+ * inverse); the iterates are those of the sequential order, bit for bit.  On
+ * return the operator of to_apply_K, to_inner_solve and to_sensitivity is that of
+ * the returned design rho_{k+n}.  With mg_legs = 1, or while the problem belongs
+ * to a batch, the iterations run in the sequential order and the moduli on return
+ * are those of rho_{k+n-1}. */
 int to_step(to_problem* P, int32_t n_outer, to_stats* stats_out, void* stream);
 
 /* Read / write the outer state: rho (n_elem), u (n_dof), the 1-based iteration
