@@ -53,8 +53,9 @@ def parse():
     ap.add_argument("--apply-only", nargs=3, type=int, metavar=("NX", "NY", "NZ"),
                     help="time only K(rho)u on a cantilever of this size (random design), FP32-mixed")
     ap.add_argument("--fp64", action="store_true", help="with --apply-only: the plain FP64 operator")
-    ap.add_argument("--op-kernel", type=int, default=0, choices=[0, 1],
-                    help="operator kernel: 0 the general kernel (default), 1 the TMA-staged FP32 kernel")
+    ap.add_argument("--op-kernel", type=int, default=0, choices=[0, 1, 2],
+                    help="operator kernel: 0 the general kernel (default), 1 the TMA-staged FP32 kernel, "
+                         "2 the tensor-core FP32 kernel")
     ap.add_argument("--mg-legs", type=int, default=0, choices=[0, 1],
                     help="multigrid levels below the fine grid: 0 one launch per step, 1 two cooperative launches per V-cycle")
     ap.add_argument("--oracle-worker", nargs=3, metavar=("WARM", "ITERS", "BUDGET_S"), help=argparse.SUPPRESS)
@@ -623,27 +624,34 @@ def main():
         tam = a_.elapsed_time(b_) / 1000.0 / 10
         bytes_m = 2 * 3 * pbm.n_node * 4 + pbm.n_elem * 4 + pbm.n_node
         Pm.close()
-        # the same apply with the TMA-staged FP32 kernel (op_kernel 1), same design and input
-        prm_t = fb.to_default_params(precision=fb.TO_FP32_MIXED, precond=fb.TO_PRECOND_MG, n_inner=2, op_kernel=1)
-        Pt = fb.Problem.from_workload(pbm, prm_t, device=local)
-        Pt.set_design(Pm_rho)
-        yt = Pt.dof()
-        for _ in range(3):
-            Pt.apply_K(um, yt)
-        a_.record(stream)
-        for _ in range(10):
-            Pt.apply_K(um, yt)
-        b_.record(stream)
-        torch.cuda.synchronize()
-        tam_tma = a_.elapsed_time(b_) / 1000.0 / 10
-        Pt.close()
-        del yt
+        # the same apply with the TMA-staged (op_kernel 1) and the tensor-core (op_kernel 2) FP32
+        # kernels, same design and input
+        tam_alt = {}
+        for okern in (1, 2):
+            prm_t = fb.to_default_params(precision=fb.TO_FP32_MIXED, precond=fb.TO_PRECOND_MG, n_inner=2,
+                                         op_kernel=okern)
+            Pt = fb.Problem.from_workload(pbm, prm_t, device=local)
+            Pt.set_design(Pm_rho)
+            yt = Pt.dof()
+            for _ in range(3):
+                Pt.apply_K(um, yt)
+            a_.record(stream)
+            for _ in range(10):
+                Pt.apply_K(um, yt)
+            b_.record(stream)
+            torch.cuda.synchronize()
+            tam_alt[okern] = a_.elapsed_time(b_) / 1000.0 / 10
+            Pt.close()
+            del yt
+        tam_tma, tam_tc = tam_alt[1], tam_alt[2]
         mbb = {"workload": "MBB half model 512x256x256 (101,649,411 DOFs), volfrac 0.15, r = 2.5, FP32-mixed, "
                            "MG-preconditioned steepest descent x2 (inputs far larger than L2)",
                "outer_iters_per_s": km / tm, "ms_per_iter": tm * 1e3 / km,
                "apply_K_us": tam * 1e6, "apply_gdofs": pbm.n_dof / tam / 1e9,
                "apply_GBs": bytes_m / tam / 1e9, "apply_frac_of_hbm": bytes_m / tam / 1e9 / hbm,
-               "apply_K_us_tma_kernel": tam_tma * 1e6, "apply_frac_of_hbm_tma_kernel": bytes_m / tam_tma / 1e9 / hbm}
+               "apply_K_us_tma_kernel": tam_tma * 1e6, "apply_frac_of_hbm_tma_kernel": bytes_m / tam_tma / 1e9 / hbm,
+               "apply_K_us_tensor_core_kernel": tam_tc * 1e6,
+               "apply_frac_of_hbm_tensor_core_kernel": bytes_m / tam_tc / 1e9 / hbm}
         del um, ym, Pm_rho
 
     # max over ranks (the timed region and the end-to-end loop)

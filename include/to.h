@@ -147,8 +147,14 @@ typedef struct {
  *               1: FP32 problems run the TMA-staged kernel (64 x 8 node tiles, element
  *               pairs in packed FP32x2, persistent CTAs) wherever its vectors are
  *               16-byte aligned, its copy coordinates fit 32 bits and the grid spans
- *               its copy boxes, else the general kernel.  FP64 problems and batches
- *               always use the general kernel.  Both give the same K^ x up to rounding
+ *               its copy boxes, else the general kernel;  2: FP32 problems run the
+ *               tensor-core kernel (the element contraction as tcgen05.mma on split-BF16
+ *               operands with FP32 accumulation in tensor memory, 31 x 7 node tiles;
+ *               about 2^-17 per product term instead of FP32's 2^-24: within the 1e-5
+ *               operator tolerance, not within the multigrid trajectory's) where the GPU
+ *               holds its shared and tensor memory, else the general kernel.  FP64
+ *               problems and batches always use the general kernel.  All give the same
+ *               K^ x up to rounding
  *   mg_legs     0 (default): the multigrid levels between the fine grid and the one-CTA
  *               coarse tail run one launch per step; 1: as two cooperative launches per
  *               V-cycle (the down leg's smoothing, residuals and restrictions, the up leg's

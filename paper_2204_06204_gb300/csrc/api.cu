@@ -99,7 +99,7 @@ static int validate(const to_grid* g, const to_material* m, const to_loads* L, c
     if (p->precond == TO_PRECOND_KRYLOV && (p->krylov_dim < 0 || p->krylov_dim > 30))
         return fail(TO_ERR_ARG, "krylov_dim must lie in [0, 30]");
     if (p->adj_stride < -1) return fail(TO_ERR_ARG, "adj_stride must be >= -1");
-    if (p->op_kernel != 0 && p->op_kernel != 1) return fail(TO_ERR_ARG, "op_kernel must be 0 or 1");
+    if (p->op_kernel < 0 || p->op_kernel > 2) return fail(TO_ERR_ARG, "op_kernel must be 0, 1 or 2");
     if (p->inner_mode < TO_INNER_SD || p->inner_mode > TO_INNER_PCG) return fail(TO_ERR_ARG, "bad inner mode");
     if (p->n_inner < 0) return fail(TO_ERR_ARG, "n_inner must be >= 0");
     if (!(p->m >= 0.0)) return fail(TO_ERR_ARG, "alpha exponent m must be >= 0");
@@ -130,6 +130,7 @@ extern "C" void to_destroy(to_problem* P) {
         dfree(tm);
         void* tm64 = L.tmask64;
         dfree(tm64);
+        dfree(L.tcb);
         dfree(L.x);
         dfree(L.b);
         dfree(L.t);
@@ -329,7 +330,7 @@ extern "C" int to_create(const to_grid* g, const to_material* m, const to_loads*
         cudaStreamDestroy(s);
         return bail(rc);
     }
-    if ((rc = project_cluster_setup(P))) {
+    if ((rc = project_cluster_setup(P)) || (rc = operator_tc_build(P))) {
         cudaStreamDestroy(s);
         return bail(rc);
     }

@@ -83,6 +83,7 @@ struct Level {
     uint8_t* mask = nullptr;  // per node: bit c set = DOF c fixed
     uint8_t* tmask = nullptr; // per operator tile column: any fixed node in its footprint
     uint8_t* tmask64 = nullptr; // the same for the 64 x kTmaTileY tiles of the TMA operator
+    void* tcb = nullptr;      // element matrix of edge h as split BF16 pieces (tensor-core operator)
     void* x = nullptr;        // V-cycle vectors (T)
     void* b = nullptr;
     void* t = nullptr;
@@ -206,6 +207,8 @@ struct to_problem {
     int op_occ[5] = {0, 0, 0, 0, 0};
     int tma_occ[5] = {0, 0, 0, 0, 0};  // the FP32 TMA operator: resident CTAs per SM of each mode
     int tma_ready = 0;                 // its shared-memory opt-ins are set
+    int tc_occ[5] = {0, 0, 0, 0, 0};   // the tensor-core FP32 operator: resident CTAs per SM of each mode
+    int tc_ready = 0;                  // its shared-memory opt-ins are set and tensor memory suffices
     int num_sms = 0;
     int coop_blocks = 0;           // co-resident blocks for the projection kernel
 };
@@ -246,6 +249,12 @@ bool operator_tma_applicable(const to_problem* P, int level, const void* x, cons
 int launch_operator_tma(to_problem* P, int level, int mode, const void* x, void* y, const void* b, cudaStream_t s,
                         double omega, int first, const OpOut* out);
 int build_tile_mask64(Level& L, const uint8_t* mask_host);
+// the FP32 operator with the element contraction on the tensor cores (optc.cu)
+int operator_tc_init(to_problem* P);
+int operator_tc_build(to_problem* P);
+bool operator_tc_applicable(const to_problem* P, int level);
+int launch_operator_tc(to_problem* P, int level, int mode, const void* x, void* y, const void* b, cudaStream_t s,
+                       double omega, int first, const OpOut* out);
 int project_cluster_setup(to_problem* P);
 int krylov_build(to_problem* P);
 int operator_autotune(to_problem* P, cudaStream_t s);

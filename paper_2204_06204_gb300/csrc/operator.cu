@@ -802,7 +802,7 @@ static int legs_build_t(to_problem* P) {
 
 int mg_legs_build(to_problem* P) {
     P->legs_grid = 0;
-    if (P->prm.precond != TO_PRECOND_MG || P->prm.mg_legs == 0 || P->prm.op_kernel == 1 || P->mg_tail < 2) return TO_OK;
+    if (P->prm.precond != TO_PRECOND_MG || P->prm.mg_legs == 0 || P->prm.op_kernel != 0 || P->mg_tail < 2) return TO_OK;
     return P->prec == TO_FP64 ? legs_build_t<double>(P) : legs_build_t<float>(P);
 }
 
@@ -846,7 +846,8 @@ static int init_t(to_problem* P) {
 int operator_init(to_problem* P) {
     if (P->prec == TO_FP64) return init_t<double, 32, 8>(P);
     int rc = init_t<float, 32, 8>(P);
-    return rc ? rc : operator_tma_init(P);
+    if (!rc) rc = operator_tma_init(P);
+    return rc ? rc : operator_tc_init(P);
 }
 
 // Tile autotuner of a problem's operator: for every multigrid level (or the fine grid
@@ -961,6 +962,7 @@ int build_tile_mask(Level& L, const uint8_t* mask_host) {
 int launch_operator(to_problem* P, int level, int mode, const void* x, void* y, const void* b,
                     cudaStream_t s, double omega, int first, const OpOut* out) {
     if (operator_tma_applicable(P, level, x, y, b)) return launch_operator_tma(P, level, mode, x, y, b, s, omega, first, out);
+    if (operator_tc_applicable(P, level)) return launch_operator_tc(P, level, mode, x, y, b, s, omega, first, out);
     if (P->prec == TO_FP64) return launch_t<double, 32, 8>(P, level, mode, x, y, b, s, omega, first, out);
     return launch_t<float, 32, 8>(P, level, mode, x, y, b, s, omega, first, out);
 }

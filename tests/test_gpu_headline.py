@@ -199,7 +199,7 @@ def _full_size_problem(fb, op_kernel=0):
     return pb, P, Ee, Ed, Hs
 
 
-@pytest.mark.parametrize("op_kernel", [0, 1])
+@pytest.mark.parametrize("op_kernel", [0, 1, 2])
 def test_residual_epilogue_full_size_sampled(op_kernel):
     fb = _fb()
     pb, P, Ee, Ed, Hs = _full_size_problem(fb, op_kernel)
@@ -232,7 +232,7 @@ def test_residual_epilogue_full_size_sampled(op_kernel):
     assert abs(sc["fu"] - fu) <= 1e-5 * float(np.abs(f * u).sum())
 
 
-@pytest.mark.parametrize("op_kernel", [0, 1])
+@pytest.mark.parametrize("op_kernel", [0, 1, 2])
 def test_smoothing_epilogue_full_size_sampled(op_kernel):
     fb = _fb()
     pb, P, Ee, Ed, Hs = _full_size_problem(fb, op_kernel)

@@ -41,7 +41,8 @@ TMA_GRIDS = [(17, 9, 5), (32, 16, 16), (40, 20, 9), (64, 8, 8), (65, 9, 3), (100
 
 
 @pytest.mark.parametrize("dims,precision,op_kernel",
-                         [(d, p, 0) for d in GRIDS for p in ("fp64", "fp32")] + [(d, "fp32", 1) for d in TMA_GRIDS])
+                         [(d, p, 0) for d in GRIDS for p in ("fp64", "fp32")] + [(d, "fp32", 1) for d in TMA_GRIDS]
+                         + [(d, "fp32", 2) for d in GRIDS + TMA_GRIDS[2:]])
 def test_apply_K_matches_assembled_operator(dims, precision, op_kernel):
     fb = _fb()
     pb = W.cantilever(*dims)
@@ -63,6 +64,26 @@ def test_apply_K_matches_assembled_operator(dims, precision, op_kernel):
                 Kabs = abs(K)
                 scale = np.linalg.norm(Kabs @ np.abs(u))
                 assert np.linalg.norm(y - yref) / scale <= 1e-5
+
+
+def test_tensor_core_operator_is_the_kernel_that_runs():
+    """op_kernel 2 computes K^ x with split-BF16 products on the tensor cores: within the
+    FP32 tolerance of the general kernel's result, but not bitwise equal to it (a silent
+    fall-back to the general kernel would be)."""
+    fb = _fb()
+    pb = W.cantilever(40, 20, 9)
+    pb.rho0 = W.random_rho(pb.n_elem, 0.0, 1.0)
+    u = W.random_u(pb.n_dof, seed=7)
+    ys = []
+    for ok in (0, 2):
+        with _problem(pb, fb.TO_FP32_MIXED, op_kernel=ok) as P:
+            P.set_design(_t(pb.rho0, P))
+            ys.append(P.apply_K(_t(u, P)).cpu().numpy().astype(np.float64))
+    S = outer.Setup(pb)
+    _, Ee_ref, _ = S.moduli(pb.rho0)
+    scale = np.linalg.norm(abs(S.K(Ee_ref)) @ np.abs(u))
+    assert np.linalg.norm(ys[1] - ys[0]) / scale <= 1e-5
+    assert not np.array_equal(ys[0], ys[1])
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
@@ -190,7 +211,7 @@ def test_outer_loop_fp64_matches_oracle_cantilever_32x16x16():
         assert abs(s["res_inf"] - h["res_inf"]) <= 1e-8 * max(h["res_inf"], 1e-30)
 
 
-@pytest.mark.parametrize("op_kernel", [0, 1])
+@pytest.mark.parametrize("op_kernel", [0, 1, 2])
 def test_outer_loop_fp32_mixed_matches_oracle_compliance(op_kernel):
     fb = _fb()
     pb = W.cantilever_32x16x16()
