@@ -643,20 +643,23 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_mg_legs(const L
                 __syncthreads();   // the next tile reuses the shared-memory ring
             }
         } else if (st.kind == LEG_RESTRICT) {
+            // node indices in 32 bits (the legs are built only while the fine level has fewer
+            // than 2^31 nodes): unsigned divisions instead of 64-bit ones
             const T* tf = st.src ? st.src : fine_src;
-            const int nxc = st.cx + 1, nyc = st.cy + 1;
-            const long long n = (long long)nxc * nyc * (st.cz + 1);
-            for (long long i = blockIdx.x * 256LL + tid; i < n; i += (long long)gridDim.x * 256) {
-                const int I = (int)(i % nxc), J = (int)((i / nxc) % nyc), K = (int)(i / ((long long)nxc * nyc));
-                restrict_node<T, int, true>(st.cx, st.cy, st.cz, I, J, K, tf, st.mf, st.mc, st.dst, st.dc, st.xc, st.omega);
+            const unsigned nxc = st.cx + 1, nxyc = nxc * (unsigned)(st.cy + 1);
+            const unsigned n = nxyc * (unsigned)(st.cz + 1);
+            for (unsigned i = blockIdx.x * 256u + tid; i < n; i += gridDim.x * 256u) {
+                const unsigned K = i / nxyc, r = i - K * nxyc, J = r / nxc, I = r - J * nxc;
+                restrict_node<T, int, true>(st.cx, st.cy, st.cz, (int)I, (int)J, (int)K, tf, st.mf, st.mc, st.dst, st.dc,
+                                            st.xc, st.omega);
             }
         } else {
             T* xf = st.dst ? st.dst : fine_dst;
-            const int nxf = 2 * st.cx + 1, nyf = 2 * st.cy + 1;
-            const long long n = (long long)nxf * nyf * (2 * st.cz + 1);
-            for (long long i = blockIdx.x * 256LL + tid; i < n; i += (long long)gridDim.x * 256) {
-                const int x = (int)(i % nxf), y = (int)((i / nxf) % nyf), z = (int)(i / ((long long)nxf * nyf));
-                prolong_node<T, int>(st.cx, st.cy, st.cz, x, y, z, st.src, st.mc, st.mf, xf);
+            const unsigned nxf = 2 * st.cx + 1, nxyf = nxf * (unsigned)(2 * st.cy + 1);
+            const unsigned n = nxyf * (unsigned)(2 * st.cz + 1);
+            for (unsigned i = blockIdx.x * 256u + tid; i < n; i += gridDim.x * 256u) {
+                const unsigned z = i / nxyf, r = i - z * nxyf, y = r / nxf, x = r - y * nxf;
+                prolong_node<T, int>(st.cx, st.cy, st.cz, (int)x, (int)y, (int)z, st.src, st.mc, st.mf, xf);
             }
         }
         if (q + 1 < nsteps && !grid_barrier(bar, err)) return;
@@ -803,6 +806,7 @@ static int legs_build_t(to_problem* P) {
 int mg_legs_build(to_problem* P) {
     P->legs_grid = 0;
     if (P->prm.precond != TO_PRECOND_MG || P->prm.mg_legs == 0 || P->prm.op_kernel != 0 || P->mg_tail < 2) return TO_OK;
+    if (P->lv[0].n_node >= (1LL << 31)) return TO_OK;   // the legs index nodes in 32 bits
     return P->prec == TO_FP64 ? legs_build_t<double>(P) : legs_build_t<float>(P);
 }
 
