@@ -16,6 +16,7 @@ kernel measured live with CUDA events on the launching stream.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import os
 import subprocess
@@ -373,7 +374,10 @@ def main():
     # --- end to end through the C ABI with host buffers: rho in, rho + stats out each step.
     # Two pinned host buffers take turns: step i reads its design from one and leaves the
     # new design in the other, which is the next step's input (no host-side copy).
+    # Everything of a step is enqueued first (design in, state set, the iteration, design
+    # and the step's stats record out) and the step ends with one synchronisation.
     rho_hb = [torch.empty(pb.n_elem, dtype=torch.float32, pin_memory=True) for _ in range(2)]
+    stats_h = torch.empty(ctypes.sizeof(fb.to_stats), dtype=torch.uint8, pin_memory=True)
     rho_d, u_d, k_d, a0_d = P32.get_state()
     rho_hb[0].copy_(rho_d)
     ke = max(3, min(args.steps, 20))
@@ -383,10 +387,14 @@ def main():
         rho_in, rho_out = rho_hb[i % 2], rho_hb[(i + 1) % 2]
         rho_d.copy_(rho_in, non_blocking=True)
         fb.to_set_state(P32, rho_d, None, k_d + i, a0_d)
-        st = P32.step(1, want_stats=True)       # synchronises: stats come back to the host
-        fb.to_get_state(P32, rho_d, None)
+        P32.step(1, want_stats=False)
+        fb.to_get_state(P32, rho_d, None, scalars=False)
         rho_out.copy_(rho_d, non_blocking=True)
+        fb.to_get_stats(P32, 1, stats_h)
         torch.cuda.synchronize()
+        rec = fb.to_stats.from_address(stats_h.data_ptr())
+        if rec.status:
+            raise RuntimeError(f"device-side error {rec.status} in the end-to-end loop")
     t_e2e = time.perf_counter() - t0
 
     # --- differentiable compliance: forward + backward through T = 5 Jacobi steps, 256x128x128, FP32
@@ -703,7 +711,7 @@ def main():
                      "algorithmic_bytes": apply_bytes(s_el),
                      "peak_source": "MEASURED_PEAKS.json hbm_gbs" if pk else "fallback 6800"},
         "e2e": {"value": job_rate(ke, t_e2e, world), "unit": "outer_iters/s", "h2d_bytes_per_step": pb.n_elem * 4,
-                "d2h_bytes_per_step": pb.n_elem * 4 + 96},
+                "d2h_bytes_per_step": pb.n_elem * 4 + ctypes.sizeof(fb.to_stats)},
         "gpu_launches": launches_per_step * args.steps * world,
         "clocks": clk.summary(),
         "cpu_baseline": cpu,

@@ -279,6 +279,17 @@ int to_project(to_problem* P, const void* w_dev, void* rho_dev, double* lambda_o
  * are those of rho_{k+n-1}. */
 int to_step(to_problem* P, int32_t n_outer, to_stats* stats_out, void* stream);
 
+/* The records of the first n outer iterations of the last to_step call (1 <= n <=
+ * its n_outer), copied into stats_out (host memory for n records) asynchronously on
+ * `stream`, ordered after that call when the stream is the same: for a caller that
+ * reads a step's results without the synchronisation to_step does for stats_out (to_step
+ * with stats_out = NULL, then this, then one synchronisation of its own).  The copy is
+ * asynchronous when stats_out is page-locked.  Device-side errors appear in each
+ * record's status once the stream has completed; this call reports none itself.
+ * TO_ERR_ARG for a null stats_out or n outside that range.  Not in the paper: an
+ * interface convenience. */
+int to_get_stats(to_problem* P, int32_t n, to_stats* stats_out, void* stream);
+
 /* Read / write the outer state: rho (n_elem), u (n_dof), the 1-based iteration
  * counter k and alpha0 (<= 0 means not yet fixed).  Any pointer may be NULL to
  * skip that part.  to_set_state recomputes rho~ and the moduli. */

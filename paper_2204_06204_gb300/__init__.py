@@ -20,7 +20,7 @@ from ._abi import (TO_FP32_MIXED, TO_FP64, TO_INNER_PCG, TO_INNER_PFBTO, TO_INNE
 
 __all__ = ["to_default_params", "to_create", "to_destroy", "to_sizes", "to_set_design", "to_apply_K",
            "to_residual", "to_smooth",
-           "to_inner_solve", "to_sensitivity", "to_filter", "to_project", "to_step", "to_get_state",
+           "to_inner_solve", "to_sensitivity", "to_filter", "to_project", "to_step", "to_get_stats", "to_get_state",
            "to_set_state", "to_check", "to_barrier_selftest", "to_last_error", "to_project_noalloc", "to_compliance_truncated",
            "to_compliance_truncated_grad", "to_compliance_truncated_id", "to_batch_create", "to_batch_destroy", "to_batch_step", "to_batch_tile", "Batch",
            "Problem", "ToError",
@@ -246,11 +246,25 @@ def to_step(P, n_outer=1, want_stats=True):
     return None
 
 
-def to_get_state(P, rho=None, u=None):
+def to_get_state(P, rho=None, u=None, scalars=True):
+    """Copy rho and u out; with scalars (the default) also return (k, alpha0), which makes the
+    call synchronise; without them the copies stay asynchronous on the current stream."""
+    if not scalars:
+        _abi.check(_lib().to_get_state(_h(P), _ptr(rho, _dt(P), P.n_elem, "rho"), _ptr(u, _dt(P), P.n_dof, "u"),
+                                       None, None, _stream(P.device)))
+        return None
     k, a0 = C.c_int64(), C.c_double()
     _abi.check(_lib().to_get_state(_h(P), _ptr(rho, _dt(P), P.n_elem, "rho"), _ptr(u, _dt(P), P.n_dof, "u"),
                                    C.byref(k), C.byref(a0), _stream(P.device)))
     return k.value, a0.value
+
+
+def to_get_stats(P, n, out):
+    """Enqueue the copy of the last to_step call's first n records into `out` (host memory
+    of n to_stats records: a pointer, or a buffer with data_ptr(), e.g. a pinned uint8
+    tensor) on the current stream; read it after synchronising (to_stats.from_address)."""
+    ptr = out.data_ptr() if hasattr(out, "data_ptr") else int(out)
+    _abi.check(_lib().to_get_stats(_h(P), int(n), C.c_void_p(ptr), _stream(P.device)))
 
 
 def to_set_state(P, rho=None, u=None, k=1, alpha0=0.0):

@@ -69,6 +69,7 @@ SIGNATURES = {
     "to_filter": (C.c_int, [P, P, P, C.c_int32, P]),
     "to_project": (C.c_int, [P, P, P, C.POINTER(C.c_double), P]),
     "to_step": (C.c_int, [P, C.c_int32, C.POINTER(to_stats), P]),
+    "to_get_stats": (C.c_int, [P, C.c_int32, P, P]),
     "to_get_state": (C.c_int, [P, P, P, C.POINTER(C.c_int64), C.POINTER(C.c_double), P]),
     "to_set_state": (C.c_int, [P, P, P, C.c_int64, C.c_double, P]),
     "to_check": (C.c_int, [P, P]),

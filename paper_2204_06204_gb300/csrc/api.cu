@@ -603,12 +603,21 @@ extern "C" int to_step(to_problem* P, int32_t n_outer, to_stats* stats_out, void
     P->precond_stale = 0;   // the last iteration refreshed it for its own moduli (pipelined: for rho)
     TO_CUDA(cudaEventRecord(P->ev_out, P->gstream));
     TO_CUDA(cudaStreamWaitEvent(s, P->ev_out, 0));
+    P->last_step_n = n_outer;
     if (stats_out) {
         TO_CUDA(cudaMemcpyAsync(stats_out, P->dstats, sizeof(to_stats) * (size_t)n_outer, cudaMemcpyDeviceToHost, s));
         TO_CUDA(cudaStreamSynchronize(s));
         for (int i = 0; i < n_outer; ++i)
             if (stats_out[i].status) return fail(stats_out[i].status, "device-side error during the outer iterations");
     }
+    return TO_OK;
+}
+
+extern "C" int to_get_stats(to_problem* P, int32_t n, to_stats* stats_out, void* stream) {
+    TO_ENTER(P);
+    if (!stats_out) return fail(TO_ERR_ARG, "stats_out is null");
+    if (n < 1 || n > P->last_step_n) return fail(TO_ERR_ARG, "n must lie in [1, n_outer of the last to_step call]");
+    TO_CUDA(cudaMemcpyAsync(stats_out, P->dstats, sizeof(to_stats) * (size_t)n, cudaMemcpyDeviceToHost, s));
     return TO_OK;
 }
 

@@ -161,6 +161,7 @@ struct to_problem {
     unsigned* counters = nullptr;
     to_stats* dstats = nullptr;    // device stats ring
     int dstats_cap = 0;
+    int last_step_n = 0;           // outer iterations of the last to_step call (its records: slots 0 .. n - 1)
 
     // truncated-solve iterates u_0 .. u_T kept for the reverse sweep
     void* iters = nullptr;

@@ -113,3 +113,26 @@ def test_batched_call_patterns_agree_bitwise():
         got = run(pattern)
         for a, b in zip(ref, got):
             assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1]) and a[2] == b[2] and a[3] == b[3]
+
+
+def test_get_stats_reads_the_last_step_records_without_a_synchronising_step():
+    """to_get_stats after to_step(stats_out = NULL) delivers the records to_step itself
+    returns with stats_out, field for field; n outside [1, the last call's n_outer] is
+    refused."""
+    import ctypes
+    fb = _fb()
+    pb = W.cantilever(32, 16, 16)
+    prm = fb.to_default_params(precision=fb.TO_FP32_MIXED, precond=fb.TO_PRECOND_MG, n_inner=2)
+    with fb.Problem.from_workload(pb, prm) as P:
+        ref = P.step(3, want_stats=True)
+    with fb.Problem.from_workload(pb, prm) as P:
+        P.step(3, want_stats=False)
+        buf = torch.empty(3 * ctypes.sizeof(fb.to_stats), dtype=torch.uint8, pin_memory=True)
+        fb.to_get_stats(P, 3, buf)
+        torch.cuda.synchronize()
+        got = [fb.to_stats.from_address(buf.data_ptr() + i * ctypes.sizeof(fb.to_stats)).as_dict() for i in range(3)]
+        for a, b in zip(ref, got):
+            assert a == b
+        for bad in (0, 4):
+            with pytest.raises(fb.ToError):
+                fb.to_get_stats(P, bad, buf)
