@@ -279,8 +279,9 @@ int to_project(to_problem* P, const void* w_dev, void* rho_dev, double* lambda_o
  * are those of rho_{k+n-1}. */
 int to_step(to_problem* P, int32_t n_outer, to_stats* stats_out, void* stream);
 
-/* The records of the first n outer iterations of the last to_step call (1 <= n <=
- * its n_outer), copied into stats_out (host memory for n records) asynchronously on
+/* The records of the first n outer iterations of the last to_step call, or of the
+ * last to_batch_step call of a batch the problem belongs to, whichever came last
+ * (1 <= n <= its n_outer), copied into stats_out (host memory for n records) asynchronously on
  * `stream`, ordered after that call when the stream is the same: for a caller that
  * reads a step's results without the synchronisation to_step does for stats_out (to_step
  * with stats_out = NULL, then this, then one synchronisation of its own).  The copy is

@@ -537,6 +537,7 @@ extern "C" int to_batch_step(to_batch* B, int32_t n_outer, to_stats* stats_out, 
         if (n_outer > P->dstats_cap)
             return fail(TO_ERR_ARG, "n_outer exceeds a problem's stats ring (run to_step once with that many iterations "
                                     "to grow it, or use fewer outer iterations per call)");
+    for (to_problem* P : B->probs) P->last_step_n = n_outer;   // each member's ring holds this call's records
     int prev = -1;
     cudaGetDevice(&prev);
     if (cudaSetDevice(B->device) != cudaSuccess) return fail(TO_ERR_CUDA, "cudaSetDevice failed");
