@@ -229,3 +229,41 @@ def test_pcg_matches_scipy_cg():
         xs, _ = spla.cg(K, S.f, x0=np.zeros_like(S.f), rtol=1e-300, atol=0.0, maxiter=it,
                         M=spla.LinearOperator(K.shape, matvec=lambda r: r / D))
         assert np.linalg.norm(x - xs) <= 1e-9 * np.linalg.norm(xs)
+
+
+def test_richardson_with_the_exact_inverse_solves_in_one_step():
+    """Constant-beta step of Algorithms 1 / 3: with M = K^-1 and beta = 1, u_1 = u_0 +
+    K^-1 (f - K u_0) is the exact solution from any u_0; r_0 = f - K u_0."""
+    pb, S, Ee = _setup(4, 2, 2, rho=lambda n: W.random_rho(n))
+    K = S.K(Ee).toarray()
+    uex = np.linalg.solve(K, S.f)
+    u0 = W.random_u(pb.n_dof, seed=3)
+    u1, r0 = solve.inner_richardson(lambda v: K @ v, S.f, u0, lambda r: np.linalg.solve(K, r), 1, 1.0)
+    assert np.linalg.norm(u1 - uex) <= 1e-10 * np.linalg.norm(uex)
+    assert np.allclose(r0, S.f - K @ u0, rtol=0, atol=1e-14 * np.abs(S.f).max())
+
+
+def test_richardson_jacobi_matches_the_iteration_matrix_power():
+    """n Jacobi-preconditioned steps with constant beta: the error obeys
+    e_n = (I - beta D^-1 K)^n e_0 (the closed form of the linear iteration, formed here as
+    an explicit dense matrix power), and for beta < 2 / lambda_max(D^-1 K) it contracts in
+    the energy norm at every step."""
+    pb, S, Ee = _setup(4, 2, 2, rho=lambda n: W.random_rho(n))
+    K = S.K(Ee).toarray()
+    D = fem.jacobi_diagonal(pb.nx, pb.ny, pb.nz, Ee, S.ke, pb.fixed_dof)
+    uex = np.linalg.solve(K, S.f)
+    u0 = W.random_u(pb.n_dof, seed=4)
+    lam = np.max(np.real(np.linalg.eigvals(K / D[:, None])))
+    beta = 1.0 / lam
+    G = np.eye(pb.n_dof) - beta * (K / D[:, None])
+    n = 7
+    un, _ = solve.inner_richardson(lambda v: K @ v, S.f, u0, lambda r: r / D, n, beta)
+    en_ref = np.linalg.matrix_power(G, n) @ (u0 - uex)
+    assert np.linalg.norm((un - uex) - en_ref) <= 1e-9 * np.linalg.norm(u0 - uex)
+    enorm = lambda e: float(np.sqrt(e @ (K @ e)))
+    u, prev = u0.copy(), enorm(u0 - uex)
+    for _ in range(n):
+        u, _ = solve.inner_richardson(lambda v: K @ v, S.f, u, lambda r: r / D, 1, beta)
+        cur = enorm(u - uex)
+        assert cur < prev
+        prev = cur
