@@ -59,6 +59,8 @@ def parse():
                          "2 the tensor-core FP32 kernel")
     ap.add_argument("--mg-legs", type=int, default=0, choices=[0, 1],
                     help="multigrid levels below the fine grid: 0 one launch per step, 1 two cooperative launches per V-cycle")
+    ap.add_argument("--mg-cluster", type=int, default=None, choices=[0, 1],
+                    help="the multigrid level above the coarse tail in one 16-CTA cluster (default: the library's)")
     ap.add_argument("--oracle-worker", nargs=3, metavar=("WARM", "ITERS", "BUDGET_S"), help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -323,7 +325,8 @@ def main():
 
     def make(precision):
         prm = fb.to_default_params(precision=precision, precond=precond, n_inner=n_inner, op_kernel=args.op_kernel,
-                                   mg_legs=args.mg_legs)
+                                   mg_legs=args.mg_legs,
+                                   **({} if args.mg_cluster is None else {"mg_cluster": args.mg_cluster}))
         return fb.Problem.from_workload(pb, prm, device=local)
 
     def time_steps(P, K, W_):
@@ -677,7 +680,7 @@ def main():
         cpu = cpu_baseline_line()
 
     ach = apply_bytes(s_el) / t_apply32 / 1e9
-    launches_per_step = _launches_per_step(use_mg, n_inner)
+    launches_per_step = _launches_per_step(use_mg, n_inner, cluster=bool(args.mg_cluster))
     line = {
         "metric": "outer TO iters/s (FP32-mixed) with K(rho)u GDOF/s, 1 GB300",
         "value": job_rate(args.steps, t32, world),
@@ -740,8 +743,9 @@ def _mg_levels(nx, ny, nz):
     return t + 1
 
 
-def _launches_per_step(mg, n_inner, dims=(128, 64, 64), nu1=2, nu2=2):
-    """Kernel launches of one outer iteration (one to_step(1) call), as issued by the library."""
+def _launches_per_step(mg, n_inner, dims=(128, 64, 64), nu1=2, nu2=2, cluster=False):
+    """Kernel launches of one outer iteration (one to_step(1) call), as issued by the library
+    (cluster: the FP32 level just above the coarse tail runs as two 16-CTA cluster launches)."""
     # stats-slot reset (once per to_step call), filter + moduli, diag, residual with the fused
     # sensitivity, (Q + update) per step, filter^T with the step-size statistics, the projection
     # (first pass, multiplier search, final pass), record
@@ -759,6 +763,11 @@ def _launches_per_step(mg, n_inner, dims=(128, 64, 64), nu1=2, nu2=2):
     # first sweep on the finest level (coarser ones come out of the restriction), per host level:
     # nu1 - 1 sweeps, b - K x, restriction, prolongation, nu2 sweeps; the dense solve or the tail kernel
     vcycle = 1 + host_levels * ((nu1 - 1) + 1 + 1 + 1 + nu2) + 1
+    if cluster and tail >= 2 and nu1 >= 1:
+        l = tail - 1
+        nx, ny, nz = (d >> l for d in dims)
+        if nz <= 16 and nx * ny <= 512 and (nx + 1) * (ny + 1) <= 640 and (nx // 2 + 1) * (ny // 2 + 1) <= 192:
+            vcycle -= ((nu1 - 1) + 1 + 1 + 1 + nu2) - 2   # that level's steps in two launches
     return base + refresh + vcycle * n_inner        # one V-cycle per step (r^T z fused into the last sweep)
 
 

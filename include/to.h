@@ -160,7 +160,14 @@ typedef struct {
  *               V-cycle (the down leg's smoothing, residuals and restrictions, the up leg's
  *               prolongations and smoothing), separated inside by bounded grid barriers
  *               (general operator kernel only).  The same steps, buffers and order: bitwise
- *               the same results */
+ *               the same results
+ *   mg_cluster  0 (default): every multigrid level above the one-CTA coarse tail runs one
+ *               launch per step;  1: FP32 problems run the level just above the tail in
+ *               one 16-CTA thread-block cluster (two launches per V-cycle around the tail,
+ *               the level's vectors in shared memory, sweeps separated by cluster barriers)
+ *               where that level has at most 16 element layers and 512 elements per layer
+ *               and the GPU can hold the cluster.  The same V-cycle up to the order of sums;
+ *               measured at the speed of the launched steps on the 128x64x64 cantilever */
 typedef struct {
     int32_t precision, precond, inner_mode, n_inner;
     double beta, alpha0, alpha_scale, m;
@@ -169,7 +176,7 @@ typedef struct {
     int32_t tile_x, tile_y, tile_z, no_graph;
     int32_t krylov_dim, proj_sort;
     int32_t adj_stride, op_kernel;
-    int32_t mg_legs, reserved_;
+    int32_t mg_legs, mg_cluster;
 } to_params;
 
 /* Per-outer-iteration record (host copy). */

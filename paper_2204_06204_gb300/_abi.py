@@ -39,7 +39,7 @@ class to_params(C.Structure):
                 ("mg_omega", C.c_double),
                 ("tile_x", C.c_int32), ("tile_y", C.c_int32), ("tile_z", C.c_int32), ("no_graph", C.c_int32),
                 ("krylov_dim", C.c_int32), ("proj_sort", C.c_int32), ("adj_stride", C.c_int32),
-                ("op_kernel", C.c_int32), ("mg_legs", C.c_int32), ("reserved_", C.c_int32)]
+                ("op_kernel", C.c_int32), ("mg_legs", C.c_int32), ("mg_cluster", C.c_int32)]
 
 
 class to_stats(C.Structure):

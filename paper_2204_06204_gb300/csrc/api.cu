@@ -211,7 +211,7 @@ extern "C" int to_create(const to_grid* g, const to_material* m, const to_loads*
         return bail(fail(TO_ERR_CUDA, "device query failed"));
     P->num_sms = dev_sms;
     if ((rc = project_coop_blocks(P->prec, P->num_sms, &P->coop_blocks))) return bail(rc);
-    if ((rc = operator_init(P))) return bail(rc);
+    if ((rc = operator_init(P)) || (rc = mg_cluster_init(P))) return bail(rc);
     if (cudaStreamCreateWithFlags(&P->gstream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&P->ev_in, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&P->ev_out, cudaEventDisableTiming) != cudaSuccess ||

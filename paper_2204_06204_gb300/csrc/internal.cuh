@@ -208,6 +208,7 @@ struct to_problem {
     int op_occ[5] = {0, 0, 0, 0, 0};
     int tma_occ[5] = {0, 0, 0, 0, 0};  // the FP32 TMA operator: resident CTAs per SM of each mode
     int tma_ready = 0;                 // its shared-memory opt-ins are set
+    int mgc_ok = 0;                    // the 16-CTA cluster of the level above the coarse tail can be resident
     int tc_occ[5] = {0, 0, 0, 0, 0};   // the tensor-core FP32 operator: resident CTAs per SM of each mode
     int tc_ready = 0;                  // its shared-memory opt-ins are set and tensor memory suffices
     int num_sms = 0;
@@ -276,6 +277,11 @@ int pipe_alloc(to_problem* P);
 void pipe_swap(to_problem* P);
 int mg_vcycle(to_problem* P, const void* r, void* z, cudaStream_t s);
 int mg_legs_build(to_problem* P);
+// the level just above the coarse tail in one 16-CTA cluster (mgcl.cu)
+int mg_cluster_init(to_problem* P);
+bool mg_cluster_applicable(const to_problem* P, int l);
+int mg_cluster_down(const to_problem* P, int l, void* x_first, void* x_iter, void* r_out, void* cfirst, cudaStream_t s);
+int mg_cluster_up(const to_problem* P, int l, void* x_iter, void* x_out, cudaStream_t s);
 int mg_legs_launch(to_problem* P, int leg, void* fine, cudaStream_t s);
 
 int outer_iteration(to_problem* P, cudaStream_t s);

@@ -19,6 +19,8 @@
 #include <algorithm>
 #include <cmath>
 
+#include <type_traits>
+
 #include "device.cuh"
 #include "haar.cuh"
 #include "transfer.cuh"
@@ -1091,6 +1093,20 @@ static int vcycle_t(to_problem* P, int l, const void* b, void* x, void* t, cudaS
     // choose the first target so that the last sweep writes into x
     void* cur = ((nu1 - 1 + nu2) % 2 == 0) ? x : t;
     void* oth = cur == x ? t : x;
+    if (std::is_same<T, float>::value && first_done && mg_cluster_applicable(P, l)) {
+        // this level (just above the tail) in one cluster: the down leg from the first sweep
+        // in cur, the tail, the up leg into x; the buffers end as in the launched steps
+        const int npre = nu1 - 1;
+        void* it_buf = (npre % 2 == 0) ? cur : oth;   // the iterate after the pre-smoothing
+        void* res_buf = it_buf == cur ? oth : cur;    // b - K x
+        void* fin = (nu2 % 2 == 0) ? it_buf : res_buf;
+        if (fin != x) return fail(TO_ERR_STATE, "V-cycle buffer parity");
+        const Level& C = P->lv[l + 1];
+        void* cfirst = ((nu1 - 1 + nu2) % 2 == 0) ? C.x : C.t;
+        if ((rc = mg_cluster_down(P, l, cur, it_buf, res_buf, l + 1 < L - 1 ? cfirst : nullptr, s))) return rc;
+        if ((rc = tail_t<T>(P, s))) return rc;
+        return mg_cluster_up(P, l, it_buf, x, s);
+    }
     if (!first_done) {
         k_jacobi_first<T><<<grid1(F.n_dof, P->num_sms), 256, 0, s>>>(F.n_dof, (const T*)b, (const T*)F.dinv, (T*)cur, (T)om);
         TO_CUDA(cudaGetLastError());

@@ -91,8 +91,9 @@ def _golden(name):
     return json.load(open(path))
 
 
-def _check_against_golden(fb, pb, rec, n, op_kernel=0):
-    prm = fb.to_default_params(precision=fb.TO_FP32_MIXED, precond=fb.TO_PRECOND_MG, n_inner=2, op_kernel=op_kernel)
+def _check_against_golden(fb, pb, rec, n, op_kernel=0, mg_cluster=0):
+    prm = fb.to_default_params(precision=fb.TO_FP32_MIXED, precond=fb.TO_PRECOND_MG, n_inner=2, op_kernel=op_kernel,
+                               mg_cluster=mg_cluster)
     with fb.Problem.from_workload(pb, prm) as P:
         st = P.step(n)
         rho = P.get_state()[0].double().cpu().numpy()
@@ -117,12 +118,42 @@ def test_mg2_outer_loop_fp32_64x32x32_vs_oracle_trajectory(which, op_kernel):
     _check_against_golden(fb, _workload(which, (64, 32, 32)), rec, 30, op_kernel)
 
 
-def test_mg2_fp32_128x64x64_200_iterations_vs_oracle():
+@pytest.mark.parametrize("mg_cluster", [0, 1])
+def test_mg2_fp32_128x64x64_200_iterations_vs_oracle(mg_cluster):
     """The benchmark workload end to end: 200 FP32-mixed outer iterations against the
-    oracle's FP64 run of the same 200 iterations."""
+    oracle's FP64 run of the same 200 iterations (mg_cluster 1: level 2 in one cluster)."""
     fb = _fb()
     rec = _golden("cantilever_128x64x64_mg2_200.json")
-    _check_against_golden(fb, W.cantilever_128x64x64(), rec, 200)
+    _check_against_golden(fb, W.cantilever_128x64x64(), rec, 200, mg_cluster=mg_cluster)
+
+
+@pytest.mark.parametrize("which", ["cantilever", "mbb"])
+def test_mg2_cluster_level_fp32_64x32x32_vs_oracle_trajectory(which):
+    """mg_cluster 1: level 1 (32x16x16, just above the coarse tail) runs in one 16-CTA
+    cluster, against the oracle's 30-iteration records."""
+    fb = _fb()
+    rec = _golden(f"{which}_64x32x32_mg2_30.json")
+    _check_against_golden(fb, _workload(which, (64, 32, 32)), rec, 30, mg_cluster=1)
+
+
+def test_mg_cluster_level_is_the_path_that_runs():
+    """The clustered level sums in another order than the launched steps: after a few outer
+    iterations at 128x64x64 the two agree to FP32 rounding but not bit for bit (a silent fall
+    back to the launched steps would)."""
+    fb = _fb()
+    pb = W.cantilever_128x64x64()
+    out = []
+    for mc in (0, 1):
+        prm = fb.to_default_params(precision=fb.TO_FP32_MIXED, precond=fb.TO_PRECOND_MG, n_inner=2, mg_cluster=mc)
+        with fb.Problem.from_workload(pb, prm) as P:
+            st = P.step(5)
+            rho, u = P.get_state()[:2]
+            out.append((rho.double().cpu().numpy(), u.double().cpu().numpy(), [x["J"] for x in st]))
+    (r0, u0, J0), (r1, u1, J1) = out
+    assert np.allclose(J0, J1, rtol=1e-5, atol=0)
+    assert np.linalg.norm(u1 - u0) <= 1e-4 * np.linalg.norm(u0)
+    assert np.abs(r1 - r0).max() <= 1e-4
+    assert not np.array_equal(u0, u1)
 
 
 # ----------------------------------------------------------------------------- sampled nodes at 128x64x64
