@@ -300,7 +300,12 @@ int to_get_stats(to_problem* P, int32_t n, to_stats* stats_out, void* stream);
 
 /* Read / write the outer state: rho (n_elem), u (n_dof), the 1-based iteration
  * counter k and alpha0 (<= 0 means not yet fixed).  Any pointer may be NULL to
- * skip that part.  to_set_state recomputes rho~ and the moduli. */
+ * skip that part.  to_set_state recomputes rho~ and the moduli.  After a to_step
+ * (outside a batch), to_set_state compares the rho it is given with the problem's
+ * rho bit for bit on the device; where they are equal the moduli and the next
+ * to_step's rebuild of the preconditioner are skipped on the device (no
+ * synchronisation), so a host loop that feeds back the design to_get_state returned
+ * pays no rebuild.  The results are the same either way. */
 int to_get_state(to_problem* P, void* rho_dev, void* u_dev, int64_t* k_out, double* alpha0_out, void* stream);
 int to_set_state(to_problem* P, const void* rho_dev, const void* u_dev, int64_t k, double alpha0, void* stream);
 

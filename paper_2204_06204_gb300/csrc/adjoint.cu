@@ -228,6 +228,7 @@ static int forward_t(to_problem* P, const void* rho, int Tn, double beta, cudaSt
     if ((rc = launch_diag(P, 0, s))) return rc;
     P->precond_stale = 1;   // a new design: the next to_inner_solve refreshes the preconditioner
     P->pipe_ready = 0;
+    P->design_check = 0;
     TO_CUDA(cudaMemsetAsync(slot<T>(P, 0), 0, bytes, s));
     void* gt = P->gt;
     P->gt = nullptr;   // no fused sensitivity in these residuals

@@ -137,7 +137,7 @@ extern "C" void to_destroy(to_problem* P) {
     }
     if (P->gexec) cudaGraphExecDestroy(P->gexec);
     for (int p = 0; p < 2; ++p)
-        for (int f = 0; f < 2; ++f)
+        for (int f = 0; f < 3; ++f)
             if (P->gexec_pipe[p][f]) cudaGraphExecDestroy(P->gexec_pipe[p][f]);
     if (P->gstream) cudaStreamSynchronize(P->gstream);
     if (P->ev_in) cudaEventDestroy(P->ev_in);
@@ -145,6 +145,7 @@ extern "C" void to_destroy(to_problem* P) {
     if (P->side) cudaStreamSynchronize(P->side);
     if (P->ev_fork) cudaEventDestroy(P->ev_fork);
     if (P->ev_join) cudaEventDestroy(P->ev_join);
+    if (P->ev_ljoin) cudaEventDestroy(P->ev_ljoin);
     if (P->side) cudaStreamDestroy(P->side);
     if (P->dside) cudaStreamSynchronize(P->dside);
     if (P->ev_dfork) cudaEventDestroy(P->ev_dfork);
@@ -368,6 +369,7 @@ extern "C" int to_set_design(to_problem* P, const void* rho_dev, void* stream) {
     if (rc) return rc;
     P->precond_stale = 1;   // refreshed by the next to_inner_solve (to_step refreshes every iteration)
     P->pipe_ready = 0;
+    P->design_check = 0;
     return TO_OK;
 }
 
@@ -508,7 +510,7 @@ static int capture_pipelined(to_problem* P, int fresh) {
         P->pipe_state[p][fresh] = -1;
         return TO_OK;
     }
-    const int rc = outer_iteration_pipelined(P, P->gstream, fresh != 0);
+    const int rc = outer_iteration_pipelined(P, P->gstream, fresh);
     const cudaError_t e = cudaStreamEndCapture(P->gstream, &g);
     if (rc != TO_OK || e != cudaSuccess || !g) {
         cudaGetLastError();
@@ -547,7 +549,7 @@ extern "C" int to_step(to_problem* P, int32_t n_outer, to_stats* stats_out, void
         P->gexec = nullptr;
         if (P->graph_state == 1) P->graph_state = 0;
         for (int p = 0; p < 2; ++p)
-            for (int f = 0; f < 2; ++f) {
+            for (int f = 0; f < 3; ++f) {
                 if (P->gexec_pipe[p][f]) cudaGraphExecDestroy(P->gexec_pipe[p][f]);
                 P->gexec_pipe[p][f] = nullptr;
                 if (P->pipe_state[p][f] == 1) P->pipe_state[p][f] = 0;
@@ -567,9 +569,11 @@ extern "C" int to_step(to_problem* P, int32_t n_outer, to_stats* stats_out, void
         pipe = false;
     }
     if (pipe) {
-        // the first iteration computes the live set itself unless the last to_step left it
-        int fresh = P->pipe_ready ? 0 : 1;
+        // the first iteration computes the live set itself unless the last to_step left it;
+        // after to_set_state only if the design it brought differs (decided on the device)
+        int fresh = P->pipe_ready ? 0 : (P->design_check ? 2 : 1);
         P->pipe_ready = 0;
+        P->design_check = 0;
         for (int i = 0; i < n_outer; ++i, fresh = 0) {
             const int p = P->set_parity;
             if (P->prm.no_graph == 0 && P->pipe_state[p][fresh] == 0) {
@@ -579,7 +583,7 @@ extern "C" int to_step(to_problem* P, int32_t n_outer, to_stats* stats_out, void
             if (P->pipe_state[p][fresh] == 1) {
                 TO_CUDA(cudaGraphLaunch(P->gexec_pipe[p][fresh], P->gstream));
             } else {
-                int rc = outer_iteration_pipelined(P, P->gstream, fresh != 0);
+                int rc = outer_iteration_pipelined(P, P->gstream, fresh);
                 if (rc) return rc;
             }
             pipe_swap(P);   // the set built for rho_{k+1} is live from here on
@@ -599,6 +603,7 @@ extern "C" int to_step(to_problem* P, int32_t n_outer, to_stats* stats_out, void
             }
         }
         P->pipe_ready = 0;   // the moduli lag rho by one iteration here
+        P->design_check = 0;
     }
     P->precond_stale = 0;   // the last iteration refreshed it for its own moduli (pipelined: for rho)
     TO_CUDA(cudaEventRecord(P->ev_out, P->gstream));
@@ -640,18 +645,59 @@ __global__ void k_set_counters(to::DevScalars* sc, long long k, double alpha0, i
     if (set_a) sc->alpha0 = alpha0 > 0.0 ? alpha0 : 0.0;
 }
 
+// rho <- rho_in, compared bitwise with the old rho: comparison number seq found a
+// difference iff afterwards sc->dchanged == sc->dseq.  Also sets k and alpha0.
+template <typename W>
+__global__ void k_take_design(const W* __restrict__ in, W* __restrict__ rho, long long n, to::DevScalars* sc,
+                              unsigned seq, long long k, double alpha0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        sc->k = k;
+        sc->alpha0 = alpha0 > 0.0 ? alpha0 : 0.0;
+        sc->dseq = seq;
+    }
+    bool diff = false;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const W v = in[i];
+        diff |= v != rho[i];
+        rho[i] = v;
+    }
+    if (__any_sync(0xffffffffu, diff) && (threadIdx.x & 31) == 0) sc->dchanged = seq;
+}
+
 extern "C" int to_set_state(to_problem* P, const void* rho_dev, const void* u_dev, int64_t k, double alpha0, void* stream) {
     TO_ENTER(P);
     if (k < 1) return fail(TO_ERR_ARG, "k must be >= 1");
     P->fwd_id = 0;
-    if (rho_dev) TO_CUDA(cudaMemcpyAsync(P->rho, rho_dev, P->n_elem * P->esz, cudaMemcpyDeviceToDevice, s));
+    // The live set (moduli, 1 / d, coarsest inverse) was built for the current rho when a
+    // pipelined to_step left it: then the incoming design is compared with rho on the
+    // device, and the moduli here and the next to_step's rebuild run only if it differs.
+    const bool check = rho_dev && P->pipe_ready && !P->in_batch &&
+                       (P->prm.precond != TO_PRECOND_MG || mg_refresh_gatable(P));
+    if (check) {
+        const long long n = P->n_elem;
+        long long nb = (n + 255) / 256;
+        if (nb > 4LL * P->num_sms) nb = 4LL * P->num_sms;
+        if (nb < 1) nb = 1;
+        const unsigned seq = ++P->dseq_host;
+        // compared as bit patterns (a NaN equals itself, -0 differs from +0)
+        if (P->prec == TO_FP64)
+            k_take_design<unsigned long long><<<(unsigned)nb, 256, 0, s>>>(
+                (const unsigned long long*)rho_dev, (unsigned long long*)P->rho, n, P->sc, seq, (long long)k, alpha0);
+        else
+            k_take_design<unsigned><<<(unsigned)nb, 256, 0, s>>>((const unsigned*)rho_dev, (unsigned*)P->rho, n, P->sc,
+                                                                 seq, (long long)k, alpha0);
+        TO_CUDA(cudaGetLastError());
+    } else {
+        if (rho_dev) TO_CUDA(cudaMemcpyAsync(P->rho, rho_dev, P->n_elem * P->esz, cudaMemcpyDeviceToDevice, s));
+        k_set_counters<<<1, 1, 0, s>>>(P->sc, (long long)k, alpha0, 1, 1);
+        TO_CUDA(cudaGetLastError());
+    }
     if (u_dev) TO_CUDA(cudaMemcpyAsync(P->u, u_dev, P->n_dof * P->esz, cudaMemcpyDeviceToDevice, s));
-    k_set_counters<<<1, 1, 0, s>>>(P->sc, (long long)k, alpha0, 1, 1);
-    TO_CUDA(cudaGetLastError());
-    int rc = launch_moduli(P, s);
+    int rc = launch_moduli(P, s, check ? &P->sc->dchanged : nullptr);
     if (rc) return rc;
     P->precond_stale = 1;   // refreshed by the next to_inner_solve (to_step refreshes every iteration)
     P->pipe_ready = 0;
+    P->design_check = check ? 1 : 0;
     return TO_OK;
 }
 

@@ -555,7 +555,7 @@ extern "C" int to_batch_step(to_batch* B, int32_t n_outer, to_stats* stats_out, 
             // the first iteration computes the live sets unless the last batched step left them
             bool fresh = false;
             for (to_problem* P : B->probs) fresh = fresh || !P->pipe_ready;
-            for (to_problem* P : B->probs) P->pipe_ready = 0;
+            for (to_problem* P : B->probs) P->pipe_ready = P->design_check = 0;
             for (int i = 0; i < n_outer; ++i, fresh = false) {
                 const int p = B->parity, f = fresh ? 1 : 0;
                 if (B->pipe_state[p][f] == 0) {
@@ -602,7 +602,7 @@ extern "C" int to_batch_step(to_batch* B, int32_t n_outer, to_stats* stats_out, 
             }
         }
         if (!B->pipe)
-            for (to_problem* P : B->probs) P->pipe_ready = 0;   // the moduli lag rho by one iteration here
+            for (to_problem* P : B->probs) P->pipe_ready = P->design_check = 0;   // the moduli lag rho by one iteration here
         TO_CUDA(cudaEventRecord(B->ev_out, B->stream));
         TO_CUDA(cudaStreamWaitEvent(s, B->ev_out, 0));
         if (stats_out) {

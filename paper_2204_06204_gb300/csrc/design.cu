@@ -55,6 +55,7 @@ struct FilterArgs {
     T* Eout;             // MODULI: E and E' / Hs
     T* Edout;
     SimpT<T> simp;
+    const unsigned* gate;   // single-problem launch: nothing is done where gate[0] != gate[1] (nullptr: always)
 };
 
 // the CTA tile (bx, by, bz) of one problem; bid / nblocks place it among the problem's
@@ -173,6 +174,7 @@ __device__ __forceinline__ void filter_body(const FilterArgs<T>& a, int bx, int 
 template <typename T, bool TRANSPOSE, bool STATS, bool PRESCALED, bool MODULI = false>
 __global__ void __launch_bounds__(256) k_filter(const FilterArgs<T> a) {
     extern __shared__ __align__(16) unsigned char fsm[];
+    if (a.gate && a.gate[0] != a.gate[1]) return;   // the whole grid: no CTA reaches a barrier
     filter_body<T, TRANSPOSE, STATS, PRESCALED, MODULI>(a, blockIdx.x, blockIdx.y, blockIdx.z, linear_block(),
                                                          grid_blocks(), fsm);
 }
@@ -226,17 +228,10 @@ __global__ void k_filter_rowsum(int nx, int ny, int nz, T* Hs, const int4* st, c
 }
 
 template <typename T>
-__global__ void k_diag(int nx, int ny, int nz, const T* E, const uint8_t* mask, T* dinv, double kdiag) {
+__global__ void k_diag(int nx, int ny, int nz, const T* E, const uint8_t* mask, T* dinv, double kdiag, const unsigned* gate) {
+    if (gate && gate[0] != gate[1]) return;
     const Idx3 t = idx3(nx + 1, ny + 1, nz + 1);
     if (t.ok) diag_node<T>(nx, ny, nz, t.i, t.j, t.k, E, mask, dinv, kdiag);
-}
-
-static int grid_for(long long n, int threads, int num_sms) {
-    long long b = (n + threads - 1) / threads;
-    const long long cap = 8LL * num_sms;
-    if (b > cap) b = cap;
-    if (b < 1) b = 1;
-    return (int)b;
 }
 
 template <typename T>
@@ -263,13 +258,15 @@ static FilterArgs<T> filter_args(const to_problem* P, const T* x, T* y, int kchu
     a.Eout = Eout;
     a.Edout = Edout;
     a.simp = simp_params<T>(P->mat);
+    a.gate = nullptr;
     return a;
 }
 
 // the filter's launch shape: 32 x 8 element columns, each CTA a chunk of z planes
 // (about four CTAs per SM), and its shared memory
 template <typename T, bool TRANSPOSE, bool STATS, bool PRESCALED, bool MODULI>
-static int filter_launch(to_problem* P, const T* x, T* y, cudaStream_t s, T* Eout = nullptr, T* Edout = nullptr) {
+static int filter_launch(to_problem* P, const T* x, T* y, cudaStream_t s, T* Eout = nullptr, T* Edout = nullptr,
+                         const unsigned* gate = nullptr) {
     const int nx = P->g.nx, ny = P->g.ny, nz = P->g.nz, R = P->filter_ext;
     constexpr bool DIV = TRANSPOSE && !PRESCALED;
     const int gx = (nx + 31) / 32, gy = (ny + 7) / 8;
@@ -295,7 +292,9 @@ static int filter_launch(to_problem* P, const T* x, T* y, cudaStream_t s, T* Eou
         opted = fs;
     }
     const dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)chunks);
-    kern<<<grid, block3(), fs, s>>>(filter_args<T>(P, x, y, kchunk, STATS, Eout, Edout));
+    FilterArgs<T> a = filter_args<T>(P, x, y, kchunk, STATS, Eout, Edout);
+    a.gate = gate;
+    kern<<<grid, block3(), fs, s>>>(a);
     TO_CUDA(cudaGetLastError());
     return TO_OK;
 }
@@ -381,28 +380,27 @@ int launch_sens_filter_T(to_problem* P, cudaStream_t s) {
 }
 
 template <typename T>
-static int moduli_t(to_problem* P, cudaStream_t s) {
+static int moduli_t(to_problem* P, cudaStream_t s, const unsigned* gate) {
     // rho~ = C(rho) and the moduli in one pass
-    return filter_launch<T, false, false, false, true>(P, (const T*)P->rho, (T*)P->rhot, s, (T*)P->lv[0].E, (T*)P->Ed);
+    return filter_launch<T, false, false, false, true>(P, (const T*)P->rho, (T*)P->rhot, s, (T*)P->lv[0].E, (T*)P->Ed,
+                                                       gate);
 }
 
-int launch_moduli(to_problem* P, cudaStream_t s) {
-    return P->prec == TO_FP64 ? moduli_t<double>(P, s) : moduli_t<float>(P, s);
+int launch_moduli(to_problem* P, cudaStream_t s, const unsigned* gate) {
+    return P->prec == TO_FP64 ? moduli_t<double>(P, s, gate) : moduli_t<float>(P, s, gate);
 }
 
 template <typename T>
-static int diag_t(to_problem* P, int level, cudaStream_t s) {
+static int diag_t(to_problem* P, int level, cudaStream_t s, const unsigned* gate) {
     const Level& L = P->lv[level];
-    const int nb = grid_for(L.n_node, 256, P->num_sms);
-    (void)nb;
     k_diag<T><<<grid3(L.nx + 1, L.ny + 1, L.nz + 1), block3(), 0, s>>>(L.nx, L.ny, L.nz, (const T*)L.E, L.mask,
-                                                                      (T*)L.dinv, L.kdiag);
+                                                                      (T*)L.dinv, L.kdiag, gate);
     TO_CUDA(cudaGetLastError());
     return TO_OK;
 }
 
-int launch_diag(to_problem* P, int level, cudaStream_t s) {
-    return P->prec == TO_FP64 ? diag_t<double>(P, level, s) : diag_t<float>(P, level, s);
+int launch_diag(to_problem* P, int level, cudaStream_t s, const unsigned* gate) {
+    return P->prec == TO_FP64 ? diag_t<double>(P, level, s, gate) : diag_t<float>(P, level, s, gate);
 }
 
 int launch_rowsum(to_problem* P, cudaStream_t s) {

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cstddef>
 #include <string>
 #include <vector>
 
@@ -46,7 +47,13 @@ struct DevScalars {
     int rec;                           // next stats slot written by the record kernel
     ProjSearch ps;                     // the projection's search, carried between its kernels
     int proj_active;                   // the volume bound is active at this projection (lambda > 0)
+    // to_set_state's comparison of the incoming design with the live set's: call number dseq
+    // found a difference iff dchanged == dseq (gates: a kernel given &dchanged returns at once
+    // when gate[0] != gate[1])
+    unsigned dchanged, dseq;
 };
+static_assert(offsetof(DevScalars, dseq) == offsetof(DevScalars, dchanged) + sizeof(unsigned),
+              "a gate reads dchanged and dseq as one pair");
 
 // Reduction scratch: one slot of up to kRedQ doubles per block, plus a
 // completion counter; the last block to finish sums the slots in block order
@@ -197,9 +204,15 @@ struct to_problem {
     void* alt_gj_tab = nullptr;
     int alt_alloc = 0;
     int set_parity = 0;
-    cudaGraphExec_t gexec_pipe[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};   // [set][fresh]
-    int pipe_state[2][2] = {{0, 0}, {0, 0}};   // as graph_state, per set and variant
+    // [set][variant]: 0 the live set is current, 1 it is rebuilt first, 2 it is rebuilt by
+    // kernels that do nothing unless dchanged says to_set_state brought a different design
+    cudaGraphExec_t gexec_pipe[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+    int pipe_state[2][3] = {{0, 0, 0}, {0, 0, 0}};   // as graph_state, per set and variant
     int pipe_ready = 0;            // the live set belongs to the current rho (a pipelined to_step left it)
+    int design_check = 0;          // to_set_state compared its design with the live set's (variant 2 may run)
+    unsigned dseq_host = 0;        // number of those comparisons
+    int levels_wait = 0;           // variant 2: the coarse levels are rebuilt on the branch; the first
+    cudaEvent_t ev_ljoin = nullptr;   // restriction to level 1 waits for ev_ljoin
     int in_batch = 0;              // a batch's tables hold this problem's buffers: no swapping
     int coarse_wait = 0;           // a forked coarsest inverse may still run: coarse solves wait for ev_join
 
@@ -221,8 +234,9 @@ namespace to {
 template <typename T> struct Launch;
 
 int launch_filter(to_problem* P, const void* x, void* y, int transpose, cudaStream_t s);
-int launch_moduli(to_problem* P, cudaStream_t s);  // rho -> rho~, E, E'
-int launch_diag(to_problem* P, int level, cudaStream_t s);
+// rho -> rho~, E, E'; with gate (&sc->dchanged), only where the design changed (read on the device)
+int launch_moduli(to_problem* P, cudaStream_t s, const unsigned* gate = nullptr);
+int launch_diag(to_problem* P, int level, cudaStream_t s, const unsigned* gate = nullptr);   // gate: as launch_moduli
 
 enum OpMode { OP_APPLY = 0, OP_RESID = 1, OP_Q = 2, OP_SMOOTH = 3, OP_BMINUS = 4 };
 // OP_RESID outputs named by the caller instead of the problem's buffers (nullptr skips one)
@@ -270,6 +284,10 @@ int mg_build(to_problem* P);
 // coarse moduli, diagonals, the coarsest inverse (on a forked branch of s; join: s waits for it
 // at once, else the first coarse solve on s does)
 int mg_refresh(to_problem* P, cudaStream_t s, bool join = true, bool inline_inv = false);
+// coarse moduli, 1 / d and the coarsest operator; its inverse (gate: as launch_moduli)
+int mg_refresh_levels(to_problem* P, cudaStream_t s, const unsigned* gate = nullptr);
+int mg_refresh_inverse(to_problem* P, cudaStream_t s, const unsigned* gate = nullptr);
+bool mg_refresh_gatable(const to_problem* P);   // the inverse takes a gate (one-CTA register form)
 // the diagonal and (multigrid) the refresh above; inline_inv: the coarsest inverse on s itself
 int refresh_preconditioner(to_problem* P, cudaStream_t s, bool join = true, bool inline_inv = false);
 // the second set of design-dependent buffers (allocated once) and the swap of the two sets
@@ -287,7 +305,7 @@ int mg_legs_launch(to_problem* P, int leg, void* fine, cudaStream_t s);
 int outer_iteration(to_problem* P, cudaStream_t s);
 // one outer iteration that also builds the next design's set; the live set must match rho,
 // or `fresh`: the iteration first computes the live set itself
-int outer_iteration_pipelined(to_problem* P, cudaStream_t s, bool fresh);
+int outer_iteration_pipelined(to_problem* P, cudaStream_t s, int fresh);   // fresh: variant 0, 1 or 2
 int inner_steps(to_problem* P, int nsteps, int from_resid, cudaStream_t s);
 
 // batched multigrid (mg.cu): the V-cycle and the per-iteration refresh of many problems

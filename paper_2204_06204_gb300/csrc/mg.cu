@@ -51,7 +51,8 @@ __device__ __forceinline__ void coarsen_elem(int cx, int cy, int I, int J, int K
 }
 
 template <typename T>
-__global__ void k_coarsen_E(int cx, int cy, int cz, const T* __restrict__ Ef, T* __restrict__ Ec) {
+__global__ void k_coarsen_E(int cx, int cy, int cz, const T* __restrict__ Ef, T* __restrict__ Ec, const unsigned* gate) {
+    if (gate && gate[0] != gate[1]) return;   // (gate: to_set_state found the design unchanged)
     const Idx3 t = idx3(cx, cy, cz);
     if (t.ok) coarsen_elem<T>(cx, cy, t.i, t.j, t.k, Ef, Ec);
 }
@@ -116,7 +117,9 @@ __device__ __forceinline__ T dense_entry(int nx, int ny, int nz, const T* __rest
 
 template <typename T>
 __global__ void k_dense_assemble(int nx, int ny, int nz, const T* __restrict__ E, const uint8_t* __restrict__ mask,
-                                 const double* __restrict__ ke, double hscale, T* __restrict__ A, int n) {
+                                 const double* __restrict__ ke, double hscale, T* __restrict__ A, int n,
+                                 const unsigned* gate) {
+    if (gate && gate[0] != gate[1]) return;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < (long long)n * n;
          idx += (long long)gridDim.x * blockDim.x)
         A[idx] = dense_entry<T>(nx, ny, nz, E, mask, ke, hscale, n, idx);
@@ -229,7 +232,8 @@ __device__ __forceinline__ void dense_invert_reg_body(const T* __restrict__ A, T
 
 template <typename T>
 __global__ void __launch_bounds__(1024) k_dense_invert_reg(const T* __restrict__ A, T* __restrict__ Ainv,
-                                                           T* __restrict__ sc, int n, int* err) {
+                                                           T* __restrict__ sc, int n, int* err, const unsigned* gate) {
+    if (gate && gate[0] != gate[1]) return;
     dense_invert_reg_body<T>(A, Ainv, sc, n, err);
 }
 
@@ -918,7 +922,8 @@ int mg_build(to_problem* P) {
     P->n_coarse = n;
     if (cudaStreamCreateWithFlags(&P->side, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming) != cudaSuccess)
+        cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&P->ev_ljoin, cudaEventDisableTiming) != cudaSuccess)
         return fail(TO_ERR_CUDA, "multigrid stream / event creation failed");
     if (cudaMalloc(&P->coarse_A, (size_t)n * n * es) != cudaSuccess ||
         cudaMalloc(&P->coarse_L, (size_t)n * n * es + (size_t)n * es) != cudaSuccess)
@@ -964,22 +969,45 @@ int mg_build(to_problem* P) {
     return TO_OK;
 }
 
+// every coarse level's moduli and 1 / d, and the coarsest level's dense operator (gate:
+// each kernel returns at once where gate[0] != gate[1])
 template <typename T>
-static int refresh_t(to_problem* P, cudaStream_t s, bool join, bool inline_inv) {
+static int refresh_levels_t(to_problem* P, cudaStream_t s, const unsigned* gate) {
     const int L = (int)P->lv.size();
     for (int l = 1; l < L; ++l) {
         const Level& C = P->lv[l];
-        k_coarsen_E<T><<<grid3(C.nx, C.ny, C.nz), block3(), 0, s>>>(C.nx, C.ny, C.nz, (const T*)P->lv[l - 1].E, (T*)C.E);
+        k_coarsen_E<T><<<grid3(C.nx, C.ny, C.nz), block3(), 0, s>>>(C.nx, C.ny, C.nz, (const T*)P->lv[l - 1].E, (T*)C.E,
+                                                                    gate);
         TO_CUDA(cudaGetLastError());
-        int rc = launch_diag(P, l, s);
+        int rc = launch_diag(P, l, s, gate);
         if (rc) return rc;
     }
     const Level& Cst = P->lv.back();
     const int n = P->n_coarse;
     k_dense_assemble<T><<<grid1((long long)n * n, P->num_sms), 256, 0, s>>>(
-        Cst.nx, Cst.ny, Cst.nz, (const T*)Cst.E, Cst.mask, P->ke_dev, Cst.h, (T*)P->coarse_A, n);
+        Cst.nx, Cst.ny, Cst.nz, (const T*)Cst.E, Cst.mask, P->ke_dev, Cst.h, (T*)P->coarse_A, n, gate);
     TO_CUDA(cudaGetLastError());
+    return TO_OK;
+}
+
+// the inverse of the coarsest operator (a gate only for the one-CTA register inverse)
+template <typename T>
+static int refresh_inverse_t(to_problem* P, cudaStream_t s, const unsigned* gate) {
+    const int n = P->n_coarse;
     T* inv = (T*)P->coarse_L;
+    if (n <= kRegDof) {
+        k_dense_invert_reg<T><<<1, dim3(32, 32), 0, s>>>((const T*)P->coarse_A, inv, inv + (size_t)n * n, n, &P->sc->err,
+                                                        gate);
+        TO_CUDA(cudaGetLastError());
+        return TO_OK;
+    }
+    if (gate) return fail(TO_ERR_STATE, "the blocked coarsest inversion has no gate");
+    return gj_launch<T>(P->gj_tab, 1, (n + kGjB - 1) / kGjB, P->num_sms, s);
+}
+
+template <typename T>
+static int refresh_t(to_problem* P, cudaStream_t s, bool join, bool inline_inv) {
+    if (int rc = refresh_levels_t<T>(P, s, nullptr)) return rc;
     // the inverse runs on a branch; the first coarse solve joins it (it is needed only
     // there) -- unless s is itself a branch that the caller joins (inline_inv)
     cudaStream_t main_s = s;
@@ -988,12 +1016,7 @@ static int refresh_t(to_problem* P, cudaStream_t s, bool join, bool inline_inv) 
         TO_CUDA(cudaStreamWaitEvent(P->side, P->ev_fork, 0));
         s = P->side;
     }
-    if (n <= kRegDof) {
-        k_dense_invert_reg<T><<<1, dim3(32, 32), 0, s>>>((const T*)P->coarse_A, inv, inv + (size_t)n * n, n, &P->sc->err);
-        TO_CUDA(cudaGetLastError());
-    } else if (int rc = gj_launch<T>(P->gj_tab, 1, (n + kGjB - 1) / kGjB, P->num_sms, s)) {
-        return rc;
-    }
+    if (int rc = refresh_inverse_t<T>(P, s, nullptr)) return rc;
     if (inline_inv) return TO_OK;
     TO_CUDA(cudaEventRecord(P->ev_join, s));
     // outside the outer iteration nothing else joins the branch: without this a later
@@ -1002,6 +1025,16 @@ static int refresh_t(to_problem* P, cudaStream_t s, bool join, bool inline_inv) 
     P->coarse_wait = join ? 0 : 1;   // the coarse solves on main_s join it
     return TO_OK;
 }
+
+int mg_refresh_levels(to_problem* P, cudaStream_t s, const unsigned* gate) {
+    return P->prec == TO_FP64 ? refresh_levels_t<double>(P, s, gate) : refresh_levels_t<float>(P, s, gate);
+}
+
+int mg_refresh_inverse(to_problem* P, cudaStream_t s, const unsigned* gate) {
+    return P->prec == TO_FP64 ? refresh_inverse_t<double>(P, s, gate) : refresh_inverse_t<float>(P, s, gate);
+}
+
+bool mg_refresh_gatable(const to_problem* P) { return P->n_coarse <= kRegDof; }
 
 int mg_refresh(to_problem* P, cudaStream_t s, bool join, bool inline_inv) {
     return P->prec == TO_FP64 ? refresh_t<double>(P, s, join, inline_inv) : refresh_t<float>(P, s, join, inline_inv);
@@ -1117,6 +1150,7 @@ static int vcycle_t(to_problem* P, int l, const void* b, void* x, void* t, cudaS
     }
     // residual into oth, restrict to the coarse right-hand side
     if ((rc = launch_operator(P, l, OP_BMINUS, cur, oth, b, s))) return rc;
+    if (P->levels_wait) TO_CUDA(cudaStreamWaitEvent(s, P->ev_ljoin, 0));   // the coarse levels of this design are ready
     if (l == 0 && P->legs_grid > 0) {
         // levels 1 .. tail - 1 as two cooperative launches around the coarse tail
         if ((rc = mg_legs_launch(P, 0, oth, s))) return rc;

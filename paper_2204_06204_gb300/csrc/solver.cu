@@ -335,6 +335,33 @@ int outer_iteration(to_problem* P, cudaStream_t s) {
     return launch_record(P, s);
 }
 
+// ----------------------------------------------------------------------------- gated refresh
+// After to_set_state the live set is rebuilt only if the design it brought differs from
+// the one the set was built for: sc->dchanged, written on the device by to_set_state's copy
+// (which has also recomputed rho~ and the moduli where the design differs).  Every rebuild
+// kernel reads the flag and returns at once if it is 0, so an unchanged design costs one
+// near-empty launch each; level 0's 1 / d is the only one on the main stream, the coarse
+// levels (moduli, 1 / d, the coarsest operator) and the coarsest inverse run on the
+// multigrid branch beside the residual.  The V-cycle's first restriction to level 1 waits
+// for the levels (ev_ljoin), the coarse solves for the inverse (ev_join).  (Conditional
+// graph nodes measured slower: each costs several microseconds even when its body does
+// not run, and the graph around them slowed down too.)
+static int gated_refresh(to_problem* P, cudaStream_t s) {
+    const unsigned* changed = &P->sc->dchanged;
+    if (P->prm.precond != TO_PRECOND_MG) return launch_diag(P, 0, s, changed);
+    TO_CUDA(cudaEventRecord(P->ev_fork, s));
+    TO_CUDA(cudaStreamWaitEvent(P->side, P->ev_fork, 0));
+    int rc = launch_diag(P, 0, s, changed);
+    if (!rc) rc = mg_refresh_levels(P, P->side, changed);
+    if (rc) return rc;
+    TO_CUDA(cudaEventRecord(P->ev_ljoin, P->side));
+    if ((rc = mg_refresh_inverse(P, P->side, changed))) return rc;
+    TO_CUDA(cudaEventRecord(P->ev_join, P->side));
+    P->levels_wait = 1;   // the V-cycle's first restriction joins the levels
+    P->coarse_wait = 1;   // the coarse solves join the inverse
+    return TO_OK;
+}
+
 // The same iteration with the next design's preconditioner built beside it.  The live
 // set (moduli, diagonals, coarsest inverse) belongs to rho_k on entry, or (`fresh`) is
 // computed first as in outer_iteration, its inverse on the multigrid branch.  After the
@@ -343,10 +370,14 @@ int outer_iteration(to_problem* P, cudaStream_t s) {
 // into the other set, while the lower-level steps run on the live set; the caller
 // swaps the sets afterwards.  Every kernel sees the same inputs as in
 // outer_iteration, so the iterates are the same.
-int outer_iteration_pipelined(to_problem* P, cudaStream_t s, bool fresh) {
+int outer_iteration_pipelined(to_problem* P, cudaStream_t s, int fresh) {
     int rc;
     const bool mg = P->prm.precond == TO_PRECOND_MG;
-    if (fresh && ((rc = launch_moduli(P, s)) || (rc = refresh_preconditioner(P, s, false, false)))) return rc;
+    if (fresh == 2) {
+        if ((rc = gated_refresh(P, s))) return rc;
+    } else if (fresh && ((rc = launch_moduli(P, s)) || (rc = refresh_preconditioner(P, s, false, false)))) {
+        return rc;
+    }
     if ((rc = launch_operator(P, 0, OP_RESID, P->u, P->r, P->f, s, 0.0, 1))) return rc;
     TO_CUDA(cudaEventRecord(P->ev_dfork, s));
     TO_CUDA(cudaStreamWaitEvent(P->dside, P->ev_dfork, 0));
@@ -364,6 +395,7 @@ int outer_iteration_pipelined(to_problem* P, cudaStream_t s, bool fresh) {
     P->coarse_wait = fresh ? 1 : 0;   // else the live inverse was completed before this iteration
     rc = run_inner(P, P->u, P->prm.n_inner, 1, s, 1);
     P->coarse_wait = 0;               // joined below (fresh: through the design branch)
+    P->levels_wait = 0;
     if (rc) return rc;
     TO_CUDA(cudaStreamWaitEvent(s, P->ev_djoin, 0));
     return launch_record(P, s);

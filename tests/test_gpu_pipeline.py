@@ -81,6 +81,48 @@ def test_live_moduli_belong_to_the_current_design(precision):
     assert torch.equal(y1, y2)
 
 
+@pytest.mark.parametrize("case", sorted(CASES))
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("change", ["none", "last_entry_one_ulp", "every_entry"])
+@pytest.mark.parametrize("no_graph", [0, 1])
+def test_set_state_rebuilds_only_a_changed_design(case, precision, change, no_graph):
+    """After a pipelined step, to_set_state compares the design it brings with the one the
+    live set was built for, on the device; the next step's rebuild kernels do nothing
+    unless they differ.  Unchanged, changed in one bit of the last entry, or changed
+    everywhere: the iterates (and K u right after the call) must equal those of the plain
+    rebuild bit for bit.  The plain rebuild is forced by to_set_design before to_set_state
+    (a design set that way is not compared)."""
+    fb = _fb()
+    pb = CASES[case][0]()
+
+    def run(plain):
+        prm = _params(fb, case, precision)
+        prm.no_graph = no_graph
+        with fb.Problem.from_workload(pb, prm) as P:
+            stats = P.step(2)
+            rho, u, k, a0 = P.get_state()
+            new = rho.clone()
+            if change == "every_entry":
+                new.mul_(0.97).add_(0.01)
+            elif change == "last_entry_one_ulp":
+                new[-1] = torch.nextafter(new[-1], torch.zeros_like(new[-1]))
+                assert not torch.equal(new, rho)
+            if plain:
+                P.set_design(new)
+            P.set_state(new, None, k, a0)
+            y = P.apply_K(u).cpu()   # the moduli of the design just set are live
+            stats += P.step(3)
+            rho2, u2, k2, a02 = P.get_state()
+            return rho2.cpu(), u2.cpu(), k2, a02, y, [(s["J"], s["beta_first"], s["lambda"]) for s in stats]
+
+    ref = run(True)
+    got = run(False)
+    assert torch.equal(ref[4], got[4])
+    assert torch.equal(ref[0], got[0]) and torch.equal(ref[1], got[1])
+    assert ref[2] == got[2] and ref[3] == got[3]
+    assert ref[5] == got[5]
+
+
 def test_batched_call_patterns_agree_bitwise():
     """The pipelined batched iteration: one call of 4 iterations, four calls of one, and
     a member's state rewritten between calls (the next call starts afresh) agree."""
