@@ -374,30 +374,20 @@ def main():
     t_apply32 = time_apply(P32)
     ips32 = args.steps / t32
 
-    # --- end to end through the C ABI with host buffers: rho in, rho + stats out each step.
+    # --- end to end through the C ABI with host buffers: rho in, rho + stats out each step,
+    # one to_step_host call per step (the design copied in from pinned host memory and
+    # compared with the live one on the device, one outer iteration, the new design and
+    # the step's record copied out, one synchronisation; a device-side error raises).
     # Two pinned host buffers take turns: step i reads its design from one and leaves the
     # new design in the other, which is the next step's input (no host-side copy).
-    # Everything of a step is enqueued first (design in, state set, the iteration, design
-    # and the step's stats record out) and the step ends with one synchronisation.
     rho_hb = [torch.empty(pb.n_elem, dtype=torch.float32, pin_memory=True) for _ in range(2)]
     stats_h = torch.empty(ctypes.sizeof(fb.to_stats), dtype=torch.uint8, pin_memory=True)
-    rho_d, u_d, k_d, a0_d = P32.get_state()
-    rho_hb[0].copy_(rho_d)
+    rho_hb[0].copy_(P32.get_state()[0])
     ke = max(3, min(args.steps, 100))
     we = max(3, args.warmup)   # untimed: the first host-fed steps capture their graph variants
 
     def e2e_step(i):
-        rho_in, rho_out = rho_hb[i % 2], rho_hb[(i + 1) % 2]
-        rho_d.copy_(rho_in, non_blocking=True)
-        fb.to_set_state(P32, rho_d, None, k_d + i, a0_d)
-        P32.step(1, want_stats=False)
-        fb.to_get_state(P32, rho_d, None, scalars=False)
-        rho_out.copy_(rho_d, non_blocking=True)
-        fb.to_get_stats(P32, 1, stats_h)
-        torch.cuda.synchronize()
-        rec = fb.to_stats.from_address(stats_h.data_ptr())
-        if rec.status:
-            raise RuntimeError(f"device-side error {rec.status} in the end-to-end loop")
+        fb.to_step_host(P32, rho_hb[i % 2], rho_hb[(i + 1) % 2], stats_h)
 
     for i in range(we):
         e2e_step(i)

@@ -309,6 +309,19 @@ int to_get_stats(to_problem* P, int32_t n, to_stats* stats_out, void* stream);
 int to_get_state(to_problem* P, void* rho_dev, void* u_dev, int64_t* k_out, double* alpha0_out, void* stream);
 int to_set_state(to_problem* P, const void* rho_dev, const void* u_dev, int64_t k, double alpha0, void* stream);
 
+/* One outer iteration (Algorithms 1 / 3) fed from host memory, for a loop that keeps
+ * the design on the host: rho_in (n_elem entries, host, page-locked for an
+ * asynchronous copy) is copied in and becomes rho as to_set_state would make it (k,
+ * alpha0 and u are kept; an unchanged design skips its rebuild), one to_step
+ * iteration runs, the new design is copied to rho_out (host, n_elem entries; may be
+ * NULL) and the iteration's record to stats_out (host, one record; may be NULL), and
+ * `stream` is synchronised once.  Returns the record's status: TO_OK or the first
+ * device-side error of the iteration.  The first call allocates a device buffer of
+ * n_elem entries (and, without stats_out, one page-locked record), kept until
+ * to_destroy.  TO_ERR_ARG for a null rho_in.  Not in the paper: an interface for
+ * serving loops. */
+int to_step_host(to_problem* P, const void* rho_in, void* rho_out, to_stats* stats_out, void* stream);
+
 /* Batches of independent design problems (each advanced exactly as to_step
  * advances it: Algorithms 1 / 3 with its own lambda, beta, alpha and state).
  * to_batch_create groups existing problems (not copied, not owned: destroy the

@@ -20,7 +20,7 @@ from ._abi import (TO_FP32_MIXED, TO_FP64, TO_INNER_PCG, TO_INNER_PFBTO, TO_INNE
 
 __all__ = ["to_default_params", "to_create", "to_destroy", "to_sizes", "to_set_design", "to_apply_K",
            "to_residual", "to_smooth",
-           "to_inner_solve", "to_sensitivity", "to_filter", "to_project", "to_step", "to_get_stats", "to_get_state",
+           "to_inner_solve", "to_sensitivity", "to_filter", "to_project", "to_step", "to_step_host", "to_get_stats", "to_get_state",
            "to_set_state", "to_check", "to_barrier_selftest", "to_last_error", "to_project_noalloc", "to_compliance_truncated",
            "to_compliance_truncated_grad", "to_compliance_truncated_id", "to_batch_create", "to_batch_destroy", "to_batch_step", "to_batch_tile", "Batch",
            "Problem", "ToError",
@@ -265,6 +265,30 @@ def to_get_stats(P, n, out):
     tensor) on the current stream; read it after synchronising (to_stats.from_address)."""
     ptr = out.data_ptr() if hasattr(out, "data_ptr") else int(out)
     _abi.check(_lib().to_get_stats(_h(P), int(n), C.c_void_p(ptr), _stream(P.device)))
+
+
+def _host_ptr(t, dtype, n, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or t.is_cuda:
+        raise TypeError(f"{name} must be a host tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous() or t.numel() != n:
+        raise ValueError(f"{name} must be contiguous with {n} entries, got {tuple(t.shape)}")
+    return C.c_void_p(t.data_ptr())
+
+
+def to_step_host(P, rho_in, rho_out=None, stats_out=None):
+    """One outer iteration fed from host memory: rho_in (host tensor, pinned for an
+    asynchronous copy) in, the new design into rho_out (host tensor) and the iteration's
+    record into stats_out (host buffer of one to_stats with data_ptr(), or None), one
+    synchronisation.  Raises ToError with the record's status on a device-side error."""
+    dt = _dt(P)
+    pin = _host_ptr(rho_in, dt, P.n_elem, "rho_in")
+    pout = None if rho_out is None else _host_ptr(rho_out, dt, P.n_elem, "rho_out")
+    pst = None if stats_out is None else C.c_void_p(stats_out.data_ptr() if hasattr(stats_out, "data_ptr")
+                                                    else int(stats_out))
+    _abi.check(_lib().to_step_host(_h(P), pin, pout, pst, _stream(P.device)))
 
 
 def to_set_state(P, rho=None, u=None, k=1, alpha0=0.0):

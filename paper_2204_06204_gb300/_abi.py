@@ -70,6 +70,7 @@ SIGNATURES = {
     "to_project": (C.c_int, [P, P, P, C.POINTER(C.c_double), P]),
     "to_step": (C.c_int, [P, C.c_int32, C.POINTER(to_stats), P]),
     "to_get_stats": (C.c_int, [P, C.c_int32, P, P]),
+    "to_step_host": (C.c_int, [P, P, P, P, P]),
     "to_get_state": (C.c_int, [P, P, P, C.POINTER(C.c_int64), C.POINTER(C.c_double), P]),
     "to_set_state": (C.c_int, [P, P, P, C.c_int64, C.c_double, P]),
     "to_check": (C.c_int, [P, P]),

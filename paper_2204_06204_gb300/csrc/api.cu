@@ -169,6 +169,8 @@ extern "C" void to_destroy(to_problem* P) {
     p = P->alt_gj_tab; dfree(p);
     p = P->counters; dfree(p);
     p = P->dstats; dfree(p);
+    p = P->rho_stage; dfree(p);
+    if (P->stats_pinned) cudaFreeHost(P->stats_pinned);
     delete P;
 }
 
@@ -646,13 +648,15 @@ __global__ void k_set_counters(to::DevScalars* sc, long long k, double alpha0, i
 }
 
 // rho <- rho_in, compared bitwise with the old rho: comparison number seq found a
-// difference iff afterwards sc->dchanged == sc->dseq.  Also sets k and alpha0.
+// difference iff afterwards sc->dchanged == sc->dseq.  Also sets k and alpha0 (set_counters).
 template <typename W>
 __global__ void k_take_design(const W* __restrict__ in, W* __restrict__ rho, long long n, to::DevScalars* sc,
-                              unsigned seq, long long k, double alpha0) {
+                              unsigned seq, int set_counters, long long k, double alpha0) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        sc->k = k;
-        sc->alpha0 = alpha0 > 0.0 ? alpha0 : 0.0;
+        if (set_counters) {
+            sc->k = k;
+            sc->alpha0 = alpha0 > 0.0 ? alpha0 : 0.0;
+        }
         sc->dseq = seq;
     }
     bool diff = false;
@@ -664,13 +668,12 @@ __global__ void k_take_design(const W* __restrict__ in, W* __restrict__ rho, lon
     if (__any_sync(0xffffffffu, diff) && (threadIdx.x & 31) == 0) sc->dchanged = seq;
 }
 
-extern "C" int to_set_state(to_problem* P, const void* rho_dev, const void* u_dev, int64_t k, double alpha0, void* stream) {
-    TO_ENTER(P);
-    if (k < 1) return fail(TO_ERR_ARG, "k must be >= 1");
-    P->fwd_id = 0;
-    // The live set (moduli, 1 / d, coarsest inverse) was built for the current rho when a
-    // pipelined to_step left it: then the incoming design is compared with rho on the
-    // device, and the moduli here and the next to_step's rebuild run only if it differs.
+// The design in from rho_dev (device memory), with k and alpha0 (set_counters), rho~ and
+// the moduli.  The live set (moduli, 1 / d, coarsest inverse) was built for the current
+// rho when a pipelined to_step left it: then the incoming design is compared with rho on
+// the device, and the moduli here and the next to_step's rebuild run only if it differs.
+static int take_design(to_problem* P, const void* rho_dev, bool set_counters, long long k, double alpha0,
+                       cudaStream_t s) {
     const bool check = rho_dev && P->pipe_ready && !P->in_batch &&
                        (P->prm.precond != TO_PRECOND_MG || mg_refresh_gatable(P));
     if (check) {
@@ -682,22 +685,55 @@ extern "C" int to_set_state(to_problem* P, const void* rho_dev, const void* u_de
         // compared as bit patterns (a NaN equals itself, -0 differs from +0)
         if (P->prec == TO_FP64)
             k_take_design<unsigned long long><<<(unsigned)nb, 256, 0, s>>>(
-                (const unsigned long long*)rho_dev, (unsigned long long*)P->rho, n, P->sc, seq, (long long)k, alpha0);
+                (const unsigned long long*)rho_dev, (unsigned long long*)P->rho, n, P->sc, seq, set_counters ? 1 : 0, k,
+                alpha0);
         else
             k_take_design<unsigned><<<(unsigned)nb, 256, 0, s>>>((const unsigned*)rho_dev, (unsigned*)P->rho, n, P->sc,
-                                                                 seq, (long long)k, alpha0);
+                                                                 seq, set_counters ? 1 : 0, k, alpha0);
         TO_CUDA(cudaGetLastError());
     } else {
         if (rho_dev) TO_CUDA(cudaMemcpyAsync(P->rho, rho_dev, P->n_elem * P->esz, cudaMemcpyDeviceToDevice, s));
-        k_set_counters<<<1, 1, 0, s>>>(P->sc, (long long)k, alpha0, 1, 1);
-        TO_CUDA(cudaGetLastError());
+        if (set_counters) {
+            k_set_counters<<<1, 1, 0, s>>>(P->sc, k, alpha0, 1, 1);
+            TO_CUDA(cudaGetLastError());
+        }
     }
-    if (u_dev) TO_CUDA(cudaMemcpyAsync(P->u, u_dev, P->n_dof * P->esz, cudaMemcpyDeviceToDevice, s));
     int rc = launch_moduli(P, s, check ? &P->sc->dchanged : nullptr);
     if (rc) return rc;
+    P->fwd_id = 0;
     P->precond_stale = 1;   // refreshed by the next to_inner_solve (to_step refreshes every iteration)
     P->pipe_ready = 0;
     P->design_check = check ? 1 : 0;
+    return TO_OK;
+}
+
+extern "C" int to_set_state(to_problem* P, const void* rho_dev, const void* u_dev, int64_t k, double alpha0, void* stream) {
+    TO_ENTER(P);
+    if (k < 1) return fail(TO_ERR_ARG, "k must be >= 1");
+    if (u_dev) TO_CUDA(cudaMemcpyAsync(P->u, u_dev, P->n_dof * P->esz, cudaMemcpyDeviceToDevice, s));
+    return take_design(P, rho_dev, true, (long long)k, alpha0, s);
+}
+
+extern "C" int to_step_host(to_problem* P, const void* rho_in, void* rho_out, to_stats* stats_out, void* stream) {
+    TO_ENTER(P);
+    if (!rho_in) return fail(TO_ERR_ARG, "rho_in is null");
+    const size_t bytes = P->n_elem * P->esz;
+    if (!P->rho_stage)
+        if (int rc = dalloc(&P->rho_stage, bytes)) return rc;
+    if (!stats_out && !P->stats_pinned) {
+        void* h = nullptr;
+        TO_CUDA(cudaMallocHost(&h, sizeof(to_stats)));
+        P->stats_pinned = (to_stats*)h;
+    }
+    to_stats* rec = stats_out ? stats_out : P->stats_pinned;
+    TO_CUDA(cudaMemcpyAsync(P->rho_stage, rho_in, bytes, cudaMemcpyHostToDevice, s));
+    int rc = take_design(P, P->rho_stage, false, 0, 0.0, s);
+    if (!rc) rc = to_step(P, 1, nullptr, stream);
+    if (rc) return rc;
+    if (rho_out) TO_CUDA(cudaMemcpyAsync(rho_out, P->rho, bytes, cudaMemcpyDeviceToHost, s));
+    TO_CUDA(cudaMemcpyAsync(rec, P->dstats, sizeof(to_stats), cudaMemcpyDeviceToHost, s));
+    TO_CUDA(cudaStreamSynchronize(s));
+    if (rec->status) return fail(rec->status, "device-side error in the outer iteration");
     return TO_OK;
 }
 

@@ -168,6 +168,8 @@ struct to_problem {
     unsigned* counters = nullptr;
     to_stats* dstats = nullptr;    // device stats ring
     int dstats_cap = 0;
+    void* rho_stage = nullptr;     // to_step_host: the design copied in from the host
+    to_stats* stats_pinned = nullptr;   // to_step_host without stats_out: the record read back
     int last_step_n = 0;           // outer iterations of the last to_step call (its records: slots 0 .. n - 1)
 
     // truncated-solve iterates u_0 .. u_T kept for the reverse sweep

@@ -123,6 +123,46 @@ def test_set_state_rebuilds_only_a_changed_design(case, precision, change, no_gr
     assert ref[5] == got[5]
 
 
+@pytest.mark.parametrize("case", sorted(CASES))
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_step_host_is_set_state_plus_step(case, precision):
+    """to_step_host (design in from host memory, one outer iteration, design and record out,
+    one synchronisation) against the device-side calls it stands for: fed back its own
+    designs it continues the device loop bit for bit; given a changed design it equals
+    to_set_state with that design (k and alpha0 kept) followed by to_step(1)."""
+    fb = _fb()
+    pb = CASES[case][0]()
+    prm = _params(fb, case, precision)
+    with fb.Problem.from_workload(pb, prm) as P, fb.Problem.from_workload(pb, prm) as Q:
+        ref = P.step(6)
+        Q.step(2)
+        rho, u, k, a0 = Q.get_state()
+        hb = [rho.cpu().pin_memory(), torch.empty_like(rho, device="cpu").pin_memory()]
+        rec = torch.empty(C_sizeof(fb), dtype=torch.uint8).pin_memory()
+        got = []
+        for i in range(4):
+            fb.to_step_host(Q, hb[i % 2], hb[(i + 1) % 2], rec)
+            got.append(fb.to_stats.from_address(rec.data_ptr()).J)
+        assert [s["J"] for s in ref[2:]] == got
+        rho_p, u_p, k_p, a0_p = P.get_state()
+        rho_q, u_q, k_q, a0_q = Q.get_state()
+        assert torch.equal(rho_p, rho_q) and torch.equal(hb[0], rho_q.cpu()) and torch.equal(u_p, u_q)
+        assert k_p == k_q == 7 and a0_p == a0_q
+        # a changed design, without rho_out and stats_out
+        new = rho_q.clone().mul_(0.97).add_(0.01)
+        fb.to_step_host(Q, new.cpu().pin_memory())
+        P.set_state(new, None, k_p, a0_p)
+        P.step(1)
+        rho_p, u_p, k_p, a0_p = P.get_state()
+        rho_q, u_q, k_q, a0_q = Q.get_state()
+        assert torch.equal(rho_p, rho_q) and torch.equal(u_p, u_q) and k_p == k_q == 8 and a0_p == a0_q
+
+
+def C_sizeof(fb):
+    import ctypes
+    return ctypes.sizeof(fb.to_stats)
+
+
 def test_batched_call_patterns_agree_bitwise():
     """The pipelined batched iteration: one call of 4 iterations, four calls of one, and
     a member's state rewritten between calls (the next call starts afresh) agree."""
