@@ -300,7 +300,7 @@ int mg_legs_build(to_problem* P);
 // the level just above the coarse tail in one 16-CTA cluster (mgcl.cu)
 int mg_cluster_init(to_problem* P);
 bool mg_cluster_applicable(const to_problem* P, int l);
-int mg_cluster_down(const to_problem* P, int l, void* x_first, void* x_iter, void* r_out, void* cfirst, cudaStream_t s);
+int mg_cluster_down(const to_problem* P, int l, void* x_first, void* x_iter, void* cfirst, cudaStream_t s);
 int mg_cluster_up(const to_problem* P, int l, void* x_iter, void* x_out, cudaStream_t s);
 int mg_legs_launch(to_problem* P, int leg, void* fine, cudaStream_t s);
 

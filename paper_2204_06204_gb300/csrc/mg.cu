@@ -1131,12 +1131,12 @@ static int vcycle_t(to_problem* P, int l, const void* b, void* x, void* t, cudaS
         // in cur, the tail, the up leg into x; the buffers end as in the launched steps
         const int npre = nu1 - 1;
         void* it_buf = (npre % 2 == 0) ? cur : oth;   // the iterate after the pre-smoothing
-        void* res_buf = it_buf == cur ? oth : cur;    // b - K x
-        void* fin = (nu2 % 2 == 0) ? it_buf : res_buf;
+        void* other = it_buf == cur ? oth : cur;
+        void* fin = (nu2 % 2 == 0) ? it_buf : other;
         if (fin != x) return fail(TO_ERR_STATE, "V-cycle buffer parity");
         const Level& C = P->lv[l + 1];
         void* cfirst = ((nu1 - 1 + nu2) % 2 == 0) ? C.x : C.t;
-        if ((rc = mg_cluster_down(P, l, cur, it_buf, res_buf, l + 1 < L - 1 ? cfirst : nullptr, s))) return rc;
+        if ((rc = mg_cluster_down(P, l, cur, it_buf, l + 1 < L - 1 ? cfirst : nullptr, s))) return rc;
         if ((rc = tail_t<T>(P, s))) return rc;
         return mg_cluster_up(P, l, it_buf, x, s);
     }

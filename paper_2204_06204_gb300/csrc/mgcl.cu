@@ -63,7 +63,6 @@ struct McArgs {
     const float* dinv;
     float* xin;              // down: the first sweep; up: the iterate (the prolongation is added here)
     float* xout;             // down: the iterate after the pre-smoothing; up: the V-cycle's result
-    float* rout;             // down: the residual b - K x
     // the coarse level (restriction on the way down, prolongation on the way up)
     int cx, cy, cz;
     const uint8_t* cmask;
@@ -71,7 +70,6 @@ struct McArgs {
     const float* cdinv;
     float* cfirst;           // down: the coarse first sweep (nullptr: none)
     const float* cxv;        // up: the coarse correction
-    int* err;
 };
 
 struct McSmem {
@@ -419,14 +417,13 @@ static void mc_level_args(const to_problem* P, int l, McArgs& a, HaarK<float>& k
     a.cy = C.ny;
     a.cz = C.nz;
     a.cmask = C.mask;
-    a.err = &P->sc->err;
     for (int n = 0; n < kHaarNnz; ++n) kh.v[n] = (float)(P->haar[n] * (F.h / P->g.h));
 }
 
 // the down leg on level l: from the first sweep in x_first, the remaining pre-smoothing
-// sweeps and b - K x; the iterate into x_iter, the residual into r_out; the restriction
+// sweeps and b - K x; the iterate into x_iter; the restriction of the residual
 // to the tail's level into its right-hand side and (cfirst) its first sweep
-int mg_cluster_down(const to_problem* P, int l, void* x_first, void* x_iter, void* r_out, void* cfirst, cudaStream_t s) {
+int mg_cluster_down(const to_problem* P, int l, void* x_first, void* x_iter, void* cfirst, cudaStream_t s) {
     McArgs a;
     HaarK<float> kh;
     mc_level_args(P, l, a, kh);
@@ -434,7 +431,6 @@ int mg_cluster_down(const to_problem* P, int l, void* x_first, void* x_iter, voi
     a.nsweep = P->prm.mg_nu_pre - 1;
     a.xin = (float*)x_first;
     a.xout = (float*)x_iter;
-    a.rout = (float*)r_out;
     a.cb = (float*)C.b;
     a.cdinv = (const float*)C.dinv;
     a.cfirst = (float*)cfirst;
