@@ -692,7 +692,7 @@ static int take_design(to_problem* P, const void* rho_dev, bool set_counters, lo
                                                                  seq, set_counters ? 1 : 0, k, alpha0);
         TO_CUDA(cudaGetLastError());
     } else {
-        if (rho_dev) TO_CUDA(cudaMemcpyAsync(P->rho, rho_dev, P->n_elem * P->esz, cudaMemcpyDeviceToDevice, s));
+        if (rho_dev) TO_CUDA(cudaMemcpyAsync(P->rho, rho_dev, P->n_elem * P->esz, cudaMemcpyDefault, s));
         if (set_counters) {
             k_set_counters<<<1, 1, 0, s>>>(P->sc, k, alpha0, 1, 1);
             TO_CUDA(cudaGetLastError());
@@ -714,23 +714,57 @@ extern "C" int to_set_state(to_problem* P, const void* rho_dev, const void* u_de
     return take_design(P, rho_dev, true, (long long)k, alpha0, s);
 }
 
+// out <- in, n words (the design into page-locked host memory through its device alias)
+template <typename W>
+__global__ void k_copy_words(const W* __restrict__ in, W* __restrict__ out, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = in[i];
+}
+
+// the device alias of page-locked host memory, or nullptr (pageable memory: copies instead)
+static void* host_alias(const void* p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 extern "C" int to_step_host(to_problem* P, const void* rho_in, void* rho_out, to_stats* stats_out, void* stream) {
     TO_ENTER(P);
     if (!rho_in) return fail(TO_ERR_ARG, "rho_in is null");
     const size_t bytes = P->n_elem * P->esz;
-    if (!P->rho_stage)
-        if (int rc = dalloc(&P->rho_stage, bytes)) return rc;
     if (!stats_out && !P->stats_pinned) {
         void* h = nullptr;
         TO_CUDA(cudaMallocHost(&h, sizeof(to_stats)));
         P->stats_pinned = (to_stats*)h;
     }
     to_stats* rec = stats_out ? stats_out : P->stats_pinned;
-    TO_CUDA(cudaMemcpyAsync(P->rho_stage, rho_in, bytes, cudaMemcpyHostToDevice, s));
-    int rc = take_design(P, P->rho_stage, false, 0, 0.0, s);
+    // page-locked input: the design is read by the comparing copy itself, over the
+    // host link; pageable input: copied in first
+    const void* in = host_alias(rho_in);
+    if (!in) {
+        if (!P->rho_stage)
+            if (int rc = dalloc(&P->rho_stage, bytes)) return rc;
+        TO_CUDA(cudaMemcpyAsync(P->rho_stage, rho_in, bytes, cudaMemcpyHostToDevice, s));
+        in = P->rho_stage;
+    }
+    int rc = take_design(P, in, false, 0, 0.0, s);
     if (!rc) rc = to_step(P, 1, nullptr, stream);
     if (rc) return rc;
-    if (rho_out) TO_CUDA(cudaMemcpyAsync(rho_out, P->rho, bytes, cudaMemcpyDeviceToHost, s));
+    if (rho_out) {
+        void* out = host_alias(rho_out);
+        if (out) {
+            const long long nw = (long long)(bytes / 4);
+            long long nb = (nw + 255) / 256;
+            if (nb > 4LL * P->num_sms) nb = 4LL * P->num_sms;
+            k_copy_words<unsigned><<<(unsigned)(nb < 1 ? 1 : nb), 256, 0, s>>>((const unsigned*)P->rho, (unsigned*)out, nw);
+            TO_CUDA(cudaGetLastError());
+        } else {
+            TO_CUDA(cudaMemcpyAsync(rho_out, P->rho, bytes, cudaMemcpyDeviceToHost, s));
+        }
+    }
     TO_CUDA(cudaMemcpyAsync(rec, P->dstats, sizeof(to_stats), cudaMemcpyDeviceToHost, s));
     TO_CUDA(cudaStreamSynchronize(s));
     if (rec->status) return fail(rec->status, "device-side error in the outer iteration");

@@ -148,14 +148,20 @@ def test_step_host_is_set_state_plus_step(case, precision):
         rho_q, u_q, k_q, a0_q = Q.get_state()
         assert torch.equal(rho_p, rho_q) and torch.equal(hb[0], rho_q.cpu()) and torch.equal(u_p, u_q)
         assert k_p == k_q == 7 and a0_p == a0_q
-        # a changed design, without rho_out and stats_out
+        # a changed design from pageable memory (copied, not read in place), without
+        # rho_out and stats_out
         new = rho_q.clone().mul_(0.97).add_(0.01)
-        fb.to_step_host(Q, new.cpu().pin_memory())
+        fb.to_step_host(Q, new.cpu())
         P.set_state(new, None, k_p, a0_p)
         P.step(1)
         rho_p, u_p, k_p, a0_p = P.get_state()
         rho_q, u_q, k_q, a0_q = Q.get_state()
         assert torch.equal(rho_p, rho_q) and torch.equal(u_p, u_q) and k_p == k_q == 8 and a0_p == a0_q
+        # pageable output
+        out = torch.empty_like(rho_q, device="cpu")
+        fb.to_step_host(Q, rho_q.cpu(), out)
+        P.step(1)
+        assert torch.equal(out, P.get_state()[0].cpu())
 
 
 def C_sizeof(fb):
