@@ -337,10 +337,11 @@ int outer_iteration(to_problem* P, cudaStream_t s) {
 
 // ----------------------------------------------------------------------------- gated refresh
 // After to_set_state the live set is rebuilt only if the design it brought differs from
-// the one the set was built for: sc->dchanged, written on the device by to_set_state's copy
-// (which has also recomputed rho~ and the moduli where the design differs).  Every rebuild
-// kernel reads the flag and returns at once if it is 0, so an unchanged design costs one
-// near-empty launch each; level 0's 1 / d is the only one on the main stream, the coarse
+// the one the set was built for: sc->dchanged == sc->dseq, written on the device by
+// to_set_state's copy (which has also recomputed rho~ and the moduli where the design
+// differs).  Every rebuild kernel reads that pair and returns at once unless they are
+// equal, so an unchanged design costs one near-empty launch each; level 0's 1 / d is the
+// only one on the main stream, the coarse
 // levels (moduli, 1 / d, the coarsest operator) and the coarsest inverse run on the
 // multigrid branch beside the residual.  The V-cycle's first restriction to level 1 waits
 // for the levels (ev_ljoin), the coarse solves for the inverse (ev_join).  (Conditional
@@ -363,8 +364,9 @@ static int gated_refresh(to_problem* P, cudaStream_t s) {
 }
 
 // The same iteration with the next design's preconditioner built beside it.  The live
-// set (moduli, diagonals, coarsest inverse) belongs to rho_k on entry, or (`fresh`) is
-// computed first as in outer_iteration, its inverse on the multigrid branch.  After the
+// set (moduli, diagonals, coarsest inverse) belongs to rho_k on entry (fresh = 0), or is
+// computed first as in outer_iteration, its inverse on the multigrid branch (fresh = 1),
+// or where to_set_state found rho_k changed (fresh = 2, gated_refresh).  After the
 // residual at u_k the design branch forms rho_{k+1} (filter transpose, step,
 // projection), then its moduli, diagonals, coarse moduli and coarsest inverse, all
 // into the other set, while the lower-level steps run on the live set; the caller
