@@ -745,8 +745,9 @@ def _launches_per_step(mg, n_inner, dims=(128, 64, 64), nu1=2, nu2=2, cluster=Fa
     (cluster: the FP32 level just above the coarse tail runs as two 16-CTA cluster launches)."""
     # stats-slot reset (once per to_step call), filter + moduli, diag, residual with the fused
     # sensitivity, (Q + update) per step, filter^T with the step-size statistics, the projection
-    # (first pass, multiplier search, final pass), record
-    base = 1 + 1 + 1 + 1 + 2 * n_inner + 1 + 3 + 1
+    # (first pass, multiplier search, final pass), the design's copy to a host buffer (returns
+    # at once unless to_step_host set one), record
+    base = 1 + 1 + 1 + 1 + 2 * n_inner + 1 + 3 + 1 + 1
     if not mg:
         return base
     L = _mg_levels(*dims)

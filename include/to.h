@@ -315,9 +315,10 @@ int to_set_state(to_problem* P, const void* rho_dev, const void* u_dev, int64_t 
  * alpha0 and u are kept; an unchanged design skips its rebuild), one to_step
  * iteration runs, the new design is copied to rho_out (host, n_elem entries; may be
  * NULL) and the iteration's record to stats_out (host, one record; may be NULL), and
- * `stream` is synchronised once.  Page-locked rho_in / rho_out are read and written
- * by kernels through their device aliases (no separate copy); pageable ones are
- * copied.  Returns the record's status: TO_OK or the first
+ * `stream` is synchronised once.  Page-locked rho_in / rho_out / stats_out are read
+ * and written by kernels through their device aliases (no separate copy; the new
+ * design is written as soon as the iteration's projection has formed it); pageable
+ * ones are copied.  Returns the record's status: TO_OK or the first
  * device-side error of the iteration.  The first call allocates a device buffer of
  * n_elem entries (and, without stats_out, one page-locked record), kept until
  * to_destroy.  TO_ERR_ARG for a null rho_in.  Not in the paper: an interface for

@@ -642,22 +642,29 @@ extern "C" int to_get_state(to_problem* P, void* rho_dev, void* u_dev, int64_t* 
     return TO_OK;
 }
 
-__global__ void k_set_counters(to::DevScalars* sc, long long k, double alpha0, int set_k, int set_a) {
+__global__ void k_set_counters(to::DevScalars* sc, long long k, double alpha0, int set_k, int set_a, void* host_out,
+                               void* host_rec) {
     if (set_k) sc->k = k;
     if (set_a) sc->alpha0 = alpha0 > 0.0 ? alpha0 : 0.0;
+    sc->host_out = host_out;
+    sc->host_rec = host_rec;
 }
 
 // rho <- rho_in, compared bitwise with the old rho: comparison number seq found a
-// difference iff afterwards sc->dchanged == sc->dseq.  Also sets k and alpha0 (set_counters).
+// difference iff afterwards sc->dchanged == sc->dseq.  Also sets k and alpha0 (set_counters)
+// and the host buffers of the next iteration's outputs.
 template <typename W>
 __global__ void k_take_design(const W* __restrict__ in, W* __restrict__ rho, long long n, to::DevScalars* sc,
-                              unsigned seq, int set_counters, long long k, double alpha0) {
+                              unsigned seq, int set_counters, long long k, double alpha0, void* host_out,
+                              void* host_rec) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         if (set_counters) {
             sc->k = k;
             sc->alpha0 = alpha0 > 0.0 ? alpha0 : 0.0;
         }
         sc->dseq = seq;
+        sc->host_out = host_out;
+        sc->host_rec = host_rec;
     }
     bool diff = false;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -673,7 +680,7 @@ __global__ void k_take_design(const W* __restrict__ in, W* __restrict__ rho, lon
 // rho when a pipelined to_step left it: then the incoming design is compared with rho on
 // the device, and the moduli here and the next to_step's rebuild run only if it differs.
 static int take_design(to_problem* P, const void* rho_dev, bool set_counters, long long k, double alpha0,
-                       cudaStream_t s) {
+                       cudaStream_t s, void* host_out = nullptr, void* host_rec = nullptr) {
     const bool check = rho_dev && P->pipe_ready && !P->in_batch &&
                        (P->prm.precond != TO_PRECOND_MG || mg_refresh_gatable(P));
     if (check) {
@@ -686,17 +693,16 @@ static int take_design(to_problem* P, const void* rho_dev, bool set_counters, lo
         if (P->prec == TO_FP64)
             k_take_design<unsigned long long><<<(unsigned)nb, 256, 0, s>>>(
                 (const unsigned long long*)rho_dev, (unsigned long long*)P->rho, n, P->sc, seq, set_counters ? 1 : 0, k,
-                alpha0);
+                alpha0, host_out, host_rec);
         else
             k_take_design<unsigned><<<(unsigned)nb, 256, 0, s>>>((const unsigned*)rho_dev, (unsigned*)P->rho, n, P->sc,
-                                                                 seq, set_counters ? 1 : 0, k, alpha0);
+                                                                 seq, set_counters ? 1 : 0, k, alpha0, host_out, host_rec);
         TO_CUDA(cudaGetLastError());
     } else {
         if (rho_dev) TO_CUDA(cudaMemcpyAsync(P->rho, rho_dev, P->n_elem * P->esz, cudaMemcpyDefault, s));
-        if (set_counters) {
-            k_set_counters<<<1, 1, 0, s>>>(P->sc, k, alpha0, 1, 1);
-            TO_CUDA(cudaGetLastError());
-        }
+        const int sc_ = set_counters ? 1 : 0;
+        k_set_counters<<<1, 1, 0, s>>>(P->sc, k, alpha0, sc_, sc_, host_out, host_rec);
+        TO_CUDA(cudaGetLastError());
     }
     int rc = launch_moduli(P, s, check ? &P->sc->dchanged : nullptr);
     if (rc) return rc;
@@ -712,13 +718,6 @@ extern "C" int to_set_state(to_problem* P, const void* rho_dev, const void* u_de
     if (k < 1) return fail(TO_ERR_ARG, "k must be >= 1");
     if (u_dev) TO_CUDA(cudaMemcpyAsync(P->u, u_dev, P->n_dof * P->esz, cudaMemcpyDeviceToDevice, s));
     return take_design(P, rho_dev, true, (long long)k, alpha0, s);
-}
-
-// out <- in, n words (the design into page-locked host memory through its device alias)
-template <typename W>
-__global__ void k_copy_words(const W* __restrict__ in, W* __restrict__ out, long long n) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        out[i] = in[i];
 }
 
 // the device alias of page-locked host memory, or nullptr (pageable memory: copies instead)
@@ -741,8 +740,10 @@ extern "C" int to_step_host(to_problem* P, const void* rho_in, void* rho_out, to
         P->stats_pinned = (to_stats*)h;
     }
     to_stats* rec = stats_out ? stats_out : P->stats_pinned;
-    // page-locked input: the design is read by the comparing copy itself, over the
-    // host link; pageable input: copied in first
+    // Page-locked buffers are used in place through their device aliases: the comparing
+    // copy reads the design over the host link, the iteration writes the new design from
+    // its design branch (beside the lower-level steps) and its record with the record.
+    // Pageable ones are copied before and after.
     const void* in = host_alias(rho_in);
     if (!in) {
         if (!P->rho_stage)
@@ -750,22 +751,18 @@ extern "C" int to_step_host(to_problem* P, const void* rho_in, void* rho_out, to
         TO_CUDA(cudaMemcpyAsync(P->rho_stage, rho_in, bytes, cudaMemcpyHostToDevice, s));
         in = P->rho_stage;
     }
-    int rc = take_design(P, in, false, 0, 0.0, s);
+    void* out = rho_out ? host_alias(rho_out) : nullptr;
+    void* rec_dev = host_alias(rec);
+    int rc = take_design(P, in, false, 0, 0.0, s, out, rec_dev);
     if (!rc) rc = to_step(P, 1, nullptr, stream);
-    if (rc) return rc;
-    if (rho_out) {
-        void* out = host_alias(rho_out);
-        if (out) {
-            const long long nw = (long long)(bytes / 4);
-            long long nb = (nw + 255) / 256;
-            if (nb > 4LL * P->num_sms) nb = 4LL * P->num_sms;
-            k_copy_words<unsigned><<<(unsigned)(nb < 1 ? 1 : nb), 256, 0, s>>>((const unsigned*)P->rho, (unsigned*)out, nw);
-            TO_CUDA(cudaGetLastError());
-        } else {
-            TO_CUDA(cudaMemcpyAsync(rho_out, P->rho, bytes, cudaMemcpyDeviceToHost, s));
-        }
+    if (rc) {
+        // nothing may write into the caller's buffers later
+        k_set_counters<<<1, 1, 0, s>>>(P->sc, 0, 0.0, 0, 0, nullptr, nullptr);
+        cudaStreamSynchronize(s);
+        return rc;
     }
-    TO_CUDA(cudaMemcpyAsync(rec, P->dstats, sizeof(to_stats), cudaMemcpyDeviceToHost, s));
+    if (rho_out && !out) TO_CUDA(cudaMemcpyAsync(rho_out, P->rho, bytes, cudaMemcpyDeviceToHost, s));
+    if (!rec_dev) TO_CUDA(cudaMemcpyAsync(rec, P->dstats, sizeof(to_stats), cudaMemcpyDeviceToHost, s));
     TO_CUDA(cudaStreamSynchronize(s));
     if (rec->status) return fail(rec->status, "device-side error in the outer iteration");
     return TO_OK;

@@ -51,6 +51,11 @@ struct DevScalars {
     // found a difference iff dchanged == dseq (gates: a kernel given &dchanged returns at once
     // when gate[0] != gate[1])
     unsigned dchanged, dseq;
+    // to_step_host: device aliases of page-locked host buffers that the next iteration
+    // writes its new design into (after the projection) and its record into (with the
+    // record); cleared by the record kernel (nullptr: none)
+    void* host_out;
+    void* host_rec;
 };
 static_assert(offsetof(DevScalars, dseq) == offsetof(DevScalars, dchanged) + sizeof(unsigned),
               "a gate reads dchanged and dseq as one pair");
@@ -258,6 +263,7 @@ int launch_precond(to_problem* P, const void* r, void* z, cudaStream_t s);
 int launch_sens_filter_T(to_problem* P, cudaStream_t s);
 int launch_energy(to_problem* P, const void* u, cudaStream_t s);
 int launch_record(to_problem* P, cudaStream_t s);
+int launch_host_out(to_problem* P, cudaStream_t s);   // rho into sc->host_out, if set
 int operator_init(to_problem* P);
 int build_tile_mask(Level& L, const uint8_t* mask_host);
 // the FP32 operator with TMA staging (optma.cu): node rows per tile, set-up, applicability

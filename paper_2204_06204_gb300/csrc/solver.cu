@@ -142,6 +142,9 @@ __global__ void k_record(DevScalars* sc, to_stats* st, int cap) {
     s.status = sc->err;
     const int slot = sc->rec;
     if (slot >= 0 && slot < cap) st[slot] = s;
+    if (sc->host_rec) *(to_stats*)sc->host_rec = s;
+    sc->host_rec = nullptr;
+    sc->host_out = nullptr;   // the design's copy ran on the design branch, joined before this
     sc->rec = slot + 1;
     sc->k += 1;
     sc->beta_first = 0.0;
@@ -151,6 +154,22 @@ __global__ void k_record(DevScalars* sc, to_stats* st, int cap) {
 __global__ void k_set_beta(DevScalars* sc, double beta) {
     sc->beta = beta;
     if (sc->beta_first == 0.0) sc->beta_first = beta;
+}
+
+// the new design into the host buffer that to_step_host left in sc->host_out (a device
+// alias of page-locked memory), n words; nothing when none is set
+__global__ void k_host_out(const DevScalars* __restrict__ sc, const unsigned* __restrict__ rho, long long n) {
+    unsigned* dst = (unsigned*)sc->host_out;
+    if (!dst) return;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        dst[i] = rho[i];
+}
+
+int launch_host_out(to_problem* P, cudaStream_t s) {
+    const long long nw = (long long)(P->n_elem * P->esz / 4);
+    k_host_out<<<grid_1d(nw, 256, P->num_sms), 256, 0, s>>>(P->sc, (const unsigned*)P->rho, nw);
+    TO_CUDA(cudaGetLastError());
+    return TO_OK;
 }
 
 int launch_record(to_problem* P, cudaStream_t s) {
@@ -327,6 +346,7 @@ int outer_iteration(to_problem* P, cudaStream_t s) {
     TO_CUDA(cudaStreamWaitEvent(P->dside, P->ev_dfork, 0));
     if ((rc = launch_sens_filter_T(P, P->dside))) return rc;
     if ((rc = launch_project(P, nullptr, P->rho, P->grad, P->rho, 1, P->dside))) return rc;
+    if ((rc = launch_host_out(P, P->dside))) return rc;
     TO_CUDA(cudaEventRecord(P->ev_djoin, P->dside));
     if ((rc = run_inner(P, P->u, P->prm.n_inner, 1, s, 1))) return rc;
     if (P->prm.precond == TO_PRECOND_MG) TO_CUDA(cudaStreamWaitEvent(s, P->ev_join, 0));
@@ -385,6 +405,7 @@ int outer_iteration_pipelined(to_problem* P, cudaStream_t s, int fresh) {
     TO_CUDA(cudaStreamWaitEvent(P->dside, P->ev_dfork, 0));
     if ((rc = launch_sens_filter_T(P, P->dside))) return rc;
     if ((rc = launch_project(P, nullptr, P->rho, P->grad, P->rho, 1, P->dside))) return rc;
+    if ((rc = launch_host_out(P, P->dside))) return rc;   // (to_step_host: the design out, beside the steps)
     // the live inverse (fresh: still on the multigrid branch) shares the assembled
     // operator and the inversion scratch with the next one
     if (fresh && mg) TO_CUDA(cudaStreamWaitEvent(P->dside, P->ev_join, 0));
