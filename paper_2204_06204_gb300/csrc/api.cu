@@ -1,5 +1,6 @@
 // C entry points (include/to.h): argument checks, device memory owned by the
 // problem, and stream-ordered calls into the kernels.
+#include <cstdint>
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
@@ -720,14 +721,17 @@ extern "C" int to_set_state(to_problem* P, const void* rho_dev, const void* u_de
     return take_design(P, rho_dev, true, (long long)k, alpha0, s);
 }
 
-// the device alias of page-locked host memory, or nullptr (pageable memory: copies instead)
-static void* host_alias(const void* p) {
+// the device alias of page-locked host memory aligned to `align` bytes for the kernels
+// that read or write it in place, or nullptr (pageable or misaligned memory: copies instead)
+static void* host_alias(const void* p, size_t align) {
+    if ((uintptr_t)p % align != 0) return nullptr;
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return nullptr;
     }
-    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+    if (at.type != cudaMemoryTypeHost || !at.devicePointer || (uintptr_t)at.devicePointer % align != 0) return nullptr;
+    return at.devicePointer;
 }
 
 extern "C" int to_step_host(to_problem* P, const void* rho_in, void* rho_out, to_stats* stats_out, void* stream) {
@@ -744,15 +748,15 @@ extern "C" int to_step_host(to_problem* P, const void* rho_in, void* rho_out, to
     // copy reads the design over the host link, the iteration writes the new design from
     // its design branch (beside the lower-level steps) and its record with the record.
     // Pageable ones are copied before and after.
-    const void* in = host_alias(rho_in);
+    const void* in = host_alias(rho_in, P->esz);
     if (!in) {
         if (!P->rho_stage)
             if (int rc = dalloc(&P->rho_stage, bytes)) return rc;
         TO_CUDA(cudaMemcpyAsync(P->rho_stage, rho_in, bytes, cudaMemcpyHostToDevice, s));
         in = P->rho_stage;
     }
-    void* out = rho_out ? host_alias(rho_out) : nullptr;
-    void* rec_dev = host_alias(rec);
+    void* out = rho_out ? host_alias(rho_out, P->esz) : nullptr;
+    void* rec_dev = host_alias(rec, alignof(to_stats));
     int rc = take_design(P, in, false, 0, 0.0, s, out, rec_dev);
     if (!rc) rc = to_step(P, 1, nullptr, stream);
     if (rc) {
